@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark of the differentiable explicit FEM step and its adjoint on GB300.
+
+One benchmark step = one whole pass of the hot path on the 1.3M-tet block:
+set the initial state, a 200-step forward rollout with checkpoints and the
+position loss, then the discrete adjoint through the rollout (segment
+recompute + reverse steps) producing d/dmu, d/dlambda, d/drho and d/dv0.
+
+Metric: forward+adjoint element-steps per second = tets x rollout steps /
+time of (rollout + adjoint incl. recompute), summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU runs are independent replicas (weak scaling, one mesh per rank, no
+collective on the data path).  --impl reference times the FP64 CPU oracle on
+the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic bytes per element-step (reads + writes the method must do):
+# forward: element stream 64 B (4 node ids, Dm^-1, V, mu, lambda) + node
+# traffic 52 B per node (x, v, w read; x, v written) x N/E; adjoint: 64 B +
+# 88 B per node (x, v read; x_bar, v_bar read + written; FP64 w_bar r/w) x N/E.
+FWD_NODE_B, ADJ_NODE_B, ELEM_B = 52.0, 88.0, 64.0
+
+
+def alg_bytes(kind_fwd, n_elems, n_nodes):
+    node = FWD_NODE_B if kind_fwd else ADJ_NODE_B
+    return ELEM_B * n_elems + node * n_nodes
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cells", type=int, default=64, help="block of cells^3 hex cells x 5 tets")
+    ap.add_argument("--rollout", type=int, default=200, help="time steps per rollout")
+    ap.add_argument("--K", type=int, default=0, help="checkpoint interval (0 = library choice)")
+    ap.add_argument("--patch", type=int, default=0, help="elements per patch (0 = tuned/default)")
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=1, help="oracle steps in the CPU sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.path = tempfile.mktemp(prefix="clocks", suffix=".csv")
+        self.p = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001 - no nvidia-smi: clocks stay unknown
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gs_kernels.cu", "gs_math.cuh"):
+        with open(os.path.join(ROOT, "paper_2104_02646_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, n_elems):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    k = d.get("kernels", {}).get(kernel)
+    if not k or d.get("source_hash") != kernel_source_hash():
+        return None
+    return float(k["dram_bytes_per_elem"]) * n_elems
+
+
+def cpu_sample(problem, steps):
+    """The FP64 oracle as it stands on a bounded sample: `steps` forward steps
+    of the same mesh plus their adjoint.  Returns (elem-steps/s, seconds)."""
+    from oracle import oracle as O
+    m = O.Model(problem)
+    xS, _ = m.rollout(problem.x0, problem.v0, problem.dt, steps)
+    target = xS + 1e-3
+    t0 = time.perf_counter()
+    m.loss_grad(problem.x0, problem.v0, problem.dt, steps, target)
+    t = time.perf_counter() - t0
+    return problem.n_elems * steps / t, t
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2104_02646_gb300 import inputs as I
+    p = I.block(n=args.cells, steps=args.rollout)
+    times = []
+    for i in range(args.warmup + args.steps):
+        _, t = cpu_sample(p, args.cpu_steps)
+        if i >= args.warmup:
+            times.append(t)
+    value = p.n_elems * args.cpu_steps * len(times) / sum(times)
+    sample = (f"block{args.cells} ({p.n_elems} tets): {args.cpu_steps} forward step(s) + their adjoint per "
+              f"benchmark step, FP64 oracle, 1 thread")
+    line = {
+        "impl": "reference", "metric": "fwd+adjoint element-steps/s", "value": value,
+        "unit": "element-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"block{args.cells}: {args.cells}^3 hex cells x 5 tets, "
+                               f"{args.rollout}-step rollout at dt 5e-5 (sampled on the CPU)"},
+        "cpu_baseline": {"value": value, "unit": "element-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "element-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def launches_per_step(S, K, have_bnd):
+    """Kernels of ours launched by one benchmark step (set_state + rollout +
+    adjoint), counted from the library's launch sequence."""
+    import math
+    K = K if K > 0 else max(1, math.ceil(math.sqrt(max(S, 1))))
+    n_ck = max(1, -(-S // K))
+    per_step = 2 if have_bnd else 1
+    n = 1                           # set_state
+    n += 1 + per_step * S + 2       # checkpoint copy, steps, loss + finalize
+    n += 1 + 1 + 5                  # seed, zero w_bar, zero 5 accumulators
+    n += n_ck + 2 * per_step * S    # per segment copy; recompute + reverse steps
+    n += 2                          # node and element gradient kernels
+    return n
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    from paper_2104_02646_gb300 import gradsim as gs
+    from paper_2104_02646_gb300 import inputs as I
+
+    gs.load()
+    p = I.block(n=args.cells, steps=args.rollout, seed=rank)
+    E, N, S = p.n_elems, p.n_nodes, args.rollout
+    ctx = gs.Context(local)
+    mesh = gs.Mesh(ctx, p, patch_elems=args.patch, block_threads=args.threads)
+    dev = torch.device("cuda", local)
+    x0 = torch.tensor(p.x0, dtype=torch.float32, device=dev)
+    v0 = torch.tensor(p.v0, dtype=torch.float32, device=dev)
+    # target: the library's own forward with 10 % stiffer materials + 1 mm noise
+    mesh.set_params(mu=torch.tensor(p.mu * 1.1, dtype=torch.float32, device=dev),
+                    lam=torch.tensor(p.lam * 1.1, dtype=torch.float32, device=dev))
+    mesh.set_state(x0, v0)
+    mesh.step(p.dt, S)
+    target = torch.empty(N, 3, device=dev)
+    mesh.get_state(target)
+    target += torch.tensor(I.position_noise(N, seed=rank), dtype=torch.float32, device=dev)
+    mesh.set_params(mu=torch.tensor(p.mu, dtype=torch.float32, device=dev),
+                    lam=torch.tensor(p.lam, dtype=torch.float32, device=dev))
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    grads = {k: torch.zeros(E, dtype=torch.float64, device=dev) for k in ("d_mu", "d_lambda", "d_density")}
+    grads["d_v0"] = torch.zeros(N, 3, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_step():
+        mesh.set_state(x0, v0)
+        mesh.rollout(p.dt, S, args.K, target, loss)
+        mesh.adjoint(grads)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if mesh.check_finite() != 0:
+        raise RuntimeError("non-finite state in the benchmark rollout")
+
+    # ---- timed region: K steps, L2 flushed between them (not timed) ----------
+    clocks = Clocks(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record()
+        one_step()
+        ends[k].record()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * E * S * args.steps / (total_ms / 1e3)
+
+    # ---- per-kernel launch durations (CUDA events per launch) ---------------
+    check = gs.check
+    L = gs.load()
+    check(L.gs_profile(ctx.h, 1))
+    torch.cuda.synchronize()
+    flush.fill_(1.0)
+    one_step()
+    torch.cuda.synchronize()
+    arr = (gs.gs_kernel_time * 16)()
+    n_out = gs.C.c_int(0)
+    check(L.gs_profile_read(ctx.h, arr, 16, gs.C.byref(n_out)))
+    check(L.gs_profile(ctx.h, 0))
+    kt = {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(n_out.value)}
+    dom = max(kt, key=lambda k: kt[k][1])
+    launches, kms = kt[dom]
+    avg_s = kms / launches / 1e3
+    abytes = alg_bytes(dom.startswith("tet_fwd") or dom.startswith("cloth_fwd"), E, N)
+    peak, peak_kind = measured_peaks()
+    achieved = abytes / avg_s / 1e9
+    traffic = ncu_traffic(dom, E)
+
+    # ---- end to end through the C ABI with pinned host buffers ---------------
+    e2e = None
+    if not args.no_e2e:
+        hx0 = x0.cpu().pin_memory()
+        hv0 = v0.cpu().pin_memory()
+        ht = target.cpu().pin_memory()
+        hloss = torch.zeros(1, dtype=torch.float64).pin_memory()
+        hg = {k: torch.zeros_like(t, device="cpu").pin_memory() for k, t in grads.items()}
+        h2d = hx0.numel() * 4 + hv0.numel() * 4 + ht.numel() * 4
+        d2h = 8 + sum(t.numel() * t.element_size() for t in hg.values())
+
+        def e2e_step():
+            mesh.set_state(hx0, hv0, host=True)
+            mesh.rollout(p.dt, S, args.K, ht, hloss, host=True)
+            mesh.adjoint(hg, host=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = 0.0
+        for _ in range(args.steps):
+            flush.fill_(2.0)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            e2e_s += time.perf_counter() - t1
+        e2e = {"value": ws * E * S * args.steps / e2e_s, "unit": "element-steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # ---- CPU baseline: the oracle on a bounded sample -------------------------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v_cpu, t_cpu = cpu_sample(p, args.cpu_steps)
+        cpu = {"value": v_cpu, "unit": "element-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"block{args.cells} ({E} tets): {args.cpu_steps} forward step(s) + adjoint, "
+                         f"FP64 oracle, 1 thread, {t_cpu:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": "fwd+adjoint element-steps/s", "value": value, "unit": "element-steps/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"block{args.cells}: {args.cells}^3 hex cells x 5 tets = {E} tets, {N} nodes, "
+                                   f"{S}-step rollout at dt {p.dt} + adjoint, K={mesh_K(args.K, S)}",
+                       "parallelism": f"replicas x{ws}", "l2": "flushed between timed iterations (512 MiB write)",
+                       "patch_elems": mesh.info.patch_elems, "block_threads": mesh.info.block_threads},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "alg_bytes_per_launch": abytes, "avg_launch_ms": avg_s * 1e3,
+                         "kernel_share": {k: v[1] / sum(x[1] for x in kt.values()) for k, v in kt.items()}},
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step(S, args.K, mesh.info.n_boundary_nodes > 0) * args.steps,
+            "cpu_baseline": cpu,
+            "wall_s": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def mesh_K(K, S):
+    import math
+    return K if K > 0 else max(1, math.ceil(math.sqrt(max(S, 1))))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,308 @@
+/*
+ * gradsim.h -- C ABI of the GB300 library for the differentiable explicit
+ * multiphysics step of gradSim (Murthy et al., ICLR 2021) and its discrete
+ * adjoint through whole rollouts.
+ *
+ * The method (paper sections in brackets):
+ *   state s = [q, u] (node positions and velocities), lumped mass M  [Sec. 2.1]
+ *   per-element forces from the stable neo-Hookean energy
+ *     Psi = mu/2 (I_C - 3) + lambda/2 (J - alpha)^2 - mu/2 log(I_C + 1)
+ *     on linear tetrahedra, and on triangles in the plane for cloth, plus
+ *     dihedral bending f_b = k_b sin(phi/2 + alpha) d          [App. A.1, C.1]
+ *   penalty contact f_n = n (k_e C + k_d dC/dt) with relaxed Coulomb
+ *     friction against a ground plane and a sphere             [App. A.1, C.2]
+ *   semi-implicit Euler u+ = u- + dt M^-1 f(s-), q+ = q- + dt u+  [App. B]
+ *   reverse mode through the whole rollout by the discrete adjoint of
+ *     that step, whose triangular Jacobians make every adjoint explicit [App. B]
+ *   a loss on final node positions stands in for the paper's image loss.
+ *
+ * Conventions
+ *   - Every call returns gs_status: 0 = GS_OK, < 0 error, > 0 warning.  On an
+ *     error nothing was enqueued and gs_last_error() (thread-local) says why.
+ *     No C++ exception crosses this boundary.
+ *   - Streams are passed as `void*` holding a cudaStream_t (0 = legacy
+ *     default stream).  Work is enqueued asynchronously on that stream; device
+ *     buffers handed in must stay valid until the stream reaches the work.
+ *   - Node arrays are [n_nodes][3] row-major float in the caller's node order;
+ *     element arrays are in the caller's element order.  The library keeps
+ *     its own (Morton-ordered) internal layout and translates at the boundary.
+ *   - `mem_space` says where a caller buffer lives: GS_MEM_DEVICE (device
+ *     pointer on the context's GPU) or GS_MEM_HOST (host pointer; the call
+ *     copies it, synchronising the stream for device->host results).
+ *   - FP32 state and element math; FP64 for the loss and for the gradient
+ *     sums over elements and time steps.  Results are deterministic: node
+ *     forces are gathered in a fixed order (no floating-point atomics), so
+ *     the same inputs give bitwise the same outputs, alone or in a batch.
+ *   - One gs_ctx per GPU; a context and everything made from it must be used
+ *     from one host thread at a time (the server runs its own thread).
+ */
+#ifndef GRADSIM_H
+#define GRADSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_VERSION 10000 /* 1.0.0 */
+
+typedef int gs_status;
+enum {
+    GS_OK = 0,
+    GS_EINVAL = -1,      /* bad argument, malformed mesh, non-finite input    */
+    GS_ENOMEM = -2,      /* allocation failed or over the context budget      */
+    GS_ECUDA = -3,       /* a CUDA runtime call failed (message has the text) */
+    GS_ESTATE = -4,      /* call out of order (e.g. adjoint before rollout)   */
+    GS_ENONFINITE = -5,  /* the simulation produced a NaN/Inf                 */
+    GS_ETIMEOUT = -6,    /* poll timed out                                    */
+    GS_ECANCELLED = -7,  /* query cancelled                                   */
+    GS_ENOTFOUND = -8,   /* unknown ticket                                    */
+    GS_EUNSUPPORTED = -9,
+    GS_PENDING = 1,      /* query not finished yet                            */
+    GS_WUNSTABLE = 2     /* dt above the explicit stability estimate (ran)    */
+};
+
+enum { GS_TET = 0, GS_CLOTH = 1 };
+enum { GS_MEM_DEVICE = 0, GS_MEM_HOST = 1 };
+
+typedef struct gs_ctx gs_ctx;
+typedef struct gs_mesh gs_mesh;
+typedef struct gs_batch gs_batch;
+typedef struct gs_server gs_server;
+
+/* Device-memory provider.  alloc returns NULL on failure; free receives the
+ * pointer and size given by alloc.  Both are called on the thread making the
+ * library call, with the stream the memory will first be used on. */
+typedef struct gs_allocator {
+    void* (*alloc)(size_t bytes, void* stream, void* user);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+    void* user;
+} gs_allocator;
+
+/* Compliant contact, App. A.1 "Contact" and App. C.2: penetration depth C
+ * along the outward normal n, f_n = n (k_e C + k_d dC/dt) with dC/dt = -v.n
+ * while C > 0; relaxed Coulomb friction on v_s = v - (v.n) n:
+ * f_f = -k_f v_s while k_f |v_s| <= mu_f |f_n|, else -mu_f |f_n| v_s/|v_s|.
+ * Plane: {y : plane_n . y = plane_h}, plane_n unit length.  Sphere: centre,
+ * radius.  Both may be active. */
+typedef struct gs_contact {
+    float ke, kd, kf, mu_f;
+    int plane_on;
+    float plane_n[3];
+    float plane_h;
+    int sphere_on;
+    float sphere_c[3];
+    float sphere_r;
+} gs_contact;
+
+/* Mesh description; every pointer is a HOST pointer and is copied.
+ *   GS_TET:   elems [n_elems][4] node ids of positively oriented tets
+ *             (det[X1-X0, X2-X0, X3-X0] > 0); density in kg/m^3.
+ *   GS_CLOTH: elems [n_elems][3] triangles; hinges [n_hinges][4] =
+ *             (x1, x2 wing tips; x3 -> x4 shared edge) with triangles
+ *             (x1, x3, x4) and (x2, x4, x3) consistently oriented; density
+ *             is areal (kg/m^2); kb is the per-hinge bending stiffness.
+ *   X: rest positions (double, also the initial positions); v0 nullable (0).
+ *   mu, lambda: Lame parameters per element (App. C.1, heterogeneous).
+ *   act, hinge_act: per-element / per-hinge actuation, nullable (0).
+ *   pinned: nullable; 1 marks a kinematic node (inverse mass 0, no gravity).
+ *   patch_elems, block_threads: work decomposition (0 = defaults, or the
+ *   tuned values); they change performance only, never results of a given
+ *   decomposition (results may differ in the last bits between different
+ *   decompositions because the FP32 force sums are grouped differently). */
+typedef struct gs_mesh_desc {
+    int kind;
+    int n_nodes;
+    int n_elems;
+    const int32_t* elems;
+    int n_hinges;
+    const int32_t* hinges;
+    const double* X;
+    const double* v0;
+    const double* mu;
+    const double* lambda;
+    const double* density;
+    const double* kb;
+    const double* act;
+    const double* hinge_act;
+    const uint8_t* pinned;
+    gs_contact contact;
+    float gravity[3];
+    int patch_elems;
+    int block_threads;
+} gs_mesh_desc;
+
+typedef struct gs_mesh_info {
+    int kind, n_nodes, n_elems, n_hinges;
+    int n_patches;          /* element patches (one CTA each)                 */
+    int n_boundary_nodes;   /* nodes shared between patches                   */
+    int patch_elems, block_threads;
+    double dt_stable;       /* explicit stability estimate (seconds)          */
+    size_t device_bytes;    /* bytes the mesh holds on the device             */
+} gs_mesh_info;
+
+/* Gradients of the loss; caller-owned DEVICE pointers in caller order, each
+ * nullable (not computed).  Parameter gradients are FP64 sums over all time
+ * steps.  For GS_TET, d_mu/d_lambda/d_density/d_act are per tet; for
+ * GS_CLOTH they are per triangle and d_kb/d_hinge_act per hinge.  d_mass is
+ * dL/dm_i per node (the chain to density goes through the lumped mass). */
+typedef struct gs_grads {
+    double* d_mu;
+    double* d_lambda;
+    double* d_density;
+    double* d_act;
+    double* d_kb;
+    double* d_hinge_act;
+    double* d_mass;
+    float* d_x0;
+    float* d_v0;
+} gs_grads;
+
+/* ---- library ------------------------------------------------------------ */
+GS_API int gs_version(void);
+/* Message of the last failed call on this thread ("" if none). */
+GS_API const char* gs_last_error(void);
+
+/* ---- context ------------------------------------------------------------ */
+/* One context per GPU.  hbm_budget_bytes caps what the library allocates
+ * through this context (0 = no cap); alloc nullable = cudaMallocAsync. */
+GS_API gs_status gs_create(gs_ctx** out, int device, size_t hbm_budget_bytes, const gs_allocator* alloc);
+GS_API void gs_destroy(gs_ctx* ctx);
+/* Bytes currently allocated through the context. */
+GS_API size_t gs_ctx_bytes(const gs_ctx* ctx);
+/* 1: capture rollout chunks in CUDA graphs (default); 0: one launch per
+ * kernel per step (the plain loop).  Results are identical. */
+GS_API gs_status gs_set_graphs(gs_ctx* ctx, int enable);
+
+/* Per-launch timing of the step kernels with CUDA events on the launching
+ * stream (measurement support; the paper has no counterpart).  While on,
+ * steps run as one launch per kernel (no graphs) with an event pair around
+ * each patch and boundary kernel.  gs_profile_read synchronises the pending
+ * events and returns, per kernel, the launch count and summed milliseconds,
+ * then clears them; n_out receives the number of kernels with launches. */
+typedef struct gs_kernel_time {
+    char name[32];
+    uint64_t launches;
+    double total_ms;
+} gs_kernel_time;
+GS_API gs_status gs_profile(gs_ctx* ctx, int enable);
+GS_API gs_status gs_profile_read(gs_ctx* ctx, gs_kernel_time* out, int max, int* n_out);
+
+/* ---- mesh (Sec. 2.1 state, App. C.1 elements, a1 set-up) ------------------ */
+/* Validates indices (range, repeated corners), rest elements (inverted or
+ * degenerate: GS_EINVAL), finiteness and positivity of parameters; builds the
+ * internal layout; computes Dm^-1, rest volume/area and lumped masses on the
+ * GPU.  Synchronous (returns when the mesh is ready). */
+GS_API gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_mesh** out);
+GS_API void gs_mesh_destroy(gs_mesh* mesh);
+GS_API gs_status gs_mesh_info_get(const gs_mesh* mesh, gs_mesh_info* out);
+/* Replace per-element parameters (nullable = unchanged), caller order, float.
+ * A new density re-runs the lumped-mass set-up.  Enqueued on `stream`. */
+GS_API gs_status gs_mesh_set_params(gs_mesh* mesh, const float* mu, const float* lambda,
+                             const float* density, const float* act, const float* kb,
+                             int mem_space, void* stream);
+/* Current state (x, v) [n_nodes][3] in caller order; nullable = unchanged. */
+GS_API gs_status gs_mesh_set_state(gs_mesh* mesh, const float* x, const float* v, int mem_space, void* stream);
+GS_API gs_status gs_mesh_get_state(gs_mesh* mesh, float* x, float* v, int mem_space, void* stream);
+/* Sticky per-mesh status from the device: GS_OK or GS_ENONFINITE (a NaN/Inf
+ * appeared in the state since the last reset).  Synchronises the stream. */
+GS_API gs_status gs_mesh_check(gs_mesh* mesh, int reset, void* stream);
+
+/* ---- forward (App. B semi-implicit Euler) --------------------------------- */
+/* Advance the current state n_steps steps of size dt in place.  Returns
+ * GS_WUNSTABLE (work still enqueued) when dt exceeds the stability estimate. */
+GS_API gs_status gs_step(gs_mesh* mesh, float dt, int n_steps, void* stream);
+
+/* Differentiable rollout: n_steps steps from the current state, keeping a
+ * checkpoint of (x, v) every K steps (K = 0: chosen by the library under the
+ * context budget, about sqrt(n_steps)).  With target (N x 3, caller order,
+ * nullable) the FP64 loss L = sum_i |x_i(S) - x*_i|^2 is written to *loss_out
+ * (DEVICE or HOST per mem_space; nullable).  The current state advances to
+ * step S.  Enables one later gs_adjoint. */
+GS_API gs_status gs_rollout(gs_mesh* mesh, float dt, int n_steps, int K, const float* target,
+                     double* loss_out, int mem_space, void* stream);
+
+/* Reverse pass of the last gs_rollout (App. B discrete adjoint): seeds
+ * dL/dx(S) = 2 (x(S) - x*) from the rollout's target (if any) plus dL_dxT,
+ * dL/dv(S) = dL_dvT (both nullable, N x 3, caller order, `mem_space`),
+ * recomputes each checkpoint segment and runs the reverse steps.  Gradient
+ * pointers in `grads` are DEVICE pointers unless mem_space is GS_MEM_HOST.
+ * GS_ESTATE without a preceding rollout.  keep != 0 keeps the checkpoints
+ * for another adjoint with different seeds. */
+GS_API gs_status gs_adjoint(gs_mesh* mesh, const float* dL_dxT, const float* dL_dvT, const gs_grads* grads,
+                     int mem_space, int keep, void* stream);
+
+/* ---- batching: many meshes, one launch per kernel per step ----------------- */
+/* The batch references the meshes (they must outlive it); each mesh keeps its
+ * own state.  Results per mesh are bitwise those of the mesh run alone. */
+GS_API gs_status gs_batch_create(gs_ctx* ctx, gs_mesh* const* meshes, int n, gs_batch** out);
+GS_API void gs_batch_destroy(gs_batch* batch);
+GS_API gs_status gs_batch_step(gs_batch* batch, const float* dt, int n_steps, void* stream);
+/* dt[n]; targets[n] (nullable entries) device pointers; loss_out device [n]. */
+GS_API gs_status gs_batch_rollout(gs_batch* batch, const float* dt, int n_steps, int K,
+                           const float* const* targets, double* loss_out, void* stream);
+/* grads[n] (device pointers inside). */
+GS_API gs_status gs_batch_adjoint(gs_batch* batch, const gs_grads* grads, void* stream);
+
+/* ---- serving: continuous batching of gradient queries ---------------------- */
+typedef struct gs_server_opts {
+    size_t hbm_budget_bytes;  /* admission budget for query state + checkpoints */
+    int max_active;           /* 0 = unlimited slots                            */
+    int K;                    /* checkpoint interval (0 = per query, ~sqrt(S))  */
+    int use_graphs;           /* reserved                                       */
+} gs_server_opts;
+
+/* A query: one system-identification gradient request (mesh, materials,
+ * dt, horizon, target).  All pointers are HOST pointers copied at submit. */
+typedef struct gs_query {
+    gs_mesh_desc mesh;
+    float dt;
+    int n_steps;
+    const float* target;      /* [n_nodes][3] */
+} gs_query;
+
+typedef struct gs_result {
+    gs_status status;
+    double loss;
+    int n_elems, n_hinges, n_nodes;
+    double* d_mu;             /* host arrays owned by the result */
+    double* d_lambda;
+    double* d_density;
+    double* d_kb;
+    float* d_x0;
+    float* d_v0;
+    double t_submit, t_admit, t_done;  /* seconds on the server clock */
+} gs_result;
+
+typedef struct gs_server_stats {
+    uint64_t submitted, completed, rejected, active, queued;
+    double p50_latency_s, p99_latency_s;
+    double elem_steps_per_s;   /* fwd+adjoint element-steps over busy time */
+    size_t admitted_bytes;
+} gs_server_stats;
+
+GS_API gs_status gs_server_create(gs_ctx* ctx, const gs_server_opts* opts, gs_server** out);
+/* Stops the server thread; pending queries end as GS_ECANCELLED. */
+GS_API void gs_server_destroy(gs_server* server);
+/* GS_ENOMEM at once if the query alone exceeds the whole budget. */
+GS_API gs_status gs_query_submit(gs_server* server, const gs_query* q, uint64_t* ticket);
+/* GS_OK (result filled; free it with gs_result_free), GS_PENDING /
+ * GS_ETIMEOUT (not done within timeout_ms; 0 = do not wait), GS_ECANCELLED,
+ * GS_ENONFINITE, GS_ENOTFOUND. */
+GS_API gs_status gs_query_poll(gs_server* server, uint64_t ticket, gs_result* out, int timeout_ms);
+GS_API gs_status gs_query_cancel(gs_server* server, uint64_t ticket);
+GS_API gs_status gs_server_stats_get(gs_server* server, gs_server_stats* out);
+GS_API void gs_result_free(gs_result* r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,370 @@
+// Device math of the explicit step and its adjoint (FP32).
+//
+// Element physics (App. A.1 / C.1 of the paper):
+//   tets   Psi = mu/2 (I_C - 3) + lambda/2 (J - alpha)^2 - mu/2 log(I_C + 1),
+//          alpha = 1 + 3 mu / (4 lambda) + a_e (rest-stable target + actuation),
+//          P = mu F (1 - 1/(I_C + 1)) + lambda (J - alpha) cof F,
+//          corner forces: columns of -V P Dm^-T, f0 = -(f1 + f2 + f3)
+//   tris   same energy with F 3x2, I_C - 2, J = |f0 x f1|,
+//          alpha = 1 + 2 mu / (3 lambda) + a_t
+//   hinges Bridson's bending force  k_b |E|^2/(|N1|+|N2|) sin(phi/2 + alpha) u_i
+// Contact (App. A.1 "Contact", App. C.2): penalty normal force and relaxed
+// Coulomb friction against a plane and a sphere.
+//
+// The adjoints below are hand-derived reverse mode of exactly these
+// forward formulas (the paper obtains its adjoints by source transformation;
+// here they are written out): for the hyperelastic elements the Hessian of
+// Psi is self-adjoint, so F_bar = dP/dF[P_bar]; the hinge and the contact
+// law are differentiated statement by statement in reverse order.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace gs {
+
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return make_float3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3& operator+=(float3& a, float3 b) { a.x += b.x; a.y += b.y; a.z += b.z; return a; }
+__device__ __forceinline__ float3& operator-=(float3& a, float3 b) { a.x -= b.x; a.y -= b.y; a.z -= b.z; return a; }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 xyz(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float4 f4(float3 a, float w) { return make_float4(a.x, a.y, a.z, w); }
+
+// ---------------------------------------------------------------------------
+// tetrahedron
+// Dm^-1 rows: D0 = (a.x a.y a.z), D1 = (a.w b.x b.y), D2 = (b.z b.w c.x);
+// V = c.y, mu = c.z, lambda = c.w.
+// ---------------------------------------------------------------------------
+struct TetState {
+    float3 F0, F1, F2;  // columns of F
+    float3 C0, C1, C2;  // columns of cof F
+    float Ic, J, inv, alpha, ca, cb;
+};
+
+__device__ __forceinline__ void tet_state(float3 x0, float3 x1, float3 x2, float3 x3, float4 a, float4 b,
+                                          float4 c, float act, TetState& s) {
+    const float3 d1 = x1 - x0, d2 = x2 - x0, d3 = x3 - x0;
+    s.F0 = d1 * a.x + d2 * a.w + d3 * b.z;
+    s.F1 = d1 * a.y + d2 * b.x + d3 * b.w;
+    s.F2 = d1 * a.z + d2 * b.y + d3 * c.x;
+    s.Ic = dot3(s.F0, s.F0) + dot3(s.F1, s.F1) + dot3(s.F2, s.F2);
+    s.C0 = cross3(s.F1, s.F2);
+    s.C1 = cross3(s.F2, s.F0);
+    s.C2 = cross3(s.F0, s.F1);
+    s.J = dot3(s.F0, s.C0);
+    const float mu = c.z, lam = c.w;
+    s.inv = 1.0f / (s.Ic + 1.0f);
+    s.alpha = 1.0f + 0.75f * mu / lam + act;
+    s.ca = mu * (1.0f - s.inv);
+    s.cb = lam * (s.J - s.alpha);
+}
+
+// corner forces f1..f3 = columns of -V P Dm^-T; f0 = -(f1 + f2 + f3)
+__device__ __forceinline__ void tet_forces(const TetState& s, float4 a, float4 b, float4 c, float3& f0,
+                                           float3& f1, float3& f2, float3& f3) {
+    const float3 P0 = s.ca * s.F0 + s.cb * s.C0;
+    const float3 P1 = s.ca * s.F1 + s.cb * s.C1;
+    const float3 P2 = s.ca * s.F2 + s.cb * s.C2;
+    const float nV = -c.y;
+    f1 = nV * (P0 * a.x + P1 * a.y + P2 * a.z);
+    f2 = nV * (P0 * a.w + P1 * b.x + P2 * b.y);
+    f3 = nV * (P0 * b.z + P1 * b.w + P2 * c.x);
+    f0 = -(f1 + f2 + f3);
+}
+
+// Reverse mode of tet_forces.  Given fb_i = dL/df_i, returns dL/dx_i and
+// dL/d(mu, lambda, act).  P_bar = -V G Dm^-1 with G = [fb1-fb0, fb2-fb0, fb3-fb0];
+// F_bar = mu (1 - 1/(I_C+1)) P_bar + 2 mu/(I_C+1)^2 (F:P_bar) F
+//         + lambda (cof F : P_bar) cof F + lambda (J - alpha) dcof[P_bar];
+// Ds_bar = F_bar Dm^-T.
+__device__ __forceinline__ void tet_adjoint(const TetState& s, float4 a, float4 b, float4 c, float3 fb0,
+                                            float3 fb1, float3 fb2, float3 fb3, float3& xb0, float3& xb1,
+                                            float3& xb2, float3& xb3, float& gmu, float& glam, float& gact) {
+    const float mu = c.z, lam = c.w, nV = -c.y;
+    const float3 G1 = fb1 - fb0, G2 = fb2 - fb0, G3 = fb3 - fb0;
+    const float3 Pb0 = nV * (G1 * a.x + G2 * a.w + G3 * b.z);
+    const float3 Pb1 = nV * (G1 * a.y + G2 * b.x + G3 * b.w);
+    const float3 Pb2 = nV * (G1 * a.z + G2 * b.y + G3 * c.x);
+    const float FP = dot3(s.F0, Pb0) + dot3(s.F1, Pb1) + dot3(s.F2, Pb2);
+    const float CP = dot3(s.C0, Pb0) + dot3(s.C1, Pb1) + dot3(s.C2, Pb2);
+    const float k2 = 2.0f * mu * s.inv * s.inv * FP;
+    const float lc = lam * CP;
+    const float3 dC0 = cross3(Pb1, s.F2) + cross3(s.F1, Pb2);
+    const float3 dC1 = cross3(Pb2, s.F0) + cross3(s.F2, Pb0);
+    const float3 dC2 = cross3(Pb0, s.F1) + cross3(s.F0, Pb1);
+    const float3 Fb0 = s.ca * Pb0 + k2 * s.F0 + lc * s.C0 + s.cb * dC0;
+    const float3 Fb1 = s.ca * Pb1 + k2 * s.F1 + lc * s.C1 + s.cb * dC1;
+    const float3 Fb2 = s.ca * Pb2 + k2 * s.F2 + lc * s.C2 + s.cb * dC2;
+    xb1 = Fb0 * a.x + Fb1 * a.y + Fb2 * a.z;
+    xb2 = Fb0 * a.w + Fb1 * b.x + Fb2 * b.y;
+    xb3 = Fb0 * b.z + Fb1 * b.w + Fb2 * c.x;
+    xb0 = -(xb1 + xb2 + xb3);
+    // dP/dmu = (1 - 1/(I_C+1)) F - 3/4 cof F;  dP/dlambda = (J - alpha + 3mu/(4lambda)) cof F;
+    // dP/dact = -lambda cof F
+    gmu = (1.0f - s.inv) * FP - 0.75f * CP;
+    glam = (s.J - s.alpha + 0.75f * mu / lam) * CP;
+    gact = -lam * CP;
+}
+
+// ---------------------------------------------------------------------------
+// membrane triangle.  Dm^-1 = [[a.x a.y], [a.z a.w]]; b = (A, mu, lambda, act)
+// ---------------------------------------------------------------------------
+struct TriState {
+    float3 F0, F1, n, dJ0, dJ1;
+    float Ic, J, inv, alpha, ca, cb;
+};
+
+__device__ __forceinline__ void tri_state(float3 x0, float3 x1, float3 x2, float4 a, float4 b, TriState& s) {
+    const float3 d1 = x1 - x0, d2 = x2 - x0;
+    s.F0 = d1 * a.x + d2 * a.z;
+    s.F1 = d1 * a.y + d2 * a.w;
+    s.Ic = dot3(s.F0, s.F0) + dot3(s.F1, s.F1);
+    const float3 cr = cross3(s.F0, s.F1);
+    s.J = sqrtf(dot3(cr, cr));
+    s.n = cr * (1.0f / s.J);
+    s.dJ0 = cross3(s.F1, s.n);
+    s.dJ1 = cross3(s.n, s.F0);
+    const float mu = b.y, lam = b.z;
+    s.inv = 1.0f / (s.Ic + 1.0f);
+    s.alpha = 1.0f + (2.0f / 3.0f) * mu / lam + b.w;
+    s.ca = mu * (1.0f - s.inv);
+    s.cb = lam * (s.J - s.alpha);
+}
+
+__device__ __forceinline__ void tri_forces(const TriState& s, float4 a, float4 b, float3& f0, float3& f1,
+                                           float3& f2) {
+    const float3 P0 = s.ca * s.F0 + s.cb * s.dJ0;
+    const float3 P1 = s.ca * s.F1 + s.cb * s.dJ1;
+    const float nA = -b.x;
+    f1 = nA * (P0 * a.x + P1 * a.y);
+    f2 = nA * (P0 * a.z + P1 * a.w);
+    f0 = -(f1 + f2);
+}
+
+// Reverse mode of tri_forces: P_bar = -A G Dm^-1, F_bar = dP/dF[P_bar] with
+// the Hessian of J applied through dn = (I - n n^T) dc / J,
+// dc = P_bar0 x f1 + f0 x P_bar1.
+__device__ __forceinline__ void tri_adjoint(const TriState& s, float4 a, float4 b, float3 fb0, float3 fb1,
+                                            float3 fb2, float3& xb0, float3& xb1, float3& xb2, float& gmu,
+                                            float& glam, float& gact) {
+    const float mu = b.y, lam = b.z, nA = -b.x;
+    const float3 G1 = fb1 - fb0, G2 = fb2 - fb0;
+    const float3 Pb0 = nA * (G1 * a.x + G2 * a.z);
+    const float3 Pb1 = nA * (G1 * a.y + G2 * a.w);
+    const float FP = dot3(s.F0, Pb0) + dot3(s.F1, Pb1);
+    const float JP = dot3(s.dJ0, Pb0) + dot3(s.dJ1, Pb1);
+    const float3 dc = cross3(Pb0, s.F1) + cross3(s.F0, Pb1);
+    const float3 dn = (dc - s.n * dot3(s.n, dc)) * (1.0f / s.J);
+    const float3 HJ0 = cross3(Pb1, s.n) + cross3(s.F1, dn);
+    const float3 HJ1 = cross3(dn, s.F0) + cross3(s.n, Pb0);
+    const float k2 = 2.0f * mu * s.inv * s.inv * FP;
+    const float lj = lam * JP;
+    const float3 Fb0 = s.ca * Pb0 + k2 * s.F0 + lj * s.dJ0 + s.cb * HJ0;
+    const float3 Fb1 = s.ca * Pb1 + k2 * s.F1 + lj * s.dJ1 + s.cb * HJ1;
+    xb1 = Fb0 * a.x + Fb1 * a.y;
+    xb2 = Fb0 * a.z + Fb1 * a.w;
+    xb0 = -(xb1 + xb2);
+    gmu = (1.0f - s.inv) * FP - (2.0f / 3.0f) * JP;
+    glam = (s.J - s.alpha + (2.0f / 3.0f) * mu / lam) * JP;
+    gact = -lam * JP;
+}
+
+// ---------------------------------------------------------------------------
+// hinge (x1, x2 wing tips; x3 -> x4 edge); p = (kb, act)
+// ---------------------------------------------------------------------------
+struct HingeState {
+    float3 E, A1, B1, A2, B2, N1, N2, Eh, n1, n2, cr, g1, g2;
+    float lE2, l1s, l2s, lE, l1, l2, sy, cx, phi, q, sn, cs, p14, p24, p13, p23;
+    bool ok;
+};
+
+__device__ __forceinline__ void hinge_state(float3 x1, float3 x2, float3 x3, float3 x4, float2 p, HingeState& s) {
+    s.E = x4 - x3;
+    s.A1 = x1 - x3;
+    s.B1 = x1 - x4;
+    s.A2 = x2 - x4;
+    s.B2 = x2 - x3;
+    s.N1 = cross3(s.A1, s.B1);
+    s.N2 = cross3(s.A2, s.B2);
+    s.lE2 = dot3(s.E, s.E);
+    s.l1s = dot3(s.N1, s.N1);
+    s.l2s = dot3(s.N2, s.N2);
+    const float tiny = 1e-24f * s.lE2 * s.lE2;
+    s.ok = s.lE2 > 0.0f && s.l1s > tiny && s.l2s > tiny;
+    if (!s.ok) return;
+    s.lE = sqrtf(s.lE2);
+    s.l1 = sqrtf(s.l1s);
+    s.l2 = sqrtf(s.l2s);
+    s.Eh = s.E * (1.0f / s.lE);
+    s.n1 = s.N1 * (1.0f / s.l1);
+    s.n2 = s.N2 * (1.0f / s.l2);
+    s.cr = cross3(s.n1, s.n2);
+    s.sy = dot3(s.cr, s.Eh);
+    s.cx = dot3(s.n1, s.n2);
+    s.phi = atan2f(s.sy, s.cx);
+    s.g1 = s.N1 * (1.0f / s.l1s);
+    s.g2 = s.N2 * (1.0f / s.l2s);
+    s.p14 = dot3(s.B1, s.Eh);
+    s.p24 = dot3(s.A2, s.Eh);
+    s.p13 = dot3(s.A1, s.Eh);
+    s.p23 = dot3(s.B2, s.Eh);
+    s.q = s.lE2 / (s.l1 + s.l2);
+    const float ang = 0.5f * s.phi + p.y;
+    s.sn = sinf(ang);
+    s.cs = cosf(ang);
+}
+
+__device__ __forceinline__ void hinge_forces(const HingeState& s, float2 p, float3& f1, float3& f2, float3& f3,
+                                             float3& f4) {
+    if (!s.ok) {
+        f1 = f2 = f3 = f4 = make_float3(0.f, 0.f, 0.f);
+        return;
+    }
+    const float sc = p.x * s.q * s.sn;
+    f1 = sc * (s.lE * s.g1);
+    f2 = sc * (s.lE * s.g2);
+    f3 = sc * (s.p14 * s.g1 + s.p24 * s.g2);
+    f4 = sc * (-(s.p13 * s.g1) - s.p23 * s.g2);
+}
+
+// Reverse mode of hinge_forces, statement by statement.
+__device__ __forceinline__ void hinge_adjoint(const HingeState& s, float2 p, float3 fb1, float3 fb2, float3 fb3,
+                                              float3 fb4, float3& xb1, float3& xb2, float3& xb3, float3& xb4,
+                                              float& gkb, float& gact) {
+    const float3 z = make_float3(0.f, 0.f, 0.f);
+    if (!s.ok) {
+        xb1 = xb2 = xb3 = xb4 = z;
+        gkb = gact = 0.f;
+        return;
+    }
+    const float kb = p.x;
+    const float sc = kb * s.q * s.sn;
+    // u_i and the scale s
+    const float3 u1 = s.lE * s.g1, u2 = s.lE * s.g2;
+    const float3 u3 = s.p14 * s.g1 + s.p24 * s.g2;
+    const float3 u4 = -(s.p13 * s.g1) - s.p23 * s.g2;
+    const float scb = dot3(fb1, u1) + dot3(fb2, u2) + dot3(fb3, u3) + dot3(fb4, u4);
+    const float3 ub1 = sc * fb1, ub2 = sc * fb2, ub3 = sc * fb3, ub4 = sc * fb4;
+    float lEb = dot3(ub1, s.g1) + dot3(ub2, s.g2);
+    float3 gb1 = s.lE * ub1 + s.p14 * ub3 - s.p13 * ub4;
+    float3 gb2 = s.lE * ub2 + s.p24 * ub3 - s.p23 * ub4;
+    const float p14b = dot3(ub3, s.g1), p24b = dot3(ub3, s.g2);
+    const float p13b = -dot3(ub4, s.g1), p23b = -dot3(ub4, s.g2);
+    // s = kb q sin(phi/2 + act)
+    gkb = s.q * s.sn * scb;
+    const float qb = kb * s.sn * scb;
+    const float snb = kb * s.q * scb;
+    const float phib = 0.5f * s.cs * snb;
+    gact = s.cs * snb;
+    const float l12 = s.l1 + s.l2;
+    float lE2b = qb / l12;
+    float l1b = -qb * s.lE2 / (l12 * l12);
+    float l2b = l1b;
+    // projections onto Eh
+    float3 B1b = p14b * s.Eh, A2b = p24b * s.Eh, A1b = p13b * s.Eh, B2b = p23b * s.Eh;
+    float3 Ehb = p14b * s.B1 + p24b * s.A2 + p13b * s.A1 + p23b * s.B2;
+    // g = N / |N|^2
+    float3 N1b = gb1 * (1.0f / s.l1s), N2b = gb2 * (1.0f / s.l2s);
+    float l1sb = -dot3(gb1, s.N1) / (s.l1s * s.l1s);
+    float l2sb = -dot3(gb2, s.N2) / (s.l2s * s.l2s);
+    // phi = atan2(sy, cx)
+    const float r2 = s.sy * s.sy + s.cx * s.cx;
+    const float syb = phib * s.cx / r2, cxb = -phib * s.sy / r2;
+    const float3 crb = syb * s.Eh;
+    Ehb += syb * s.cr;
+    float3 n1b = cxb * s.n2 + cross3(s.n2, crb);
+    float3 n2b = cxb * s.n1 + cross3(crb, s.n1);
+    // n = N / |N|
+    N1b += n1b * (1.0f / s.l1);
+    l1b += -dot3(n1b, s.N1) / (s.l1 * s.l1);
+    N2b += n2b * (1.0f / s.l2);
+    l2b += -dot3(n2b, s.N2) / (s.l2 * s.l2);
+    // Eh = E / |E|
+    float3 Eb = Ehb * (1.0f / s.lE);
+    lEb += -dot3(Ehb, s.E) / s.lE2;
+    // square roots and squared norms
+    lE2b += lEb / (2.0f * s.lE);
+    l1sb += l1b / (2.0f * s.l1);
+    l2sb += l2b / (2.0f * s.l2);
+    Eb += (2.0f * lE2b) * s.E;
+    N1b += (2.0f * l1sb) * s.N1;
+    N2b += (2.0f * l2sb) * s.N2;
+    // N1 = A1 x B1, N2 = A2 x B2
+    A1b += cross3(s.B1, N1b);
+    B1b += cross3(N1b, s.A1);
+    A2b += cross3(s.B2, N2b);
+    B2b += cross3(N2b, s.A2);
+    // A1 = x1 - x3, B1 = x1 - x4, A2 = x2 - x4, B2 = x2 - x3, E = x4 - x3
+    xb1 = A1b + B1b;
+    xb2 = A2b + B2b;
+    xb3 = -(A1b + B2b + Eb);
+    xb4 = Eb - B1b - A2b;
+}
+
+// ---------------------------------------------------------------------------
+// contact
+// ---------------------------------------------------------------------------
+struct ContactParams {
+    float ke, kd, kf, mu_f;
+};
+
+// one contact with outward normal n and penetration C > 0
+__device__ __forceinline__ float3 contact_one(float3 v, float3 n, float C, const ContactParams& cp) {
+    const float vn = dot3(v, n);
+    const float fn = cp.ke * C - cp.kd * vn;
+    float3 f = fn * n;
+    const float3 vs = v - vn * n;
+    const float vsl = sqrtf(dot3(vs, vs));
+    const float afn = fabsf(fn);
+    if (cp.kf * vsl <= cp.mu_f * afn) {
+        f -= cp.kf * vs;
+    } else {
+        f -= (cp.mu_f * afn / vsl) * vs;
+    }
+    return f;
+}
+
+// Reverse mode of contact_one for a fixed normal (plane) or a normal that
+// depends on x (sphere: handled by the caller through nb / Cb).
+__device__ __forceinline__ void contact_one_adjoint(float3 v, float3 n, float C, const ContactParams& cp,
+                                                    float3 fb, float3& vb, float3& nb, float& Cb, float3& f) {
+    const float vn = dot3(v, n);
+    const float fn = cp.ke * C - cp.kd * vn;
+    const float3 vs = v - vn * n;
+    const float vsl = sqrtf(dot3(vs, vs));
+    const float afn = fabsf(fn);
+    f = fn * n;
+    // f = fn n
+    nb = fn * fb;
+    float fnb = dot3(fb, n);
+    float3 vsb;
+    if (cp.kf * vsl <= cp.mu_f * afn) {
+        f -= cp.kf * vs;
+        vsb = -cp.kf * fb;
+    } else {
+        const float k = cp.mu_f * afn / vsl;
+        f -= k * vs;
+        const float kb = -dot3(fb, vs);
+        vsb = -k * fb - (kb * k / (vsl * vsl)) * vs;
+        const float afnb = kb * cp.mu_f / vsl;
+        fnb += fn > 0.0f ? afnb : (fn < 0.0f ? -afnb : 0.0f);
+    }
+    // vs = v - vn n
+    vb = vsb;
+    float vnb = -dot3(vsb, n);
+    nb -= vn * vsb;
+    // fn = ke C - kd vn
+    Cb = cp.ke * fnb;
+    vnb -= cp.kd * fnb;
+    // vn = v . n
+    vb += vnb * n;
+    nb += vnb * v;
+}
+
+}  // namespace gs

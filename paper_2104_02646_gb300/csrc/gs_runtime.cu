@@ -1,0 +1,1250 @@
+// Host runtime of the gradsim C ABI: context, mesh construction, launch sets,
+// checkpointed rollout and adjoint, batching.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gs_internal.h"
+#include "gs_runtime.h"
+
+namespace gs {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+gs_status set_error(gs_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+gs_status cuda_error(cudaError_t e, const char* what) {
+    return set_error(GS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+void clear_error() { g_last_error.clear(); }
+
+// ---------------------------------------------------------------------------
+// memory through the context
+// ---------------------------------------------------------------------------
+gs_status Buf::alloc(gs_ctx* c, size_t nbytes, cudaStream_t s) {
+    release(s);
+    if (nbytes == 0) return GS_OK;
+    if (c->budget && c->used + nbytes > c->budget)
+        return set_error(GS_ENOMEM, "allocation of " + std::to_string(nbytes) + " bytes exceeds the context budget");
+    void* q = nullptr;
+    if (c->has_alloc) {
+        q = c->alloc.alloc(nbytes, (void*)s, c->alloc.user);
+        if (!q) return set_error(GS_ENOMEM, "allocator callback returned NULL for " + std::to_string(nbytes) + " bytes");
+    } else {
+        cudaError_t e = cudaMallocAsync(&q, nbytes, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(GS_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+        }
+    }
+    ctx = c;
+    p = q;
+    bytes = nbytes;
+    c->used += nbytes;
+    return GS_OK;
+}
+
+void Buf::release(cudaStream_t s) {
+    if (!p) return;
+    if (ctx->has_alloc) ctx->alloc.free(p, bytes, (void*)s, ctx->alloc.user);
+    else cudaFreeAsync(p, s);
+    ctx->used -= bytes;
+    p = nullptr;
+    bytes = 0;
+}
+
+template <class T>
+static gs_status upload(gs_ctx* c, Buf& b, const std::vector<T>& v, cudaStream_t s) {
+    GS_TRY(b.alloc(c, std::max<size_t>(v.size(), 1) * sizeof(T), s));
+    if (!v.empty()) GS_CUDA(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return GS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// mesh construction (host): ordering, patches, local CSR, boundary CSR
+// ---------------------------------------------------------------------------
+static uint64_t spread21(uint64_t v) {
+    v &= 0x1fffff;
+    v = (v | v << 32) & 0x1f00000000ffffULL;
+    v = (v | v << 16) & 0x1f0000ff0000ffULL;
+    v = (v | v << 8) & 0x100f00f00f00f00fULL;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+    v = (v | v << 2) & 0x1249249249249249ULL;
+    return v;
+}
+
+struct Topology {
+    std::vector<int> elem_perm, hinge_perm, node_perm, node_inv;
+    std::vector<PatchDesc> patches;
+    std::vector<uint2> eidx, hidx;
+    std::vector<int> bnd_ids;
+    std::vector<uint16_t> loc_rowptr, loc_slots;
+    std::vector<int> bnd_rowptr, bnd_parts;
+    int n_int = 0, n_bnd = 0, max_loc = 0, max_slots = 0;
+};
+
+static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
+    const int N = d.n_nodes, E = d.n_elems, B = d.kind == GS_CLOTH ? d.n_hinges : 0;
+    const int nc = d.kind == GS_TET ? 4 : 3;
+    // 1. Morton order of element centroids
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = 0; i < N; ++i)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], d.X[3 * i + k]);
+            hi[k] = std::max(hi[k], d.X[3 * i + k]);
+        }
+    double ext = 0.0;
+    for (int k = 0; k < 3; ++k) ext = std::max(ext, hi[k] - lo[k]);
+    if (!(ext > 0.0)) ext = 1.0;
+    std::vector<std::pair<uint64_t, int>> key(E);
+    for (int e = 0; e < E; ++e) {
+        double c[3] = {0, 0, 0};
+        for (int j = 0; j < nc; ++j)
+            for (int k = 0; k < 3; ++k) c[k] += d.X[3 * d.elems[nc * e + j] + k];
+        uint64_t q[3];
+        for (int k = 0; k < 3; ++k) {
+            const double t = (c[k] / nc - lo[k]) / ext;
+            q[k] = (uint64_t)std::min(2097151.0, std::max(0.0, t * 2097151.0));
+        }
+        key[e] = {spread21(q[0]) | spread21(q[1]) << 1 | spread21(q[2]) << 2, e};
+    }
+    std::sort(key.begin(), key.end());
+    T.elem_perm.resize(E);
+    std::vector<int> elem_inv(E);
+    for (int e = 0; e < E; ++e) {
+        T.elem_perm[e] = key[e].second;
+        elem_inv[key[e].second] = e;
+    }
+    const int P = (E + pe - 1) / pe;
+    // 2. hinges follow the patch of the triangle (x1, x3, x4)
+    std::vector<int> hinge_patch(B, 0);
+    if (B) {
+        std::unordered_map<uint64_t, int> tri_of;
+        tri_of.reserve(2 * E);
+        auto tkey = [](int a, int b, int c) {
+            int v[3] = {a, b, c};
+            std::sort(v, v + 3);
+            return (uint64_t)v[0] * 0x9E3779B97F4A7C15ULL ^ ((uint64_t)v[1] << 21) ^ ((uint64_t)v[2] << 42);
+        };
+        for (int t = 0; t < E; ++t) tri_of[tkey(d.elems[3 * t], d.elems[3 * t + 1], d.elems[3 * t + 2])] = t;
+        for (int h = 0; h < B; ++h) {
+            const int* q = d.hinges + 4 * h;
+            auto it = tri_of.find(tkey(q[0], q[2], q[3]));
+            if (it == tri_of.end())
+                return set_error(GS_EINVAL, "hinge " + std::to_string(h) + ": triangle (x1, x3, x4) is not in the mesh");
+            hinge_patch[h] = elem_inv[it->second] / pe;
+        }
+        std::vector<std::pair<int, int>> hk(B);
+        for (int h = 0; h < B; ++h) hk[h] = {hinge_patch[h], h};
+        std::sort(hk.begin(), hk.end());
+        T.hinge_perm.resize(B);
+        for (int h = 0; h < B; ++h) T.hinge_perm[h] = hk[h].second;
+    }
+    // per patch element / hinge ranges
+    T.patches.assign(P, PatchDesc{});
+    for (int p = 0; p < P; ++p) {
+        T.patches[p].e_begin = p * pe;
+        T.patches[p].n_e = std::min(pe, E - p * pe);
+    }
+    for (int h = 0, p = 0; p < P; ++p) {
+        T.patches[p].h_begin = h;
+        while (h < B && hinge_patch[T.hinge_perm[h]] == p) ++h;
+        T.patches[p].n_h = h - T.patches[p].h_begin;
+    }
+    // corner nodes of internal element e / hinge h (caller node ids)
+    auto ecorner = [&](int e, int c) { return d.elems[nc * T.elem_perm[e] + c]; };
+    auto hcorner = [&](int h, int c) { return d.hinges[4 * T.hinge_perm[h] + c]; };
+    // 3. patches touching each node
+    std::vector<int> cnt(N, 0), last(N, -1), first(N, -1);
+    auto touch = [&](int p, int u) {
+        if (last[u] != p) {
+            last[u] = p;
+            if (cnt[u]++ == 0) first[u] = p;
+        }
+    };
+    for (int p = 0; p < P; ++p) {
+        const PatchDesc& q = T.patches[p];
+        for (int e = q.e_begin; e < q.e_begin + q.n_e; ++e)
+            for (int c = 0; c < nc; ++c) touch(p, ecorner(e, c));
+        for (int h = q.h_begin; h < q.h_begin + q.n_h; ++h)
+            for (int c = 0; c < 4; ++c) touch(p, hcorner(h, c));
+    }
+    // 4. internal node numbering: interior nodes patch by patch, then boundary
+    //    nodes by (first patch, id), then untouched nodes
+    std::vector<std::vector<int>> interior(P);
+    std::vector<std::pair<int, int>> bnodes;
+    std::vector<int> loose;
+    for (int u = 0; u < N; ++u) {
+        if (cnt[u] == 1) interior[first[u]].push_back(u);
+        else if (cnt[u] > 1) bnodes.push_back({first[u], u});
+        else loose.push_back(u);
+    }
+    std::sort(bnodes.begin(), bnodes.end());
+    T.node_perm.clear();
+    T.node_perm.reserve(N);
+    for (int p = 0; p < P; ++p) {
+        T.patches[p].int_begin = (int)T.node_perm.size();
+        T.patches[p].n_int = (int)interior[p].size();
+        for (int u : interior[p]) T.node_perm.push_back(u);
+    }
+    T.n_int = (int)T.node_perm.size();
+    for (auto& b : bnodes) T.node_perm.push_back(b.second);
+    for (int u : loose) T.node_perm.push_back(u);
+    T.n_bnd = N - T.n_int;
+    T.node_inv.assign(N, -1);
+    for (int i = 0; i < N; ++i) T.node_inv[T.node_perm[i]] = i;
+    // 5. per patch: boundary list, local indices, local CSR
+    T.eidx.assign(E, make_uint2(0, 0));
+    T.hidx.assign(B, make_uint2(0, 0));
+    std::vector<int> loc(N, -1);
+    std::vector<std::vector<int>> bparts(T.n_bnd);
+    for (int p = 0; p < P; ++p) {
+        PatchDesc& q = T.patches[p];
+        std::vector<int> bl;  // internal ids of boundary nodes touched by p
+        auto note = [&](int u) {
+            const int g = T.node_inv[u];
+            if (g >= T.n_int && loc[g] == -1) {
+                loc[g] = -2;
+                bl.push_back(g);
+            }
+        };
+        for (int e = q.e_begin; e < q.e_begin + q.n_e; ++e)
+            for (int c = 0; c < nc; ++c) note(ecorner(e, c));
+        for (int h = q.h_begin; h < q.h_begin + q.n_h; ++h)
+            for (int c = 0; c < 4; ++c) note(hcorner(h, c));
+        std::sort(bl.begin(), bl.end());
+        q.bnd_begin = (int)T.bnd_ids.size();
+        q.n_bnd = (int)bl.size();
+        for (int k = 0; k < q.n_bnd; ++k) {
+            loc[bl[k]] = q.n_int + k;
+            T.bnd_ids.push_back(bl[k]);
+            bparts[bl[k] - T.n_int].push_back(q.bnd_begin + k);
+        }
+        for (int l = 0; l < q.n_int; ++l) loc[q.int_begin + l] = l;
+        const int n_loc = q.n_int + q.n_bnd;
+        const int n_slots = nc * q.n_e + 4 * q.n_h;
+        if (n_loc > 65535 || n_slots > 65535)
+            return set_error(GS_EINVAL, "patch too large for 16-bit local indices; lower patch_elems");
+        auto lid = [&](int u) { return (uint32_t)loc[T.node_inv[u]]; };
+        // local ids and CSR in ascending slot order (= ascending element order)
+        std::vector<int> rc(n_loc + 1, 0);
+        std::vector<int> slot_node(n_slots);
+        for (int le = 0; le < q.n_e; ++le) {
+            const int e = q.e_begin + le;
+            uint32_t l[4] = {0, 0, 0, 0};
+            for (int c = 0; c < nc; ++c) {
+                l[c] = lid(ecorner(e, c));
+                slot_node[nc * le + c] = (int)l[c];
+            }
+            T.eidx[e] = make_uint2(l[0] | l[1] << 16, l[2] | l[3] << 16);
+        }
+        for (int lh = 0; lh < q.n_h; ++lh) {
+            const int h = q.h_begin + lh;
+            uint32_t l[4];
+            for (int c = 0; c < 4; ++c) {
+                l[c] = lid(hcorner(h, c));
+                slot_node[nc * q.n_e + 4 * lh + c] = (int)l[c];
+            }
+            T.hidx[h] = make_uint2(l[0] | l[1] << 16, l[2] | l[3] << 16);
+        }
+        for (int s = 0; s < n_slots; ++s) rc[slot_node[s] + 1]++;
+        for (int l = 0; l < n_loc; ++l) rc[l + 1] += rc[l];
+        q.lr_begin = (int)T.loc_rowptr.size();
+        q.slot_begin = (int)T.loc_slots.size();
+        for (int l = 0; l <= n_loc; ++l) T.loc_rowptr.push_back((uint16_t)rc[l]);
+        std::vector<uint16_t> slots(n_slots);
+        std::vector<int> fill(rc.begin(), rc.end() - 1);
+        for (int s = 0; s < n_slots; ++s) slots[fill[slot_node[s]]++] = (uint16_t)s;
+        T.loc_slots.insert(T.loc_slots.end(), slots.begin(), slots.end());
+        T.max_loc = std::max(T.max_loc, n_loc);
+        T.max_slots = std::max(T.max_slots, n_slots);
+        for (int g : bl) loc[g] = -1;
+        for (int l = 0; l < q.n_int; ++l) loc[q.int_begin + l] = -1;
+        q.mesh = 0;
+    }
+    // 6. boundary CSR (partials in patch order)
+    T.bnd_rowptr.assign(T.n_bnd + 1, 0);
+    for (int b = 0; b < T.n_bnd; ++b) T.bnd_rowptr[b + 1] = T.bnd_rowptr[b] + (int)bparts[b].size();
+    T.bnd_parts.reserve(T.bnd_rowptr[T.n_bnd]);
+    for (int b = 0; b < T.n_bnd; ++b) T.bnd_parts.insert(T.bnd_parts.end(), bparts[b].begin(), bparts[b].end());
+    return GS_OK;
+}
+
+static std::vector<NodeBlock> make_blocks(int begin, int n, int per, int mesh) {
+    std::vector<NodeBlock> v;
+    for (int i = 0; i < n; i += per) v.push_back(NodeBlock{mesh, begin + i, std::min(per, n - i), 0});
+    return v;
+}
+
+// explicit stability estimate (warning only): elastic dt < 2/omega with
+// omega^2 ~ (lambda + 2 mu) V |Dm^-1|_F^2 / m_corner, contact and damping
+// limits dt < 2/sqrt(k_e/m), dt < 2 m / k_d, dt < 2 m / k_f
+static double stability_estimate(const gs_mesh_desc& d) {
+    const int N = d.n_nodes, E = d.n_elems, nc = d.kind == GS_TET ? 4 : 3;
+    std::vector<double> m(N, 0.0), V(E, 0.0), G(E, 0.0);
+    for (int e = 0; e < E; ++e) {
+        const int* q = d.elems + nc * e;
+        double a[3], b[3], c[3];
+        for (int k = 0; k < 3; ++k) {
+            a[k] = d.X[3 * q[1] + k] - d.X[3 * q[0] + k];
+            b[k] = d.X[3 * q[2] + k] - d.X[3 * q[0] + k];
+            c[k] = nc == 4 ? d.X[3 * q[3] + k] - d.X[3 * q[0] + k] : 0.0;
+        }
+        double la = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        double lb = std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+        double lc = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        double h = nc == 4 ? std::min(la, std::min(lb, lc)) : std::min(la, lb);
+        double n0 = a[1] * b[2] - a[2] * b[1], n1 = a[2] * b[0] - a[0] * b[2], n2 = a[0] * b[1] - a[1] * b[0];
+        if (nc == 4) V[e] = std::fabs(n0 * c[0] + n1 * c[1] + n2 * c[2]) / 6.0;
+        else V[e] = 0.5 * std::sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+        G[e] = (h > 0) ? 3.0 / (h * h) : 0.0;
+        const double share = d.density[e] * V[e] / nc;
+        for (int j = 0; j < nc; ++j) m[q[j]] += share;
+    }
+    double om2 = 0.0, mmin = 1e300;
+    for (int e = 0; e < E; ++e) {
+        const int* q = d.elems + nc * e;
+        double me = 1e300;
+        for (int j = 0; j < nc; ++j)
+            if (!(d.pinned && d.pinned[q[j]])) me = std::min(me, m[q[j]]);
+        if (me >= 1e300 || me <= 0) continue;
+        om2 = std::max(om2, (d.lambda[e] + 2 * d.mu[e]) * V[e] * G[e] * 4.0 / me);
+    }
+    for (int i = 0; i < N; ++i)
+        if (m[i] > 0 && !(d.pinned && d.pinned[i])) mmin = std::min(mmin, m[i]);
+    double dt = om2 > 0 ? 2.0 / std::sqrt(om2) : 1e300;
+    if (mmin < 1e300 && (d.contact.plane_on || d.contact.sphere_on)) {
+        if (d.contact.ke > 0) dt = std::min(dt, 2.0 / std::sqrt(d.contact.ke / mmin));
+        if (d.contact.kd > 0) dt = std::min(dt, 2.0 * mmin / d.contact.kd);
+        if (d.contact.kf > 0) dt = std::min(dt, 2.0 * mmin / d.contact.kf);
+    }
+    return dt;
+}
+
+static bool finite_all(const double* p, int n) {
+    if (!p) return true;
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+static gs_status validate(const gs_mesh_desc& d) {
+    if (d.kind != GS_TET && d.kind != GS_CLOTH) return set_error(GS_EINVAL, "kind must be GS_TET or GS_CLOTH");
+    if (d.n_nodes <= 0 || d.n_elems <= 0) return set_error(GS_EINVAL, "mesh needs nodes and elements");
+    if (!d.elems || !d.X || !d.mu || !d.lambda || !d.density) return set_error(GS_EINVAL, "missing mesh array");
+    const int nc = d.kind == GS_TET ? 4 : 3;
+    for (int e = 0; e < d.n_elems; ++e) {
+        const int* q = d.elems + nc * e;
+        for (int j = 0; j < nc; ++j) {
+            if (q[j] < 0 || q[j] >= d.n_nodes)
+                return set_error(GS_EINVAL, "element " + std::to_string(e) + " has node index out of range");
+            for (int k = 0; k < j; ++k)
+                if (q[k] == q[j]) return set_error(GS_EINVAL, "element " + std::to_string(e) + " repeats a node");
+        }
+        if (!(d.mu[e] > 0) || !(d.lambda[e] > 0) || !(d.density[e] > 0) || !std::isfinite(d.mu[e]) ||
+            !std::isfinite(d.lambda[e]) || !std::isfinite(d.density[e]))
+            return set_error(GS_EINVAL, "element " + std::to_string(e) + ": mu, lambda, density must be finite and > 0");
+    }
+    if (d.kind == GS_CLOTH) {
+        if (d.n_hinges < 0 || (d.n_hinges > 0 && (!d.hinges || !d.kb)))
+            return set_error(GS_EINVAL, "cloth hinges need indices and kb");
+        for (int h = 0; h < d.n_hinges; ++h) {
+            const int* q = d.hinges + 4 * h;
+            for (int j = 0; j < 4; ++j)
+                if (q[j] < 0 || q[j] >= d.n_nodes)
+                    return set_error(GS_EINVAL, "hinge " + std::to_string(h) + " has node index out of range");
+            if (!std::isfinite(d.kb[h])) return set_error(GS_EINVAL, "non-finite kb");
+        }
+        if (!finite_all(d.hinge_act, d.n_hinges)) return set_error(GS_EINVAL, "non-finite hinge actuation");
+    }
+    if (!finite_all(d.X, 3 * d.n_nodes) || !finite_all(d.v0, 3 * d.n_nodes) || !finite_all(d.act, d.n_elems))
+        return set_error(GS_EINVAL, "non-finite positions, velocities or actuation");
+    const gs_contact& c = d.contact;
+    if (c.plane_on) {
+        const double n = std::sqrt((double)c.plane_n[0] * c.plane_n[0] + (double)c.plane_n[1] * c.plane_n[1] +
+                                   (double)c.plane_n[2] * c.plane_n[2]);
+        if (std::fabs(n - 1.0) > 1e-5) return set_error(GS_EINVAL, "plane normal must have unit length");
+    }
+    if (c.sphere_on && !(c.sphere_r > 0)) return set_error(GS_EINVAL, "sphere radius must be > 0");
+    if (!(c.ke >= 0 && c.kd >= 0 && c.kf >= 0 && c.mu_f >= 0)) return set_error(GS_EINVAL, "contact parameters must be >= 0");
+    return GS_OK;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+// ---------------------------------------------------------------------------
+// mesh
+// ---------------------------------------------------------------------------
+gs_status gs_mesh::refresh_rt() {
+    MeshRT& r = rt;
+    r.st_x = (float4*)st.p;
+    r.st_v = st.p ? (float4*)st.p + (size_t)n_bufs * n_pad : nullptr;
+    r.buf_stride = n_pad;
+    r.xb = (float4*)xb.p;
+    r.vb = (float4*)vb.p;
+    r.wbar = (double*)wbar.p;
+    r.g_mu = (double*)g_mu.p;
+    r.g_lam = (double*)g_lam.p;
+    r.g_act = (double*)g_act.p;
+    r.g_kb = (double*)g_kb.p;
+    r.g_hact = (double*)g_hact.p;
+    return GS_OK;
+}
+
+// grow the state block to hold `n` buffers, keeping buffer 0
+gs_status gs_mesh::ensure_buffers(int n, cudaStream_t s) {
+    if (n <= n_bufs && st.p) return GS_OK;
+    Buf nb;
+    GS_TRY(nb.alloc(ctx, (size_t)2 * n * n_pad * sizeof(float4), s));
+    if (st.p) {
+        GS_CUDA(cudaMemcpyAsync(nb.p, st.p, (size_t)n_pad * sizeof(float4), cudaMemcpyDeviceToDevice, s));
+        GS_CUDA(cudaMemcpyAsync((float4*)nb.p + (size_t)n * n_pad, (float4*)st.p + (size_t)n_bufs * n_pad,
+                                (size_t)n_pad * sizeof(float4), cudaMemcpyDeviceToDevice, s));
+    }
+    st.release(s);
+    st = std::move(nb);
+    n_bufs = n;
+    return refresh_rt();
+}
+
+gs_status gs_mesh::ensure_adjoint(cudaStream_t s) {
+    if (xb.p) return GS_OK;
+    GS_TRY(xb.alloc(ctx, (size_t)n_pad * sizeof(float4), s));
+    GS_TRY(vb.alloc(ctx, (size_t)n_pad * sizeof(float4), s));
+    GS_TRY(wbar.alloc(ctx, (size_t)n_pad * sizeof(double), s));
+    GS_TRY(mbar.alloc(ctx, (size_t)n_pad * sizeof(double), s));
+    GS_TRY(g_mu.alloc(ctx, (size_t)info.n_elems * sizeof(double), s));
+    GS_TRY(g_lam.alloc(ctx, (size_t)info.n_elems * sizeof(double), s));
+    GS_TRY(g_act.alloc(ctx, (size_t)info.n_elems * sizeof(double), s));
+    if (info.n_hinges) {
+        GS_TRY(g_kb.alloc(ctx, (size_t)info.n_hinges * sizeof(double), s));
+        GS_TRY(g_hact.alloc(ctx, (size_t)info.n_hinges * sizeof(double), s));
+    }
+    return refresh_rt();
+}
+
+gs_mesh::~gs_mesh() {
+    cudaStream_t s = 0;
+    for (Buf* b : {&eidx, &ea, &eb, &ec, &eact, &hidx, &hp, &bnd_ids, &loc_rowptr, &loc_slots, &bnd_rowptr,
+                   &bnd_parts, &partials, &node_perm, &elem_perm, &hinge_perm, &w, &X, &rho, &pinned, &st, &xb, &vb,
+                   &wbar, &mbar, &g_mu, &g_lam, &g_act, &g_kb, &g_hact, &status, &target, &scratch})
+        b->release(s);
+    self.reset();
+    cudaStreamSynchronize(s);
+}
+
+extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_mesh** out) {
+    clear_error();
+    if (!ctx || !desc || !out) return set_error(GS_EINVAL, "null argument");
+    *out = nullptr;
+    GS_CUDA(cudaSetDevice(ctx->device));
+    const gs_mesh_desc& d = *desc;
+    GS_TRY(validate(d));
+    const int nc = d.kind == GS_TET ? 4 : 3;
+    int threads = d.block_threads > 0 ? d.block_threads : 256;
+    if (threads % 32 || threads > 1024) return set_error(GS_EINVAL, "block_threads must be a multiple of 32, <= 1024");
+    int pe = d.patch_elems > 0 ? d.patch_elems : (d.kind == GS_TET ? 1024 : 512);
+    if (pe > 16383) return set_error(GS_EINVAL, "patch_elems must be <= 16383");
+    Topology T;
+    GS_TRY(build_topology(d, pe, T));
+    std::unique_ptr<gs_mesh> m(new gs_mesh());
+    m->ctx = ctx;
+    const int N = d.n_nodes, E = d.n_elems, B = d.kind == GS_CLOTH ? d.n_hinges : 0;
+    m->info.kind = d.kind;
+    m->info.n_nodes = N;
+    m->info.n_elems = E;
+    m->info.n_hinges = B;
+    m->info.n_patches = (int)T.patches.size();
+    m->info.n_boundary_nodes = T.n_bnd;
+    m->info.patch_elems = pe;
+    m->info.block_threads = threads;
+    m->info.dt_stable = stability_estimate(d);
+    m->n_pad = (N + 31) & ~31;
+    m->threads = threads;
+    m->max_loc = T.max_loc;
+    m->max_slots = T.max_slots;
+    m->patches = T.patches;
+    m->bnd_blocks = make_blocks(0, T.n_bnd, 256, 0);
+    m->node_blocks = make_blocks(0, N, 256, 0);
+    const size_t need = smem_bytes(d.kind, true, T.max_loc, T.max_slots);
+    if (need > ctx->smem_optin)
+        return set_error(GS_EINVAL, "patch needs " + std::to_string(need) + " B of shared memory; lower patch_elems");
+    cudaStream_t s = 0;
+    // element data in internal order
+    std::vector<float4> ea(E), eb(E), ec(d.kind == GS_TET ? E : 0);
+    std::vector<float> eact;
+    std::vector<float> rho(E);
+    bool has_act = d.act != nullptr;
+    for (int e = 0; e < E; ++e) {
+        const int u = T.elem_perm[e];
+        rho[e] = (float)d.density[u];
+        const float act = has_act ? (float)d.act[u] : 0.0f;
+        if (d.kind == GS_TET) {
+            ec[e] = make_float4(0.f, 0.f, (float)d.mu[u], (float)d.lambda[u]);
+            ea[e] = eb[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            ea[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            eb[e] = make_float4(0.f, (float)d.mu[u], (float)d.lambda[u], act);
+        }
+    }
+    if (d.kind == GS_TET) {
+        eact.assign(E, 0.0f);
+        if (has_act)
+            for (int e = 0; e < E; ++e) eact[e] = (float)d.act[T.elem_perm[e]];
+    }
+    std::vector<float2> hp(B);
+    for (int h = 0; h < B; ++h) {
+        const int u = T.hinge_perm[h];
+        hp[h] = make_float2((float)d.kb[u], d.hinge_act ? (float)d.hinge_act[u] : 0.0f);
+    }
+    std::vector<double> X(3 * (size_t)N);
+    std::vector<uint8_t> pin(N, 0);
+    for (int i = 0; i < N; ++i) {
+        const int u = T.node_perm[i];
+        for (int k = 0; k < 3; ++k) X[3 * (size_t)i + k] = d.X[3 * (size_t)u + k];
+        pin[i] = d.pinned ? d.pinned[u] : 0;
+    }
+    GS_TRY(upload(ctx, m->eidx, T.eidx, s));
+    GS_TRY(upload(ctx, m->ea, ea, s));
+    GS_TRY(upload(ctx, m->eb, eb, s));
+    GS_TRY(upload(ctx, m->ec, ec, s));
+    GS_TRY(upload(ctx, m->eact, eact, s));
+    GS_TRY(upload(ctx, m->hidx, T.hidx, s));
+    GS_TRY(upload(ctx, m->hp, hp, s));
+    GS_TRY(upload(ctx, m->bnd_ids, T.bnd_ids, s));
+    GS_TRY(upload(ctx, m->loc_rowptr, T.loc_rowptr, s));
+    GS_TRY(upload(ctx, m->loc_slots, T.loc_slots, s));
+    GS_TRY(upload(ctx, m->bnd_rowptr, T.bnd_rowptr, s));
+    GS_TRY(upload(ctx, m->bnd_parts, T.bnd_parts, s));
+    GS_TRY(m->partials.alloc(ctx, std::max<size_t>(T.bnd_ids.size(), 1) * sizeof(float4), s));
+    GS_TRY(upload(ctx, m->node_perm, T.node_perm, s));
+    GS_TRY(upload(ctx, m->elem_perm, T.elem_perm, s));
+    GS_TRY(upload(ctx, m->hinge_perm, T.hinge_perm, s));
+    GS_TRY(m->w.alloc(ctx, (size_t)m->n_pad * sizeof(float), s));
+    GS_TRY(upload(ctx, m->X, X, s));
+    GS_TRY(upload(ctx, m->rho, rho, s));
+    GS_TRY(upload(ctx, m->pinned, pin, s));
+    GS_TRY(m->status.alloc(ctx, 4 * sizeof(int), s));
+    GS_CUDA(cudaMemsetAsync(m->status.p, 0, 4 * sizeof(int), s));
+    GS_TRY(m->ensure_buffers(1, s));
+    GS_CUDA(cudaMemsetAsync(m->st.p, 0, m->st.bytes, s));
+    // runtime record
+    MeshRT& r = m->rt;
+    std::memset(&r, 0, sizeof(r));
+    r.kind = d.kind;
+    r.n_nodes = N;
+    r.n_int = T.n_int;
+    r.n_bnd = T.n_bnd;
+    r.n_elems = E;
+    r.n_hinges = B;
+    r.active = ACT_FWD | ACT_ADJ;
+    r.eidx = (const uint2*)m->eidx.p;
+    r.ea = (float4*)m->ea.p;
+    r.eb = (float4*)m->eb.p;
+    r.ec = (float4*)m->ec.p;
+    r.eact = d.kind == GS_TET ? (float*)m->eact.p : nullptr;
+    r.hidx = (const uint2*)m->hidx.p;
+    r.hp = (float2*)m->hp.p;
+    r.bnd_ids = (const int*)m->bnd_ids.p;
+    r.loc_rowptr = (const uint16_t*)m->loc_rowptr.p;
+    r.loc_slots = (const uint16_t*)m->loc_slots.p;
+    r.bnd_rowptr = (const int*)m->bnd_rowptr.p;
+    r.bnd_parts = (const int*)m->bnd_parts.p;
+    r.partials = (float4*)m->partials.p;
+    r.node_perm = (const int*)m->node_perm.p;
+    r.elem_perm = (const int*)m->elem_perm.p;
+    r.hinge_perm = (const int*)m->hinge_perm.p;
+    r.w = (float*)m->w.p;
+    r.ck_tick = -1;
+    r.gx = d.gravity[0];
+    r.gy = d.gravity[1];
+    r.gz = d.gravity[2];
+    r.ke = d.contact.ke;
+    r.kd = d.contact.kd;
+    r.kf = d.contact.kf;
+    r.mu_f = d.contact.mu_f;
+    r.plane_on = d.contact.plane_on;
+    r.pnx = d.contact.plane_n[0];
+    r.pny = d.contact.plane_n[1];
+    r.pnz = d.contact.plane_n[2];
+    r.ph = d.contact.plane_h;
+    r.sphere_on = d.contact.sphere_on;
+    r.scx = d.contact.sphere_c[0];
+    r.scy = d.contact.sphere_c[1];
+    r.scz = d.contact.sphere_c[2];
+    r.sr = d.contact.sphere_r;
+    r.status = (int*)m->status.p;
+    m->refresh_rt();
+    // the mesh's own launch set (its device MeshRT record)
+    m->self.reset(new LaunchSet());
+    GS_TRY(m->self->build(ctx, std::vector<gs_mesh*>{m.get()}, s));
+    // a1 set-up on the GPU: Dm^-1, V / A, masses, inverse masses
+    GS_TRY(m->run_setup(1, s));
+    // initial state: x = X, v = v0
+    std::vector<float> x0(3 * (size_t)N), v0(3 * (size_t)N, 0.0f);
+    for (size_t i = 0; i < 3 * (size_t)N; ++i) {
+        x0[i] = (float)d.X[i];
+        if (d.v0) v0[i] = (float)d.v0[i];
+    }
+    GS_TRY(m->scratch.alloc(ctx, 6 * (size_t)N * sizeof(float), s));
+    GS_CUDA(cudaMemcpyAsync(m->scratch.p, x0.data(), 3 * (size_t)N * sizeof(float), cudaMemcpyHostToDevice, s));
+    GS_CUDA(cudaMemcpyAsync((float*)m->scratch.p + 3 * (size_t)N, v0.data(), 3 * (size_t)N * sizeof(float),
+                            cudaMemcpyHostToDevice, s));
+    launch_set_state(m->rt_dev(), 0, (const float*)m->scratch.p, (const float*)m->scratch.p + 3 * N, s);
+    GS_CUDA(cudaStreamSynchronize(s));
+    GS_CUDA(cudaGetLastError());
+    int bad = 0;
+    GS_CUDA(cudaMemcpy(&bad, (int*)m->status.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bad) return set_error(GS_EINVAL, "inverted or degenerate rest element (non-positive volume or area)");
+    m->info.device_bytes = 0;
+    for (Buf* b : {&m->eidx, &m->ea, &m->eb, &m->ec, &m->eact, &m->hidx, &m->hp, &m->bnd_ids, &m->loc_rowptr,
+                   &m->loc_slots, &m->bnd_rowptr, &m->bnd_parts, &m->partials, &m->node_perm, &m->elem_perm,
+                   &m->hinge_perm, &m->w, &m->X, &m->rho, &m->pinned, &m->st})
+        m->info.device_bytes += b->bytes;
+    *out = m.release();
+    return GS_OK;
+}
+
+gs_status gs_mesh::run_setup(int geometry, cudaStream_t s) {
+    Buf mass, part;
+    GS_TRY(mass.alloc(ctx, (size_t)n_pad * sizeof(double), s));
+    GS_TRY(part.alloc(ctx, std::max<size_t>(bnd_ids.bytes / sizeof(int), 1) * sizeof(double), s));
+    const size_t sm = sizeof(double) * (3 * (size_t)max_loc + (size_t)max_slots);
+    launch_setup_mesh(self->launch, (const double*)X.p, (const float*)rho.p, (double*)mass.p, (double*)part.p,
+                      (const uint8_t*)pinned.p, (int*)status.p + 1, geometry, sm, s);
+    GS_CUDA(cudaGetLastError());
+    mass.release(s);
+    part.release(s);
+    return GS_OK;
+}
+
+extern "C" void gs_mesh_destroy(gs_mesh* m) { delete m; }
+
+extern "C" gs_status gs_mesh_info_get(const gs_mesh* m, gs_mesh_info* out) {
+    if (!m || !out) return set_error(GS_EINVAL, "null argument");
+    *out = m->info;
+    return GS_OK;
+}
+
+// copy a caller buffer to a device scratch when it lives on the host
+static gs_status stage_in(gs_ctx* ctx, Buf& tmp, const float* src, size_t n, int mem, cudaStream_t s,
+                          const float** dev) {
+    if (!src) {
+        *dev = nullptr;
+        return GS_OK;
+    }
+    if (mem == GS_MEM_DEVICE) {
+        *dev = src;
+        return GS_OK;
+    }
+    GS_TRY(tmp.alloc(ctx, n * sizeof(float), s));
+    GS_CUDA(cudaMemcpyAsync(tmp.p, src, n * sizeof(float), cudaMemcpyHostToDevice, s));
+    *dev = (const float*)tmp.p;
+    return GS_OK;
+}
+
+extern "C" gs_status gs_mesh_set_params(gs_mesh* m, const float* mu, const float* lambda, const float* density,
+                                        const float* act, const float* kb, int mem, void* stream) {
+    clear_error();
+    if (!m) return set_error(GS_EINVAL, "null mesh");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t E = m->info.n_elems, B = m->info.n_hinges;
+    Buf t1, t2, t3, t4, t5;
+    const float *dmu, *dlam, *drho, *dact, *dkb;
+    GS_TRY(stage_in(m->ctx, t1, mu, E, mem, s, &dmu));
+    GS_TRY(stage_in(m->ctx, t2, lambda, E, mem, s, &dlam));
+    GS_TRY(stage_in(m->ctx, t3, density, E, mem, s, &drho));
+    GS_TRY(stage_in(m->ctx, t4, act, E, mem, s, &dact));
+    GS_TRY(stage_in(m->ctx, t5, kb, B, mem, s, &dkb));
+    GS_TRY(m->self->sync_rt(s));
+    if (dmu || dlam || dact || dkb) launch_scatter_params(m->rt_dev(), dmu, dlam, dact, dkb, s);
+    if (drho) {
+        // density -> internal order, then the lumped-mass set-up
+        launch_gather_elems(m->rt_dev(), drho, (float*)m->rho.p, s);
+        GS_TRY(m->run_setup(0, s));
+    }
+    m->ro.valid = false;
+    GS_CUDA(cudaGetLastError());
+    for (Buf* b : {&t1, &t2, &t3, &t4, &t5}) b->release(s);
+    return GS_OK;
+}
+
+extern "C" gs_status gs_mesh_set_state(gs_mesh* m, const float* x, const float* v, int mem, void* stream) {
+    clear_error();
+    if (!m) return set_error(GS_EINVAL, "null mesh");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = 3 * (size_t)m->info.n_nodes;
+    Buf t1, t2;
+    const float *dx, *dv;
+    GS_TRY(stage_in(m->ctx, t1, x, n, mem, s, &dx));
+    GS_TRY(stage_in(m->ctx, t2, v, n, mem, s, &dv));
+    GS_TRY(m->self->sync_rt(s));
+    launch_set_state(m->rt_dev(), 0, dx, dv, s);
+    GS_CUDA(cudaGetLastError());
+    t1.release(s);
+    t2.release(s);
+    m->ro.valid = false;
+    return GS_OK;
+}
+
+extern "C" gs_status gs_mesh_get_state(gs_mesh* m, float* x, float* v, int mem, void* stream) {
+    clear_error();
+    if (!m) return set_error(GS_EINVAL, "null mesh");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = 3 * (size_t)m->info.n_nodes;
+    GS_TRY(m->self->sync_rt(s));
+    if (mem == GS_MEM_DEVICE) {
+        launch_get_state(m->rt_dev(), 0, x, v, s);
+        GS_CUDA(cudaGetLastError());
+        return GS_OK;
+    }
+    Buf t;
+    GS_TRY(t.alloc(m->ctx, 2 * n * sizeof(float), s));
+    launch_get_state(m->rt_dev(), 0, x ? (float*)t.p : nullptr, v ? (float*)t.p + n : nullptr, s);
+    if (x) GS_CUDA(cudaMemcpyAsync(x, t.p, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (v) GS_CUDA(cudaMemcpyAsync(v, (float*)t.p + n, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+    t.release(s);
+    return GS_OK;
+}
+
+extern "C" gs_status gs_mesh_check(gs_mesh* m, int reset, void* stream) {
+    clear_error();
+    if (!m) return set_error(GS_EINVAL, "null mesh");
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = 0;
+    GS_CUDA(cudaMemcpyAsync(&st, m->status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+    if (reset) GS_CUDA(cudaMemsetAsync(m->status.p, 0, sizeof(int), s));
+    if (st & 1) return set_error(GS_ENONFINITE, "non-finite state");
+    return GS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch sets
+// ---------------------------------------------------------------------------
+gs_status LaunchSet::build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStream_t s) {
+    ctx = c;
+    meshes = ms;
+    std::vector<PatchDesc> tp, cp;
+    std::vector<NodeBlock> bb, nb;
+    int max_loc_t = 0, max_slots_t = 0, max_loc_c = 0, max_slots_c = 0;
+    threads = 32;
+    node_block_begin.clear();
+    for (int i = 0; i < (int)ms.size(); ++i) {
+        gs_mesh* m = ms[i];
+        auto& dst = m->info.kind == GS_TET ? tp : cp;
+        for (PatchDesc p : m->patches) {
+            p.mesh = i;
+            dst.push_back(p);
+        }
+        for (NodeBlock b : m->bnd_blocks) {
+            b.mesh = i;
+            bb.push_back(b);
+        }
+        node_block_begin.push_back((int)nb.size());
+        for (NodeBlock b : m->node_blocks) {
+            b.mesh = i;
+            nb.push_back(b);
+        }
+        if (m->info.kind == GS_TET) {
+            max_loc_t = std::max(max_loc_t, m->max_loc);
+            max_slots_t = std::max(max_slots_t, m->max_slots);
+        } else {
+            max_loc_c = std::max(max_loc_c, m->max_loc);
+            max_slots_c = std::max(max_slots_c, m->max_slots);
+        }
+        threads = std::max(threads, m->threads);
+    }
+    node_block_begin.push_back((int)nb.size());
+    GS_TRY(upload(c, d_tet, tp, s));
+    GS_TRY(upload(c, d_cloth, cp, s));
+    GS_TRY(upload(c, d_bnd, bb, s));
+    GS_TRY(upload(c, d_nodes, nb, s));
+    GS_TRY(d_rt.alloc(c, std::max<size_t>(ms.size(), 1) * sizeof(MeshRT), s));
+    GS_TRY(d_loss.alloc(c, std::max<size_t>(nb.size(), 1) * sizeof(double), s));
+    host_rt.resize(ms.size());
+    launch.tet_patches = (const PatchDesc*)d_tet.p;
+    launch.n_tet_patches = (int)tp.size();
+    launch.cloth_patches = (const PatchDesc*)d_cloth.p;
+    launch.n_cloth_patches = (int)cp.size();
+    launch.bnd_blocks = (const NodeBlock*)d_bnd.p;
+    launch.n_bnd_blocks = (int)bb.size();
+    launch.node_blocks = (const NodeBlock*)d_nodes.p;
+    launch.n_node_blocks = (int)nb.size();
+    launch.rt = (MeshRT*)d_rt.p;
+    launch.threads = threads;
+    launch.smem_tet_fwd = smem_bytes(GS_TET, false, max_loc_t, max_slots_t);
+    launch.smem_tet_adj = smem_bytes(GS_TET, true, max_loc_t, max_slots_t);
+    launch.smem_cloth_fwd = smem_bytes(GS_CLOTH, false, max_loc_c, max_slots_c);
+    launch.smem_cloth_adj = smem_bytes(GS_CLOTH, true, max_loc_c, max_slots_c);
+    return sync_rt(s);
+}
+
+gs_status LaunchSet::sync_rt(cudaStream_t s) {
+    for (size_t i = 0; i < meshes.size(); ++i) host_rt[i] = meshes[i]->rt;
+    GS_CUDA(cudaMemcpyAsync(d_rt.p, host_rt.data(), host_rt.size() * sizeof(MeshRT), cudaMemcpyHostToDevice, s));
+    return GS_OK;
+}
+
+LaunchSet::~LaunchSet() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    for (Buf* b : {&d_tet, &d_cloth, &d_bnd, &d_nodes, &d_rt, &d_loss}) b->release(0);
+}
+
+// `steps` forward (phase 0) or adjoint (phase 1) steps, ticks 0..steps-1
+gs_status LaunchSet::run(int phase, int steps, cudaStream_t s) {
+    if (steps <= 0) return GS_OK;
+    if (!ctx->graphs || ctx->prof) {
+        for (int t = 0; t < steps; ++t) {
+            if (phase == 0) launch_forward_step(launch, t, s, ctx->prof);
+            else launch_adjoint_step(launch, t, s, ctx->prof);
+        }
+        GS_CUDA(cudaGetLastError());
+        return GS_OK;
+    }
+    const std::pair<int, int> key{phase, steps};
+    auto it = graphs.find(key);
+    if (it == graphs.end()) {
+        cudaStream_t cs = ctx->capture_stream;
+        GS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        for (int t = 0; t < steps; ++t) {
+            if (phase == 0) launch_forward_step(launch, t, cs);
+            else launch_adjoint_step(launch, t, cs);
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+        cudaGraphExec_t ge = nullptr;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+        it = graphs.emplace(key, ge).first;
+    }
+    GS_CUDA(cudaGraphLaunch(it->second, s));
+    return GS_OK;
+}
+
+static int choose_K(int S, int K) {
+    if (K > 0) return std::min(K, std::max(S, 1));
+    int k = (int)std::ceil(std::sqrt((double)std::max(S, 1)));
+    return std::max(1, k);
+}
+
+// forward rollout over a launch set (App. B, checkpoint every K steps)
+gs_status LaunchSet::rollout(const std::vector<float>& dts, int S, int K, const std::vector<const float*>& targets,
+                             double* loss_dev, cudaStream_t s) {
+    if (S < 0) return set_error(GS_EINVAL, "n_steps must be >= 0");
+    K = choose_K(S, K);
+    const int n_ck = std::max(1, (S + K - 1) / K);
+    const int n_bufs = 1 + n_ck + K + 1;
+    gs_status warn = GS_OK;
+    for (size_t i = 0; i < meshes.size(); ++i) {
+        gs_mesh* m = meshes[i];
+        if (!(dts[i] > 0.0f) || !std::isfinite(dts[i])) return set_error(GS_EINVAL, "dt must be finite and > 0");
+        if (dts[i] > m->info.dt_stable) warn = GS_WUNSTABLE;
+        GS_TRY(m->ensure_buffers(n_bufs, s));
+        m->rt.dt = dts[i];
+        m->ro.valid = false;
+        if (targets[i]) {
+            GS_TRY(m->target.alloc(ctx, 3 * (size_t)m->info.n_nodes * sizeof(float), s));
+            GS_CUDA(cudaMemcpyAsync(m->target.p, targets[i], m->target.bytes, cudaMemcpyDeviceToDevice, s));
+        } else {
+            m->target.release(s);
+        }
+        m->rt.target = (const float*)m->target.p;
+        m->rt.active = ACT_FWD | ACT_ADJ;
+        // checkpoint 0 = the current state
+        m->rt.cp_src = 0;
+        m->rt.cp_dst = 1;
+    }
+    GS_TRY(sync_rt(s));
+    launch_copy_state(launch, s);
+    for (int c = 0; c < n_ck; ++c) {
+        const int steps = std::min(K, S - c * K);
+        for (gs_mesh* m : meshes) {
+            m->rt.in_a = m->rt.in_b = m->rt.out_a = m->rt.out_b = 0;
+            m->rt.ck_tick = (c + 1 < n_ck) ? steps - 1 : -1;
+            m->rt.ck_buf = 2 + c;
+        }
+        GS_TRY(sync_rt(s));
+        GS_TRY(run(0, steps, s));
+    }
+    for (gs_mesh* m : meshes) m->rt.ck_tick = -1;
+    GS_TRY(sync_rt(s));
+    if (loss_dev) {
+        launch_seed_loss(launch, (double*)d_loss.p, 0, s);
+        for (size_t i = 0; i < meshes.size(); ++i)
+            launch_loss_finalize((const double*)d_loss.p, node_block_begin[i],
+                                 node_block_begin[i + 1] - node_block_begin[i], loss_dev + i, s);
+    }
+    for (gs_mesh* m : meshes) {
+        m->ro.valid = true;
+        m->ro.S = S;
+        m->ro.K = K;
+        m->ro.n_ck = n_ck;
+    }
+    GS_CUDA(cudaGetLastError());
+    return warn;
+}
+
+// discrete adjoint over the whole rollout: per segment (last first) restore
+// the checkpoint, recompute and store the segment's states, then run the
+// reverse steps (App. B)
+gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std::vector<const float*>& seed_v,
+                             const std::vector<gs_grads>& grads, int keep, cudaStream_t s) {
+    for (gs_mesh* m : meshes)
+        if (!m->ro.valid) return set_error(GS_ESTATE, "gs_adjoint needs a preceding gs_rollout");
+    const int S = meshes[0]->ro.S, K = meshes[0]->ro.K, n_ck = meshes[0]->ro.n_ck;
+    for (gs_mesh* m : meshes)
+        if (m->ro.S != S || m->ro.K != K) return set_error(GS_ESTATE, "batch meshes have different rollouts");
+    for (size_t i = 0; i < meshes.size(); ++i) {
+        gs_mesh* m = meshes[i];
+        GS_TRY(m->ensure_adjoint(s));
+        m->rt.seed_x = seed_x[i];
+        m->rt.seed_v = seed_v[i];
+    }
+    GS_TRY(sync_rt(s));
+    launch_seed_loss(launch, (double*)d_loss.p, 1, s);
+    launch_zero_adjoint(launch, s);
+    for (gs_mesh* m : meshes) {
+        launch_zero_f64((double*)m->g_mu.p, m->info.n_elems, s);
+        launch_zero_f64((double*)m->g_lam.p, m->info.n_elems, s);
+        launch_zero_f64((double*)m->g_act.p, m->info.n_elems, s);
+        launch_zero_f64((double*)m->g_kb.p, m->info.n_hinges, s);
+        launch_zero_f64((double*)m->g_hact.p, m->info.n_hinges, s);
+    }
+    const int seg0 = 1 + n_ck;
+    for (int sg = n_ck - 1; sg >= 0; --sg) {
+        const int steps = std::min(K, S - sg * K);
+        for (gs_mesh* m : meshes) {
+            MeshRT& r = m->rt;
+            r.cp_src = 1 + sg;
+            r.cp_dst = seg0;
+            r.in_a = seg0;
+            r.in_b = 1;
+            r.out_a = seg0 + 1;
+            r.out_b = 1;
+            r.ck_tick = -1;
+            r.adj_a = seg0 + steps - 1;
+            r.adj_b = -1;
+        }
+        GS_TRY(sync_rt(s));
+        launch_copy_state(launch, s);
+        GS_TRY(run(0, steps, s));
+        GS_TRY(run(1, steps, s));
+    }
+    for (size_t i = 0; i < meshes.size(); ++i) {
+        gs_mesh* m = meshes[i];
+        m->rt.seed_x = m->rt.seed_v = nullptr;
+        const size_t sm = std::max(sizeof(double) * (size_t)m->max_loc, (size_t)16);
+        GS_TRY(m->self->sync_rt(s));
+        launch_finalize_grads(m->self->launch, (double*)m->mbar.p, grads[i], sm, s);
+        if (!keep) m->ro.valid = false;
+    }
+    GS_TRY(sync_rt(s));
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status LaunchSet::step(const std::vector<float>& dts, int n, cudaStream_t s) {
+    gs_status warn = GS_OK;
+    for (size_t i = 0; i < meshes.size(); ++i) {
+        gs_mesh* m = meshes[i];
+        if (!(dts[i] > 0.0f) || !std::isfinite(dts[i])) return set_error(GS_EINVAL, "dt must be finite and > 0");
+        if (dts[i] > m->info.dt_stable) warn = GS_WUNSTABLE;
+        m->rt.dt = dts[i];
+        m->rt.in_a = m->rt.in_b = m->rt.out_a = m->rt.out_b = 0;
+        m->rt.ck_tick = -1;
+        m->rt.active = ACT_FWD | ACT_ADJ;
+        m->ro.valid = false;
+    }
+    GS_TRY(sync_rt(s));
+    const int chunk = 64;
+    for (int done = 0; done < n; done += chunk) GS_TRY(run(0, std::min(chunk, n - done), s));
+    return warn;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: library, context, single-mesh calls
+// ---------------------------------------------------------------------------
+extern "C" int gs_version(void) { return GS_VERSION; }
+extern "C" const char* gs_last_error(void) { return g_last_error_cstr(); }
+
+namespace gs {
+const char* g_last_error_cstr() { return g_last_error.c_str(); }
+}  // namespace gs
+
+extern "C" gs_status gs_create(gs_ctx** out, int device, size_t budget, const gs_allocator* alloc) {
+    clear_error();
+    if (!out) return set_error(GS_EINVAL, "null argument");
+    *out = nullptr;
+    int n = 0;
+    GS_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return set_error(GS_EINVAL, "no such device");
+    GS_CUDA(cudaSetDevice(device));
+    std::unique_ptr<gs_ctx> c(new gs_ctx());
+    c->device = device;
+    c->budget = budget;
+    if (alloc && alloc->alloc && alloc->free) {
+        c->alloc = *alloc;
+        c->has_alloc = true;
+    }
+    int optin = 0;
+    GS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    GS_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+    c->smem_optin = (size_t)optin;
+    set_kernel_smem_limits(c->smem_optin);
+    GS_CUDA(cudaGetLastError());
+    GS_CUDA(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    *out = c.release();
+    return GS_OK;
+}
+
+cudaEvent_t EventProf::get() {
+    if (pool.empty()) {
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+}
+void EventProf::begin(int, cudaStream_t s) {
+    open = get();
+    cudaEventRecord(open, s);
+}
+void EventProf::end(int kind, cudaStream_t s) {
+    cudaEvent_t b = get();
+    cudaEventRecord(b, s);
+    pending.push_back(Pending{kind, open, b});
+    open = nullptr;
+}
+void EventProf::collect() {
+    for (const Pending& p : pending) {
+        cudaEventSynchronize(p.b);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            total_ms[p.kind] += ms;
+            launches[p.kind] += 1;
+        }
+        pool.push_back(p.a);
+        pool.push_back(p.b);
+    }
+    pending.clear();
+}
+EventProf::~EventProf() {
+    collect();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+
+extern "C" gs_status gs_profile(gs_ctx* c, int enable) {
+    clear_error();
+    if (!c) return set_error(GS_EINVAL, "null context");
+    if (enable && !c->prof) c->prof = new EventProf();
+    if (!enable && c->prof) {
+        delete c->prof;
+        c->prof = nullptr;
+    }
+    return GS_OK;
+}
+
+extern "C" gs_status gs_profile_read(gs_ctx* c, gs_kernel_time* out, int max, int* n_out) {
+    clear_error();
+    if (!c || !c->prof) return set_error(GS_ESTATE, "profiling is off");
+    c->prof->collect();
+    int n = 0;
+    for (int k = 0; k < KT_COUNT; ++k) {
+        if (!c->prof->launches[k]) continue;
+        if (out && n < max) {
+            std::memset(&out[n], 0, sizeof(gs_kernel_time));
+            std::strncpy(out[n].name, kernel_name(k), sizeof(out[n].name) - 1);
+            out[n].launches = c->prof->launches[k];
+            out[n].total_ms = c->prof->total_ms[k];
+        }
+        ++n;
+        c->prof->launches[k] = 0;
+        c->prof->total_ms[k] = 0.0;
+    }
+    if (n_out) *n_out = n;
+    return GS_OK;
+}
+
+extern "C" void gs_destroy(gs_ctx* c) {
+    if (!c) return;
+    delete c->prof;
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    delete c;
+}
+
+extern "C" size_t gs_ctx_bytes(const gs_ctx* c) { return c ? c->used : 0; }
+
+extern "C" gs_status gs_set_graphs(gs_ctx* c, int enable) {
+    if (!c) return set_error(GS_EINVAL, "null context");
+    c->graphs = enable != 0;
+    return GS_OK;
+}
+
+extern "C" gs_status gs_step(gs_mesh* m, float dt, int n, void* stream) {
+    clear_error();
+    if (!m) return set_error(GS_EINVAL, "null mesh");
+    if (n < 0) return set_error(GS_EINVAL, "n_steps must be >= 0");
+    return m->self->step(std::vector<float>{dt}, n, (cudaStream_t)stream);
+}
+
+extern "C" gs_status gs_rollout(gs_mesh* m, float dt, int S, int K, const float* target, double* loss_out, int mem,
+                                void* stream) {
+    clear_error();
+    if (!m) return set_error(GS_EINVAL, "null mesh");
+    cudaStream_t s = (cudaStream_t)stream;
+    Buf tt;
+    const float* dtarget;
+    GS_TRY(stage_in(m->ctx, tt, target, 3 * (size_t)m->info.n_nodes, mem, s, &dtarget));
+    double* dloss = nullptr;
+    Buf tl;
+    if (loss_out) {
+        if (mem == GS_MEM_DEVICE) dloss = loss_out;
+        else {
+            GS_TRY(tl.alloc(m->ctx, sizeof(double), s));
+            dloss = (double*)tl.p;
+        }
+    }
+    if (loss_out && !dtarget) return set_error(GS_EINVAL, "loss_out needs a target");
+    gs_status st = m->self->rollout(std::vector<float>{dt}, S, K, std::vector<const float*>{dtarget}, dloss, s);
+    if (st < 0) return st;
+    if (loss_out && mem == GS_MEM_HOST) {
+        GS_CUDA(cudaMemcpyAsync(loss_out, dloss, sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaStreamSynchronize(s));
+    }
+    tt.release(s);
+    tl.release(s);
+    return st;
+}
+
+extern "C" gs_status gs_adjoint(gs_mesh* m, const float* dLdx, const float* dLdv, const gs_grads* grads, int mem,
+                                int keep, void* stream) {
+    clear_error();
+    if (!m) return set_error(GS_EINVAL, "null mesh");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n3 = 3 * (size_t)m->info.n_nodes;
+    Buf t1, t2;
+    const float *sx, *sv;
+    GS_TRY(stage_in(m->ctx, t1, dLdx, n3, mem, s, &sx));
+    GS_TRY(stage_in(m->ctx, t2, dLdv, n3, mem, s, &sv));
+    gs_grads g{};
+    if (grads) g = *grads;
+    if (mem == GS_MEM_DEVICE) {
+        GS_TRY(m->self->adjoint({sx}, {sv}, {g}, keep, s));
+        return GS_OK;
+    }
+    // host gradients: compute into device scratch, then copy back
+    const size_t E = m->info.n_elems, B = m->info.n_hinges, N = m->info.n_nodes;
+    Buf hb;
+    const size_t bytes = sizeof(double) * (4 * E + 2 * B + N) + sizeof(float) * 2 * n3;
+    GS_TRY(hb.alloc(m->ctx, bytes, s));
+    char* p = (char*)hb.p;
+    gs_grads dg{};
+    auto take = [&](size_t nbytes) {
+        char* q = p;
+        p += nbytes;
+        return (void*)q;
+    };
+    dg.d_mu = g.d_mu ? (double*)take(8 * E) : nullptr;
+    dg.d_lambda = g.d_lambda ? (double*)take(8 * E) : nullptr;
+    dg.d_density = g.d_density ? (double*)take(8 * E) : nullptr;
+    dg.d_act = g.d_act ? (double*)take(8 * E) : nullptr;
+    dg.d_kb = g.d_kb ? (double*)take(8 * B) : nullptr;
+    dg.d_hinge_act = g.d_hinge_act ? (double*)take(8 * B) : nullptr;
+    dg.d_mass = g.d_mass ? (double*)take(8 * N) : nullptr;
+    dg.d_x0 = g.d_x0 ? (float*)take(4 * n3) : nullptr;
+    dg.d_v0 = g.d_v0 ? (float*)take(4 * n3) : nullptr;
+    GS_TRY(m->self->adjoint({sx}, {sv}, {dg}, keep, s));
+    auto back = [&](void* dst, const void* src, size_t nbytes) -> gs_status {
+        if (dst && src) GS_CUDA(cudaMemcpyAsync(dst, src, nbytes, cudaMemcpyDeviceToHost, s));
+        return GS_OK;
+    };
+    GS_TRY(back(g.d_mu, dg.d_mu, 8 * E));
+    GS_TRY(back(g.d_lambda, dg.d_lambda, 8 * E));
+    GS_TRY(back(g.d_density, dg.d_density, 8 * E));
+    GS_TRY(back(g.d_act, dg.d_act, 8 * E));
+    GS_TRY(back(g.d_kb, dg.d_kb, 8 * B));
+    GS_TRY(back(g.d_hinge_act, dg.d_hinge_act, 8 * B));
+    GS_TRY(back(g.d_mass, dg.d_mass, 8 * N));
+    GS_TRY(back(g.d_x0, dg.d_x0, 4 * n3));
+    GS_TRY(back(g.d_v0, dg.d_v0, 4 * n3));
+    GS_CUDA(cudaStreamSynchronize(s));
+    hb.release(s);
+    t1.release(s);
+    t2.release(s);
+    return GS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+struct gs_batch {
+    gs_ctx* ctx = nullptr;
+    std::vector<gs_mesh*> meshes;
+    std::unique_ptr<LaunchSet> ls;
+};
+
+extern "C" gs_status gs_batch_create(gs_ctx* ctx, gs_mesh* const* meshes, int n, gs_batch** out) {
+    clear_error();
+    if (!ctx || !meshes || n <= 0 || !out) return set_error(GS_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    std::unique_ptr<gs_batch> b(new gs_batch());
+    b->ctx = ctx;
+    b->meshes.assign(meshes, meshes + n);
+    for (gs_mesh* m : b->meshes)
+        if (!m || m->ctx != ctx) return set_error(GS_EINVAL, "batch meshes must belong to the context");
+    b->ls.reset(new LaunchSet());
+    GS_TRY(b->ls->build(ctx, b->meshes, 0));
+    GS_CUDA(cudaStreamSynchronize(0));
+    *out = b.release();
+    return GS_OK;
+}
+
+extern "C" void gs_batch_destroy(gs_batch* b) { delete b; }
+
+extern "C" gs_status gs_batch_step(gs_batch* b, const float* dt, int n, void* stream) {
+    clear_error();
+    if (!b || !dt) return set_error(GS_EINVAL, "null argument");
+    return b->ls->step(std::vector<float>(dt, dt + b->meshes.size()), n, (cudaStream_t)stream);
+}
+
+extern "C" gs_status gs_batch_rollout(gs_batch* b, const float* dt, int S, int K, const float* const* targets,
+                                      double* loss_out, void* stream) {
+    clear_error();
+    if (!b || !dt) return set_error(GS_EINVAL, "null argument");
+    std::vector<const float*> t(b->meshes.size(), nullptr);
+    if (targets)
+        for (size_t i = 0; i < t.size(); ++i) t[i] = targets[i];
+    return b->ls->rollout(std::vector<float>(dt, dt + b->meshes.size()), S, K, t, loss_out, (cudaStream_t)stream);
+}
+
+extern "C" gs_status gs_batch_adjoint(gs_batch* b, const gs_grads* grads, void* stream) {
+    clear_error();
+    if (!b) return set_error(GS_EINVAL, "null argument");
+    const size_t n = b->meshes.size();
+    std::vector<const float*> z(n, nullptr);
+    std::vector<gs_grads> g(n, gs_grads{});
+    if (grads)
+        for (size_t i = 0; i < n; ++i) g[i] = grads[i];
+    return b->ls->adjoint(z, z, g, 0, (cudaStream_t)stream);
+}

@@ -249,21 +249,24 @@ def block(n: int = 64, steps: int = 200, seed: int = 0, h: float = 0.025) -> Pro
                    rho=np.full(E, 1000.0), v0=v0, contact=Contact(), dt=5.0e-5, steps=steps)
 
 
-def cloth(variant: str = "3s", n: int = 256, steps: int = 500) -> Problem:
+def cloth(variant: str = "3s", n: int = 256, steps: int = 500, grid_scaled: bool = False) -> Problem:
     """n x n cloth over [0,1]^2 at y = 0.305 draped on a sphere (r 0.3 at (0.5, 0, 0.5)).
 
     "3": mu = 5e3, lambda = 1e4, kb = 1e-2, areal density 0.2, ke = 1e4,
     kd = 10, kf = 1 -- explicitly unstable at dt = 1e-4 (tiny node masses).
     "3s": mu = 10, lambda = 20, kb = 1e-6, ke = 100, kd = 1e-3, kf = 1e-3.
+    ``grid_scaled`` multiplies the stiffnesses by ((255/(n-1))^2), the ratio
+    of node masses, so a coarser grid keeps the 256^2 grid's time scales.
     """
     X, tris, hinges = cloth_grid(n, 1.0, 0.305)
     T, B = tris.shape[0], hinges.shape[0]
+    sc = (255.0 / (n - 1)) ** 2 if grid_scaled else 1.0
     if variant == "3":
-        mu, lam, kb = 5.0e3, 1.0e4, 1.0e-2
-        con = Contact(ke=1.0e4, kd=10.0, kf=1.0, mu_f=0.5)
+        mu, lam, kb = 5.0e3 * sc, 1.0e4 * sc, 1.0e-2 * sc
+        con = Contact(ke=1.0e4 * sc, kd=10.0 * sc, kf=1.0 * sc, mu_f=0.5)
     elif variant == "3s":
-        mu, lam, kb = 10.0, 20.0, 1.0e-6
-        con = Contact(ke=100.0, kd=1.0e-3, kf=1.0e-3, mu_f=0.5)
+        mu, lam, kb = 10.0 * sc, 20.0 * sc, 1.0e-6 * sc
+        con = Contact(ke=100.0 * sc, kd=1.0e-3 * sc, kf=1.0e-3 * sc, mu_f=0.5)
     else:
         raise ValueError(variant)
     con.plane_on, con.plane_h = True, 0.0

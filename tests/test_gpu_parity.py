@@ -1,0 +1,173 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded inputs.
+
+Tolerances (FP32 GPU vs FP64 oracle):
+  positions   rel-L2 <= 1e-4 for contact-free rollouts, <= 1e-3 with contact
+              (norm: |x - x_ref| / |x_ref - centroid|)
+  gradients   rel-L2 <= 1e-3 per gradient array and cosine >= 0.9999
+"""
+import numpy as np
+import pytest
+
+from paper_2104_02646_gb300 import inputs as I
+
+from gpu_util import CLOTH_KEYS, TET_KEYS, cosine, make_target, rel, rel_pos, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+POS_FREE, POS_CONTACT, GRAD_REL, GRAD_COS = 1e-4, 1e-3, 1e-3, 0.9999
+
+
+@pytest.fixture(scope="module")
+def ctx(gs):
+    return gs.Context(0)
+
+
+def check_grads(g_gpu, g_ref, keys, skip=()):
+    for ok, gk in keys.items():
+        if ok in skip:
+            continue
+        a, b = g_gpu[gk], g_ref[ok]
+        assert np.all(np.isfinite(a)), gk
+        assert rel(a, b) <= GRAD_REL, (gk, rel(a, b))
+        assert cosine(a, b) >= GRAD_COS, (gk, cosine(a, b))
+
+
+def test_bar_1a_contact_free_forward_and_gradients(gs, ctx):
+    p = I.bar("a", steps=1000)
+    tgt = make_target(p, 1000)
+    ref = run_oracle(p, 1000, tgt)
+    out = run_gpu(gs, ctx, p, 1000, tgt)
+    assert rel_pos(out["x"], ref["x"]) <= POS_FREE
+    assert out["loss"] == pytest.approx(ref["loss"], rel=1e-3)
+    # 1a never touches the ground: the bar falls rigidly, so the loss does not
+    # depend on the materials (the oracle's material gradients are round-off,
+    # ~1e-23).  Degenerate case: check the sensitivities are negligible and
+    # compare the state gradients, which are not.
+    check_grads(out, ref, TET_KEYS, skip=("tet_mu", "tet_lam", "tet_rho"))
+    L = ref["loss"]
+    for k, par in (("d_mu", p.mu), ("d_lambda", p.lam), ("d_density", p.rho)):
+        assert np.abs(out[k] * par).sum() <= 1e-2 * L, k
+
+
+def test_bar_1a_100_steps_forward(gs, ctx):
+    p = I.bar("a", steps=100)
+    ref = run_oracle(p, 100)
+    out = run_gpu(gs, ctx, p, 100, grads=False)
+    assert rel_pos(out["x"], ref["x"]) <= POS_FREE
+    # FP32 position round-off (~1e-8 m) excites the stiffest modes
+    # (omega ~ 2e3 / s), so velocities carry noise of order omega * 1e-8
+    assert rel(out["v"], ref["v"]) <= 1e-3
+
+
+def test_bar_1b_with_contact(gs, ctx):
+    p = I.bar("b", steps=1000)
+    tgt = make_target(p, 1000)
+    ref = run_oracle(p, 1000, tgt)
+    from oracle import oracle as O
+    traj = O.Model(p).rollout(p.x0, p.v0, p.dt, 1000, traj=True)[2]
+    assert traj[:, :, 1].min() < 0.0  # the bar lands (near step 640) and bounces
+    out = run_gpu(gs, ctx, p, 1000, tgt)
+    assert rel_pos(out["x"], ref["x"]) <= POS_CONTACT
+    assert out["loss"] == pytest.approx(ref["loss"], rel=1e-3)
+    check_grads(out, ref, TET_KEYS)
+
+
+@pytest.mark.parametrize("patch_elems", [300, 1000])
+def test_block_many_patches_ragged(gs, ctx, patch_elems):
+    # 8^3 cells (2560 tets) split into several patches with a ragged last one;
+    # heterogeneous materials, random velocities, ground contact from step 0
+    p = I.block(n=8, steps=100, seed=3)
+    tgt = make_target(p, 100)
+    ref = run_oracle(p, 100, tgt)
+    out = run_gpu(gs, ctx, p, 100, tgt, patch_elems=patch_elems)
+    assert out["mesh"].info.n_patches == -(-p.n_elems // patch_elems)
+    assert out["mesh"].info.n_boundary_nodes > 0
+    assert rel_pos(out["x"], ref["x"]) <= POS_CONTACT
+    check_grads(out, ref, TET_KEYS)
+
+
+def test_cloth_on_sphere(gs, ctx):
+    # the stable variant on a 24^2 grid, stiffnesses scaled with the node mass
+    p = I.cloth("3s", n=24, steps=500, grid_scaled=True)
+    tgt = make_target(p, 500)
+    ref = run_oracle(p, 500, tgt)
+    assert ref["x"][:, 1].min() < 0.3  # draped onto the sphere
+    out = run_gpu(gs, ctx, p, 500, tgt, patch_elems=128)
+    assert out["mesh"].info.n_patches > 1
+    assert rel_pos(out["x"], ref["x"]) <= POS_CONTACT
+    check_grads(out, ref, CLOTH_KEYS)
+
+
+def test_checkpoint_interval_does_not_change_results(gs, ctx):
+    p = I.block(n=6, steps=57, seed=5)
+    tgt = make_target(p, 57)
+    a = run_gpu(gs, ctx, p, 57, tgt, K=1, patch_elems=200)
+    b = run_gpu(gs, ctx, p, 57, tgt, K=8, patch_elems=200)
+    c = run_gpu(gs, ctx, p, 57, tgt, K=57, patch_elems=200)
+    for k in ("x", "d_mu", "d_lambda", "d_density", "d_v0", "d_x0"):
+        np.testing.assert_array_equal(a[k], b[k])
+        np.testing.assert_array_equal(a[k], c[k])
+
+
+def test_deterministic_and_graphs_match_plain_loop(gs, ctx):
+    p = I.block(n=6, steps=40, seed=6)
+    tgt = make_target(p, 40)
+    a = run_gpu(gs, ctx, p, 40, tgt, patch_elems=250)
+    b = run_gpu(gs, ctx, p, 40, tgt, patch_elems=250)
+    ctx.set_graphs(False)
+    try:
+        c = run_gpu(gs, ctx, p, 40, tgt, patch_elems=250)
+    finally:
+        ctx.set_graphs(True)
+    for k in ("x", "v", "d_mu", "d_lambda", "d_density", "d_v0", "d_x0"):
+        np.testing.assert_array_equal(a[k], b[k])
+        np.testing.assert_array_equal(a[k], c[k])
+    assert a["loss"] == b["loss"] == c["loss"]
+
+
+def test_step_matches_rollout_and_oracle(gs, ctx):
+    import torch
+    p = I.block(n=5, steps=30, seed=7)
+    m = gs.Mesh(ctx, p, patch_elems=200)
+    m.step(p.dt, 30)
+    x = torch.empty(p.n_nodes, 3, device="cuda")
+    m.get_state(x)
+    r = run_gpu(gs, ctx, p, 30, grads=False, patch_elems=200)
+    np.testing.assert_array_equal(x.cpu().numpy(), r["x"].astype(np.float32))
+    ref = run_oracle(p, 30)
+    assert rel_pos(r["x"], ref["x"]) <= POS_CONTACT
+
+
+def test_set_params_and_state_round_trip(gs, ctx):
+    import torch
+    p = I.block(n=4, steps=20, seed=8)
+    m = gs.Mesh(ctx, p, patch_elems=128)
+    q = I.block(n=4, steps=20, seed=9)  # same mesh, other materials and velocities
+    m.set_params(mu=torch.tensor(q.mu, dtype=torch.float32, device="cuda"),
+                 lam=torch.tensor(q.lam, dtype=torch.float32, device="cuda"),
+                 rho=torch.tensor(q.rho * 1.3, dtype=torch.float32, device="cuda"))
+    m.set_state(x=torch.tensor(q.x0, dtype=torch.float32, device="cuda"),
+                v=torch.tensor(q.v0, dtype=torch.float32, device="cuda"))
+    m.step(q.dt, 20)
+    x = torch.empty(p.n_nodes, 3, device="cuda")
+    m.get_state(x)
+    q.rho = q.rho * 1.3
+    ref = run_oracle(q, 20)
+    assert rel_pos(x.cpu().numpy().astype(np.float64), ref["x"]) <= POS_CONTACT
+
+
+def test_pinned_beam_gradients(gs, ctx):
+    # a beam hanging from its top face (the paper's deformable system-ID scene)
+    X, tets = I.hex_block(2, 6, 2, 0.025, origin=(0, 0.3, 0))
+    E = tets.shape[0]
+    mu, lam = I.lame(2e4, 0.3)
+    pinned = (X[:, 1] >= X[:, 1].max() - 1e-12).astype(np.uint8)
+    p = I.Problem(name="beam", kind=I.TET, X=X, elems=tets, mu=np.full(E, float(mu)),
+                  lam=np.full(E, float(lam)), rho=np.full(E, 1000.0), pinned=pinned,
+                  contact=I.Contact(plane_on=False), dt=1e-4, steps=400)
+    tgt = make_target(p, 400)
+    ref = run_oracle(p, 400, tgt)
+    out = run_gpu(gs, ctx, p, 400, tgt)
+    np.testing.assert_array_equal(out["x"][pinned == 1], X[pinned == 1].astype(np.float32))
+    assert rel_pos(out["x"], ref["x"]) <= POS_FREE
+    check_grads(out, ref, TET_KEYS)
