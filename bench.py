@@ -229,7 +229,7 @@ def main():
     # target: the library's own forward with 10 % stiffer materials + 1 mm noise
     mesh.set_params(mu=torch.tensor(p.mu * 1.1, dtype=torch.float32, device=dev),
                     lam=torch.tensor(p.lam * 1.1, dtype=torch.float32, device=dev))
-    mesh.set_state(x0, v0)
+    mesh.reset()
     mesh.step(p.dt, S)
     target = torch.empty(N, 3, device=dev)
     mesh.get_state(target)
@@ -242,7 +242,7 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def one_step():
-        mesh.set_state(x0, v0)
+        mesh.reset()
         mesh.rollout(p.dt, S, args.K, target, loss)
         mesh.adjoint(grads)
 

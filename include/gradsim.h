@@ -211,6 +211,9 @@ GS_API gs_status gs_mesh_set_params(gs_mesh* mesh, const float* mu, const float*
                              int mem_space, void* stream);
 /* Current state (x, v) [n_nodes][3] in caller order; nullable = unchanged. */
 GS_API gs_status gs_mesh_set_state(gs_mesh* mesh, const float* x, const float* v, int mem_space, void* stream);
+/* Back to the description's initial state: x = X exactly (the state is
+ * held as the displacement from X), v = v0.  Enqueued on `stream`. */
+GS_API gs_status gs_mesh_reset(gs_mesh* mesh, void* stream);
 GS_API gs_status gs_mesh_get_state(gs_mesh* mesh, float* x, float* v, int mem_space, void* stream);
 /* Sticky per-mesh status from the device: GS_OK or GS_ENONFINITE (a NaN/Inf
  * appeared in the state since the last reset).  Synchronises the stream. */

@@ -55,10 +55,11 @@ struct MeshRT {
     const uint2* eidx;       // [E] 4 (tets) / 3 (tris) uint16 local node ids
     float4* ea;              // tets: Dm^-1 00 01 02 10 | tris: Dm^-1 00 01 10 11
     float4* eb;              // tets: Dm^-1 11 12 20 21 | tris: A, mu, lambda, act
-    float4* ec;              // tets: Dm^-1 22, V, mu, lambda
+    float4* ec;              // tets: Dm^-1 22, V, mu, lambda | tris: rest frame r0, r1.x
+    float2* ed;              // tris: rest frame r1.y, r1.z
     float* eact;             // tets: actuation [E] (nullable)
     const uint2* hidx;       // [B] 4 uint16 local ids (x1, x2, x3, x4)
-    float2* hp;              // [B] (kb, act)
+    float4* hq;              // [3B] (X1-X3, kb), (X2-X3, act), (X4-X3, 0)
     const int* bnd_ids;      // per-patch boundary lists (internal node ids)
     const uint16_t* loc_rowptr;
     const uint16_t* loc_slots;
@@ -69,8 +70,12 @@ struct MeshRT {
     const int* elem_perm;    // internal element -> caller element
     const int* hinge_perm;   // internal hinge -> caller hinge
     float* w;                // inverse masses [N]
-    // state buffers: buffer b at st_x + b * buf_stride
-    float4* st_x;            // (x, y, z, w)
+    const float4* Xs;        // per node: X - sphere centre, |X - c|^2 - r^2 (FP64-derived)
+    const float* Xp;         // per node: plane offset h - n.X (FP64-derived)
+    const double* Xd;        // rest positions (FP64, for state in/out and the loss)
+    // state buffers: buffer b at st_x + b * buf_stride; the state holds the
+    // displacement u = x - X (and the inverse mass in .w)
+    float4* st_x;            // (ux, uy, uz, w)
     float4* st_v;            // (vx, vy, vz, 0)
     long long buf_stride;
     int in_a, in_b, out_a, out_b;   // forward: in = in_a + in_b * tick, out likewise
@@ -140,6 +145,7 @@ void launch_scatter_params(const MeshRT* rt_dev, const float* mu, const float* l
                            const float* kb, cudaStream_t s);
 void launch_set_state(const MeshRT* rt_dev, int buf, const float* x, const float* v, cudaStream_t s);
 void launch_get_state(const MeshRT* rt_dev, int buf, float* x, float* v, cudaStream_t s);
+void launch_reset_state(const MeshRT* rt_dev, const float* v0_caller, cudaStream_t s);
 void launch_finalize_grads(const Launch& L, double* mbar, const gs_grads& g, size_t smem, cudaStream_t s);
 
 // --------------------------------------------------------------------------

@@ -34,45 +34,54 @@ __device__ __forceinline__ ContactParams cparams(const MeshRT& m) {
     return c;
 }
 
-// total contact force on a node at (x, v): plane and sphere
-__device__ __forceinline__ float3 contact_force(const MeshRT& m, float3 x, float3 v) {
+// Contact geometry from the displacement u of node g.  The penetrations are
+// formed from FP64-derived rest offsets so that FP32 keeps their relative
+// precision near contact: plane C = (h - n.X) - n.u; sphere
+// C = r - |d| = -(|X - c|^2 - r^2 + 2 (X - c).u + u.u) / (|d| + r), d = X - c + u.
+
+// total contact force on a node: plane and sphere
+__device__ __forceinline__ float3 contact_force(const MeshRT& m, int g, float3 u, float3 v) {
     float3 f = make_float3(0.f, 0.f, 0.f);
     const ContactParams cp = cparams(m);
     if (m.plane_on) {
         const float3 n = make_float3(m.pnx, m.pny, m.pnz);
-        const float C = m.ph - dot3(n, x);
+        const float C = m.Xp[g] - dot3(n, u);
         if (C > 0.0f) f += contact_one(v, n, C, cp);
     }
     if (m.sphere_on) {
-        const float3 d = x - make_float3(m.scx, m.scy, m.scz);
+        const float4 xs = m.Xs[g];
+        const float3 d = xyz(xs) + u;
+        const float q = xs.w + 2.0f * dot3(xyz(xs), u) + dot3(u, u);
         const float dist = sqrtf(dot3(d, d));
-        const float C = m.sr - dist;
+        const float C = -q / (dist + m.sr);
         if (C > 0.0f && dist > 0.0f) f += contact_one(v, d * (1.0f / dist), C, cp);
     }
     return f;
 }
 
-// reverse mode of contact_force: adds dL/dx, dL/dv for fb = dL/df and returns f
-__device__ __forceinline__ float3 contact_adjoint(const MeshRT& m, float3 x, float3 v, float3 fb, float3& xb,
+// reverse mode of contact_force: adds dL/du, dL/dv for fb = dL/df and returns f
+__device__ __forceinline__ float3 contact_adjoint(const MeshRT& m, int g, float3 u, float3 v, float3 fb, float3& xb,
                                                   float3& vb) {
     float3 f = make_float3(0.f, 0.f, 0.f);
     const ContactParams cp = cparams(m);
     if (m.plane_on) {
         const float3 n = make_float3(m.pnx, m.pny, m.pnz);
-        const float C = m.ph - dot3(n, x);
+        const float C = m.Xp[g] - dot3(n, u);
         if (C > 0.0f) {
             float3 vb1, nb, f1;
             float Cb;
             contact_one_adjoint(v, n, C, cp, fb, vb1, nb, Cb, f1);
             f += f1;
             vb += vb1;
-            xb -= Cb * n;  // C = h - n.x
+            xb -= Cb * n;  // dC/du = -n
         }
     }
     if (m.sphere_on) {
-        const float3 d = x - make_float3(m.scx, m.scy, m.scz);
+        const float4 xs = m.Xs[g];
+        const float3 d = xyz(xs) + u;
+        const float q = xs.w + 2.0f * dot3(xyz(xs), u) + dot3(u, u);
         const float dist = sqrtf(dot3(d, d));
-        const float C = m.sr - dist;
+        const float C = -q / (dist + m.sr);
         if (C > 0.0f && dist > 0.0f) {
             const float inv = 1.0f / dist;
             const float3 n = d * inv;
@@ -81,7 +90,7 @@ __device__ __forceinline__ float3 contact_adjoint(const MeshRT& m, float3 x, flo
             contact_one_adjoint(v, n, C, cp, fb, vb1, nb, Cb, f1);
             f += f1;
             vb += vb1;
-            // n = d / dist, C = r - dist, dist = |d|
+            // n = d / dist, C = r - dist, dist = |d|, d = X - c + u
             const float distb = -Cb - dot3(nb, d) * inv * inv;
             xb += nb * inv + (distb * inv) * d;
         }
@@ -91,10 +100,10 @@ __device__ __forceinline__ float3 contact_adjoint(const MeshRT& m, float3 x, flo
 
 // forward node update (App. B): v+ = v + dt (w f + g [w > 0]), x+ = x + dt v+
 __device__ __forceinline__ void node_forward(const MeshRT& m, int tick, int gid, float4 x4, float4 v4, float3 fel) {
-    const float3 x = xyz(x4);
+    const float3 x = xyz(x4);  // displacement u
     float3 v = xyz(v4);
     const float w = x4.w;
-    const float3 f = fel + contact_force(m, x, v);
+    const float3 f = fel + contact_force(m, gid, x, v);
     if (w > 0.0f) {
         v.x = v.x + m.dt * (w * f.x + m.gx);
         v.y = v.y + m.dt * (w * f.y + m.gy);
@@ -125,7 +134,7 @@ __device__ __forceinline__ void node_adjoint(const MeshRT& m, int gid, float4 x4
     const float3 fb = (m.dt * w) * vh;          // dL/df
     float3 xb = xbn + xsum;
     float3 vb = vh;
-    const float3 fc = contact_adjoint(m, xyz(x4), xyz(v4), fb, xb, vb);
+    const float3 fc = contact_adjoint(m, gid, xyz(x4), xyz(v4), fb, xb, vb);
     m.xb[gid] = f4(xb, 0.0f);
     m.vb[gid] = f4(vb, 0.0f);
     m.wbar[gid] += (double)(m.dt * (ssum + dot3(fc, vh)));
@@ -197,9 +206,11 @@ __global__ void k_cloth_fwd(const PatchDesc* __restrict__ patches, const MeshRT*
     for (int lt = threadIdx.x; lt < p.n_e; lt += blockDim.x) {
         const int t = p.e_begin + lt;
         const uint2 id = m.eidx[t];
-        const float4 a = m.ea[t], b = m.eb[t];
+        const float4 a = m.ea[t], b = m.eb[t], r = m.ec[t];
+        const float2 r2 = m.ed[t];
         TriState s;
-        tri_state(xyz(xs[id.x & 0xffff]), xyz(xs[id.x >> 16]), xyz(xs[id.y & 0xffff]), a, b, s);
+        tri_state(xyz(xs[id.x & 0xffff]), xyz(xs[id.x >> 16]), xyz(xs[id.y & 0xffff]), a, b,
+                  make_float3(r.x, r.y, r.z), make_float3(r.w, r2.x, r2.y), s);
         float3 f0, f1, f2;
         tri_forces(s, a, b, f0, f1, f2);
         fc[3 * lt + 0] = f4(f0, 0.f);
@@ -210,11 +221,12 @@ __global__ void k_cloth_fwd(const PatchDesc* __restrict__ patches, const MeshRT*
     for (int lh = threadIdx.x; lh < p.n_h; lh += blockDim.x) {
         const int h = p.h_begin + lh;
         const uint2 id = m.hidx[h];
-        const float2 hp = m.hp[h];
+        const float4 q0 = m.hq[3 * h], q1 = m.hq[3 * h + 1], q2 = m.hq[3 * h + 2];
         HingeState s;
-        hinge_state(xyz(xs[id.x & 0xffff]), xyz(xs[id.x >> 16]), xyz(xs[id.y & 0xffff]), xyz(xs[id.y >> 16]), hp, s);
+        hinge_state(xyz(xs[id.x & 0xffff]), xyz(xs[id.x >> 16]), xyz(xs[id.y & 0xffff]), xyz(xs[id.y >> 16]),
+                    xyz(q0), xyz(q1), xyz(q2), q1.w, s);
         float3 f1, f2, f3, f4_;
-        hinge_forces(s, hp, f1, f2, f3, f4_);
+        hinge_forces(s, q0.w, f1, f2, f3, f4_);
         fh[4 * lh + 0] = f4(f1, 0.f);
         fh[4 * lh + 1] = f4(f2, 0.f);
         fh[4 * lh + 2] = f4(f3, 0.f);
@@ -342,11 +354,12 @@ __global__ void k_cloth_adj(const PatchDesc* __restrict__ patches, const MeshRT*
         const int t = p.e_begin + lt;
         const uint2 id = m.eidx[t];
         const int i0 = id.x & 0xffff, i1 = id.x >> 16, i2 = id.y & 0xffff;
-        const float4 a = m.ea[t], b = m.eb[t];
+        const float4 a = m.ea[t], b = m.eb[t], r = m.ec[t];
+        const float2 r2 = m.ed[t];
         const float4 x0 = xs[i0], x1 = xs[i1], x2 = xs[i2];
         const float3 v0 = xyz(vh[i0]), v1 = xyz(vh[i1]), v2 = xyz(vh[i2]);
         TriState s;
-        tri_state(xyz(x0), xyz(x1), xyz(x2), a, b, s);
+        tri_state(xyz(x0), xyz(x1), xyz(x2), a, b, make_float3(r.x, r.y, r.z), make_float3(r.w, r2.x, r2.y), s);
         float3 f0, f1, f2;
         tri_forces(s, a, b, f0, f1, f2);
         float3 xb0, xb1, xb2;
@@ -364,16 +377,16 @@ __global__ void k_cloth_adj(const PatchDesc* __restrict__ patches, const MeshRT*
         const int h = p.h_begin + lh;
         const uint2 id = m.hidx[h];
         const int i1 = id.x & 0xffff, i2 = id.x >> 16, i3 = id.y & 0xffff, i4 = id.y >> 16;
-        const float2 hp = m.hp[h];
+        const float4 q0 = m.hq[3 * h], q1 = m.hq[3 * h + 1], q2 = m.hq[3 * h + 2];
         const float4 x1 = xs[i1], x2 = xs[i2], x3 = xs[i3], x4 = xs[i4];
         const float3 v1 = xyz(vh[i1]), v2 = xyz(vh[i2]), v3 = xyz(vh[i3]), v4 = xyz(vh[i4]);
         HingeState s;
-        hinge_state(xyz(x1), xyz(x2), xyz(x3), xyz(x4), hp, s);
+        hinge_state(xyz(x1), xyz(x2), xyz(x3), xyz(x4), xyz(q0), xyz(q1), xyz(q2), q1.w, s);
         float3 f1, f2, f3, f4_;
-        hinge_forces(s, hp, f1, f2, f3, f4_);
+        hinge_forces(s, q0.w, f1, f2, f3, f4_);
         float3 xb1, xb2, xb3, xb4;
         float gkb, gact;
-        hinge_adjoint(s, hp, (dt * x1.w) * v1, (dt * x2.w) * v2, (dt * x3.w) * v3, (dt * x4.w) * v4, xb1, xb2, xb3,
+        hinge_adjoint(s, q0.w, (dt * x1.w) * v1, (dt * x2.w) * v2, (dt * x3.w) * v3, (dt * x4.w) * v4, xb1, xb2, xb3,
                       xb4, gkb, gact);
         fh[4 * lh + 0] = f4(xb1, dot3(f1, v1));
         fh[4 * lh + 1] = f4(xb2, dot3(f2, v2));
@@ -445,12 +458,15 @@ __global__ void k_seed_loss(const NodeBlock* __restrict__ blocks, const MeshRT* 
     for (int i = threadIdx.x; i < nb.count; i += blockDim.x) {
         const int g = nb.begin + i;
         const int u = m.node_perm[g];
-        const float3 x = xyz(m.st_x[g]);
+        const float4 q = m.st_x[g];
         float3 xb = make_float3(0.f, 0.f, 0.f), vb = make_float3(0.f, 0.f, 0.f);
         if (m.target) {
-            const float3 d = x - make_float3(m.target[3 * u], m.target[3 * u + 1], m.target[3 * u + 2]);
-            acc += (double)d.x * d.x + (double)d.y * d.y + (double)d.z * d.z;
-            xb = 2.0f * d;
+            // x = X + u in FP64 against the target
+            const double dx = m.Xd[3 * g] + (double)q.x - (double)m.target[3 * u];
+            const double dy = m.Xd[3 * g + 1] + (double)q.y - (double)m.target[3 * u + 1];
+            const double dz = m.Xd[3 * g + 2] + (double)q.z - (double)m.target[3 * u + 2];
+            acc += dx * dx + dy * dy + dz * dz;
+            xb = make_float3((float)(2.0 * dx), (float)(2.0 * dy), (float)(2.0 * dz));
         }
         if (m.seed_x) xb += make_float3(m.seed_x[3 * u], m.seed_x[3 * u + 1], m.seed_x[3 * u + 2]);
         if (m.seed_v) vb = make_float3(m.seed_v[3 * u], m.seed_v[3 * u + 1], m.seed_v[3 * u + 2]);
@@ -572,17 +588,46 @@ __global__ void k_setup_patch(const PatchDesc* __restrict__ patches, const MeshR
             const double det = A11 * A22 - A12 * A21;
             const double area = 0.5 * ln;
             if (a.geometry) {
-                m.ea[e] = make_float4((float)(A22 / det), (float)(-A12 / det), (float)(-A21 / det), (float)(A11 / det));
+                const double d00 = A22 / det, d01 = -A12 / det, d10 = -A21 / det, d11 = A11 / det;
+                m.ea[e] = make_float4((float)d00, (float)d01, (float)d10, (float)d11);
                 float4 b = m.eb[e];
                 b.x = (float)area;
                 m.eb[e] = b;
+                // rest frame R0 = Ds_rest Dm^-1 (orthonormal columns)
+                double r0[3], r1[3];
+                for (int r = 0; r < 3; ++r) {
+                    r0[r] = e1[r] * d00 + e2[r] * d10;
+                    r1[r] = e1[r] * d01 + e2[r] * d11;
+                }
+                m.ec[e] = make_float4((float)r0[0], (float)r0[1], (float)r0[2], (float)r1[0]);
+                m.ed[e] = make_float2((float)r1[1], (float)r1[2]);
             }
             share = (double)a.rho[e] * area / 3.0;
         }
         for (int c = 0; c < nc; ++c) mc[nc * le + c] = share;
     }
-    // hinge corners carry no mass
+    // hinge corners carry no mass; hinge rest vectors X1-X3, X2-X3, X4-X3
     for (int lh = threadIdx.x; lh < 4 * p.n_h; lh += blockDim.x) mc[3 * p.n_e + lh] = 0.0;
+    if (a.geometry) {
+        for (int lh = threadIdx.x; lh < p.n_h; lh += blockDim.x) {
+            const int h = p.h_begin + lh;
+            const uint2 id = m.hidx[h];
+            const int l1 = id.x & 0xffff, l2 = id.x >> 16, l3 = id.y & 0xffff, l4 = id.y >> 16;
+            float4 q0 = m.hq[3 * h], q1 = m.hq[3 * h + 1], q2 = m.hq[3 * h + 2];
+            q0.x = (float)(xs[3 * l1] - xs[3 * l3]);
+            q0.y = (float)(xs[3 * l1 + 1] - xs[3 * l3 + 1]);
+            q0.z = (float)(xs[3 * l1 + 2] - xs[3 * l3 + 2]);
+            q1.x = (float)(xs[3 * l2] - xs[3 * l3]);
+            q1.y = (float)(xs[3 * l2 + 1] - xs[3 * l3 + 1]);
+            q1.z = (float)(xs[3 * l2 + 2] - xs[3 * l3 + 2]);
+            q2.x = (float)(xs[3 * l4] - xs[3 * l3]);
+            q2.y = (float)(xs[3 * l4 + 1] - xs[3 * l3 + 1]);
+            q2.z = (float)(xs[3 * l4 + 2] - xs[3 * l3 + 2]);
+            m.hq[3 * h] = q0;
+            m.hq[3 * h + 1] = q1;
+            m.hq[3 * h + 2] = q2;
+        }
+    }
     __syncthreads();
     const uint16_t* rp = m.loc_rowptr + p.lr_begin;
     const uint16_t* sl = m.loc_slots + p.slot_begin;
@@ -644,11 +689,8 @@ __global__ void k_scatter_params(const MeshRT* __restrict__ rts, const float* mu
         }
     }
     if (kb && m.kind == GS_CLOTH) {
-        for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < m.n_hinges; h += gridDim.x * blockDim.x) {
-            float2 q = m.hp[h];
-            q.x = kb[m.hinge_perm[h]];
-            m.hp[h] = q;
-        }
+        for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < m.n_hinges; h += gridDim.x * blockDim.x)
+            m.hq[3 * h].w = kb[m.hinge_perm[h]];
     }
 }
 
@@ -662,8 +704,21 @@ __global__ void k_set_state(const MeshRT* __restrict__ rts, int buf, const float
     const MeshRT& m = rts[0];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.n_nodes; i += gridDim.x * blockDim.x) {
         const int u = m.node_perm[i];
-        if (x) bufx(m, buf)[i] = make_float4(x[3 * u], x[3 * u + 1], x[3 * u + 2], m.w[i]);
+        if (x)
+            bufx(m, buf)[i] = make_float4((float)((double)x[3 * u] - m.Xd[3 * i]),
+                                          (float)((double)x[3 * u + 1] - m.Xd[3 * i + 1]),
+                                          (float)((double)x[3 * u + 2] - m.Xd[3 * i + 2]), m.w[i]);
         if (v) bufv(m, buf)[i] = make_float4(v[3 * u], v[3 * u + 1], v[3 * u + 2], 0.f);
+    }
+}
+
+// rest state: u = 0 (x = X), inverse mass in .w, v = v0 (caller order)
+__global__ void k_reset_state(const MeshRT* __restrict__ rts, const float* v0) {
+    const MeshRT& m = rts[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.n_nodes; i += gridDim.x * blockDim.x) {
+        const int u = m.node_perm[i];
+        m.st_x[i] = make_float4(0.f, 0.f, 0.f, m.w[i]);
+        m.st_v[i] = make_float4(v0[3 * u], v0[3 * u + 1], v0[3 * u + 2], 0.f);
     }
 }
 
@@ -673,7 +728,9 @@ __global__ void k_get_state(const MeshRT* __restrict__ rts, int buf, float* x, f
         const int u = m.node_perm[i];
         if (x) {
             const float4 q = bufx(m, buf)[i];
-            x[3 * u] = q.x; x[3 * u + 1] = q.y; x[3 * u + 2] = q.z;
+            x[3 * u] = (float)(m.Xd[3 * i] + (double)q.x);
+            x[3 * u + 1] = (float)(m.Xd[3 * i + 1] + (double)q.y);
+            x[3 * u + 2] = (float)(m.Xd[3 * i + 2] + (double)q.z);
         }
         if (v) {
             const float4 q = bufv(m, buf)[i];
@@ -829,6 +886,10 @@ void launch_gather_elems(const MeshRT* rt_dev, const float* src, float* dst, cud
 
 void launch_set_state(const MeshRT* rt_dev, int buf, const float* x, const float* v, cudaStream_t s) {
     k_set_state<<<512, 256, 0, s>>>(rt_dev, buf, x, v);
+}
+
+void launch_reset_state(const MeshRT* rt_dev, const float* v0, cudaStream_t s) {
+    k_reset_state<<<512, 256, 0, s>>>(rt_dev, v0);
 }
 
 void launch_get_state(const MeshRT* rt_dev, int buf, float* x, float* v, cudaStream_t s) {

@@ -37,40 +37,70 @@ __device__ __forceinline__ float3 xyz(float4 a) { return make_float3(a.x, a.y, a
 __device__ __forceinline__ float4 f4(float3 a, float w) { return make_float4(a.x, a.y, a.z, w); }
 
 // ---------------------------------------------------------------------------
+// Displacement form.  The state holds u = x - X (X: rest positions), so the
+// deformation gradient is F = I + H (tets) or F = R0 + H (triangles; R0 the
+// rest frame), H = [u1-u0, u2-u0, (u3-u0)] Dm^-1.  Stress and energy
+// derivatives are written in terms of H without subtracting O(1) terms, so
+// FP32 keeps full relative precision at small strain and an element at rest
+// carries exactly zero force:
+//   det(I+H) = 1 + tr H + i2(H) + det H,  cof(I+H) = (1 + tr H) I - H^T + cof H,
+//   mu F (1 - 1/(I_C+1)) - 3/4 mu cof F = mu [3/4 (H + H^T - tr H I - cof H)
+//                                             + (I_C - 3)/(4 (I_C + 1)) F].
+// ---------------------------------------------------------------------------
+
+// ---------------------------------------------------------------------------
 // tetrahedron
 // Dm^-1 rows: D0 = (a.x a.y a.z), D1 = (a.w b.x b.y), D2 = (b.z b.w c.x);
 // V = c.y, mu = c.z, lambda = c.w.
 // ---------------------------------------------------------------------------
 struct TetState {
-    float3 F0, F1, F2;  // columns of F
+    float3 F0, F1, F2;  // columns of F = I + H
     float3 C0, C1, C2;  // columns of cof F
-    float Ic, J, inv, alpha, ca, cb;
+    float3 M0, M1, M2;  // columns of dP/dmu = F (1 - 1/(I_C+1)) - 3/4 cof F
+    float inv;          // 1 / (I_C + 1)
+    float cm;           // J - 1 - act
+    float ca, cb;       // mu (1 - inv), lambda (J - alpha)
 };
 
-__device__ __forceinline__ void tet_state(float3 x0, float3 x1, float3 x2, float3 x3, float4 a, float4 b,
+__device__ __forceinline__ void tet_state(float3 u0, float3 u1, float3 u2, float3 u3, float4 a, float4 b,
                                           float4 c, float act, TetState& s) {
-    const float3 d1 = x1 - x0, d2 = x2 - x0, d3 = x3 - x0;
-    s.F0 = d1 * a.x + d2 * a.w + d3 * b.z;
-    s.F1 = d1 * a.y + d2 * b.x + d3 * b.w;
-    s.F2 = d1 * a.z + d2 * b.y + d3 * c.x;
-    s.Ic = dot3(s.F0, s.F0) + dot3(s.F1, s.F1) + dot3(s.F2, s.F2);
-    s.C0 = cross3(s.F1, s.F2);
-    s.C1 = cross3(s.F2, s.F0);
-    s.C2 = cross3(s.F0, s.F1);
-    s.J = dot3(s.F0, s.C0);
+    const float3 d1 = u1 - u0, d2 = u2 - u0, d3 = u3 - u0;
+    const float3 H0 = d1 * a.x + d2 * a.w + d3 * b.z;  // columns of H
+    const float3 H1 = d1 * a.y + d2 * b.x + d3 * b.w;
+    const float3 H2 = d1 * a.z + d2 * b.y + d3 * c.x;
+    const float tr = H0.x + H1.y + H2.z;
+    const float Ic3 = 2.0f * tr + dot3(H0, H0) + dot3(H1, H1) + dot3(H2, H2);  // I_C - 3
+    const float3 K0 = cross3(H1, H2), K1 = cross3(H2, H0), K2 = cross3(H0, H1);  // cof H
+    const float jm1 = tr + (K0.x + K1.y + K2.z) + dot3(H0, K0);                  // J - 1
+    const float3 T0 = make_float3(H0.x, H1.x, H2.x);                             // columns of H^T
+    const float3 T1 = make_float3(H0.y, H1.y, H2.y);
+    const float3 T2 = make_float3(H0.z, H1.z, H2.z);
+    const float t1 = 1.0f + tr;
+    s.F0 = make_float3(H0.x + 1.0f, H0.y, H0.z);
+    s.F1 = make_float3(H1.x, H1.y + 1.0f, H1.z);
+    s.F2 = make_float3(H2.x, H2.y, H2.z + 1.0f);
+    s.C0 = make_float3(t1, 0.f, 0.f) - T0 + K0;
+    s.C1 = make_float3(0.f, t1, 0.f) - T1 + K1;
+    s.C2 = make_float3(0.f, 0.f, t1) - T2 + K2;
     const float mu = c.z, lam = c.w;
-    s.inv = 1.0f / (s.Ic + 1.0f);
-    s.alpha = 1.0f + 0.75f * mu / lam + act;
-    s.ca = mu * (1.0f - s.inv);
-    s.cb = lam * (s.J - s.alpha);
+    s.inv = 1.0f / (Ic3 + 4.0f);
+    const float q = 0.25f * Ic3 * s.inv;
+    s.M0 = 0.75f * (H0 + T0 - make_float3(tr, 0.f, 0.f) - K0) + q * s.F0;
+    s.M1 = 0.75f * (H1 + T1 - make_float3(0.f, tr, 0.f) - K1) + q * s.F1;
+    s.M2 = 0.75f * (H2 + T2 - make_float3(0.f, 0.f, tr) - K2) + q * s.F2;
+    s.cm = jm1 - act;
+    s.ca = mu * (Ic3 + 3.0f) * s.inv;
+    s.cb = lam * s.cm - 0.75f * mu;
 }
 
-// corner forces f1..f3 = columns of -V P Dm^-T; f0 = -(f1 + f2 + f3)
+// corner forces f1..f3 = columns of -V P Dm^-T; f0 = -(f1 + f2 + f3),
+// P = mu dP/dmu + lambda (J - 1 - act) cof F
 __device__ __forceinline__ void tet_forces(const TetState& s, float4 a, float4 b, float4 c, float3& f0,
                                            float3& f1, float3& f2, float3& f3) {
-    const float3 P0 = s.ca * s.F0 + s.cb * s.C0;
-    const float3 P1 = s.ca * s.F1 + s.cb * s.C1;
-    const float3 P2 = s.ca * s.F2 + s.cb * s.C2;
+    const float mu = c.z, lc = c.w * s.cm;
+    const float3 P0 = mu * s.M0 + lc * s.C0;
+    const float3 P1 = mu * s.M1 + lc * s.C1;
+    const float3 P2 = mu * s.M2 + lc * s.C2;
     const float nV = -c.y;
     f1 = nV * (P0 * a.x + P1 * a.y + P2 * a.z);
     f2 = nV * (P0 * a.w + P1 * b.x + P2 * b.y);
@@ -78,7 +108,7 @@ __device__ __forceinline__ void tet_forces(const TetState& s, float4 a, float4 b
     f0 = -(f1 + f2 + f3);
 }
 
-// Reverse mode of tet_forces.  Given fb_i = dL/df_i, returns dL/dx_i and
+// Reverse mode of tet_forces.  Given fb_i = dL/df_i, returns dL/du_i and
 // dL/d(mu, lambda, act).  P_bar = -V G Dm^-1 with G = [fb1-fb0, fb2-fb0, fb3-fb0];
 // F_bar = mu (1 - 1/(I_C+1)) P_bar + 2 mu/(I_C+1)^2 (F:P_bar) F
 //         + lambda (cof F : P_bar) cof F + lambda (J - alpha) dcof[P_bar];
@@ -93,6 +123,7 @@ __device__ __forceinline__ void tet_adjoint(const TetState& s, float4 a, float4 
     const float3 Pb2 = nV * (G1 * a.z + G2 * b.y + G3 * c.x);
     const float FP = dot3(s.F0, Pb0) + dot3(s.F1, Pb1) + dot3(s.F2, Pb2);
     const float CP = dot3(s.C0, Pb0) + dot3(s.C1, Pb1) + dot3(s.C2, Pb2);
+    const float MP = dot3(s.M0, Pb0) + dot3(s.M1, Pb1) + dot3(s.M2, Pb2);
     const float k2 = 2.0f * mu * s.inv * s.inv * FP;
     const float lc = lam * CP;
     const float3 dC0 = cross3(Pb1, s.F2) + cross3(s.F1, Pb2);
@@ -105,42 +136,58 @@ __device__ __forceinline__ void tet_adjoint(const TetState& s, float4 a, float4 
     xb2 = Fb0 * a.w + Fb1 * b.x + Fb2 * b.y;
     xb3 = Fb0 * b.z + Fb1 * b.w + Fb2 * c.x;
     xb0 = -(xb1 + xb2 + xb3);
-    // dP/dmu = (1 - 1/(I_C+1)) F - 3/4 cof F;  dP/dlambda = (J - alpha + 3mu/(4lambda)) cof F;
-    // dP/dact = -lambda cof F
-    gmu = (1.0f - s.inv) * FP - 0.75f * CP;
-    glam = (s.J - s.alpha + 0.75f * mu / lam) * CP;
+    // dP/dmu = M;  dP/dlambda = (J - 1 - act) cof F;  dP/dact = -lambda cof F
+    gmu = MP;
+    glam = s.cm * CP;
     gact = -lam * CP;
 }
 
 // ---------------------------------------------------------------------------
-// membrane triangle.  Dm^-1 = [[a.x a.y], [a.z a.w]]; b = (A, mu, lambda, act)
+// membrane triangle.  Dm^-1 = [[a.x a.y], [a.z a.w]]; b = (A, mu, lambda, act);
+// R0 = rest F (3x2, orthonormal columns r0, r1).  With F = R0 + H,
+// G = F^T F = I + E, E = R0^T H + H^T R0 + H^T H;  I_C = 2 + tr E,
+// J = sqrt(det G) = 1 + (tr E + det E)/(J + 1),  dJ/dF = F adj(G) / J,
+// P = mu F [s1 I + 2 E / (3 J)] + lambda (J - 1 - act) dJ/dF with
+// s1 = (6 (J-1) + 3 (J-1) tr E - 5 tr E - 2 (tr E)^2) / (3 J (3 + tr E)).
 // ---------------------------------------------------------------------------
 struct TriState {
-    float3 F0, F1, n, dJ0, dJ1;
-    float Ic, J, inv, alpha, ca, cb;
+    float3 F0, F1, n, dJ0, dJ1, M0, M1;
+    float inv, iJ, cm, ca, cb;
 };
 
-__device__ __forceinline__ void tri_state(float3 x0, float3 x1, float3 x2, float4 a, float4 b, TriState& s) {
-    const float3 d1 = x1 - x0, d2 = x2 - x0;
-    s.F0 = d1 * a.x + d2 * a.z;
-    s.F1 = d1 * a.y + d2 * a.w;
-    s.Ic = dot3(s.F0, s.F0) + dot3(s.F1, s.F1);
-    const float3 cr = cross3(s.F0, s.F1);
-    s.J = sqrtf(dot3(cr, cr));
-    s.n = cr * (1.0f / s.J);
-    s.dJ0 = cross3(s.F1, s.n);
-    s.dJ1 = cross3(s.n, s.F0);
+__device__ __forceinline__ void tri_state(float3 u0, float3 u1, float3 u2, float4 a, float4 b, float3 r0,
+                                          float3 r1, TriState& s) {
+    const float3 d1 = u1 - u0, d2 = u2 - u0;
+    const float3 H0 = d1 * a.x + d2 * a.z;
+    const float3 H1 = d1 * a.y + d2 * a.w;
+    s.F0 = r0 + H0;
+    s.F1 = r1 + H1;
+    const float E00 = 2.0f * dot3(r0, H0) + dot3(H0, H0);
+    const float E11 = 2.0f * dot3(r1, H1) + dot3(H1, H1);
+    const float E01 = dot3(r0, H1) + dot3(H0, r1) + dot3(H0, H1);
+    const float trE = E00 + E11, detE = E00 * E11 - E01 * E01;
+    const float J = sqrtf(1.0f + trE + detE);
+    const float jm1 = (trE + detE) / (J + 1.0f);
+    s.iJ = 1.0f / J;
+    s.inv = 1.0f / (trE + 3.0f);
+    s.dJ0 = (s.F0 * (1.0f + E11) - s.F1 * E01) * s.iJ;
+    s.dJ1 = (s.F1 * (1.0f + E00) - s.F0 * E01) * s.iJ;
+    const float s1 = (6.0f * jm1 + 3.0f * jm1 * trE - 5.0f * trE - 2.0f * trE * trE) / (3.0f * J * (3.0f + trE));
+    const float t = (2.0f / 3.0f) * s.iJ;
+    s.M0 = s.F0 * (s1 + t * E00) + s.F1 * (t * E01);
+    s.M1 = s.F0 * (t * E01) + s.F1 * (s1 + t * E11);
+    s.n = cross3(s.F0, s.F1) * s.iJ;
     const float mu = b.y, lam = b.z;
-    s.inv = 1.0f / (s.Ic + 1.0f);
-    s.alpha = 1.0f + (2.0f / 3.0f) * mu / lam + b.w;
-    s.ca = mu * (1.0f - s.inv);
-    s.cb = lam * (s.J - s.alpha);
+    s.cm = jm1 - b.w;
+    s.ca = mu * (trE + 2.0f) * s.inv;
+    s.cb = lam * s.cm - (2.0f / 3.0f) * mu;
 }
 
 __device__ __forceinline__ void tri_forces(const TriState& s, float4 a, float4 b, float3& f0, float3& f1,
                                            float3& f2) {
-    const float3 P0 = s.ca * s.F0 + s.cb * s.dJ0;
-    const float3 P1 = s.ca * s.F1 + s.cb * s.dJ1;
+    const float mu = b.y, lc = b.z * s.cm;
+    const float3 P0 = mu * s.M0 + lc * s.dJ0;
+    const float3 P1 = mu * s.M1 + lc * s.dJ1;
     const float nA = -b.x;
     f1 = nA * (P0 * a.x + P1 * a.y);
     f2 = nA * (P0 * a.z + P1 * a.w);
@@ -159,8 +206,9 @@ __device__ __forceinline__ void tri_adjoint(const TriState& s, float4 a, float4 
     const float3 Pb1 = nA * (G1 * a.y + G2 * a.w);
     const float FP = dot3(s.F0, Pb0) + dot3(s.F1, Pb1);
     const float JP = dot3(s.dJ0, Pb0) + dot3(s.dJ1, Pb1);
+    const float MP = dot3(s.M0, Pb0) + dot3(s.M1, Pb1);
     const float3 dc = cross3(Pb0, s.F1) + cross3(s.F0, Pb1);
-    const float3 dn = (dc - s.n * dot3(s.n, dc)) * (1.0f / s.J);
+    const float3 dn = (dc - s.n * dot3(s.n, dc)) * s.iJ;
     const float3 HJ0 = cross3(Pb1, s.n) + cross3(s.F1, dn);
     const float3 HJ1 = cross3(dn, s.F0) + cross3(s.n, Pb0);
     const float k2 = 2.0f * mu * s.inv * s.inv * FP;
@@ -170,8 +218,8 @@ __device__ __forceinline__ void tri_adjoint(const TriState& s, float4 a, float4 
     xb1 = Fb0 * a.x + Fb1 * a.y;
     xb2 = Fb0 * a.z + Fb1 * a.w;
     xb0 = -(xb1 + xb2);
-    gmu = (1.0f - s.inv) * FP - (2.0f / 3.0f) * JP;
-    glam = (s.J - s.alpha + (2.0f / 3.0f) * mu / lam) * JP;
+    gmu = MP;
+    glam = s.cm * JP;
     gact = -lam * JP;
 }
 
@@ -184,12 +232,15 @@ struct HingeState {
     bool ok;
 };
 
-__device__ __forceinline__ void hinge_state(float3 x1, float3 x2, float3 x3, float3 x4, float2 p, HingeState& s) {
-    s.E = x4 - x3;
-    s.A1 = x1 - x3;
-    s.B1 = x1 - x4;
-    s.A2 = x2 - x4;
-    s.B2 = x2 - x3;
+// Hinge edge vectors from the rest differences R1 = X1 - X3, R2 = X2 - X3,
+// R4 = X4 - X3 (precomputed in FP64) plus displacement differences.
+__device__ __forceinline__ void hinge_state(float3 u1, float3 u2, float3 u3, float3 u4, float3 R1, float3 R2,
+                                            float3 R4, float act, HingeState& s) {
+    s.E = R4 + (u4 - u3);
+    s.A1 = R1 + (u1 - u3);
+    s.B1 = (R1 - R4) + (u1 - u4);
+    s.A2 = (R2 - R4) + (u2 - u4);
+    s.B2 = R2 + (u2 - u3);
     s.N1 = cross3(s.A1, s.B1);
     s.N2 = cross3(s.A2, s.B2);
     s.lE2 = dot3(s.E, s.E);
@@ -215,18 +266,18 @@ __device__ __forceinline__ void hinge_state(float3 x1, float3 x2, float3 x3, flo
     s.p13 = dot3(s.A1, s.Eh);
     s.p23 = dot3(s.B2, s.Eh);
     s.q = s.lE2 / (s.l1 + s.l2);
-    const float ang = 0.5f * s.phi + p.y;
+    const float ang = 0.5f * s.phi + act;
     s.sn = sinf(ang);
     s.cs = cosf(ang);
 }
 
-__device__ __forceinline__ void hinge_forces(const HingeState& s, float2 p, float3& f1, float3& f2, float3& f3,
+__device__ __forceinline__ void hinge_forces(const HingeState& s, float kb, float3& f1, float3& f2, float3& f3,
                                              float3& f4) {
     if (!s.ok) {
         f1 = f2 = f3 = f4 = make_float3(0.f, 0.f, 0.f);
         return;
     }
-    const float sc = p.x * s.q * s.sn;
+    const float sc = kb * s.q * s.sn;
     f1 = sc * (s.lE * s.g1);
     f2 = sc * (s.lE * s.g2);
     f3 = sc * (s.p14 * s.g1 + s.p24 * s.g2);
@@ -234,7 +285,7 @@ __device__ __forceinline__ void hinge_forces(const HingeState& s, float2 p, floa
 }
 
 // Reverse mode of hinge_forces, statement by statement.
-__device__ __forceinline__ void hinge_adjoint(const HingeState& s, float2 p, float3 fb1, float3 fb2, float3 fb3,
+__device__ __forceinline__ void hinge_adjoint(const HingeState& s, float kb, float3 fb1, float3 fb2, float3 fb3,
                                               float3 fb4, float3& xb1, float3& xb2, float3& xb3, float3& xb4,
                                               float& gkb, float& gact) {
     const float3 z = make_float3(0.f, 0.f, 0.f);
@@ -243,7 +294,6 @@ __device__ __forceinline__ void hinge_adjoint(const HingeState& s, float2 p, flo
         gkb = gact = 0.f;
         return;
     }
-    const float kb = p.x;
     const float sc = kb * s.q * s.sn;
     // u_i and the scale s
     const float3 u1 = s.lE * s.g1, u2 = s.lE * s.g2;

@@ -440,7 +440,7 @@ gs_status gs_mesh::ensure_adjoint(cudaStream_t s) {
 
 gs_mesh::~gs_mesh() {
     cudaStream_t s = 0;
-    for (Buf* b : {&eidx, &ea, &eb, &ec, &eact, &hidx, &hp, &bnd_ids, &loc_rowptr, &loc_slots, &bnd_rowptr,
+    for (Buf* b : {&eidx, &ea, &eb, &ec, &ed, &eact, &hidx, &hq, &Xs, &Xp, &v0, &bnd_ids, &loc_rowptr, &loc_slots, &bnd_rowptr,
                    &bnd_parts, &partials, &node_perm, &elem_perm, &hinge_perm, &w, &X, &rho, &pinned, &st, &xb, &vb,
                    &wbar, &mbar, &g_mu, &g_lam, &g_act, &g_kb, &g_hact, &status, &target, &scratch})
         b->release(s);
@@ -507,25 +507,49 @@ extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_me
         if (has_act)
             for (int e = 0; e < E; ++e) eact[e] = (float)d.act[T.elem_perm[e]];
     }
-    std::vector<float2> hp(B);
+    // hinge data: (rest vectors written by the set-up kernel, kb), (.., act), (..)
+    std::vector<float4> hq(3 * (size_t)B, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int h = 0; h < B; ++h) {
         const int u = T.hinge_perm[h];
-        hp[h] = make_float2((float)d.kb[u], d.hinge_act ? (float)d.hinge_act[u] : 0.0f);
+        hq[3 * (size_t)h].w = (float)d.kb[u];
+        hq[3 * (size_t)h + 1].w = d.hinge_act ? (float)d.hinge_act[u] : 0.0f;
     }
+    std::vector<float2> ed(d.kind == GS_CLOTH ? E : 0, make_float2(0.f, 0.f));
     std::vector<double> X(3 * (size_t)N);
+    // contact offsets of the rest positions, formed in FP64
+    std::vector<float4> Xs(N);
+    std::vector<float> Xp(N);
+    std::vector<float> v0(3 * (size_t)N, 0.0f);
     std::vector<uint8_t> pin(N, 0);
     for (int i = 0; i < N; ++i) {
         const int u = T.node_perm[i];
         for (int k = 0; k < 3; ++k) X[3 * (size_t)i + k] = d.X[3 * (size_t)u + k];
+        const double* xi = &X[3 * (size_t)i];
+        double dc[3], q = 0.0, np = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            dc[k] = xi[k] - (double)d.contact.sphere_c[k];
+            q += dc[k] * dc[k];
+            np += (double)d.contact.plane_n[k] * xi[k];
+        }
+        q -= (double)d.contact.sphere_r * (double)d.contact.sphere_r;
+        Xs[i] = make_float4((float)dc[0], (float)dc[1], (float)dc[2], (float)q);
+        Xp[i] = (float)((double)d.contact.plane_h - np);
         pin[i] = d.pinned ? d.pinned[u] : 0;
     }
+    // initial velocities in caller order (the state is set through the caller-order kernel)
+    if (d.v0)
+        for (size_t k = 0; k < 3 * (size_t)N; ++k) v0[k] = (float)d.v0[k];
     GS_TRY(upload(ctx, m->eidx, T.eidx, s));
     GS_TRY(upload(ctx, m->ea, ea, s));
     GS_TRY(upload(ctx, m->eb, eb, s));
-    GS_TRY(upload(ctx, m->ec, ec, s));
+    GS_TRY(upload(ctx, m->ec, d.kind == GS_TET ? ec : std::vector<float4>(E, make_float4(0.f, 0.f, 0.f, 0.f)), s));
+    GS_TRY(upload(ctx, m->ed, ed, s));
     GS_TRY(upload(ctx, m->eact, eact, s));
     GS_TRY(upload(ctx, m->hidx, T.hidx, s));
-    GS_TRY(upload(ctx, m->hp, hp, s));
+    GS_TRY(upload(ctx, m->hq, hq, s));
+    GS_TRY(upload(ctx, m->Xs, Xs, s));
+    GS_TRY(upload(ctx, m->Xp, Xp, s));
+    GS_TRY(upload(ctx, m->v0, v0, s));
     GS_TRY(upload(ctx, m->bnd_ids, T.bnd_ids, s));
     GS_TRY(upload(ctx, m->loc_rowptr, T.loc_rowptr, s));
     GS_TRY(upload(ctx, m->loc_slots, T.loc_slots, s));
@@ -557,9 +581,13 @@ extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_me
     r.ea = (float4*)m->ea.p;
     r.eb = (float4*)m->eb.p;
     r.ec = (float4*)m->ec.p;
+    r.ed = (float2*)m->ed.p;
     r.eact = d.kind == GS_TET ? (float*)m->eact.p : nullptr;
     r.hidx = (const uint2*)m->hidx.p;
-    r.hp = (float2*)m->hp.p;
+    r.hq = (float4*)m->hq.p;
+    r.Xs = (const float4*)m->Xs.p;
+    r.Xp = (const float*)m->Xp.p;
+    r.Xd = (const double*)m->X.p;
     r.bnd_ids = (const int*)m->bnd_ids.p;
     r.loc_rowptr = (const uint16_t*)m->loc_rowptr.p;
     r.loc_slots = (const uint16_t*)m->loc_slots.p;
@@ -595,24 +623,15 @@ extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_me
     GS_TRY(m->self->build(ctx, std::vector<gs_mesh*>{m.get()}, s));
     // a1 set-up on the GPU: Dm^-1, V / A, masses, inverse masses
     GS_TRY(m->run_setup(1, s));
-    // initial state: x = X, v = v0
-    std::vector<float> x0(3 * (size_t)N), v0(3 * (size_t)N, 0.0f);
-    for (size_t i = 0; i < 3 * (size_t)N; ++i) {
-        x0[i] = (float)d.X[i];
-        if (d.v0) v0[i] = (float)d.v0[i];
-    }
-    GS_TRY(m->scratch.alloc(ctx, 6 * (size_t)N * sizeof(float), s));
-    GS_CUDA(cudaMemcpyAsync(m->scratch.p, x0.data(), 3 * (size_t)N * sizeof(float), cudaMemcpyHostToDevice, s));
-    GS_CUDA(cudaMemcpyAsync((float*)m->scratch.p + 3 * (size_t)N, v0.data(), 3 * (size_t)N * sizeof(float),
-                            cudaMemcpyHostToDevice, s));
-    launch_set_state(m->rt_dev(), 0, (const float*)m->scratch.p, (const float*)m->scratch.p + 3 * N, s);
+    // initial state: u = 0 (x = X exactly), v = v0
+    launch_reset_state(m->rt_dev(), (const float*)m->v0.p, s);
     GS_CUDA(cudaStreamSynchronize(s));
     GS_CUDA(cudaGetLastError());
     int bad = 0;
     GS_CUDA(cudaMemcpy(&bad, (int*)m->status.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
     if (bad) return set_error(GS_EINVAL, "inverted or degenerate rest element (non-positive volume or area)");
     m->info.device_bytes = 0;
-    for (Buf* b : {&m->eidx, &m->ea, &m->eb, &m->ec, &m->eact, &m->hidx, &m->hp, &m->bnd_ids, &m->loc_rowptr,
+    for (Buf* b : {&m->eidx, &m->ea, &m->eb, &m->ec, &m->ed, &m->eact, &m->hidx, &m->hq, &m->Xs, &m->Xp, &m->v0, &m->bnd_ids, &m->loc_rowptr,
                    &m->loc_slots, &m->bnd_rowptr, &m->bnd_parts, &m->partials, &m->node_perm, &m->elem_perm,
                    &m->hinge_perm, &m->w, &m->X, &m->rho, &m->pinned, &m->st})
         m->info.device_bytes += b->bytes;
@@ -698,6 +717,17 @@ extern "C" gs_status gs_mesh_set_state(gs_mesh* m, const float* x, const float* 
     GS_CUDA(cudaGetLastError());
     t1.release(s);
     t2.release(s);
+    m->ro.valid = false;
+    return GS_OK;
+}
+
+extern "C" gs_status gs_mesh_reset(gs_mesh* m, void* stream) {
+    clear_error();
+    if (!m) return set_error(GS_EINVAL, "null mesh");
+    cudaStream_t s = (cudaStream_t)stream;
+    GS_TRY(m->self->sync_rt(s));
+    launch_reset_state(m->rt_dev(), (const float*)m->v0.p, s);
+    GS_CUDA(cudaGetLastError());
     m->ro.valid = false;
     return GS_OK;
 }

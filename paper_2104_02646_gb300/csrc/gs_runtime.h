@@ -108,7 +108,7 @@ struct gs_mesh {
     int n_pad = 0, threads = 256, max_loc = 0, max_slots = 0, n_bufs = 0;
     std::vector<gs::PatchDesc> patches;
     std::vector<gs::NodeBlock> bnd_blocks, node_blocks;
-    gs::Buf eidx, ea, eb, ec, eact, hidx, hp, bnd_ids, loc_rowptr, loc_slots, bnd_rowptr, bnd_parts, partials,
+    gs::Buf eidx, ea, eb, ec, ed, eact, hidx, hq, Xs, Xp, v0, bnd_ids, loc_rowptr, loc_slots, bnd_rowptr, bnd_parts, partials,
         node_perm, elem_perm, hinge_perm, w, X, rho, pinned, st, xb, vb, wbar, mbar, g_mu, g_lam, g_act, g_kb,
         g_hact, status, target, scratch;
     gs::MeshRT rt{};

@@ -102,6 +102,7 @@ _PROTOS = {
     "gs_mesh_set_params": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
     "gs_mesh_set_state": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
     "gs_mesh_get_state": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
+    "gs_mesh_reset": (C.c_int, [_vp, _vp]),
     "gs_mesh_check": (C.c_int, [_vp, C.c_int, _vp]),
     "gs_step": (C.c_int, [_vp, C.c_float, C.c_int, _vp]),
     "gs_rollout": (C.c_int, [_vp, C.c_float, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp]),
@@ -306,6 +307,9 @@ class Mesh:
     def set_state(self, x=None, v=None, host=False, stream=None):
         check(load().gs_mesh_set_state(self.h, _ptr(x), _ptr(v), GS_MEM_HOST if host else GS_MEM_DEVICE,
                                        _stream(stream)))
+
+    def reset(self, stream=None):
+        check(load().gs_mesh_reset(self.h, _stream(stream)))
 
     def get_state(self, x=None, v=None, host=False, stream=None):
         check(load().gs_mesh_get_state(self.h, _ptr(x), _ptr(v), GS_MEM_HOST if host else GS_MEM_DEVICE,

@@ -171,3 +171,20 @@ def test_pinned_beam_gradients(gs, ctx):
     np.testing.assert_array_equal(out["x"][pinned == 1], X[pinned == 1].astype(np.float32))
     assert rel_pos(out["x"], ref["x"]) <= POS_FREE
     check_grads(out, ref, TET_KEYS)
+
+
+def test_rest_state_is_exactly_force_free(gs, ctx):
+    # the state is the displacement from the rest shape: an undeformed mesh
+    # without gravity or contact feels exactly zero force, in FP32 too
+    import torch
+    for p in (I.block(n=5, steps=10, seed=11), I.cloth("3s", n=16, steps=10, grid_scaled=True)):
+        p.gravity = (0.0, 0.0, 0.0)
+        p.contact = I.Contact(plane_on=False, sphere_on=False)
+        p.v0 = np.zeros_like(p.X)
+        m = gs.Mesh(ctx, p, patch_elems=128)
+        m.step(p.dt, 100)
+        x = torch.empty(p.n_nodes, 3, device="cuda")
+        v = torch.empty(p.n_nodes, 3, device="cuda")
+        m.get_state(x, v)
+        np.testing.assert_array_equal(x.cpu().numpy(), p.X.astype(np.float32))
+        assert float(v.abs().max()) == 0.0
