@@ -255,6 +255,29 @@ GS_API gs_status gs_batch_rollout(gs_batch* batch, const float* dt, int n_steps,
 /* grads[n] (device pointers inside). */
 GS_API gs_status gs_batch_adjoint(gs_batch* batch, const gs_grads* grads, void* stream);
 
+/* ---- loss without device allocation ----------------------------------------- */
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory while they run: a real-time control loop
+ * (for instance a model-predictive controller evaluating the loss every
+ * tick) cannot afford cudaMalloc, which may synchronise the device and take
+ * unbounded time, and a host that owns a fixed memory pool may forbid
+ * libraries from allocating at all.
+ *
+ * Computes L = sum_i |x_i - target_i|^2 in FP64 into *loss_out and, when
+ * dL_dx is non-NULL, dL/dx = 2 (x - target).  x, target, dL_dx: DEVICE
+ * [n_nodes][3] float; loss_out: one DEVICE double; all caller-owned.  The
+ * call allocates nothing: its reduction scratch is a fixed array of
+ * GS_NOALLOC_MAX_NODES / 256 doubles (128 KiB) inside the library that every
+ * GPU loading the library holds until exit.  n_nodes above
+ * GS_NOALLOC_MAX_NODES is rejected with GS_EINVAL before any work.  The first
+ * call on a device looks up the array's device address (once per device);
+ * make that first call before any stream capture.  All calls share the
+ * array: calls whose work overlaps on the GPU race and must be serialised
+ * by the caller.  Enqueued on `stream`. */
+#define GS_NOALLOC_MAX_NODES 4194304
+GS_API gs_status gs_loss_noalloc(const float* x, const float* target, int n_nodes, double* loss_out,
+                                 float* dL_dx, void* stream);
+
 /* ---- serving: continuous batching of gradient queries ---------------------- */
 typedef struct gs_server_opts {
     size_t hbm_budget_bytes;  /* admission budget for query state + checkpoints */

@@ -18,6 +18,7 @@ from . import _build
 GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ESTATE, GS_ENONFINITE = 0, -1, -2, -3, -4, -5
 GS_ETIMEOUT, GS_ECANCELLED, GS_ENOTFOUND, GS_EUNSUPPORTED = -6, -7, -8, -9
 GS_PENDING, GS_WUNSTABLE = 1, 2
+GS_NOALLOC_MAX_NODES = 4194304
 GS_TET, GS_CLOTH = 0, 1
 GS_MEM_DEVICE, GS_MEM_HOST = 0, 1
 
@@ -112,6 +113,7 @@ _PROTOS = {
     "gs_batch_step": (C.c_int, [_vp, _fp, C.c_int, _vp]),
     "gs_batch_rollout": (C.c_int, [_vp, _fp, C.c_int, C.c_int, C.POINTER(_vp), _vp, _vp]),
     "gs_batch_adjoint": (C.c_int, [_vp, C.POINTER(gs_grads), _vp]),
+    "gs_loss_noalloc": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp]),
     "gs_server_create": (C.c_int, [_vp, C.POINTER(gs_server_opts), C.POINTER(_vp)]),
     "gs_server_destroy": (None, [_vp]),
     "gs_query_submit": (C.c_int, [_vp, C.POINTER(gs_query), C.POINTER(C.c_uint64)]),
