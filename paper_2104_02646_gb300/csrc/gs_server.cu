@@ -1,15 +1,591 @@
-// Continuous-batching server for gradient queries (see gradsim.h).
+// Continuous-batching server for system-identification gradient queries.
+//
+// A query is a whole gradient request (mesh, materials, dt, horizon, target;
+// the paper's parameter-estimation loop, Sec. 3, with a position loss).  One
+// worker thread owns the GPU work on its own stream and advances time in
+// ticks.  Every tick launches the forward step kernels once and the adjoint
+// step kernels once over the patches of *all* active queries; each query is
+// in its own phase (forward chunk, segment recompute, or reverse steps), which
+// its device record selects through the active flags and the tick-affine
+// buffer indices (in = in_a + in_b * tick, ...).  Queries are admitted from a
+// FIFO as slots and the HBM budget free up, so queries that arrive while
+// others run join the next tick; finished queries leave and release memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
 #include "gs_runtime.h"
 
 using namespace gs;
 
-extern "C" gs_status gs_server_create(gs_ctx*, const gs_server_opts*, gs_server** out) {
-    if (out) *out = nullptr;
-    return set_error(GS_EUNSUPPORTED, "server not built yet");
+namespace {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
-extern "C" void gs_server_destroy(gs_server*) {}
-extern "C" gs_status gs_query_submit(gs_server*, const gs_query*, uint64_t*) { return set_error(GS_EUNSUPPORTED, "server"); }
-extern "C" gs_status gs_query_poll(gs_server*, uint64_t, gs_result*, int) { return set_error(GS_EUNSUPPORTED, "server"); }
-extern "C" gs_status gs_query_cancel(gs_server*, uint64_t) { return set_error(GS_EUNSUPPORTED, "server"); }
-extern "C" gs_status gs_server_stats_get(gs_server*, gs_server_stats*) { return set_error(GS_EUNSUPPORTED, "server"); }
-extern "C" void gs_result_free(gs_result*) {}
+
+enum Phase { P_FWD, P_REC, P_ADJ, P_FINISHING, P_DONE };
+
+struct Query {
+    uint64_t id = 0;
+    // deep copy of the request
+    gs_mesh_desc desc{};
+    std::vector<int32_t> elems, hinges;
+    std::vector<double> X, v0, mu, lam, rho, kb;
+    std::vector<float> target;
+    float dt = 0.f;
+    int S = 0, K = 1, n_ck = 1;
+    size_t bytes = 0;
+    // run state
+    gs_mesh* mesh = nullptr;
+    Phase phase = P_FWD;
+    int chunk = 0;          // forward chunk or segment index
+    int t0 = 0;             // tick at which the phase started
+    int steps = 0;          // steps of the phase
+    int done = 0;           // steps done in the phase
+    bool cancelled = false;
+    // results
+    Buf g_dev;              // device gradients
+    double* h_stage = nullptr;  // pinned host staging
+    size_t stage_bytes = 0;
+    cudaEvent_t ev = nullptr;
+    gs_result res{};
+    bool ready = false;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+};
+
+size_t estimate_bytes(const gs_mesh_desc& d, int S, int K) {
+    const size_t N = d.n_nodes, E = d.n_elems, B = d.kind == GS_CLOTH ? d.n_hinges : 0;
+    const int n_ck = std::max(1, (S + K - 1) / K);
+    const size_t bufs = 2 + n_ck + K;
+    return E * 200 + B * 80 + N * (32 * bufs + 160) + ((size_t)1 << 20);
+}
+
+}  // namespace
+
+struct gs_server {
+    gs_ctx* ctx = nullptr;
+    gs_server_opts opts{};
+    cudaStream_t stream = nullptr;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv;      // wakes the worker
+    std::condition_variable cv_done; // wakes pollers
+    bool stop = false;
+    uint64_t next_id = 1;
+    std::deque<Query*> pending;
+    std::vector<Query*> active;      // admitted, in some phase
+    std::map<uint64_t, Query*> all;  // every query not yet collected
+    size_t admitted = 0;
+    uint64_t submitted = 0, completed = 0, rejected = 0;
+    std::vector<double> latencies;
+    double busy_since = -1.0, busy_time = 0.0, elem_steps = 0.0;
+    LaunchSet ls;
+    bool ls_valid = false;  // ls holds exactly the meshes of `active`
+    bool ls_dirty = false;  // a query left: rebuild before the next launch
+    int tick = 0;
+    std::deque<cudaEvent_t> tick_events;
+
+    void run();
+    void admit_locked(std::vector<Query*>& fresh);
+    gs_status start_query(Query* q);
+    void set_phase(Query* q, Phase ph, int chunk);
+    gs_status enter_phase(Query* q);
+    void finish(Query* q);
+    void collect();
+};
+
+void gs_server::set_phase(Query* q, Phase ph, int chunk) {
+    q->phase = ph;
+    q->chunk = chunk;
+    q->t0 = tick;
+    q->done = 0;
+}
+
+// per-query actions at the start of a phase and its device record fields
+gs_status gs_server::enter_phase(Query* q) {
+    gs_mesh* m = q->mesh;
+    MeshRT& r = m->rt;
+    const int seg0 = 1 + q->n_ck;
+    if (q->phase == P_FWD) {
+        q->steps = std::min(q->K, q->S - q->chunk * q->K);
+        r.active = ACT_FWD;
+        r.in_a = r.in_b = r.out_a = r.out_b = 0;
+        r.ck_tick = (q->chunk + 1 < q->n_ck) ? q->t0 + q->steps - 1 : -1;
+        r.ck_buf = 2 + q->chunk;
+    } else if (q->phase == P_REC) {
+        q->steps = std::min(q->K, q->S - q->chunk * q->K);
+        r.active = ACT_FWD;
+        r.cp_src = 1 + q->chunk;
+        r.cp_dst = seg0;
+        GS_TRY(m->self->sync_rt(stream));
+        launch_copy_state(m->self->launch, stream);
+        r.in_a = seg0 - q->t0;
+        r.in_b = 1;
+        r.out_a = seg0 + 1 - q->t0;
+        r.out_b = 1;
+        r.ck_tick = -1;
+    } else if (q->phase == P_ADJ) {
+        r.active = ACT_ADJ;
+        r.adj_a = seg0 + q->steps - 1 + q->t0;
+        r.adj_b = -1;
+    }
+    return GS_OK;
+}
+
+gs_status gs_server::start_query(Query* q) {
+    gs_mesh* m = nullptr;
+    gs_status st = gs_mesh_create(ctx, &q->desc, &m);
+    if (st < 0) return st;
+    q->mesh = m;
+    q->K = opts.K > 0 ? std::min(opts.K, std::max(q->S, 1))
+                      : std::max(1, (int)std::ceil(std::sqrt((double)std::max(q->S, 1))));
+    q->n_ck = std::max(1, (q->S + q->K - 1) / q->K);
+    GS_TRY(m->ensure_buffers(1 + q->n_ck + q->K + 1, stream));
+    GS_TRY(m->ensure_adjoint(stream));
+    GS_TRY(m->target.alloc(ctx, q->target.size() * sizeof(float), stream));
+    GS_CUDA(cudaMemcpyAsync(m->target.p, q->target.data(), m->target.bytes, cudaMemcpyHostToDevice, stream));
+    m->rt.target = (const float*)m->target.p;
+    m->rt.dt = q->dt;
+    // checkpoint 0 = the initial state
+    m->rt.cp_src = 0;
+    m->rt.cp_dst = 1;
+    m->rt.active = ACT_FWD;
+    GS_TRY(m->self->sync_rt(stream));
+    launch_copy_state(m->self->launch, stream);
+    set_phase(q, P_FWD, 0);
+    return enter_phase(q);
+}
+
+// last reverse step done: gradients out, device -> pinned host, event
+void gs_server::finish(Query* q) {
+    gs_mesh* m = q->mesh;
+    const size_t E = m->info.n_elems, B = m->info.n_hinges, N = m->info.n_nodes;
+    m->rt.active = 0;
+    q->stage_bytes = sizeof(double) * (3 * E + B + 1) + sizeof(float) * 6 * N;
+    if (q->g_dev.alloc(ctx, q->stage_bytes, stream) < 0 || cudaMallocHost((void**)&q->h_stage, q->stage_bytes) != cudaSuccess) {
+        q->res.status = GS_ENOMEM;
+        q->phase = P_FINISHING;
+        cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming);
+        cudaEventRecord(q->ev, stream);
+        return;
+    }
+    char* p = (char*)q->g_dev.p;
+    gs_grads g{};
+    g.d_mu = (double*)p;
+    g.d_lambda = g.d_mu + E;
+    g.d_density = g.d_lambda + E;
+    g.d_kb = B ? g.d_density + E : nullptr;
+    double* d_loss = g.d_density + E + B;
+    g.d_x0 = (float*)(d_loss + 1);
+    g.d_v0 = g.d_x0 + 3 * N;
+    m->self->sync_rt(stream);
+    const size_t sm = std::max(sizeof(double) * (size_t)m->max_loc, (size_t)16);
+    launch_finalize_grads(m->self->launch, (double*)m->mbar.p, g, sm, stream);
+    // the loss of the final state
+    launch_seed_loss(m->self->launch, (double*)m->self->d_loss.p, 0, stream);
+    launch_loss_finalize((const double*)m->self->d_loss.p, 0, (int)m->node_blocks.size(), d_loss, stream);
+    cudaMemcpyAsync(q->h_stage, q->g_dev.p, q->stage_bytes, cudaMemcpyDeviceToHost, stream);
+    cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming);
+    cudaEventRecord(q->ev, stream);
+    q->phase = P_FINISHING;
+}
+
+// finished queries whose copies landed: fill results, release the mesh
+void gs_server::collect() {
+    std::vector<Query*> keep;
+    bool any = false;
+    for (Query* q : active) {
+        if (q->phase != P_FINISHING || cudaEventQuery(q->ev) != cudaSuccess) {
+            keep.push_back(q);
+            continue;
+        }
+        gs_mesh* m = q->mesh;
+        const size_t E = m->info.n_elems, B = m->info.n_hinges, N = m->info.n_nodes;
+        gs_result& r = q->res;
+        if (r.status == GS_OK && q->h_stage) {
+            int st = 0;
+            cudaMemcpy(&st, m->status.p, sizeof(int), cudaMemcpyDeviceToHost);
+            r.status = (st & 1) ? GS_ENONFINITE : GS_OK;
+            const double* d = q->h_stage;
+            r.n_elems = (int)E;
+            r.n_hinges = (int)B;
+            r.n_nodes = (int)N;
+            r.d_mu = (double*)malloc(8 * E);
+            r.d_lambda = (double*)malloc(8 * E);
+            r.d_density = (double*)malloc(8 * E);
+            std::memcpy(r.d_mu, d, 8 * E);
+            std::memcpy(r.d_lambda, d + E, 8 * E);
+            std::memcpy(r.d_density, d + 2 * E, 8 * E);
+            if (B) {
+                r.d_kb = (double*)malloc(8 * B);
+                std::memcpy(r.d_kb, d + 3 * E, 8 * B);
+            }
+            r.loss = d[3 * E + B];
+            const float* f = (const float*)(d + 3 * E + B + 1);
+            r.d_x0 = (float*)malloc(12 * N);
+            r.d_v0 = (float*)malloc(12 * N);
+            std::memcpy(r.d_x0, f, 12 * N);
+            std::memcpy(r.d_v0, f + 3 * N, 12 * N);
+        }
+        q->t_done = now_s();
+        r.t_submit = q->t_submit;
+        r.t_admit = q->t_admit;
+        r.t_done = q->t_done;
+        cudaEventDestroy(q->ev);
+        q->ev = nullptr;
+        if (q->h_stage) cudaFreeHost(q->h_stage);
+        q->h_stage = nullptr;
+        q->g_dev.release(stream);
+        gs_mesh_destroy(q->mesh);
+        q->mesh = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            admitted -= q->bytes;
+            completed++;
+            if (r.status == GS_OK) {
+                latencies.push_back(q->t_done - q->t_submit);
+                elem_steps += (double)E * q->S;
+            }
+            q->ready = true;
+            q->phase = P_DONE;
+        }
+        any = true;
+    }
+    active.swap(keep);
+    if (any) {
+        ls_dirty = true;
+        cv_done.notify_all();
+    }
+}
+
+void gs_server::admit_locked(std::vector<Query*>& fresh) {
+    while (!pending.empty()) {
+        Query* q = pending.front();
+        if (q->cancelled) {
+            pending.pop_front();
+            q->res.status = GS_ECANCELLED;
+            q->ready = true;
+            completed++;
+            cv_done.notify_all();
+            continue;
+        }
+        const int n_active = (int)(active.size() + fresh.size());
+        if (opts.max_active > 0 && n_active >= opts.max_active) break;
+        if (opts.hbm_budget_bytes && admitted + q->bytes > opts.hbm_budget_bytes && n_active > 0) break;
+        pending.pop_front();
+        admitted += q->bytes;
+        fresh.push_back(q);
+    }
+}
+
+void gs_server::run() {
+    cudaSetDevice(ctx->device);
+    while (true) {
+        std::vector<Query*> fresh;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (stop) break;
+            admit_locked(fresh);
+            if (active.empty() && fresh.empty()) {
+                if (busy_since >= 0) {
+                    busy_time += now_s() - busy_since;
+                    busy_since = -1.0;
+                }
+                cv.wait_for(lk, std::chrono::milliseconds(50));
+                continue;
+            }
+            if (busy_since < 0) busy_since = now_s();
+        }
+        bool changed = !fresh.empty();
+        for (Query* q : fresh) {
+            q->t_admit = now_s();
+            gs_status st = start_query(q);
+            if (st < 0) {
+                if (q->mesh) gs_mesh_destroy(q->mesh);
+                q->mesh = nullptr;
+                std::lock_guard<std::mutex> lk(mu);
+                admitted -= q->bytes;
+                q->res.status = st;
+                q->t_done = now_s();
+                q->ready = true;
+                completed++;
+                cv_done.notify_all();
+                continue;
+            }
+            active.push_back(q);
+        }
+        // cancellations of running queries
+        for (Query* q : active) {
+            bool c;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                c = q->cancelled;
+            }
+            if (c && q->phase != P_FINISHING) {
+                q->mesh->rt.active = 0;
+                q->res.status = GS_ECANCELLED;
+                q->phase = P_FINISHING;
+                cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming);
+                cudaEventRecord(q->ev, stream);
+                changed = true;
+            }
+        }
+        // phase transitions (queries whose phase has run all its steps)
+        for (Query* q : active) {
+            while (q->phase != P_FINISHING && q->done >= q->steps) {
+                changed = true;
+                if (q->phase == P_FWD) {
+                    if ((q->chunk + 1) * q->K < q->S) {
+                        set_phase(q, P_FWD, q->chunk + 1);
+                    } else {
+                        // forward done: seed dL/dx(S) from the target, zero the accumulators
+                        gs_mesh* m = q->mesh;
+                        m->rt.active = ACT_FWD | ACT_ADJ;
+                        m->self->sync_rt(stream);
+                        launch_seed_loss(m->self->launch, (double*)m->self->d_loss.p, 1, stream);
+                        launch_zero_adjoint(m->self->launch, stream);
+                        launch_zero_f64((double*)m->g_mu.p, m->info.n_elems, stream);
+                        launch_zero_f64((double*)m->g_lam.p, m->info.n_elems, stream);
+                        launch_zero_f64((double*)m->g_act.p, m->info.n_elems, stream);
+                        launch_zero_f64((double*)m->g_kb.p, m->info.n_hinges, stream);
+                        launch_zero_f64((double*)m->g_hact.p, m->info.n_hinges, stream);
+                        set_phase(q, P_REC, q->n_ck - 1);
+                    }
+                } else if (q->phase == P_REC) {
+                    const int st = q->steps;
+                    set_phase(q, P_ADJ, q->chunk);
+                    q->steps = st;
+                } else if (q->phase == P_ADJ) {
+                    if (q->chunk > 0) {
+                        set_phase(q, P_REC, q->chunk - 1);
+                    } else {
+                        finish(q);
+                        break;
+                    }
+                }
+                if (q->phase != P_FINISHING) enter_phase(q);
+            }
+        }
+        if (changed || ls_dirty || !ls_valid) {
+            std::vector<gs_mesh*> ms;
+            for (Query* q : active) ms.push_back(q->mesh);
+            ls_valid = !ms.empty() && ls.build(ctx, ms, stream) == GS_OK;
+            ls_dirty = false;
+        } else {
+            ls.sync_rt(stream);
+        }
+        // one tick: forward over FWD/REC queries, adjoint over ADJ queries
+        bool any_f = false, any_a = false;
+        for (Query* q : active) {
+            if (q->phase == P_FWD || q->phase == P_REC) any_f = true;
+            if (q->phase == P_ADJ) any_a = true;
+        }
+        if ((any_f || any_a) && ls_valid) {
+            if (any_f) launch_forward_step(ls.launch, tick, stream);
+            if (any_a) launch_adjoint_step(ls.launch, tick, stream);
+            for (Query* q : active)
+                if (q->phase == P_FWD || q->phase == P_REC || q->phase == P_ADJ) q->done++;
+            tick++;
+            // bound the work in flight: wait for the tick 8 back
+            cudaEvent_t e;
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+            cudaEventRecord(e, stream);
+            tick_events.push_back(e);
+            if (tick_events.size() > 8) {
+                cudaEventSynchronize(tick_events.front());
+                cudaEventDestroy(tick_events.front());
+                tick_events.pop_front();
+            }
+            // keep ticks in a range where tick-affine indices stay small
+            if (tick > (1 << 28)) {
+                for (Query* q : active) {
+                    MeshRT& r = q->mesh->rt;
+                    const int sh = tick;
+                    q->t0 -= sh;
+                    r.in_a += r.in_b * sh;
+                    r.out_a += r.out_b * sh;
+                    r.adj_a += r.adj_b * sh;
+                    if (r.ck_tick >= 0) r.ck_tick -= sh;
+                }
+                tick = 0;
+            }
+        } else {
+            cudaStreamSynchronize(stream);
+        }
+        collect();
+    }
+    cudaStreamSynchronize(stream);
+    for (cudaEvent_t e : tick_events) cudaEventDestroy(e);
+    tick_events.clear();
+}
+
+extern "C" gs_status gs_server_create(gs_ctx* ctx, const gs_server_opts* opts, gs_server** out) {
+    clear_error();
+    if (!ctx || !out) return set_error(GS_EINVAL, "null argument");
+    *out = nullptr;
+    GS_CUDA(cudaSetDevice(ctx->device));
+    std::unique_ptr<gs_server> s(new gs_server());
+    s->ctx = ctx;
+    if (opts) s->opts = *opts;
+    GS_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    gs_server* raw = s.get();
+    s->worker = std::thread([raw] { raw->run(); });
+    *out = s.release();
+    return GS_OK;
+}
+
+extern "C" void gs_server_destroy(gs_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        for (auto& kv : s->all) kv.second->cancelled = true;
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (Query* q : s->active) {
+        if (q->mesh) gs_mesh_destroy(q->mesh);
+        if (q->h_stage) cudaFreeHost(q->h_stage);
+        if (q->ev) cudaEventDestroy(q->ev);
+    }
+    for (auto& kv : s->all) {
+        gs_result_free(&kv.second->res);
+        delete kv.second;
+    }
+    cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+extern "C" gs_status gs_query_submit(gs_server* s, const gs_query* q, uint64_t* ticket) {
+    clear_error();
+    if (!s || !q || !ticket) return set_error(GS_EINVAL, "null argument");
+    const gs_mesh_desc& d = q->mesh;
+    if (d.n_nodes <= 0 || d.n_elems <= 0 || !d.elems || !d.X || !d.mu || !d.lambda || !d.density || !q->target)
+        return set_error(GS_EINVAL, "query needs a mesh, materials and a target");
+    if (q->n_steps < 0 || !(q->dt > 0.f)) return set_error(GS_EINVAL, "query needs dt > 0 and n_steps >= 0");
+    std::unique_ptr<Query> Q(new Query());
+    const int nc = d.kind == GS_TET ? 4 : 3;
+    const size_t N = d.n_nodes, E = d.n_elems, B = d.kind == GS_CLOTH ? d.n_hinges : 0;
+    Q->elems.assign(d.elems, d.elems + nc * E);
+    Q->X.assign(d.X, d.X + 3 * N);
+    if (d.v0) Q->v0.assign(d.v0, d.v0 + 3 * N);
+    Q->mu.assign(d.mu, d.mu + E);
+    Q->lam.assign(d.lambda, d.lambda + E);
+    Q->rho.assign(d.density, d.density + E);
+    if (B) {
+        if (!d.hinges || !d.kb) return set_error(GS_EINVAL, "cloth query needs hinges and kb");
+        Q->hinges.assign(d.hinges, d.hinges + 4 * B);
+        Q->kb.assign(d.kb, d.kb + B);
+    }
+    Q->target.assign(q->target, q->target + 3 * N);
+    Q->desc = d;
+    Q->desc.elems = Q->elems.data();
+    Q->desc.X = Q->X.data();
+    Q->desc.v0 = d.v0 ? Q->v0.data() : nullptr;
+    Q->desc.mu = Q->mu.data();
+    Q->desc.lambda = Q->lam.data();
+    Q->desc.density = Q->rho.data();
+    Q->desc.hinges = B ? Q->hinges.data() : nullptr;
+    Q->desc.kb = B ? Q->kb.data() : nullptr;
+    Q->desc.act = nullptr;
+    Q->desc.hinge_act = nullptr;
+    Q->desc.pinned = nullptr;
+    Q->dt = q->dt;
+    Q->S = q->n_steps;
+    const int K = s->opts.K > 0 ? s->opts.K : std::max(1, (int)std::ceil(std::sqrt((double)std::max(Q->S, 1))));
+    Q->bytes = estimate_bytes(d, Q->S, K);
+    Q->t_submit = now_s();
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->submitted++;
+    if (s->opts.hbm_budget_bytes && Q->bytes > s->opts.hbm_budget_bytes) {
+        s->rejected++;
+        return set_error(GS_ENOMEM, "query needs more than the whole server budget");
+    }
+    Q->id = s->next_id++;
+    *ticket = Q->id;
+    s->all[Q->id] = Q.get();
+    s->pending.push_back(Q.release());
+    s->cv.notify_all();
+    return GS_OK;
+}
+
+extern "C" gs_status gs_query_poll(gs_server* s, uint64_t ticket, gs_result* out, int timeout_ms) {
+    clear_error();
+    if (!s) return set_error(GS_EINVAL, "null server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return set_error(GS_ENOTFOUND, "unknown ticket");
+    Query* q = it->second;
+    if (!q->ready && timeout_ms > 0)
+        s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [q] { return q->ready; });
+    if (!q->ready) return timeout_ms > 0 ? GS_ETIMEOUT : GS_PENDING;
+    const gs_status st = q->res.status;
+    if (out) {
+        *out = q->res;  // ownership of the host arrays passes to the caller
+        std::memset(&q->res, 0, sizeof(q->res));
+    }
+    s->all.erase(it);
+    delete q;
+    if (st == GS_ECANCELLED) return set_error(GS_ECANCELLED, "query cancelled");
+    if (st == GS_ENONFINITE) return set_error(GS_ENONFINITE, "query produced a non-finite state");
+    if (st < 0) return set_error(st, "query failed");
+    return GS_OK;
+}
+
+extern "C" gs_status gs_query_cancel(gs_server* s, uint64_t ticket) {
+    clear_error();
+    if (!s) return set_error(GS_EINVAL, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return set_error(GS_ENOTFOUND, "unknown ticket");
+    it->second->cancelled = true;
+    s->cv.notify_all();
+    return GS_OK;
+}
+
+extern "C" gs_status gs_server_stats_get(gs_server* s, gs_server_stats* out) {
+    clear_error();
+    if (!s || !out) return set_error(GS_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    out->rejected = s->rejected;
+    out->active = s->active.size();
+    out->queued = s->pending.size();
+    out->admitted_bytes = s->admitted;
+    std::vector<double> l = s->latencies;
+    if (!l.empty()) {
+        std::sort(l.begin(), l.end());
+        auto pct = [&](double p) { return l[std::min(l.size() - 1, (size_t)std::floor(p * (l.size() - 1) + 0.5))]; };
+        out->p50_latency_s = pct(0.50);
+        out->p99_latency_s = pct(0.99);
+    }
+    double busy = s->busy_time + (s->busy_since >= 0 ? now_s() - s->busy_since : 0.0);
+    out->elem_steps_per_s = busy > 0 ? s->elem_steps / busy : 0.0;
+    return GS_OK;
+}
+
+extern "C" void gs_result_free(gs_result* r) {
+    if (!r) return;
+    free(r->d_mu);
+    free(r->d_lambda);
+    free(r->d_density);
+    free(r->d_kb);
+    free(r->d_x0);
+    free(r->d_v0);
+    r->d_mu = r->d_lambda = r->d_density = r->d_kb = nullptr;
+    r->d_x0 = r->d_v0 = nullptr;
+}

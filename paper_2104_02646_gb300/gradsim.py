@@ -385,3 +385,57 @@ class Batch:
             self.close()
         except Exception:  # noqa: BLE001
             pass
+
+
+class Server:
+    """Continuous-batching gradient-query server (gs_server_*)."""
+
+    def __init__(self, ctx: Context, budget: int = 0, max_active: int = 0, K: int = 0):
+        self.ctx = ctx
+        o = gs_server_opts(budget, max_active, K, 0)
+        self.h = _vp()
+        check(load().gs_server_create(ctx.h, C.byref(o), C.byref(self.h)))
+        self._keep = {}
+
+    def submit(self, problem, target, dt=None, steps=None) -> int:
+        d, keep = mesh_desc(problem)
+        t = np.ascontiguousarray(target, dtype=np.float32)
+        q = gs_query(d, float(problem.dt if dt is None else dt), int(problem.steps if steps is None else steps),
+                     t.ctypes.data_as(_fp))
+        ticket = C.c_uint64(0)
+        check(load().gs_query_submit(self.h, C.byref(q), C.byref(ticket)))
+        return ticket.value
+
+    def poll(self, ticket: int, timeout_ms: int = 0):
+        """(status, result dict or None); result arrays are copied to numpy."""
+        r = gs_result()
+        st = load().gs_query_poll(self.h, C.c_uint64(ticket), C.byref(r), int(timeout_ms))
+        if st in (GS_PENDING, GS_ETIMEOUT) or st == GS_ENOTFOUND:
+            return st, None
+        out = {"status": st, "loss": r.loss, "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done}
+        E, B, N = r.n_elems, r.n_hinges, r.n_nodes
+        for name, n, ct in (("d_mu", E, C.c_double), ("d_lambda", E, C.c_double), ("d_density", E, C.c_double),
+                            ("d_kb", B, C.c_double), ("d_x0", 3 * N, C.c_float), ("d_v0", 3 * N, C.c_float)):
+            ptr = getattr(r, name)
+            out[name] = np.ctypeslib.as_array(ptr, shape=(n,)).copy() if (ptr and n) else None
+        load().gs_result_free(C.byref(r))
+        return st, out
+
+    def cancel(self, ticket: int) -> int:
+        return load().gs_query_cancel(self.h, C.c_uint64(ticket))
+
+    def stats(self) -> dict:
+        s = gs_server_stats()
+        check(load().gs_server_stats_get(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in gs_server_stats._fields_}
+
+    def close(self):
+        if self.h:
+            load().gs_server_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

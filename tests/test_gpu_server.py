@@ -1,0 +1,98 @@
+"""Continuous-batching server: every query's result equals the query run
+alone (bitwise: same kernels, same decomposition, no float atomics), queries
+overlap on the device, admission respects the budget, cancel works."""
+import numpy as np
+import pytest
+
+from paper_2104_02646_gb300 import inputs as I
+
+from gpu_util import make_target, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _queries(n_tet=4, n_cloth=2, seed=0):
+    out = []
+    for i in range(n_tet):
+        p = I.batch_member(i, steps=40 + 23 * i, lo=300, hi=4000, seed=seed)
+        out.append((p, make_target(p, p.steps, seed=i)))
+    for j in range(n_cloth):
+        p = I.cloth("3s", n=10 + 4 * j, steps=50 + 17 * j, grid_scaled=True)
+        out.append((p, make_target(p, p.steps, seed=10 + j)))
+    return out
+
+
+def _alone(gs, ctx, p, tgt):
+    return run_gpu(gs, ctx, p, p.steps, tgt)
+
+
+def test_server_results_equal_alone_and_overlap(gs):
+    qs = _queries()
+    ctx_alone = gs.Context(0)
+    alone = [_alone(gs, ctx_alone, p, t) for p, t in qs]
+    ctx = gs.Context(0)
+    server = gs.Server(ctx, budget=8 << 30)
+    tickets = [server.submit(p, t) for p, t in qs]
+    res = []
+    for t in tickets:
+        st, r = server.poll(t, timeout_ms=120000)
+        assert st == gs.GS_OK, st
+        res.append(r)
+    for (p, _), a, r in zip(qs, alone, res):
+        assert r["loss"] == a["loss"]
+        np.testing.assert_array_equal(r["d_mu"], a["d_mu"])
+        np.testing.assert_array_equal(r["d_lambda"], a["d_lambda"])
+        np.testing.assert_array_equal(r["d_density"], a["d_density"])
+        np.testing.assert_array_equal(r["d_v0"].reshape(-1, 3), a["d_v0"].astype(np.float32))
+        np.testing.assert_array_equal(r["d_x0"].reshape(-1, 3), a["d_x0"].astype(np.float32))
+        if p.n_hinges:
+            np.testing.assert_array_equal(r["d_kb"], a["d_kb"])
+    # continuous batching: later queries were admitted before earlier ones finished
+    first_done = min(r["t_done"] for r in res)
+    assert sum(r["t_admit"] < first_done for r in res) >= 3
+    s = server.stats()
+    assert s["completed"] == len(qs) and s["p99_latency_s"] >= s["p50_latency_s"] > 0
+    server.close()
+
+
+def test_server_budget_admission_and_rejection(gs):
+    qs = _queries(n_tet=3, n_cloth=0, seed=1)
+    ctx = gs.Context(0)
+    # room for one query at a time: all still complete, one after the other
+    server = gs.Server(ctx, budget=200 << 20, max_active=1)
+    tickets = [server.submit(p, t) for p, t in qs]
+    res = [server.poll(t, timeout_ms=120000) for t in tickets]
+    assert all(st == gs.GS_OK for st, _ in res)
+    rs = [r for _, r in res]
+    for a, b in zip(rs, rs[1:]):
+        assert b["t_admit"] >= a["t_done"] - 1e-3
+    ctx_alone = gs.Context(0)
+    for (p, t), r in zip(qs, rs):
+        a = _alone(gs, ctx_alone, p, t)
+        np.testing.assert_array_equal(r["d_mu"], a["d_mu"])
+    server.close()
+    # a query larger than the whole budget is refused at once
+    tiny = gs.Server(gs.Context(0), budget=1 << 20)
+    p, t = qs[0]
+    with pytest.raises(gs.GradsimError) as e:
+        tiny.submit(p, t)
+    assert e.value.status == gs.GS_ENOMEM
+    tiny.close()
+
+
+def test_server_cancel_and_unknown_ticket(gs):
+    ctx = gs.Context(0)
+    server = gs.Server(ctx, budget=4 << 30)
+    p = I.block(n=12, steps=3000, seed=2)
+    t = server.submit(p, p.X + 0.001)
+    assert server.cancel(t) == gs.GS_OK
+    st, r = server.poll(t, timeout_ms=60000)
+    assert st == gs.GS_ECANCELLED
+    st, _ = server.poll(987654321, timeout_ms=0)
+    assert st == gs.GS_ENOTFOUND
+    # the server keeps serving after a cancellation
+    q, tq = _queries(n_tet=1, n_cloth=0, seed=3)[0]
+    t2 = server.submit(q, tq)
+    st, r = server.poll(t2, timeout_ms=60000)
+    assert st == gs.GS_OK and np.isfinite(r["loss"])
+    server.close()
