@@ -180,6 +180,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value, dist=None, device=None):
+    """Max of a per-rank scalar over all ranks (the job's wall time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(n_ranks, n_elems, steps_per_rollout, bench_steps, total_ms):
+    """Whole-job fwd+adjoint element-steps/s of independent replicas."""
+    return n_ranks * n_elems * steps_per_rollout * bench_steps / (total_ms / 1e3)
+
+
 def launches_per_step(S, K, have_bnd):
     """Kernels of ours launched by one benchmark step (set_state + rollout +
     adjoint), counted from the library's launch sequence."""
@@ -189,7 +204,7 @@ def launches_per_step(S, K, have_bnd):
     per_step = 2 if have_bnd else 1
     n = 1                           # set_state
     n += 1 + per_step * S + 2       # checkpoint copy, steps, loss + finalize
-    n += 1 + 1 + 5                  # seed, zero w_bar, zero 5 accumulators
+    n += 1 + 1 + 3                  # seed, zero w_bar, zero the mu, lambda, kb accumulators
     n += n_ck + 2 * per_step * S    # per segment copy; recompute + reverse steps
     n += 2                          # node and element gradient kernels
     return n
@@ -268,12 +283,8 @@ def main():
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    total_ms = sum(ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * E * S * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(ms), dist, dev)
+    value = throughput(ws, E, S, args.steps, total_ms)
 
     # ---- per-kernel launch durations (CUDA events per launch) ---------------
     check = gs.check

@@ -31,13 +31,23 @@ namespace gs {
 // --------------------------------------------------------------------------
 // device-side tables
 // --------------------------------------------------------------------------
+// Element records, 4 float4 planes (plane k of element e at rec[k * E + e]);
+// a patch's slice of each plane is contiguous, so 4 bulk copies stage it:
+//   tet   [0] Dm^-1 00 01 02 10  [1] Dm^-1 11 12 20 21  [2] Dm^-1 22, V, mu, lambda
+//         [3] ids (0|1<<16), ids (2|3<<16) as bits, act, 0
+//   tri   [0] Dm^-1 00 01 10 11  [1] A, mu, lambda, act  [2] r0.x r0.y r0.z r1.x
+//         [3] ids (0|1<<16), ids (2) as bits, r1.y, r1.z       (r0, r1: rest frame R0)
+//   hinge [0] X1-X3, kb  [1] X2-X3, act  [2] X4-X3, 0  [3] ids (1|2<<16), ids (3|4<<16) as bits, 0, 0
+// In shared memory the planes are [4][n_rec] over the patch's records
+// (triangles first, then hinges); a corner result of record r, corner c is
+// written in place to plane c, row r.  CSR slot s = (record << 2) | corner.
 struct PatchDesc {
     int e_begin, n_e;      // elements (tets or triangles), internal order
     int h_begin, n_h;      // hinges (cloth)
     int int_begin, n_int;  // interior nodes: internal ids [int_begin, int_begin + n_int)
-    int bnd_begin, n_bnd;  // boundary local nodes: bnd_ids / partials [bnd_begin, +n_bnd)
-    int lr_begin;          // local CSR row pointers: n_int + n_bnd + 1 entries
-    int slot_begin;        // local CSR slot list
+    int bnd_begin, n_bnd;  // boundary local nodes: bnd_ids / partials [bnd_begin, +n_bnd), 16 B aligned
+    int lr_begin;          // local CSR row pointers: n_int + n_bnd + 1 entries (16 B aligned)
+    int slot_begin;        // local CSR slot list (16 B aligned)
     int mesh;              // index into the launch set's MeshRT array
     int pad;
 };
@@ -52,14 +62,8 @@ struct MeshRT {
     // static mesh data
     int kind, n_nodes, n_int, n_bnd;
     int n_elems, n_hinges, active, pad0;
-    const uint2* eidx;       // [E] 4 (tets) / 3 (tris) uint16 local node ids
-    float4* ea;              // tets: Dm^-1 00 01 02 10 | tris: Dm^-1 00 01 10 11
-    float4* eb;              // tets: Dm^-1 11 12 20 21 | tris: A, mu, lambda, act
-    float4* ec;              // tets: Dm^-1 22, V, mu, lambda | tris: rest frame r0, r1.x
-    float2* ed;              // tris: rest frame r1.y, r1.z
-    float* eact;             // tets: actuation [E] (nullable)
-    const uint2* hidx;       // [B] 4 uint16 local ids (x1, x2, x3, x4)
-    float4* hq;              // [3B] (X1-X3, kb), (X2-X3, act), (X4-X3, 0)
+    float4* rec;             // [4][E] element records as 4 planes of float4 (layout below)
+    float4* hrec;            // [4][B] hinge records
     const int* bnd_ids;      // per-patch boundary lists (internal node ids)
     const uint16_t* loc_rowptr;
     const uint16_t* loc_slots;
@@ -116,13 +120,17 @@ struct Launch {
     int n_node_blocks = 0;
     MeshRT* rt = nullptr;
     int threads = 256;
-    size_t smem_tet_fwd = 0, smem_tet_adj = 0, smem_cloth_fwd = 0, smem_cloth_adj = 0;
+    // patch kernels (tet fwd, cloth fwd, tet adj, cloth adj): persistent grid
+    // size and bytes of one of the two shared-memory pipeline stages
+    int grid[4] = {0, 0, 0, 0};
+    int stage[4] = {0, 0, 0, 0};
 };
 
 // --------------------------------------------------------------------------
 // kernels (gs_kernels.cu)
 // --------------------------------------------------------------------------
-size_t smem_bytes(int kind, bool adjoint, int max_loc, int max_slots);
+size_t patch_smem_bytes(int n_rec, int n_loc, int n_int, int n_slots, bool adjoint);
+int patch_grid(int which, int threads, int stage_bytes, int n_patches, int num_sms);
 void set_kernel_smem_limits(size_t bytes);
 // kernels whose launches can be timed one by one (gs_profile)
 enum { KT_TET_FWD, KT_CLOTH_FWD, KT_FWD_BND, KT_TET_ADJ, KT_CLOTH_ADJ, KT_ADJ_BND, KT_COUNT };

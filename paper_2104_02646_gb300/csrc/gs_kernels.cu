@@ -1,13 +1,17 @@
 // Kernels of the explicit step (forward) and of its discrete adjoint.
 //
-// One CTA per element patch.  Shared memory holds, for the patch's local
-// nodes, the gathered node data (positions with inverse mass in .w; in the
-// adjoint also the total adjoint velocity v_hat), and one float4 per element
-// corner.  The element phase writes corner results; the node phase sums the
-// corners of every local node through the patch's CSR in a fixed order,
-// finishes interior nodes (contact + semi-implicit Euler, or the reverse of
-// both) and writes one partial per boundary node, which the boundary kernel
-// sums in patch order.  Nothing uses floating-point atomics.
+// One CTA per element patch.  At the start one elected thread moves the
+// patch's element records, its local CSR and the state of its interior nodes
+// (all contiguous, 16 B aligned) into shared memory with TMA bulk copies
+// (cp.async.bulk) that complete on an mbarrier, while the other threads
+// gather the boundary nodes with ordinary loads; the CTA then waits for both.
+// The element phase computes each element from its shared record and writes
+// its corner results in place over that record (each record is read and
+// overwritten by one thread only).  The node phase sums the corners of every
+// local node through the shared CSR in a fixed order, finishes interior nodes
+// (contact + semi-implicit Euler, or the reverse of both) and writes one
+// partial per boundary node, which the boundary kernel sums in patch order.
+// Nothing uses floating-point atomics.
 #include <cuda_runtime.h>
 
 #include "gs_internal.h"
@@ -34,18 +38,108 @@ __device__ __forceinline__ ContactParams cparams(const MeshRT& m) {
     return c;
 }
 
+__device__ __forceinline__ uint2 rec_ids(float4 w) { return make_uint2(__float_as_uint(w.x), __float_as_uint(w.y)); }
+
+
+// ---------------------------------------------------------------------------
+// TMA bulk copies global -> shared completing on an mbarrier
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(saddr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// bytes: multiple of 16; src, dst: 16 B aligned
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     saddr(dst)),
+                 "l"(src), "r"(bytes), "r"(saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the given phase parity of the barrier.  try_wait suspends for a
+// hardware-defined interval per call, so the limit is seconds, far above
+// any real transfer; on expiry the kernel reports GS error bit 2 and, after
+// a second bounded wait for its own copies, the caller returns.
+constexpr int kWaitLimit = 1 << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
+    for (int i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicOr(status, 2);
+    for (int i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) break;
+    return false;
+}
+
+__host__ __device__ __forceinline__ int r16(int bytes) { return (bytes + 15) & ~15; }
+
+// Shared-memory layout of one pipeline stage (byte offsets, 16 B aligned).
+// The adjoint also holds v_hat for all local nodes, the interior adjoint
+// state and the boundary nodes' raw adjoint state.
+struct Layout {
+    int rec, rp, sl, xs, vh, vs, xb, vb, xbB, vbB, gmu, glam, total;
+};
+
+__host__ __device__ __forceinline__ Layout patch_layout(int n_rec, int n_loc, int n_int, int n_slots, bool adjoint) {
+    const int n_bnd = n_loc - n_int;
+    Layout L;
+    L.rec = 0;
+    L.rp = L.rec + 64 * n_rec;
+    L.sl = L.rp + r16(2 * (n_loc + 1));
+    L.xs = L.sl + r16(2 * n_slots);
+    L.vh = L.xs + 16 * n_loc;
+    L.vs = L.vh + (adjoint ? 16 * n_loc : 0);
+    L.xb = L.vs + 16 * n_int;
+    L.vb = L.xb + (adjoint ? 16 * n_int : 0);
+    L.xbB = L.vb + (adjoint ? 16 * n_int : 0);
+    L.vbB = L.xbB + (adjoint ? 16 * n_bnd : 0);
+    // adjoint: the patch's FP64 dL/dmu, dL/dlambda accumulators (records 0..n_rec)
+    L.gmu = L.vbB + (adjoint ? 16 * n_bnd : 0);
+    L.glam = L.gmu + (adjoint ? r16(8 * n_rec) : 0);
+    L.total = L.glam + (adjoint ? r16(8 * n_rec) : 0);
+    return L;
+}
+
+// cp.async 16 B global -> shared (LDGSTS), groups per thread
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// order earlier generic-proxy accesses of shared memory before async-proxy writes
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Contact geometry from the displacement u of node g.  The penetrations are
 // formed from FP64-derived rest offsets so that FP32 keeps their relative
 // precision near contact: plane C = (h - n.X) - n.u; sphere
 // C = r - |d| = -(|X - c|^2 - r^2 + 2 (X - c).u + u.u) / (|d| + r), d = X - c + u.
 
-// total contact force on a node: plane and sphere
-__device__ __forceinline__ float3 contact_force(const MeshRT& m, int g, float3 u, float3 v) {
+// total contact force on a node: plane and sphere; `ph` = h - n.X of the
+// node (carried in the .w lane of its velocity)
+__device__ __forceinline__ float3 contact_force(const MeshRT& m, int g, float3 u, float3 v, float ph) {
     float3 f = make_float3(0.f, 0.f, 0.f);
     const ContactParams cp = cparams(m);
     if (m.plane_on) {
         const float3 n = make_float3(m.pnx, m.pny, m.pnz);
-        const float C = m.Xp[g] - dot3(n, u);
+        const float C = ph - dot3(n, u);
         if (C > 0.0f) f += contact_one(v, n, C, cp);
     }
     if (m.sphere_on) {
@@ -60,13 +154,13 @@ __device__ __forceinline__ float3 contact_force(const MeshRT& m, int g, float3 u
 }
 
 // reverse mode of contact_force: adds dL/du, dL/dv for fb = dL/df and returns f
-__device__ __forceinline__ float3 contact_adjoint(const MeshRT& m, int g, float3 u, float3 v, float3 fb, float3& xb,
-                                                  float3& vb) {
+__device__ __forceinline__ float3 contact_adjoint(const MeshRT& m, int g, float3 u, float3 v, float ph, float3 fb,
+                                                  float3& xb, float3& vb) {
     float3 f = make_float3(0.f, 0.f, 0.f);
     const ContactParams cp = cparams(m);
     if (m.plane_on) {
         const float3 n = make_float3(m.pnx, m.pny, m.pnz);
-        const float C = m.Xp[g] - dot3(n, u);
+        const float C = ph - dot3(n, u);
         if (C > 0.0f) {
             float3 vb1, nb, f1;
             float Cb;
@@ -103,7 +197,7 @@ __device__ __forceinline__ void node_forward(const MeshRT& m, int tick, int gid,
     const float3 x = xyz(x4);  // displacement u
     float3 v = xyz(v4);
     const float w = x4.w;
-    const float3 f = fel + contact_force(m, gid, x, v);
+    const float3 f = fel + contact_force(m, gid, x, v, v4.w);
     if (w > 0.0f) {
         v.x = v.x + m.dt * (w * f.x + m.gx);
         v.y = v.y + m.dt * (w * f.y + m.gy);
@@ -111,7 +205,7 @@ __device__ __forceinline__ void node_forward(const MeshRT& m, int tick, int gid,
     }
     const float3 xn = x + m.dt * v;
     const int ob = m.out_a + m.out_b * tick;
-    const float4 xo = f4(xn, w), vo = f4(v, 0.0f);
+    const float4 xo = f4(xn, w), vo = f4(v, v4.w);
     bufx(m, ob)[gid] = xo;
     bufv(m, ob)[gid] = vo;
     if (tick == m.ck_tick) {
@@ -122,131 +216,437 @@ __device__ __forceinline__ void node_forward(const MeshRT& m, int tick, int gid,
         atomicOr(m.status, 1);
 }
 
-// reverse of node_forward for one node.  Inputs: state (x, v) at step n,
+// reverse of node_forward for one node.  Inputs: state (u, v) at step n, the
 // adjoint (xb, vb) of step n+1, the gathered element terms xsum = sum of
-// corner dL/dx and ssum = sum of corner f . v_hat.  Outputs the adjoint of
-// step n in place and accumulates dL/dw (FP64).
-__device__ __forceinline__ void node_adjoint(const MeshRT& m, int gid, float4 x4, float4 v4, float3 xsum, float ssum) {
+// corner dL/du and ssum = sum of corner f . v_hat.  Writes the adjoint of
+// step n and accumulates dL/dw (FP64).
+__device__ __forceinline__ void node_adjoint(const MeshRT& m, int gid, float4 x4, float4 v4, float4 xb4, float4 vb4,
+                                             float3 xsum, float ssum) {
     const float w = x4.w;
-    const float4 xb4 = m.xb[gid], vb4 = m.vb[gid];
     const float3 xbn = xyz(xb4);
     const float3 vh = xyz(vb4) + m.dt * xbn;    // dL/dv+ (total)
     const float3 fb = (m.dt * w) * vh;          // dL/df
     float3 xb = xbn + xsum;
     float3 vb = vh;
-    const float3 fc = contact_adjoint(m, gid, xyz(x4), xyz(v4), fb, xb, vb);
+    const float3 fc = contact_adjoint(m, gid, xyz(x4), xyz(v4), v4.w, fb, xb, vb);
     m.xb[gid] = f4(xb, 0.0f);
     m.vb[gid] = f4(vb, 0.0f);
     m.wbar[gid] += (double)(m.dt * (ssum + dot3(fc, vh)));
 }
 
-}  // namespace
+// A staged patch in shared memory.
+struct Stage {
+    int n_rec;
+    float4* rec;  // planes [4][n_rec]
+    uint16_t* rp;
+    uint16_t* sl;
+    float4* xs;   // local node state (u, w)
+    float4* vh;   // adjoint: v_hat of local nodes
+    float4* vs;   // interior v
+    float4* xb;   // adjoint: interior x_bar
+    float4* vb;   // adjoint: interior v_bar
+    float4* xbB;  // adjoint: boundary x_bar (raw)
+    float4* vbB;  // adjoint: boundary v_bar (raw)
+    double* gmu;  // adjoint: staged accumulators of the patch's elements
+    double* glam;
+};
 
-// ===========================================================================
-// forward
-// ===========================================================================
-// dynamic shared memory: xs[max_loc] (float4) then fc[max_slots] (float4)
-__global__ void k_tet_fwd(const PatchDesc* __restrict__ patches, const MeshRT* __restrict__ rts, int tick) {
-    extern __shared__ float4 smem[];
-    const PatchDesc p = patches[blockIdx.x];
-    const MeshRT& m = rts[p.mesh];
-    if (!(m.active & ACT_FWD)) return;
+__device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned char* buf, bool adjoint) {
     const int n_loc = p.n_int + p.n_bnd;
-    float4* xs = smem;
-    float4* fc = smem + n_loc;
-    const int ib = m.in_a + m.in_b * tick;
-    const float4* __restrict__ X = bufx(m, ib);
-    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) xs[l] = X[local_gid(p, m, l)];
-    __syncthreads();
-    for (int le = threadIdx.x; le < p.n_e; le += blockDim.x) {
-        const int e = p.e_begin + le;
-        const uint2 id = m.eidx[e];
-        const float4 a = m.ea[e], b = m.eb[e], c = m.ec[e];
-        const float act = m.eact ? m.eact[e] : 0.0f;
-        TetState s;
-        tet_state(xyz(xs[id.x & 0xffff]), xyz(xs[id.x >> 16]), xyz(xs[id.y & 0xffff]), xyz(xs[id.y >> 16]), a, b,
-                  c, act, s);
-        float3 f0, f1, f2, f3;
-        tet_forces(s, a, b, c, f0, f1, f2, f3);
-        fc[4 * le + 0] = f4(f0, 0.f);
-        fc[4 * le + 1] = f4(f1, 0.f);
-        fc[4 * le + 2] = f4(f2, 0.f);
-        fc[4 * le + 3] = f4(f3, 0.f);
+    const int n_rec = p.n_e + p.n_h;
+    const int n_slots = (kind == GS_TET ? 4 : 3) * p.n_e + 4 * p.n_h;
+    const Layout L = patch_layout(n_rec, n_loc, p.n_int, n_slots, adjoint);
+    Stage S;
+    S.n_rec = n_rec;
+    S.rec = (float4*)(buf + L.rec);
+    S.rp = (uint16_t*)(buf + L.rp);
+    S.sl = (uint16_t*)(buf + L.sl);
+    S.xs = (float4*)(buf + L.xs);
+    S.vh = (float4*)(buf + L.vh);
+    S.vs = (float4*)(buf + L.vs);
+    S.xb = (float4*)(buf + L.xb);
+    S.vb = (float4*)(buf + L.vb);
+    S.xbB = (float4*)(buf + L.xbB);
+    S.vbB = (float4*)(buf + L.vbB);
+    S.gmu = (double*)(buf + L.gmu);
+    S.glam = (double*)(buf + L.glam);
+    return S;
+}
+
+// state buffers a patch reads
+__device__ __forceinline__ int in_buffer(const MeshRT& m, int tick, bool adjoint) {
+    return adjoint ? m.adj_a + m.adj_b * tick : m.in_a + m.in_b * tick;
+}
+
+// Elected thread: bulk copies of the patch's records, CSR and interior node
+// data into `buf`, completing on `bar` (called by thread 0 only).
+__device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT& m, int tick, unsigned char* buf,
+                                           uint64_t* bar, bool adjoint) {
+    const Stage S = stage_at(p, m.kind, buf, adjoint);
+    const int n_loc = p.n_int + p.n_bnd;
+    const int n_rec = S.n_rec;
+    const int n_slots = (m.kind == GS_TET ? 4 : 3) * p.n_e + 4 * p.n_h;
+    const int ib = in_buffer(m, tick, adjoint);
+    const float4* X = bufx(m, ib);
+    const float4* V = bufv(m, ib);
+    const uint32_t b_rp = r16(2 * (n_loc + 1)), b_sl = r16(2 * n_slots), b_int = 16 * p.n_int;
+    // accumulators are staged for the tet / triangle records (8 B each, the
+    // copy rounded up to 16 B into the arrays' tail padding)
+    const uint32_t b_g = adjoint ? (uint32_t)r16(8 * p.n_e) : 0u;
+    const uint32_t tx = 64u * n_rec + b_rp + b_sl + (p.n_int ? (adjoint ? 4u : 2u) * b_int : 0u) + 2u * b_g;
+    fence_proxy_async();
+    mbar_expect_tx(bar, tx);
+    for (int k = 0; k < 4; ++k) {
+        if (p.n_e) bulk_g2s(S.rec + k * n_rec, m.rec + (size_t)k * m.n_elems + p.e_begin, 16u * p.n_e, bar);
+        if (p.n_h) bulk_g2s(S.rec + k * n_rec + p.n_e, m.hrec + (size_t)k * m.n_hinges + p.h_begin, 16u * p.n_h, bar);
     }
-    __syncthreads();
-    const uint16_t* rp = m.loc_rowptr + p.lr_begin;
-    const uint16_t* sl = m.loc_slots + p.slot_begin;
-    const float4* __restrict__ Vin = bufv(m, ib);
-    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
-        float3 f = make_float3(0.f, 0.f, 0.f);
-        const int k1 = rp[l + 1];
-        for (int k = rp[l]; k < k1; ++k) f += xyz(fc[sl[k]]);
-        if (l < p.n_int) {
-            const int gid = p.int_begin + l;
-            node_forward(m, tick, gid, xs[l], Vin[gid], f);
-        } else {
-            m.partials[p.bnd_begin + (l - p.n_int)] = f4(f, 0.f);
+    bulk_g2s(S.rp, m.loc_rowptr + p.lr_begin, b_rp, bar);
+    bulk_g2s(S.sl, m.loc_slots + p.slot_begin, b_sl, bar);
+    if (p.n_int) {
+        bulk_g2s(S.xs, X + p.int_begin, b_int, bar);
+        bulk_g2s(S.vs, V + p.int_begin, b_int, bar);
+        if (adjoint) {
+            bulk_g2s(S.xb, m.xb + p.int_begin, b_int, bar);
+            bulk_g2s(S.vb, m.vb + p.int_begin, b_int, bar);
+        }
+    }
+    if (b_g) {
+        bulk_g2s(S.gmu, m.g_mu + p.e_begin, b_g, bar);
+        bulk_g2s(S.glam, m.g_lam + p.e_begin, b_g, bar);
+    }
+}
+
+// boundary-node ids held in registers between their load and the gather
+constexpr int kIdsPerThread = 4;
+
+__device__ __forceinline__ void load_ids(const PatchDesc& p, const MeshRT& m, int* ids) {
+#pragma unroll
+    for (int j = 0; j < kIdsPerThread; ++j) {
+        const int k = threadIdx.x + j * blockDim.x;
+        ids[j] = k < p.n_bnd ? m.bnd_ids[p.bnd_begin + k] : 0;
+    }
+}
+
+// all threads: asynchronous gather of the boundary nodes into `buf`
+__device__ __forceinline__ void issue_gather(const PatchDesc& p, const MeshRT& m, int tick, unsigned char* buf,
+                                             bool adjoint, const int* ids) {
+    const Stage S = stage_at(p, m.kind, buf, adjoint);
+    const float4* X = bufx(m, in_buffer(m, tick, adjoint));
+#pragma unroll
+    for (int j = 0; j < kIdsPerThread; ++j) {
+        const int k = threadIdx.x + j * blockDim.x;
+        if (k < p.n_bnd) {
+            const int g = ids[j];
+            cp16(S.xs + p.n_int + k, X + g);
+            if (adjoint) {
+                cp16(S.xbB + k, m.xb + g);
+                cp16(S.vbB + k, m.vb + g);
+            }
+        }
+    }
+    for (int k = threadIdx.x + kIdsPerThread * blockDim.x; k < p.n_bnd; k += blockDim.x) {
+        const int g = m.bnd_ids[p.bnd_begin + k];
+        cp16(S.xs + p.n_int + k, X + g);
+        if (adjoint) {
+            cp16(S.xbB + k, m.xb + g);
+            cp16(S.vbB + k, m.vb + g);
         }
     }
 }
 
-// cloth: triangles (3 corner slots each) then hinges (4 each)
-__global__ void k_cloth_fwd(const PatchDesc* __restrict__ patches, const MeshRT* __restrict__ rts, int tick) {
-    extern __shared__ float4 smem[];
-    const PatchDesc p = patches[blockIdx.x];
-    const MeshRT& m = rts[p.mesh];
-    if (!(m.active & ACT_FWD)) return;
-    const int n_loc = p.n_int + p.n_bnd;
-    float4* xs = smem;
-    float4* fc = smem + n_loc;
-    const int ib = m.in_a + m.in_b * tick;
-    const float4* __restrict__ X = bufx(m, ib);
-    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) xs[l] = X[local_gid(p, m, l)];
-    __syncthreads();
-    for (int lt = threadIdx.x; lt < p.n_e; lt += blockDim.x) {
-        const int t = p.e_begin + lt;
-        const uint2 id = m.eidx[t];
-        const float4 a = m.ea[t], b = m.eb[t], r = m.ec[t];
-        const float2 r2 = m.ed[t];
-        TriState s;
-        tri_state(xyz(xs[id.x & 0xffff]), xyz(xs[id.x >> 16]), xyz(xs[id.y & 0xffff]), a, b,
-                  make_float3(r.x, r.y, r.z), make_float3(r.w, r2.x, r2.y), s);
-        float3 f0, f1, f2;
-        tri_forces(s, a, b, f0, f1, f2);
-        fc[3 * lt + 0] = f4(f0, 0.f);
-        fc[3 * lt + 1] = f4(f1, 0.f);
-        fc[3 * lt + 2] = f4(f2, 0.f);
+// corner result of slot s (record << 2 | corner): plane (s & 3), row (s >> 2)
+__device__ __forceinline__ float4 corner4(const Stage& S, int s) { return S.rec[(s & 3) * S.n_rec + (s >> 2)]; }
+__device__ __forceinline__ float3 corner3(const Stage& S, int s) { return xyz(corner4(S, s)); }
+__device__ __forceinline__ void put(const Stage& S, int r, int c, float4 f) { S.rec[c * S.n_rec + r] = f; }
+
+// ---------------------------------------------------------------------------
+// element phases (one thread per element record)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tet_elements_fwd(const PatchDesc& p, const Stage& S) {
+    const int nr = S.n_rec;
+    for (int le = threadIdx.x; le < p.n_e; le += blockDim.x) {
+        const float4 a = S.rec[le], b = S.rec[nr + le], c = S.rec[2 * nr + le], w = S.rec[3 * nr + le];
+        const uint2 id = rec_ids(w);
+        TetState s;
+        tet_state(xyz(S.xs[id.x & 0xffff]), xyz(S.xs[id.x >> 16]), xyz(S.xs[id.y & 0xffff]), xyz(S.xs[id.y >> 16]), a,
+                  b, c, w.z, s);
+        float3 f0, f1, f2, f3;
+        tet_forces(s, a, b, c, f0, f1, f2, f3);
+        put(S, le, 0, f4(f0, 0.f));
+        put(S, le, 1, f4(f1, 0.f));
+        put(S, le, 2, f4(f2, 0.f));
+        put(S, le, 3, f4(f3, 0.f));
     }
-    float4* fh = fc + 3 * p.n_e;
-    for (int lh = threadIdx.x; lh < p.n_h; lh += blockDim.x) {
-        const int h = p.h_begin + lh;
-        const uint2 id = m.hidx[h];
-        const float4 q0 = m.hq[3 * h], q1 = m.hq[3 * h + 1], q2 = m.hq[3 * h + 2];
-        HingeState s;
-        hinge_state(xyz(xs[id.x & 0xffff]), xyz(xs[id.x >> 16]), xyz(xs[id.y & 0xffff]), xyz(xs[id.y >> 16]),
-                    xyz(q0), xyz(q1), xyz(q2), q1.w, s);
-        float3 f1, f2, f3, f4_;
-        hinge_forces(s, q0.w, f1, f2, f3, f4_);
-        fh[4 * lh + 0] = f4(f1, 0.f);
-        fh[4 * lh + 1] = f4(f2, 0.f);
-        fh[4 * lh + 2] = f4(f3, 0.f);
-        fh[4 * lh + 3] = f4(f4_, 0.f);
-    }
-    __syncthreads();
-    const uint16_t* rp = m.loc_rowptr + p.lr_begin;
-    const uint16_t* sl = m.loc_slots + p.slot_begin;
-    const float4* __restrict__ Vin = bufv(m, ib);
-    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
-        float3 f = make_float3(0.f, 0.f, 0.f);
-        const int k1 = rp[l + 1];
-        for (int k = rp[l]; k < k1; ++k) f += xyz(fc[sl[k]]);
-        if (l < p.n_int) {
-            const int gid = p.int_begin + l;
-            node_forward(m, tick, gid, xs[l], Vin[gid], f);
+}
+
+__device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Stage& S) {
+    const int nr = S.n_rec;
+    for (int lr = threadIdx.x; lr < nr; lr += blockDim.x) {
+        const float4 a = S.rec[lr], b = S.rec[nr + lr], c = S.rec[2 * nr + lr], w = S.rec[3 * nr + lr];
+        const uint2 id = rec_ids(w);
+        if (lr < p.n_e) {
+            TriState s;
+            tri_state(xyz(S.xs[id.x & 0xffff]), xyz(S.xs[id.x >> 16]), xyz(S.xs[id.y & 0xffff]), a, b,
+                      make_float3(c.x, c.y, c.z), make_float3(c.w, w.z, w.w), s);
+            float3 f0, f1, f2;
+            tri_forces(s, a, b, f0, f1, f2);
+            put(S, lr, 0, f4(f0, 0.f));
+            put(S, lr, 1, f4(f1, 0.f));
+            put(S, lr, 2, f4(f2, 0.f));
         } else {
-            m.partials[p.bnd_begin + (l - p.n_int)] = f4(f, 0.f);
+            HingeState s;
+            hinge_state(xyz(S.xs[id.x & 0xffff]), xyz(S.xs[id.x >> 16]), xyz(S.xs[id.y & 0xffff]),
+                        xyz(S.xs[id.y >> 16]), xyz(a), xyz(b), xyz(c), b.w, s);
+            float3 f1, f2, f3, f4_;
+            hinge_forces(s, a.w, f1, f2, f3, f4_);
+            put(S, lr, 0, f4(f1, 0.f));
+            put(S, lr, 1, f4(f2, 0.f));
+            put(S, lr, 2, f4(f3, 0.f));
+            put(S, lr, 3, f4(f4_, 0.f));
         }
     }
+}
+
+// corner result (dL/du_corner, f_corner . v_hat_node) in place
+__device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshRT& m, const Stage& S) {
+    const float dt = m.dt;
+    const int nr = S.n_rec;
+    for (int le = threadIdx.x; le < p.n_e; le += blockDim.x) {
+        const float4 a = S.rec[le], b = S.rec[nr + le], c = S.rec[2 * nr + le], w = S.rec[3 * nr + le];
+        const uint2 id = rec_ids(w);
+        const int i0 = id.x & 0xffff, i1 = id.x >> 16, i2 = id.y & 0xffff, i3 = id.y >> 16;
+        const float4 x0 = S.xs[i0], x1 = S.xs[i1], x2 = S.xs[i2], x3 = S.xs[i3];
+        const float3 v0 = xyz(S.vh[i0]), v1 = xyz(S.vh[i1]), v2 = xyz(S.vh[i2]), v3 = xyz(S.vh[i3]);
+        TetState s;
+        tet_state(xyz(x0), xyz(x1), xyz(x2), xyz(x3), a, b, c, w.z, s);
+        float3 f0, f1, f2, f3;
+        tet_forces(s, a, b, c, f0, f1, f2, f3);
+        float3 xb0, xb1, xb2, xb3;
+        float gmu, glam, gact;
+        tet_adjoint(s, a, b, c, (dt * x0.w) * v0, (dt * x1.w) * v1, (dt * x2.w) * v2, (dt * x3.w) * v3, xb0, xb1,
+                    xb2, xb3, gmu, glam, gact);
+        put(S, le, 0, f4(xb0, dot3(f0, v0)));
+        put(S, le, 1, f4(xb1, dot3(f1, v1)));
+        put(S, le, 2, f4(xb2, dot3(f2, v2)));
+        put(S, le, 3, f4(xb3, dot3(f3, v3)));
+        const int e = p.e_begin + le;
+        m.g_mu[e] = S.gmu[le] + (double)gmu;
+        m.g_lam[e] = S.glam[le] + (double)glam;
+        if (m.g_act) m.g_act[e] += (double)gact;
+    }
+}
+
+__device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const MeshRT& m, const Stage& S) {
+    const float dt = m.dt;
+    const int nr = S.n_rec;
+    for (int lr = threadIdx.x; lr < nr; lr += blockDim.x) {
+        const float4 a = S.rec[lr], b = S.rec[nr + lr], c = S.rec[2 * nr + lr], w = S.rec[3 * nr + lr];
+        const uint2 id = rec_ids(w);
+        if (lr < p.n_e) {
+            const int i0 = id.x & 0xffff, i1 = id.x >> 16, i2 = id.y & 0xffff;
+            const float4 x0 = S.xs[i0], x1 = S.xs[i1], x2 = S.xs[i2];
+            const float3 v0 = xyz(S.vh[i0]), v1 = xyz(S.vh[i1]), v2 = xyz(S.vh[i2]);
+            TriState s;
+            tri_state(xyz(x0), xyz(x1), xyz(x2), a, b, make_float3(c.x, c.y, c.z), make_float3(c.w, w.z, w.w), s);
+            float3 f0, f1, f2;
+            tri_forces(s, a, b, f0, f1, f2);
+            float3 xb0, xb1, xb2;
+            float gmu, glam, gact;
+            tri_adjoint(s, a, b, (dt * x0.w) * v0, (dt * x1.w) * v1, (dt * x2.w) * v2, xb0, xb1, xb2, gmu, glam, gact);
+            put(S, lr, 0, f4(xb0, dot3(f0, v0)));
+            put(S, lr, 1, f4(xb1, dot3(f1, v1)));
+            put(S, lr, 2, f4(xb2, dot3(f2, v2)));
+            const int t = p.e_begin + lr;
+            m.g_mu[t] = S.gmu[lr] + (double)gmu;
+            m.g_lam[t] = S.glam[lr] + (double)glam;
+            if (m.g_act) m.g_act[t] += (double)gact;
+        } else {
+            const int i1 = id.x & 0xffff, i2 = id.x >> 16, i3 = id.y & 0xffff, i4 = id.y >> 16;
+            const float4 x1 = S.xs[i1], x2 = S.xs[i2], x3 = S.xs[i3], x4 = S.xs[i4];
+            const float3 v1 = xyz(S.vh[i1]), v2 = xyz(S.vh[i2]), v3 = xyz(S.vh[i3]), v4 = xyz(S.vh[i4]);
+            HingeState s;
+            hinge_state(xyz(x1), xyz(x2), xyz(x3), xyz(x4), xyz(a), xyz(b), xyz(c), b.w, s);
+            float3 f1, f2, f3, f4_;
+            hinge_forces(s, a.w, f1, f2, f3, f4_);
+            float3 xb1, xb2, xb3, xb4;
+            float gkb, gact;
+            hinge_adjoint(s, a.w, (dt * x1.w) * v1, (dt * x2.w) * v2, (dt * x3.w) * v3, (dt * x4.w) * v4, xb1, xb2,
+                          xb3, xb4, gkb, gact);
+            put(S, lr, 0, f4(xb1, dot3(f1, v1)));
+            put(S, lr, 1, f4(xb2, dot3(f2, v2)));
+            put(S, lr, 2, f4(xb3, dot3(f3, v3)));
+            put(S, lr, 3, f4(xb4, dot3(f4_, v4)));
+            const int h = p.h_begin + (lr - p.n_e);
+            m.g_kb[h] += (double)gkb;
+            if (m.g_hact) m.g_hact[h] += (double)gact;
+        }
+    }
+}
+
+// Fixed-order sum of the corner results of CSR row [k, k1): four slots at a
+// time with all loads issued before the adds (the adds stay in row order, so
+// the result is the same as a one-by-one walk).
+__device__ __forceinline__ void add4(float4& acc, float4 q) {
+    acc.x += q.x;
+    acc.y += q.y;
+    acc.z += q.z;
+    acc.w += q.w;
+}
+__device__ __forceinline__ float4 row_sum(const Stage& S, int k, int k1) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (; k + 4 <= k1; k += 4) {
+        const int s0 = S.sl[k], s1 = S.sl[k + 1], s2 = S.sl[k + 2], s3 = S.sl[k + 3];
+        const float4 q0 = corner4(S, s0), q1 = corner4(S, s1), q2 = corner4(S, s2), q3 = corner4(S, s3);
+        add4(acc, q0);
+        add4(acc, q1);
+        add4(acc, q2);
+        add4(acc, q3);
+    }
+    for (; k < k1; ++k) add4(acc, corner4(S, S.sl[k]));
+    return acc;
+}
+
+// node phases: fixed-order corner sums, then interior update or partial
+__device__ __forceinline__ void forward_nodes(const PatchDesc& p, const MeshRT& m, int tick, const Stage& S) {
+    const int n_loc = p.n_int + p.n_bnd;
+    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
+        const float3 f = xyz(row_sum(S, S.rp[l], S.rp[l + 1]));
+        if (l < p.n_int) node_forward(m, tick, p.int_begin + l, S.xs[l], S.vs[l], f);
+        else m.partials[p.bnd_begin + (l - p.n_int)] = f4(f, 0.f);
+    }
+}
+
+__device__ __forceinline__ void adjoint_nodes(const PatchDesc& p, const MeshRT& m, const Stage& S) {
+    const int n_loc = p.n_int + p.n_bnd;
+    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
+        const float4 acc = row_sum(S, S.rp[l], S.rp[l + 1]);
+        if (l < p.n_int) node_adjoint(m, p.int_begin + l, S.xs[l], S.vs[l], S.xb[l], S.vb[l], xyz(acc), acc.w);
+        else m.partials[p.bnd_begin + (l - p.n_int)] = acc;
+    }
+}
+
+// boundary nodes: partials of the row in patch order, loads grouped by four
+__device__ __forceinline__ float4 partial_sum(const MeshRT& m, int b) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int k = m.bnd_rowptr[b];
+    const int k1 = m.bnd_rowptr[b + 1];
+    for (; k + 4 <= k1; k += 4) {
+        const int s0 = m.bnd_parts[k], s1 = m.bnd_parts[k + 1], s2 = m.bnd_parts[k + 2], s3 = m.bnd_parts[k + 3];
+        const float4 q0 = m.partials[s0], q1 = m.partials[s1], q2 = m.partials[s2], q3 = m.partials[s3];
+        add4(acc, q0);
+        add4(acc, q1);
+        add4(acc, q2);
+        add4(acc, q3);
+    }
+    for (; k < k1; ++k) add4(acc, m.partials[m.bnd_parts[k]]);
+    return acc;
+}
+
+// ---------------------------------------------------------------------------
+// the pipeline: a persistent CTA walks patches blockIdx.x, +gridDim.x, ...
+// with two shared-memory stages; while patch i computes, patch i+1's bulk
+// copies and boundary gathers are in flight.
+// ---------------------------------------------------------------------------
+template <int KIND, bool ADJ>
+__device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ patches, int n_patches,
+                                               const MeshRT* __restrict__ rts, int tick, int stage_bytes) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t* bars = (uint64_t*)sm;
+    unsigned char* const buf0 = sm + 128;
+    const int mask = ADJ ? ACT_ADJ : ACT_FWD;
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0]);
+        mbar_init(&bars[1]);
+    }
+    __syncthreads();
+    uint32_t parity = 0u;  // bit b: phase parity of buffer b's barrier
+    int ids[kIdsPerThread];
+    // prologue: stage the first patch into buffer 0
+    int pi = blockIdx.x;
+    bool live = pi < n_patches && (rts[patches[pi].mesh].active & mask);
+    if (live) {
+        const PatchDesc p = patches[pi];
+        const MeshRT& m = rts[p.mesh];
+        if (threadIdx.x == 0) issue_bulk(p, m, tick, buf0, &bars[0], ADJ);
+        load_ids(p, m, ids);
+        issue_gather(p, m, tick, buf0, ADJ, ids);
+    }
+    cp_commit();
+    for (int it = 0; pi < n_patches; ++it, pi += gridDim.x) {
+        const int cur = it & 1, nxt = cur ^ 1;
+        unsigned char* const bcur = buf0 + cur * stage_bytes;
+        unsigned char* const bnxt = buf0 + nxt * stage_bytes;
+        const int pn = pi + gridDim.x;
+        const bool live_n = pn < n_patches && (rts[patches[pn].mesh].active & mask);
+        if (live_n) {
+            const PatchDesc q = patches[pn];
+            const MeshRT& mq = rts[q.mesh];
+            if (threadIdx.x == 0) issue_bulk(q, mq, tick, bnxt, &bars[nxt], ADJ);
+            load_ids(q, mq, ids);
+        }
+        const PatchDesc p = patches[pi];
+        const MeshRT& m = rts[p.mesh];
+        Stage S = stage_at(p, KIND, bcur, ADJ);
+        if (live) {
+            cp_wait_all();
+            const bool ok = mbar_wait_bounded(&bars[cur], (parity >> cur) & 1u, m.status);
+            parity ^= 1u << cur;
+            if (__syncthreads_or(!ok)) return;
+            if (ADJ) {
+                for (int l = threadIdx.x; l < p.n_int; l += blockDim.x)
+                    S.vh[l] = f4(xyz(S.vb[l]) + m.dt * xyz(S.xb[l]), 0.f);
+                for (int k = threadIdx.x; k < p.n_bnd; k += blockDim.x)
+                    S.vh[p.n_int + k] = f4(xyz(S.vbB[k]) + m.dt * xyz(S.xbB[k]), 0.f);
+                __syncthreads();
+            }
+            if (KIND == GS_TET) {
+                if (ADJ) tet_elements_adj(p, m, S);
+                else tet_elements_fwd(p, S);
+            } else {
+                if (ADJ) cloth_elements_adj(p, m, S);
+                else cloth_elements_fwd(p, S);
+            }
+        }
+        // the next patch's boundary gathers, issued before this patch's node phase
+        if (live_n) {
+            const PatchDesc q = patches[pn];
+            issue_gather(q, rts[q.mesh], tick, bnxt, ADJ, ids);
+        }
+        cp_commit();
+        if (live) {
+            __syncthreads();
+            if (ADJ) adjoint_nodes(p, m, S);
+            else forward_nodes(p, m, tick, S);
+        }
+        // this thread's generic shared writes of buffer `cur` are ordered before
+        // the async-proxy (bulk copy) writes that will refill it
+        fence_proxy_async();
+        __syncthreads();  // buffer `cur` is free for the patch after next
+        live = live_n;
+    }
+    cp_wait_all();
+}
+
+}  // namespace
+
+// ===========================================================================
+// patch kernels (persistent, pipelined)
+// ===========================================================================
+__global__ void k_tet_fwd(const PatchDesc* __restrict__ patches, int n_patches, const MeshRT* __restrict__ rts,
+                          int tick, int stage_bytes) {
+    patch_pipeline<GS_TET, false>(patches, n_patches, rts, tick, stage_bytes);
+}
+__global__ void k_cloth_fwd(const PatchDesc* __restrict__ patches, int n_patches, const MeshRT* __restrict__ rts,
+                            int tick, int stage_bytes) {
+    patch_pipeline<GS_CLOTH, false>(patches, n_patches, rts, tick, stage_bytes);
+}
+__global__ void k_tet_adj(const PatchDesc* __restrict__ patches, int n_patches, const MeshRT* __restrict__ rts,
+                          int tick, int stage_bytes) {
+    patch_pipeline<GS_TET, true>(patches, n_patches, rts, tick, stage_bytes);
+}
+__global__ void k_cloth_adj(const PatchDesc* __restrict__ patches, int n_patches, const MeshRT* __restrict__ rts,
+                            int tick, int stage_bytes) {
+    patch_pipeline<GS_CLOTH, true>(patches, n_patches, rts, tick, stage_bytes);
 }
 
 // boundary nodes: sum the per-patch partials in patch order, then finish
@@ -257,161 +657,9 @@ __global__ void k_fwd_boundary(const NodeBlock* __restrict__ blocks, const MeshR
     const int ib = m.in_a + m.in_b * tick;
     for (int i = threadIdx.x; i < nb.count; i += blockDim.x) {
         const int b = nb.begin + i;
-        float3 f = make_float3(0.f, 0.f, 0.f);
-        const int k1 = m.bnd_rowptr[b + 1];
-        for (int k = m.bnd_rowptr[b]; k < k1; ++k) f += xyz(m.partials[m.bnd_parts[k]]);
         const int gid = m.n_int + b;
-        node_forward(m, tick, gid, bufx(m, ib)[gid], bufv(m, ib)[gid], f);
-    }
-}
-
-// ===========================================================================
-// adjoint
-// ===========================================================================
-// dynamic shared memory: xs[max_loc], vh[max_loc], fc[max_slots] (float4)
-// corner result: (dL/dx_corner, f_corner . v_hat_node)
-__global__ void k_tet_adj(const PatchDesc* __restrict__ patches, const MeshRT* __restrict__ rts, int tick) {
-    extern __shared__ float4 smem[];
-    const PatchDesc p = patches[blockIdx.x];
-    const MeshRT& m = rts[p.mesh];
-    if (!(m.active & ACT_ADJ)) return;
-    const int n_loc = p.n_int + p.n_bnd;
-    float4* xs = smem;
-    float4* vh = smem + n_loc;
-    float4* fc = vh + n_loc;
-    const int sb = m.adj_a + m.adj_b * tick;
-    const float4* __restrict__ X = bufx(m, sb);
-    const float dt = m.dt;
-    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
-        const int g = local_gid(p, m, l);
-        xs[l] = X[g];
-        vh[l] = f4(xyz(m.vb[g]) + dt * xyz(m.xb[g]), 0.f);
-    }
-    __syncthreads();
-    for (int le = threadIdx.x; le < p.n_e; le += blockDim.x) {
-        const int e = p.e_begin + le;
-        const uint2 id = m.eidx[e];
-        const int i0 = id.x & 0xffff, i1 = id.x >> 16, i2 = id.y & 0xffff, i3 = id.y >> 16;
-        const float4 a = m.ea[e], b = m.eb[e], c = m.ec[e];
-        const float act = m.eact ? m.eact[e] : 0.0f;
-        const float4 x0 = xs[i0], x1 = xs[i1], x2 = xs[i2], x3 = xs[i3];
-        const float3 v0 = xyz(vh[i0]), v1 = xyz(vh[i1]), v2 = xyz(vh[i2]), v3 = xyz(vh[i3]);
-        TetState s;
-        tet_state(xyz(x0), xyz(x1), xyz(x2), xyz(x3), a, b, c, act, s);
-        float3 f0, f1, f2, f3;
-        tet_forces(s, a, b, c, f0, f1, f2, f3);
-        float3 xb0, xb1, xb2, xb3;
-        float gmu, glam, gact;
-        tet_adjoint(s, a, b, c, (dt * x0.w) * v0, (dt * x1.w) * v1, (dt * x2.w) * v2, (dt * x3.w) * v3, xb0, xb1,
-                    xb2, xb3, gmu, glam, gact);
-        fc[4 * le + 0] = f4(xb0, dot3(f0, v0));
-        fc[4 * le + 1] = f4(xb1, dot3(f1, v1));
-        fc[4 * le + 2] = f4(xb2, dot3(f2, v2));
-        fc[4 * le + 3] = f4(xb3, dot3(f3, v3));
-        m.g_mu[e] += (double)gmu;
-        m.g_lam[e] += (double)glam;
-        if (m.g_act) m.g_act[e] += (double)gact;
-    }
-    __syncthreads();
-    const uint16_t* rp = m.loc_rowptr + p.lr_begin;
-    const uint16_t* sl = m.loc_slots + p.slot_begin;
-    const float4* __restrict__ V = bufv(m, sb);
-    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int k1 = rp[l + 1];
-        for (int k = rp[l]; k < k1; ++k) {
-            const float4 q = fc[sl[k]];
-            acc.x += q.x; acc.y += q.y; acc.z += q.z; acc.w += q.w;
-        }
-        if (l < p.n_int) {
-            const int gid = p.int_begin + l;
-            node_adjoint(m, gid, xs[l], V[gid], xyz(acc), acc.w);
-        } else {
-            m.partials[p.bnd_begin + (l - p.n_int)] = acc;
-        }
-    }
-}
-
-__global__ void k_cloth_adj(const PatchDesc* __restrict__ patches, const MeshRT* __restrict__ rts, int tick) {
-    extern __shared__ float4 smem[];
-    const PatchDesc p = patches[blockIdx.x];
-    const MeshRT& m = rts[p.mesh];
-    if (!(m.active & ACT_ADJ)) return;
-    const int n_loc = p.n_int + p.n_bnd;
-    float4* xs = smem;
-    float4* vh = smem + n_loc;
-    float4* fc = vh + n_loc;
-    const int sb = m.adj_a + m.adj_b * tick;
-    const float4* __restrict__ X = bufx(m, sb);
-    const float dt = m.dt;
-    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
-        const int g = local_gid(p, m, l);
-        xs[l] = X[g];
-        vh[l] = f4(xyz(m.vb[g]) + dt * xyz(m.xb[g]), 0.f);
-    }
-    __syncthreads();
-    for (int lt = threadIdx.x; lt < p.n_e; lt += blockDim.x) {
-        const int t = p.e_begin + lt;
-        const uint2 id = m.eidx[t];
-        const int i0 = id.x & 0xffff, i1 = id.x >> 16, i2 = id.y & 0xffff;
-        const float4 a = m.ea[t], b = m.eb[t], r = m.ec[t];
-        const float2 r2 = m.ed[t];
-        const float4 x0 = xs[i0], x1 = xs[i1], x2 = xs[i2];
-        const float3 v0 = xyz(vh[i0]), v1 = xyz(vh[i1]), v2 = xyz(vh[i2]);
-        TriState s;
-        tri_state(xyz(x0), xyz(x1), xyz(x2), a, b, make_float3(r.x, r.y, r.z), make_float3(r.w, r2.x, r2.y), s);
-        float3 f0, f1, f2;
-        tri_forces(s, a, b, f0, f1, f2);
-        float3 xb0, xb1, xb2;
-        float gmu, glam, gact;
-        tri_adjoint(s, a, b, (dt * x0.w) * v0, (dt * x1.w) * v1, (dt * x2.w) * v2, xb0, xb1, xb2, gmu, glam, gact);
-        fc[3 * lt + 0] = f4(xb0, dot3(f0, v0));
-        fc[3 * lt + 1] = f4(xb1, dot3(f1, v1));
-        fc[3 * lt + 2] = f4(xb2, dot3(f2, v2));
-        m.g_mu[t] += (double)gmu;
-        m.g_lam[t] += (double)glam;
-        if (m.g_act) m.g_act[t] += (double)gact;
-    }
-    float4* fh = fc + 3 * p.n_e;
-    for (int lh = threadIdx.x; lh < p.n_h; lh += blockDim.x) {
-        const int h = p.h_begin + lh;
-        const uint2 id = m.hidx[h];
-        const int i1 = id.x & 0xffff, i2 = id.x >> 16, i3 = id.y & 0xffff, i4 = id.y >> 16;
-        const float4 q0 = m.hq[3 * h], q1 = m.hq[3 * h + 1], q2 = m.hq[3 * h + 2];
-        const float4 x1 = xs[i1], x2 = xs[i2], x3 = xs[i3], x4 = xs[i4];
-        const float3 v1 = xyz(vh[i1]), v2 = xyz(vh[i2]), v3 = xyz(vh[i3]), v4 = xyz(vh[i4]);
-        HingeState s;
-        hinge_state(xyz(x1), xyz(x2), xyz(x3), xyz(x4), xyz(q0), xyz(q1), xyz(q2), q1.w, s);
-        float3 f1, f2, f3, f4_;
-        hinge_forces(s, q0.w, f1, f2, f3, f4_);
-        float3 xb1, xb2, xb3, xb4;
-        float gkb, gact;
-        hinge_adjoint(s, q0.w, (dt * x1.w) * v1, (dt * x2.w) * v2, (dt * x3.w) * v3, (dt * x4.w) * v4, xb1, xb2, xb3,
-                      xb4, gkb, gact);
-        fh[4 * lh + 0] = f4(xb1, dot3(f1, v1));
-        fh[4 * lh + 1] = f4(xb2, dot3(f2, v2));
-        fh[4 * lh + 2] = f4(xb3, dot3(f3, v3));
-        fh[4 * lh + 3] = f4(xb4, dot3(f4_, v4));
-        m.g_kb[h] += (double)gkb;
-        if (m.g_hact) m.g_hact[h] += (double)gact;
-    }
-    __syncthreads();
-    const uint16_t* rp = m.loc_rowptr + p.lr_begin;
-    const uint16_t* sl = m.loc_slots + p.slot_begin;
-    const float4* __restrict__ V = bufv(m, sb);
-    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int k1 = rp[l + 1];
-        for (int k = rp[l]; k < k1; ++k) {
-            const float4 q = fc[sl[k]];
-            acc.x += q.x; acc.y += q.y; acc.z += q.z; acc.w += q.w;
-        }
-        if (l < p.n_int) {
-            const int gid = p.int_begin + l;
-            node_adjoint(m, gid, xs[l], V[gid], xyz(acc), acc.w);
-        } else {
-            m.partials[p.bnd_begin + (l - p.n_int)] = acc;
-        }
+        const float4 x4 = bufx(m, ib)[gid], v4 = bufv(m, ib)[gid];
+        node_forward(m, tick, gid, x4, v4, xyz(partial_sum(m, b)));
     }
 }
 
@@ -422,14 +670,10 @@ __global__ void k_adj_boundary(const NodeBlock* __restrict__ blocks, const MeshR
     const int sb = m.adj_a + m.adj_b * tick;
     for (int i = threadIdx.x; i < nb.count; i += blockDim.x) {
         const int b = nb.begin + i;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int k1 = m.bnd_rowptr[b + 1];
-        for (int k = m.bnd_rowptr[b]; k < k1; ++k) {
-            const float4 q = m.partials[m.bnd_parts[k]];
-            acc.x += q.x; acc.y += q.y; acc.z += q.z; acc.w += q.w;
-        }
         const int gid = m.n_int + b;
-        node_adjoint(m, gid, bufx(m, sb)[gid], bufv(m, sb)[gid], xyz(acc), acc.w);
+        const float4 x4 = bufx(m, sb)[gid], v4 = bufv(m, sb)[gid], xb4 = m.xb[gid], vb4 = m.vb[gid];
+        const float4 acc = partial_sum(m, b);
+        node_adjoint(m, gid, x4, v4, xb4, vb4, xyz(acc), acc.w);
     }
 }
 
@@ -522,7 +766,7 @@ __global__ void k_setup_patch(const PatchDesc* __restrict__ patches, const MeshR
     const MeshRT& m = rts[p.mesh];
     const int n_loc = p.n_int + p.n_bnd;
     double* xs = dsm;               // 3 per local node
-    double* mc = dsm + 3 * n_loc;   // one per corner slot
+    double* mc = dsm + 3 * n_loc;   // one per slot code (record << 2 | corner)
     for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
         const int g = local_gid(p, m, l);
         xs[3 * l] = a.X[3 * g];
@@ -533,7 +777,7 @@ __global__ void k_setup_patch(const PatchDesc* __restrict__ patches, const MeshR
     const int nc = m.kind == GS_TET ? 4 : 3;
     for (int le = threadIdx.x; le < p.n_e; le += blockDim.x) {
         const int e = p.e_begin + le;
-        const uint2 id = m.eidx[e];
+        const uint2 id = rec_ids(m.rec[3 * (size_t)m.n_elems + e]);
         const int li[4] = {(int)(id.x & 0xffff), (int)(id.x >> 16), (int)(id.y & 0xffff), (int)(id.y >> 16)};
         double share;
         if (m.kind == GS_TET) {
@@ -556,12 +800,13 @@ __global__ void k_setup_patch(const PatchDesc* __restrict__ patches, const MeshR
             const double i22 = (D[0][0] * D[1][1] - D[0][1] * D[1][0]) * id_;
             const double V = det / 6.0;
             if (a.geometry) {
-                m.ea[e] = make_float4((float)i00, (float)i01, (float)i02, (float)i10);
-                m.eb[e] = make_float4((float)i11, (float)i12, (float)i20, (float)i21);
-                float4 c = m.ec[e];
+                const size_t E = m.n_elems;
+                m.rec[e] = make_float4((float)i00, (float)i01, (float)i02, (float)i10);
+                m.rec[E + e] = make_float4((float)i11, (float)i12, (float)i20, (float)i21);
+                float4 c = m.rec[2 * E + e];
                 c.x = (float)i22;
                 c.y = (float)V;
-                m.ec[e] = c;
+                m.rec[2 * E + e] = c;
             }
             share = (double)a.rho[e] * V / 4.0;
         } else {
@@ -589,31 +834,36 @@ __global__ void k_setup_patch(const PatchDesc* __restrict__ patches, const MeshR
             const double area = 0.5 * ln;
             if (a.geometry) {
                 const double d00 = A22 / det, d01 = -A12 / det, d10 = -A21 / det, d11 = A11 / det;
-                m.ea[e] = make_float4((float)d00, (float)d01, (float)d10, (float)d11);
-                float4 b = m.eb[e];
+                const size_t E = m.n_elems;
+                m.rec[e] = make_float4((float)d00, (float)d01, (float)d10, (float)d11);
+                float4 b = m.rec[E + e];
                 b.x = (float)area;
-                m.eb[e] = b;
+                m.rec[E + e] = b;
                 // rest frame R0 = Ds_rest Dm^-1 (orthonormal columns)
                 double r0[3], r1[3];
                 for (int r = 0; r < 3; ++r) {
                     r0[r] = e1[r] * d00 + e2[r] * d10;
                     r1[r] = e1[r] * d01 + e2[r] * d11;
                 }
-                m.ec[e] = make_float4((float)r0[0], (float)r0[1], (float)r0[2], (float)r1[0]);
-                m.ed[e] = make_float2((float)r1[1], (float)r1[2]);
+                m.rec[2 * E + e] = make_float4((float)r0[0], (float)r0[1], (float)r0[2], (float)r1[0]);
+                float4 w = m.rec[3 * E + e];
+                w.z = (float)r1[1];
+                w.w = (float)r1[2];
+                m.rec[3 * E + e] = w;
             }
             share = (double)a.rho[e] * area / 3.0;
         }
-        for (int c = 0; c < nc; ++c) mc[nc * le + c] = share;
+        for (int c = 0; c < 4; ++c) mc[4 * le + c] = c < nc ? share : 0.0;
     }
     // hinge corners carry no mass; hinge rest vectors X1-X3, X2-X3, X4-X3
-    for (int lh = threadIdx.x; lh < 4 * p.n_h; lh += blockDim.x) mc[3 * p.n_e + lh] = 0.0;
+    for (int lh = threadIdx.x; lh < 4 * p.n_h; lh += blockDim.x) mc[4 * p.n_e + lh] = 0.0;
     if (a.geometry) {
         for (int lh = threadIdx.x; lh < p.n_h; lh += blockDim.x) {
             const int h = p.h_begin + lh;
-            const uint2 id = m.hidx[h];
+            const size_t B = m.n_hinges;
+            const uint2 id = rec_ids(m.hrec[3 * B + h]);
             const int l1 = id.x & 0xffff, l2 = id.x >> 16, l3 = id.y & 0xffff, l4 = id.y >> 16;
-            float4 q0 = m.hq[3 * h], q1 = m.hq[3 * h + 1], q2 = m.hq[3 * h + 2];
+            float4 q0 = m.hrec[h], q1 = m.hrec[B + h], q2 = m.hrec[2 * B + h];
             q0.x = (float)(xs[3 * l1] - xs[3 * l3]);
             q0.y = (float)(xs[3 * l1 + 1] - xs[3 * l3 + 1]);
             q0.z = (float)(xs[3 * l1 + 2] - xs[3 * l3 + 2]);
@@ -623,9 +873,9 @@ __global__ void k_setup_patch(const PatchDesc* __restrict__ patches, const MeshR
             q2.x = (float)(xs[3 * l4] - xs[3 * l3]);
             q2.y = (float)(xs[3 * l4 + 1] - xs[3 * l3 + 1]);
             q2.z = (float)(xs[3 * l4 + 2] - xs[3 * l3 + 2]);
-            m.hq[3 * h] = q0;
-            m.hq[3 * h + 1] = q1;
-            m.hq[3 * h + 2] = q2;
+            m.hrec[h] = q0;
+            m.hrec[B + h] = q1;
+            m.hrec[2 * B + h] = q2;
         }
     }
     __syncthreads();
@@ -674,23 +924,24 @@ __global__ void k_scatter_params(const MeshRT* __restrict__ rts, const float* mu
     const MeshRT& m = rts[0];
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m.n_elems; e += gridDim.x * blockDim.x) {
         const int u = m.elem_perm[e];
+        const size_t E = m.n_elems;
         if (m.kind == GS_TET) {
-            float4 c = m.ec[e];
+            float4 c = m.rec[2 * E + e];
             if (mu) c.z = mu[u];
             if (lam) c.w = lam[u];
-            m.ec[e] = c;
-            if (act && m.eact) m.eact[e] = act[u];
+            m.rec[2 * E + e] = c;
+            if (act) m.rec[3 * E + e].z = act[u];
         } else {
-            float4 b = m.eb[e];
+            float4 b = m.rec[E + e];
             if (mu) b.y = mu[u];
             if (lam) b.z = lam[u];
             if (act) b.w = act[u];
-            m.eb[e] = b;
+            m.rec[E + e] = b;
         }
     }
     if (kb && m.kind == GS_CLOTH) {
         for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < m.n_hinges; h += gridDim.x * blockDim.x)
-            m.hq[3 * h].w = kb[m.hinge_perm[h]];
+            m.hrec[h].w = kb[m.hinge_perm[h]];
     }
 }
 
@@ -708,7 +959,7 @@ __global__ void k_set_state(const MeshRT* __restrict__ rts, int buf, const float
             bufx(m, buf)[i] = make_float4((float)((double)x[3 * u] - m.Xd[3 * i]),
                                           (float)((double)x[3 * u + 1] - m.Xd[3 * i + 1]),
                                           (float)((double)x[3 * u + 2] - m.Xd[3 * i + 2]), m.w[i]);
-        if (v) bufv(m, buf)[i] = make_float4(v[3 * u], v[3 * u + 1], v[3 * u + 2], 0.f);
+        if (v) bufv(m, buf)[i] = make_float4(v[3 * u], v[3 * u + 1], v[3 * u + 2], m.Xp[i]);
     }
 }
 
@@ -718,7 +969,7 @@ __global__ void k_reset_state(const MeshRT* __restrict__ rts, const float* v0) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.n_nodes; i += gridDim.x * blockDim.x) {
         const int u = m.node_perm[i];
         m.st_x[i] = make_float4(0.f, 0.f, 0.f, m.w[i]);
-        m.st_v[i] = make_float4(v0[3 * u], v0[3 * u + 1], v0[3 * u + 2], 0.f);
+        m.st_v[i] = make_float4(v0[3 * u], v0[3 * u + 1], v0[3 * u + 2], m.Xp[i]);
     }
 }
 
@@ -773,14 +1024,15 @@ __global__ void k_elem_grads(const PatchDesc* __restrict__ patches, const MeshRT
     for (int le = threadIdx.x; le < p.n_e; le += blockDim.x) {
         const int e = p.e_begin + le;
         const int u = m.elem_perm[e];
-        const uint2 id = m.eidx[e];
+        const size_t E = m.n_elems;
+        const uint2 id = rec_ids(m.rec[3 * E + e]);
         if (d_rho) {
             if (m.kind == GS_TET) {
                 const double s = msm[id.x & 0xffff] + msm[id.x >> 16] + msm[id.y & 0xffff] + msm[id.y >> 16];
-                d_rho[u] = s * ((double)m.ec[e].y / 4.0);
+                d_rho[u] = s * ((double)m.rec[2 * E + e].y / 4.0);
             } else {
                 const double s = msm[id.x & 0xffff] + msm[id.x >> 16] + msm[id.y & 0xffff];
-                d_rho[u] = s * ((double)m.eb[e].x / 3.0);
+                d_rho[u] = s * ((double)m.rec[E + e].x / 3.0);
             }
         }
         if (d_mu) d_mu[u] = m.g_mu[e];
@@ -798,9 +1050,25 @@ __global__ void k_elem_grads(const PatchDesc* __restrict__ patches, const MeshRT
 // ===========================================================================
 // launchers
 // ===========================================================================
-size_t smem_bytes(int kind, bool adjoint, int max_loc, int max_slots) {
-    (void)kind;
-    return sizeof(float4) * ((size_t)max_loc * (adjoint ? 2 : 1) + (size_t)max_slots);
+size_t patch_smem_bytes(int n_rec, int n_loc, int n_int, int n_slots, bool adjoint) {
+    return (size_t)((patch_layout(n_rec, n_loc, n_int, n_slots, adjoint).total + 127) & ~127);
+}
+
+// persistent grid: resident CTAs per SM x SMs, at most one CTA per patch
+int patch_grid(int which, int threads, int stage_bytes, int n_patches, int num_sms) {
+    if (n_patches <= 0) return 0;
+    const void* f = which == 0 ? (const void*)k_tet_fwd
+                  : which == 1 ? (const void*)k_cloth_fwd
+                  : which == 2 ? (const void*)k_tet_adj
+                               : (const void*)k_cloth_adj;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, 128 + 2 * (size_t)stage_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    nb = nb < 1 ? 1 : nb;
+    const long long g = (long long)nb * num_sms;
+    return (int)(g < n_patches ? g : n_patches);
 }
 
 void set_kernel_smem_limits(size_t bytes) {
@@ -827,22 +1095,22 @@ const char* kernel_name(int kind) {
 
 void launch_forward_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
     if (L.n_tet_patches)
-        GS_TIMED(KT_TET_FWD, (k_tet_fwd<<<L.n_tet_patches, L.threads, L.smem_tet_fwd, s>>>(L.tet_patches, L.rt, tick)));
+        GS_TIMED(KT_TET_FWD, (k_tet_fwd<<<L.grid[0], L.threads, 128 + 2 * (size_t)L.stage[0], s>>>(
+                                 L.tet_patches, L.n_tet_patches, L.rt, tick, L.stage[0])));
     if (L.n_cloth_patches)
-        GS_TIMED(KT_CLOTH_FWD,
-                 (k_cloth_fwd<<<L.n_cloth_patches, L.threads, L.smem_cloth_fwd, s>>>(L.cloth_patches, L.rt, tick)));
-    if (L.n_bnd_blocks)
-        GS_TIMED(KT_FWD_BND, (k_fwd_boundary<<<L.n_bnd_blocks, 256, 0, s>>>(L.bnd_blocks, L.rt, tick)));
+        GS_TIMED(KT_CLOTH_FWD, (k_cloth_fwd<<<L.grid[1], L.threads, 128 + 2 * (size_t)L.stage[1], s>>>(
+                                   L.cloth_patches, L.n_cloth_patches, L.rt, tick, L.stage[1])));
+    if (L.n_bnd_blocks) GS_TIMED(KT_FWD_BND, (k_fwd_boundary<<<L.n_bnd_blocks, 256, 0, s>>>(L.bnd_blocks, L.rt, tick)));
 }
 
 void launch_adjoint_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
     if (L.n_tet_patches)
-        GS_TIMED(KT_TET_ADJ, (k_tet_adj<<<L.n_tet_patches, L.threads, L.smem_tet_adj, s>>>(L.tet_patches, L.rt, tick)));
+        GS_TIMED(KT_TET_ADJ, (k_tet_adj<<<L.grid[2], L.threads, 128 + 2 * (size_t)L.stage[2], s>>>(
+                                 L.tet_patches, L.n_tet_patches, L.rt, tick, L.stage[2])));
     if (L.n_cloth_patches)
-        GS_TIMED(KT_CLOTH_ADJ,
-                 (k_cloth_adj<<<L.n_cloth_patches, L.threads, L.smem_cloth_adj, s>>>(L.cloth_patches, L.rt, tick)));
-    if (L.n_bnd_blocks)
-        GS_TIMED(KT_ADJ_BND, (k_adj_boundary<<<L.n_bnd_blocks, 256, 0, s>>>(L.bnd_blocks, L.rt, tick)));
+        GS_TIMED(KT_CLOTH_ADJ, (k_cloth_adj<<<L.grid[3], L.threads, 128 + 2 * (size_t)L.stage[3], s>>>(
+                                   L.cloth_patches, L.n_cloth_patches, L.rt, tick, L.stage[3])));
+    if (L.n_bnd_blocks) GS_TIMED(KT_ADJ_BND, (k_adj_boundary<<<L.n_bnd_blocks, 256, 0, s>>>(L.bnd_blocks, L.rt, tick)));
 }
 
 void launch_copy_state(const Launch& L, cudaStream_t s) {

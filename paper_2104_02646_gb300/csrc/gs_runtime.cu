@@ -93,7 +93,8 @@ struct Topology {
     std::vector<int> bnd_ids;
     std::vector<uint16_t> loc_rowptr, loc_slots;
     std::vector<int> bnd_rowptr, bnd_parts;
-    int n_int = 0, n_bnd = 0, max_loc = 0, max_slots = 0;
+    int n_int = 0, n_bnd = 0, max_loc = 0, max_slots = 0, max_rec = 0;
+    size_t smem_fwd = 0, smem_adj = 0;
 };
 
 static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
@@ -235,19 +236,22 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
         }
         for (int l = 0; l < q.n_int; ++l) loc[q.int_begin + l] = l;
         const int n_loc = q.n_int + q.n_bnd;
+        const int n_rec = q.n_e + q.n_h;
         const int n_slots = nc * q.n_e + 4 * q.n_h;
-        if (n_loc > 65535 || n_slots > 65535)
+        if (n_loc > 65535 || 4 * n_rec > 65535)
             return set_error(GS_EINVAL, "patch too large for 16-bit local indices; lower patch_elems");
         auto lid = [&](int u) { return (uint32_t)loc[T.node_inv[u]]; };
-        // local ids and CSR in ascending slot order (= ascending element order)
+        // local ids, and the CSR over slot codes (record << 2 | corner) in
+        // ascending code order (= ascending element order, hinges last)
         std::vector<int> rc(n_loc + 1, 0);
-        std::vector<int> slot_node(n_slots);
+        std::vector<std::pair<int, int>> code_node;  // (code, local node)
+        code_node.reserve(n_slots);
         for (int le = 0; le < q.n_e; ++le) {
             const int e = q.e_begin + le;
             uint32_t l[4] = {0, 0, 0, 0};
             for (int c = 0; c < nc; ++c) {
                 l[c] = lid(ecorner(e, c));
-                slot_node[nc * le + c] = (int)l[c];
+                code_node.push_back({4 * le + c, (int)l[c]});
             }
             T.eidx[e] = make_uint2(l[0] | l[1] << 16, l[2] | l[3] << 16);
         }
@@ -256,24 +260,35 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
             uint32_t l[4];
             for (int c = 0; c < 4; ++c) {
                 l[c] = lid(hcorner(h, c));
-                slot_node[nc * q.n_e + 4 * lh + c] = (int)l[c];
+                code_node.push_back({4 * (q.n_e + lh) + c, (int)l[c]});
             }
             T.hidx[h] = make_uint2(l[0] | l[1] << 16, l[2] | l[3] << 16);
         }
-        for (int s = 0; s < n_slots; ++s) rc[slot_node[s] + 1]++;
+        for (auto& cn : code_node) rc[cn.second + 1]++;
         for (int l = 0; l < n_loc; ++l) rc[l + 1] += rc[l];
+        // 16 B aligned starts for the bulk copies
+        while (T.loc_rowptr.size() % 8) T.loc_rowptr.push_back(0);
+        while (T.loc_slots.size() % 8) T.loc_slots.push_back(0);
         q.lr_begin = (int)T.loc_rowptr.size();
         q.slot_begin = (int)T.loc_slots.size();
         for (int l = 0; l <= n_loc; ++l) T.loc_rowptr.push_back((uint16_t)rc[l]);
         std::vector<uint16_t> slots(n_slots);
         std::vector<int> fill(rc.begin(), rc.end() - 1);
-        for (int s = 0; s < n_slots; ++s) slots[fill[slot_node[s]]++] = (uint16_t)s;
+        for (auto& cn : code_node) slots[fill[cn.second]++] = (uint16_t)cn.first;
         T.loc_slots.insert(T.loc_slots.end(), slots.begin(), slots.end());
         T.max_loc = std::max(T.max_loc, n_loc);
         T.max_slots = std::max(T.max_slots, n_slots);
+        T.max_rec = std::max(T.max_rec, n_rec);
+        T.smem_fwd = std::max(T.smem_fwd, patch_smem_bytes(n_rec, n_loc, q.n_int, n_slots, false));
+        T.smem_adj = std::max(T.smem_adj, patch_smem_bytes(n_rec, n_loc, q.n_int, n_slots, true));
         for (int g : bl) loc[g] = -1;
         for (int l = 0; l < q.n_int; ++l) loc[q.int_begin + l] = -1;
         q.mesh = 0;
+    }
+    // tail padding so a rounded-up bulk copy of the last patch stays in bounds
+    for (int k = 0; k < 16; ++k) {
+        T.loc_rowptr.push_back(0);
+        T.loc_slots.push_back(0);
     }
     // 6. boundary CSR (partials in patch order)
     T.bnd_rowptr.assign(T.n_bnd + 1, 0);
@@ -428,8 +443,9 @@ gs_status gs_mesh::ensure_adjoint(cudaStream_t s) {
     GS_TRY(vb.alloc(ctx, (size_t)n_pad * sizeof(float4), s));
     GS_TRY(wbar.alloc(ctx, (size_t)n_pad * sizeof(double), s));
     GS_TRY(mbar.alloc(ctx, (size_t)n_pad * sizeof(double), s));
-    GS_TRY(g_mu.alloc(ctx, (size_t)info.n_elems * sizeof(double), s));
-    GS_TRY(g_lam.alloc(ctx, (size_t)info.n_elems * sizeof(double), s));
+    // +2: tail padding for the rounded-up bulk copy of the last patch
+    GS_TRY(g_mu.alloc(ctx, ((size_t)info.n_elems + 2) * sizeof(double), s));
+    GS_TRY(g_lam.alloc(ctx, ((size_t)info.n_elems + 2) * sizeof(double), s));
     GS_TRY(g_act.alloc(ctx, (size_t)info.n_elems * sizeof(double), s));
     if (info.n_hinges) {
         GS_TRY(g_kb.alloc(ctx, (size_t)info.n_hinges * sizeof(double), s));
@@ -440,7 +456,7 @@ gs_status gs_mesh::ensure_adjoint(cudaStream_t s) {
 
 gs_mesh::~gs_mesh() {
     cudaStream_t s = 0;
-    for (Buf* b : {&eidx, &ea, &eb, &ec, &ed, &eact, &hidx, &hq, &Xs, &Xp, &v0, &bnd_ids, &loc_rowptr, &loc_slots, &bnd_rowptr,
+    for (Buf* b : {&rec, &hrec, &Xs, &Xp, &v0, &bnd_ids, &loc_rowptr, &loc_slots, &bnd_rowptr,
                    &bnd_parts, &partials, &node_perm, &elem_perm, &hinge_perm, &w, &X, &rho, &pinned, &st, &xb, &vb,
                    &wbar, &mbar, &g_mu, &g_lam, &g_act, &g_kb, &g_hact, &status, &target, &scratch})
         b->release(s);
@@ -456,9 +472,10 @@ extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_me
     const gs_mesh_desc& d = *desc;
     GS_TRY(validate(d));
     const int nc = d.kind == GS_TET ? 4 : 3;
-    int threads = d.block_threads > 0 ? d.block_threads : 256;
+    int threads = d.block_threads > 0 ? d.block_threads : 128;
     if (threads % 32 || threads > 1024) return set_error(GS_EINVAL, "block_threads must be a multiple of 32, <= 1024");
-    int pe = d.patch_elems > 0 ? d.patch_elems : (d.kind == GS_TET ? 1024 : 512);
+    int pe = d.patch_elems > 0 ? d.patch_elems : (d.kind == GS_TET ? 256 : 256);
+    pe = (pe + 1) & ~1;  // even, so every patch's FP64 accumulators start 16 B aligned
     if (pe > 16383) return set_error(GS_EINVAL, "patch_elems must be <= 16383");
     Topology T;
     GS_TRY(build_topology(d, pe, T));
@@ -478,43 +495,43 @@ extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_me
     m->threads = threads;
     m->max_loc = T.max_loc;
     m->max_slots = T.max_slots;
+    m->max_rec = T.max_rec;
+    m->smem_fwd = T.smem_fwd;
+    m->smem_adj = T.smem_adj;
     m->patches = T.patches;
     m->bnd_blocks = make_blocks(0, T.n_bnd, 256, 0);
     m->node_blocks = make_blocks(0, N, 256, 0);
-    const size_t need = smem_bytes(d.kind, true, T.max_loc, T.max_slots);
+    const size_t need = std::max(128 + 2 * T.smem_adj, sizeof(double) * (3 * (size_t)T.max_loc + 4 * (size_t)T.max_rec));
     if (need > ctx->smem_optin)
         return set_error(GS_EINVAL, "patch needs " + std::to_string(need) + " B of shared memory; lower patch_elems");
     cudaStream_t s = 0;
-    // element data in internal order
-    std::vector<float4> ea(E), eb(E), ec(d.kind == GS_TET ? E : 0);
-    std::vector<float> eact;
+    // element records in internal order, 4 planes (geometry filled by the set-up kernel)
+    std::vector<float4> rec(4 * (size_t)E, make_float4(0.f, 0.f, 0.f, 0.f));
     std::vector<float> rho(E);
-    bool has_act = d.act != nullptr;
+    auto bits = [](uint32_t u) {
+        float f;
+        std::memcpy(&f, &u, 4);
+        return f;
+    };
     for (int e = 0; e < E; ++e) {
         const int u = T.elem_perm[e];
         rho[e] = (float)d.density[u];
-        const float act = has_act ? (float)d.act[u] : 0.0f;
+        const float act = d.act ? (float)d.act[u] : 0.0f;
         if (d.kind == GS_TET) {
-            ec[e] = make_float4(0.f, 0.f, (float)d.mu[u], (float)d.lambda[u]);
-            ea[e] = eb[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            rec[2 * (size_t)E + e] = make_float4(0.f, 0.f, (float)d.mu[u], (float)d.lambda[u]);
+            rec[3 * (size_t)E + e] = make_float4(bits(T.eidx[e].x), bits(T.eidx[e].y), act, 0.f);
         } else {
-            ea[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-            eb[e] = make_float4(0.f, (float)d.mu[u], (float)d.lambda[u], act);
+            rec[(size_t)E + e] = make_float4(0.f, (float)d.mu[u], (float)d.lambda[u], act);
+            rec[3 * (size_t)E + e] = make_float4(bits(T.eidx[e].x), bits(T.eidx[e].y), 0.f, 0.f);
         }
     }
-    if (d.kind == GS_TET) {
-        eact.assign(E, 0.0f);
-        if (has_act)
-            for (int e = 0; e < E; ++e) eact[e] = (float)d.act[T.elem_perm[e]];
-    }
-    // hinge data: (rest vectors written by the set-up kernel, kb), (.., act), (..)
-    std::vector<float4> hq(3 * (size_t)B, make_float4(0.f, 0.f, 0.f, 0.f));
+    std::vector<float4> hrec(4 * (size_t)B, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int h = 0; h < B; ++h) {
         const int u = T.hinge_perm[h];
-        hq[3 * (size_t)h].w = (float)d.kb[u];
-        hq[3 * (size_t)h + 1].w = d.hinge_act ? (float)d.hinge_act[u] : 0.0f;
+        hrec[h].w = (float)d.kb[u];
+        hrec[(size_t)B + h].w = d.hinge_act ? (float)d.hinge_act[u] : 0.0f;
+        hrec[3 * (size_t)B + h] = make_float4(bits(T.hidx[h].x), bits(T.hidx[h].y), 0.f, 0.f);
     }
-    std::vector<float2> ed(d.kind == GS_CLOTH ? E : 0, make_float2(0.f, 0.f));
     std::vector<double> X(3 * (size_t)N);
     // contact offsets of the rest positions, formed in FP64
     std::vector<float4> Xs(N);
@@ -539,14 +556,8 @@ extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_me
     // initial velocities in caller order (the state is set through the caller-order kernel)
     if (d.v0)
         for (size_t k = 0; k < 3 * (size_t)N; ++k) v0[k] = (float)d.v0[k];
-    GS_TRY(upload(ctx, m->eidx, T.eidx, s));
-    GS_TRY(upload(ctx, m->ea, ea, s));
-    GS_TRY(upload(ctx, m->eb, eb, s));
-    GS_TRY(upload(ctx, m->ec, d.kind == GS_TET ? ec : std::vector<float4>(E, make_float4(0.f, 0.f, 0.f, 0.f)), s));
-    GS_TRY(upload(ctx, m->ed, ed, s));
-    GS_TRY(upload(ctx, m->eact, eact, s));
-    GS_TRY(upload(ctx, m->hidx, T.hidx, s));
-    GS_TRY(upload(ctx, m->hq, hq, s));
+    GS_TRY(upload(ctx, m->rec, rec, s));
+    GS_TRY(upload(ctx, m->hrec, hrec, s));
     GS_TRY(upload(ctx, m->Xs, Xs, s));
     GS_TRY(upload(ctx, m->Xp, Xp, s));
     GS_TRY(upload(ctx, m->v0, v0, s));
@@ -577,14 +588,8 @@ extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_me
     r.n_elems = E;
     r.n_hinges = B;
     r.active = ACT_FWD | ACT_ADJ;
-    r.eidx = (const uint2*)m->eidx.p;
-    r.ea = (float4*)m->ea.p;
-    r.eb = (float4*)m->eb.p;
-    r.ec = (float4*)m->ec.p;
-    r.ed = (float2*)m->ed.p;
-    r.eact = d.kind == GS_TET ? (float*)m->eact.p : nullptr;
-    r.hidx = (const uint2*)m->hidx.p;
-    r.hq = (float4*)m->hq.p;
+    r.rec = (float4*)m->rec.p;
+    r.hrec = (float4*)m->hrec.p;
     r.Xs = (const float4*)m->Xs.p;
     r.Xp = (const float*)m->Xp.p;
     r.Xd = (const double*)m->X.p;
@@ -631,7 +636,7 @@ extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_me
     GS_CUDA(cudaMemcpy(&bad, (int*)m->status.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
     if (bad) return set_error(GS_EINVAL, "inverted or degenerate rest element (non-positive volume or area)");
     m->info.device_bytes = 0;
-    for (Buf* b : {&m->eidx, &m->ea, &m->eb, &m->ec, &m->ed, &m->eact, &m->hidx, &m->hq, &m->Xs, &m->Xp, &m->v0, &m->bnd_ids, &m->loc_rowptr,
+    for (Buf* b : {&m->rec, &m->hrec, &m->Xs, &m->Xp, &m->v0, &m->bnd_ids, &m->loc_rowptr,
                    &m->loc_slots, &m->bnd_rowptr, &m->bnd_parts, &m->partials, &m->node_perm, &m->elem_perm,
                    &m->hinge_perm, &m->w, &m->X, &m->rho, &m->pinned, &m->st})
         m->info.device_bytes += b->bytes;
@@ -643,7 +648,7 @@ gs_status gs_mesh::run_setup(int geometry, cudaStream_t s) {
     Buf mass, part;
     GS_TRY(mass.alloc(ctx, (size_t)n_pad * sizeof(double), s));
     GS_TRY(part.alloc(ctx, std::max<size_t>(bnd_ids.bytes / sizeof(int), 1) * sizeof(double), s));
-    const size_t sm = sizeof(double) * (3 * (size_t)max_loc + (size_t)max_slots);
+    const size_t sm = sizeof(double) * (3 * (size_t)max_loc + 4 * (size_t)max_rec);
     launch_setup_mesh(self->launch, (const double*)X.p, (const float*)rho.p, (double*)mass.p, (double*)part.p,
                       (const uint8_t*)pinned.p, (int*)status.p + 1, geometry, sm, s);
     GS_CUDA(cudaGetLastError());
@@ -773,7 +778,7 @@ gs_status LaunchSet::build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStrea
     meshes = ms;
     std::vector<PatchDesc> tp, cp;
     std::vector<NodeBlock> bb, nb;
-    int max_loc_t = 0, max_slots_t = 0, max_loc_c = 0, max_slots_c = 0;
+    size_t sf_t = 0, sa_t = 0, sf_c = 0, sa_c = 0;
     threads = 32;
     node_block_begin.clear();
     for (int i = 0; i < (int)ms.size(); ++i) {
@@ -793,11 +798,11 @@ gs_status LaunchSet::build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStrea
             nb.push_back(b);
         }
         if (m->info.kind == GS_TET) {
-            max_loc_t = std::max(max_loc_t, m->max_loc);
-            max_slots_t = std::max(max_slots_t, m->max_slots);
+            sf_t = std::max(sf_t, m->smem_fwd);
+            sa_t = std::max(sa_t, m->smem_adj);
         } else {
-            max_loc_c = std::max(max_loc_c, m->max_loc);
-            max_slots_c = std::max(max_slots_c, m->max_slots);
+            sf_c = std::max(sf_c, m->smem_fwd);
+            sa_c = std::max(sa_c, m->smem_adj);
         }
         threads = std::max(threads, m->threads);
     }
@@ -819,10 +824,14 @@ gs_status LaunchSet::build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStrea
     launch.n_node_blocks = (int)nb.size();
     launch.rt = (MeshRT*)d_rt.p;
     launch.threads = threads;
-    launch.smem_tet_fwd = smem_bytes(GS_TET, false, max_loc_t, max_slots_t);
-    launch.smem_tet_adj = smem_bytes(GS_TET, true, max_loc_t, max_slots_t);
-    launch.smem_cloth_fwd = smem_bytes(GS_CLOTH, false, max_loc_c, max_slots_c);
-    launch.smem_cloth_adj = smem_bytes(GS_CLOTH, true, max_loc_c, max_slots_c);
+    launch.stage[0] = (int)sf_t;
+    launch.stage[1] = (int)sf_c;
+    launch.stage[2] = (int)sa_t;
+    launch.stage[3] = (int)sa_c;
+    launch.grid[0] = patch_grid(0, threads, launch.stage[0], (int)tp.size(), c->num_sms);
+    launch.grid[1] = patch_grid(1, threads, launch.stage[1], (int)cp.size(), c->num_sms);
+    launch.grid[2] = patch_grid(2, threads, launch.stage[2], (int)tp.size(), c->num_sms);
+    launch.grid[3] = patch_grid(3, threads, launch.stage[3], (int)cp.size(), c->num_sms);
     return sync_rt(s);
 }
 
@@ -948,6 +957,9 @@ gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std:
         GS_TRY(m->ensure_adjoint(s));
         m->rt.seed_x = seed_x[i];
         m->rt.seed_v = seed_v[i];
+        // actuation gradients only when asked for (saves an FP64 read-modify-write per element-step)
+        m->rt.g_act = grads[i].d_act ? (double*)m->g_act.p : nullptr;
+        m->rt.g_hact = grads[i].d_hinge_act ? (double*)m->g_hact.p : nullptr;
     }
     GS_TRY(sync_rt(s));
     launch_seed_loss(launch, (double*)d_loss.p, 1, s);
@@ -955,9 +967,9 @@ gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std:
     for (gs_mesh* m : meshes) {
         launch_zero_f64((double*)m->g_mu.p, m->info.n_elems, s);
         launch_zero_f64((double*)m->g_lam.p, m->info.n_elems, s);
-        launch_zero_f64((double*)m->g_act.p, m->info.n_elems, s);
+        if (m->rt.g_act) launch_zero_f64((double*)m->g_act.p, m->info.n_elems, s);
         launch_zero_f64((double*)m->g_kb.p, m->info.n_hinges, s);
-        launch_zero_f64((double*)m->g_hact.p, m->info.n_hinges, s);
+        if (m->rt.g_hact) launch_zero_f64((double*)m->g_hact.p, m->info.n_hinges, s);
     }
     const int seg0 = 1 + n_ck;
     for (int sg = n_ck - 1; sg >= 0; --sg) {

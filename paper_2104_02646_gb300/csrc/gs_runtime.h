@@ -105,10 +105,11 @@ void launch_gather_elems(const MeshRT* rt_dev, const float* src_caller_order, fl
 struct gs_mesh {
     gs_ctx* ctx = nullptr;
     gs_mesh_info info{};
-    int n_pad = 0, threads = 256, max_loc = 0, max_slots = 0, n_bufs = 0;
+    int n_pad = 0, threads = 256, max_loc = 0, max_slots = 0, max_rec = 0, n_bufs = 0;
+    size_t smem_fwd = 0, smem_adj = 0;
     std::vector<gs::PatchDesc> patches;
     std::vector<gs::NodeBlock> bnd_blocks, node_blocks;
-    gs::Buf eidx, ea, eb, ec, ed, eact, hidx, hq, Xs, Xp, v0, bnd_ids, loc_rowptr, loc_slots, bnd_rowptr, bnd_parts, partials,
+    gs::Buf rec, hrec, Xs, Xp, v0, bnd_ids, loc_rowptr, loc_slots, bnd_rowptr, bnd_parts, partials,
         node_perm, elem_perm, hinge_perm, w, X, rho, pinned, st, xb, vb, wbar, mbar, g_mu, g_lam, g_act, g_kb,
         g_hact, status, target, scratch;
     gs::MeshRT rt{};

@@ -154,6 +154,8 @@ gs_status gs_server::start_query(Query* q) {
     q->n_ck = std::max(1, (q->S + q->K - 1) / q->K);
     GS_TRY(m->ensure_buffers(1 + q->n_ck + q->K + 1, stream));
     GS_TRY(m->ensure_adjoint(stream));
+    m->rt.g_act = nullptr;  // results carry no actuation gradients
+    m->rt.g_hact = nullptr;
     GS_TRY(m->target.alloc(ctx, q->target.size() * sizeof(float), stream));
     GS_CUDA(cudaMemcpyAsync(m->target.p, q->target.data(), m->target.bytes, cudaMemcpyHostToDevice, stream));
     m->rt.target = (const float*)m->target.p;
