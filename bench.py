@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=1, help="oracle steps in the CPU sample")
+    ap.add_argument("--workload", default="block", choices=["block", "bar", "cloth", "batch", "serve"],
+                    help="block: the 1.3M-tet solid (default line); the others measure the remaining workloads")
+    ap.add_argument("--meshes", type=int, default=512, help="batch: number of meshes")
+    ap.add_argument("--rates", default="10,20,50,100,200,500", help="serve: arrival rates (req/s)")
+    ap.add_argument("--queries", type=int, default=200, help="serve: queries per rate")
     return ap.parse_args()
 
 
@@ -215,6 +220,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.workload != "block":
+        WORKLOADS[args.workload](args)
+        return
     import numpy as np
     import torch
 
@@ -374,6 +382,203 @@ def mesh_K(K, S):
     import math
     return K if K > 0 else max(1, math.ceil(math.sqrt(max(S, 1))))
 
+
+
+# ---------------------------------------------------------------------------
+# the other workloads (one JSON line each; the default line is the block)
+# ---------------------------------------------------------------------------
+def _events_ms(fn, reps=1):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _grads(problem, dev):
+    import torch
+    E, N, B = problem.n_elems, problem.n_nodes, problem.n_hinges
+    g = {k: torch.zeros(E, dtype=torch.float64, device=dev) for k in ("d_mu", "d_lambda", "d_density")}
+    g["d_v0"] = torch.zeros(N, 3, device=dev)
+    if B:
+        g["d_kb"] = torch.zeros(B, dtype=torch.float64, device=dev)
+    return g
+
+
+def _single_mesh_line(args, name, problem, extra_cfg):
+    """Forward rollout + adjoint of one mesh: element-steps/s and steps/s."""
+    import torch
+    from paper_2104_02646_gb300 import gradsim as gs
+    gs.load()
+    dev = torch.device("cuda", 0)
+    ctx = gs.Context(0)
+    mesh = gs.Mesh(ctx, problem, patch_elems=args.patch, block_threads=args.threads)
+    S = problem.steps
+    target = torch.tensor(problem.X + 1e-3, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = _grads(problem, dev)
+
+    def fwd():
+        mesh.reset()
+        mesh.rollout(problem.dt, S, args.K, target, loss)
+
+    def both():
+        fwd()
+        mesh.adjoint(g)
+
+    for _ in range(args.warmup):
+        both()
+    t_fwd = min(_events_ms(fwd) for _ in range(args.steps))
+    t_all = min(_events_ms(both) for _ in range(args.steps))
+    ctx.set_graphs(False)
+    t_plain = min(_events_ms(both) for _ in range(max(1, args.steps // 2)))
+    ctx.set_graphs(True)
+    E = problem.n_elems
+    line = {"metric": "fwd+adjoint element-steps/s", "workload": name, "value": E * S / (t_all / 1e3),
+            "unit": "element-steps/s", "ms_per_rollout_fwd": t_fwd, "ms_per_rollout_fwd_adj": t_all,
+            "fwd_steps_per_s": S / (t_fwd / 1e3), "fwd_adj_steps_per_s": S / (t_all / 1e3),
+            "us_per_step_fwd_adj": 1e3 * t_all / S, "plain_loop_value": E * S / (t_plain / 1e3),
+            "finite": mesh.check_finite() == 0, "dtype": "f32", "data": "synthetic",
+            "config": dict(extra_cfg, elems=E, nodes=problem.n_nodes, hinges=problem.n_hinges, steps=S,
+                           dt=problem.dt, patch_elems=mesh.info.patch_elems)}
+    print(json.dumps(line), flush=True)
+
+
+def workload_bar(args):
+    from paper_2104_02646_gb300 import inputs as I
+    for v in ("a", "b"):
+        _single_mesh_line(args, f"bar1{v}", I.bar(v, steps=1000), {"cells": "4x4x4", "drop": "0.2 m" if v == "a" else "0.02 m"})
+
+
+def workload_cloth(args):
+    from paper_2104_02646_gb300 import inputs as I
+    # the stated materials diverge under explicit Euler at dt 1e-4 (reported
+    # by `finite`); the stable variant has the same mesh and work
+    for v in ("3s", "3"):
+        _single_mesh_line(args, f"cloth{v}", I.cloth(v, n=256, steps=500), {"grid": "256x256", "variant": v})
+
+
+def workload_batch(args):
+    """512 heterogeneous meshes: one launch per kernel per step (graphs) vs the
+    plain loop (one mesh per launch, one step per launch, no graphs)."""
+    import torch
+    from paper_2104_02646_gb300 import gradsim as gs
+    from paper_2104_02646_gb300 import inputs as I
+    gs.load()
+    dev = torch.device("cuda", 0)
+    probs = I.batch(args.meshes, steps=300)
+    ctx = gs.Context(0)
+    t0 = time.perf_counter()
+    meshes = [gs.Mesh(ctx, p, patch_elems=args.patch, block_threads=args.threads) for p in probs]
+    t_create = time.perf_counter() - t0
+    batch = gs.Batch(ctx, meshes)
+    S = 300
+    E = sum(p.n_elems for p in probs)
+    targets = [torch.tensor(p.X + 1e-3, dtype=torch.float32, device=dev) for p in probs]
+    loss = torch.zeros(len(probs), dtype=torch.float64, device=dev)
+    grads = [_grads(p, dev) for p in probs]
+    dts = [p.dt for p in probs]
+
+    def batched():
+        for m in meshes:
+            m.reset()
+        batch.rollout(dts, S, args.K, targets, loss)
+        batch.adjoint(grads)
+
+    losses = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in probs]
+
+    def plain():
+        for m, p, t, l, g in zip(meshes, probs, targets, losses, grads):
+            m.reset()
+            m.rollout(p.dt, S, args.K, t, l)
+            m.adjoint(g)
+
+    batched()
+    t_b = min(_events_ms(batched) for _ in range(max(1, args.steps)))
+    ctx.set_graphs(False)
+    plain()
+    t_p = _events_ms(plain)
+    ctx.set_graphs(True)
+    line = {"metric": "fwd+adjoint element-steps/s", "workload": f"batch{len(probs)}",
+            "value": E * S / (t_b / 1e3), "unit": "element-steps/s",
+            "plain_loop_value": E * S / (t_p / 1e3), "speedup_vs_plain": t_p / t_b,
+            "ms_batched": t_b, "ms_plain": t_p, "dtype": "f32", "data": "synthetic",
+            "config": {"meshes": len(probs), "tets": E, "nodes": sum(p.n_nodes for p in probs), "steps": S,
+                       "dt": 1e-4, "mesh_create_s": t_create}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_serve(args):
+    """Poisson gradient queries through the continuous-batching server vs the
+    plain loop (each query alone, in arrival order, one launch per kernel)."""
+    import numpy as np
+    import torch
+    from paper_2104_02646_gb300 import gradsim as gs
+    from paper_2104_02646_gb300 import inputs as I
+    gs.load()
+    dev = torch.device("cuda", 0)
+    for rate in [float(r) for r in args.rates.split(",")]:
+        qs = I.query_stream(rate, args.queries, seed=int(rate))
+        work = sum(q.problem.n_elems * q.problem.steps for q in qs)
+        ctx = gs.Context(0)
+        server = gs.Server(ctx, budget=120 << 30)
+        t0 = time.perf_counter()
+        tickets = []
+        for q in qs:
+            delay = t0 + q.t_arrival - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(server.submit(q.problem, q.problem.X + q.target_offset))
+        res = [server.poll(t, timeout_ms=600000) for t in tickets]
+        t_all = time.perf_counter() - t0
+        ok = [r for st, r in res if st == gs.GS_OK]
+        lat = sorted(r["t_done"] - r["t_submit"] for r in ok)
+        stats = server.stats()
+        server.close()
+        # plain loop: FIFO, one query at a time (no batching, no graphs)
+        ctx2 = gs.Context(0)
+        ctx2.set_graphs(False)
+        clock = 0.0
+        plain_lat = []
+        busy = 0.0
+        for q in qs:
+            p = q.problem
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            # service time includes building the mesh, as the server's latency does
+            m = gs.Mesh(ctx2, p)
+            t = torch.tensor(p.X + q.target_offset, dtype=torch.float32, device=dev)
+            l = torch.zeros(1, dtype=torch.float64, device=dev)
+            g = _grads(p, dev)
+            m.rollout(p.dt, p.steps, 0, t, l)
+            m.adjoint(g)
+            torch.cuda.synchronize()
+            dur = time.perf_counter() - w0
+            busy += dur
+            clock = max(clock, q.t_arrival) + dur
+            plain_lat.append(clock - q.t_arrival)
+            m.close()
+        plain_lat.sort()
+        pct = lambda v, f: v[min(len(v) - 1, int(round(f * (len(v) - 1))))] if v else None
+        line = {"metric": "p50/p99 query latency and aggregate element-steps/s", "workload": "serve",
+                "rate_req_s": rate, "queries": len(qs), "completed": len(ok),
+                "p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99), "elem_steps_per_s": stats["elem_steps_per_s"],
+                "wall_s": t_all, "plain_p50_s": pct(plain_lat, 0.5), "plain_p99_s": pct(plain_lat, 0.99),
+                "plain_elem_steps_per_s": work / busy, "data": "synthetic",
+                "server_time_s": {k: round(stats[k], 4) for k in
+                                  ("busy_s", "build_s", "start_s", "rebuild_s", "rt_sync_s", "gpu_wait_s")},
+                "server_counts": {k: int(stats[k]) for k in ("ticks", "rebuilds", "rt_syncs")},
+                "config": {"budget_GB": 120, "tets": "log-uniform 1e3..2e5", "cloth": "32^2..192^2",
+                           "horizon": "100..1000", "dt": 1e-4, "service_time": "mesh build + rollout + adjoint"}}
+        print(json.dumps(line), flush=True)
+
+
+WORKLOADS = {"bar": workload_bar, "cloth": workload_cloth, "batch": workload_batch, "serve": workload_serve}
 
 if __name__ == "__main__":
     main()

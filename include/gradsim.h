@@ -284,6 +284,7 @@ typedef struct gs_server_opts {
     int max_active;           /* 0 = unlimited slots                            */
     int K;                    /* checkpoint interval (0 = per query, ~sqrt(S))  */
     int use_graphs;           /* reserved                                       */
+    int build_threads;        /* host threads that build query meshes (0 = 4)   */
 } gs_server_opts;
 
 /* A query: one system-identification gradient request (mesh, materials,
@@ -313,6 +314,12 @@ typedef struct gs_server_stats {
     double p50_latency_s, p99_latency_s;
     double elem_steps_per_s;   /* fwd+adjoint element-steps over busy time */
     size_t admitted_bytes;
+    /* where the time went (seconds): wall time with work in the server;
+     * builder-thread time building meshes (summed over threads); worker time
+     * starting queries, rebuilding launch lists, uploading device records,
+     * and blocked on the GPU (bounding the ticks in flight) */
+    double busy_s, build_s, start_s, rebuild_s, rt_sync_s, gpu_wait_s;
+    uint64_t ticks, rebuilds, rt_syncs;
 } gs_server_stats;
 
 GS_API gs_status gs_server_create(gs_ctx* ctx, const gs_server_opts* opts, gs_server** out);

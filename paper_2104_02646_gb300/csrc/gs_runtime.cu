@@ -37,23 +37,30 @@ void clear_error() { g_last_error.clear(); }
 gs_status Buf::alloc(gs_ctx* c, size_t nbytes, cudaStream_t s) {
     release(s);
     if (nbytes == 0) return GS_OK;
-    if (c->budget && c->used + nbytes > c->budget)
+    // reserve first, so concurrent allocations cannot overshoot the budget together
+    const size_t before = c->used.fetch_add(nbytes);
+    if (c->budget && before + nbytes > c->budget) {
+        c->used.fetch_sub(nbytes);
         return set_error(GS_ENOMEM, "allocation of " + std::to_string(nbytes) + " bytes exceeds the context budget");
+    }
     void* q = nullptr;
     if (c->has_alloc) {
         q = c->alloc.alloc(nbytes, (void*)s, c->alloc.user);
-        if (!q) return set_error(GS_ENOMEM, "allocator callback returned NULL for " + std::to_string(nbytes) + " bytes");
+        if (!q) {
+            c->used.fetch_sub(nbytes);
+            return set_error(GS_ENOMEM, "allocator callback returned NULL for " + std::to_string(nbytes) + " bytes");
+        }
     } else {
         cudaError_t e = cudaMallocAsync(&q, nbytes, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
+            c->used.fetch_sub(nbytes);
             return set_error(GS_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
         }
     }
     ctx = c;
     p = q;
     bytes = nbytes;
-    c->used += nbytes;
     return GS_OK;
 }
 
@@ -61,7 +68,7 @@ void Buf::release(cudaStream_t s) {
     if (!p) return;
     if (ctx->has_alloc) ctx->alloc.free(p, bytes, (void*)s, ctx->alloc.user);
     else cudaFreeAsync(p, s);
-    ctx->used -= bytes;
+    ctx->used.fetch_sub(bytes);
     p = nullptr;
     bytes = 0;
 }
@@ -468,6 +475,12 @@ extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_me
     clear_error();
     if (!ctx || !desc || !out) return set_error(GS_EINVAL, "null argument");
     *out = nullptr;
+    return gs::mesh_create(ctx, desc, 0, out);
+}
+
+// Builds a mesh with all its uploads and set-up kernels on stream s and waits
+// for them; the mesh is ready for use on any stream when this returns.
+gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s, gs_mesh** out) {
     GS_CUDA(cudaSetDevice(ctx->device));
     const gs_mesh_desc& d = *desc;
     GS_TRY(validate(d));
@@ -504,7 +517,6 @@ extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_me
     const size_t need = std::max(128 + 2 * T.smem_adj, sizeof(double) * (3 * (size_t)T.max_loc + 4 * (size_t)T.max_rec));
     if (need > ctx->smem_optin)
         return set_error(GS_EINVAL, "patch needs " + std::to_string(need) + " B of shared memory; lower patch_elems");
-    cudaStream_t s = 0;
     // element records in internal order, 4 planes (geometry filled by the set-up kernel)
     std::vector<float4> rec(4 * (size_t)E, make_float4(0.f, 0.f, 0.f, 0.f));
     std::vector<float> rho(E);
@@ -630,10 +642,10 @@ extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_me
     GS_TRY(m->run_setup(1, s));
     // initial state: u = 0 (x = X exactly), v = v0
     launch_reset_state(m->rt_dev(), (const float*)m->v0.p, s);
+    int bad = 0;
+    GS_CUDA(cudaMemcpyAsync(&bad, (int*)m->status.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
     GS_CUDA(cudaStreamSynchronize(s));
     GS_CUDA(cudaGetLastError());
-    int bad = 0;
-    GS_CUDA(cudaMemcpy(&bad, (int*)m->status.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
     if (bad) return set_error(GS_EINVAL, "inverted or degenerate rest element (non-positive volume or area)");
     m->info.device_bytes = 0;
     for (Buf* b : {&m->rec, &m->hrec, &m->Xs, &m->Xp, &m->v0, &m->bnd_ids, &m->loc_rowptr,
@@ -1135,7 +1147,7 @@ extern "C" void gs_destroy(gs_ctx* c) {
     delete c;
 }
 
-extern "C" size_t gs_ctx_bytes(const gs_ctx* c) { return c ? c->used : 0; }
+extern "C" size_t gs_ctx_bytes(const gs_ctx* c) { return c ? c->used.load() : (size_t)0; }
 
 extern "C" gs_status gs_set_graphs(gs_ctx* c, int enable) {
     if (!c) return set_error(GS_EINVAL, "null context");

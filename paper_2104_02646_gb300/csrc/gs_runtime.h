@@ -2,6 +2,7 @@
 // server translation units).
 #pragma once
 
+#include <atomic>
 #include <map>
 #include <memory>
 #include <utility>
@@ -33,7 +34,7 @@ struct gs_ctx {
     gs::EventProf* prof = nullptr;  // non-null while gs_profile is on
     int device = 0;
     size_t budget = 0;
-    size_t used = 0;
+    std::atomic<size_t> used{0};  // device bytes held (builder threads allocate concurrently)
     gs_allocator alloc{};
     bool has_alloc = false;
     bool graphs = true;
@@ -126,3 +127,7 @@ struct gs_mesh {
     gs_status run_setup(int geometry, cudaStream_t s);
     ~gs_mesh();
 };
+
+namespace gs {
+gs_status mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s, gs_mesh** out);
+}

@@ -10,6 +10,11 @@
 // buffer indices (in = in_a + in_b * tick, ...).  Queries are admitted from a
 // FIFO as slots and the HBM budget free up, so queries that arrive while
 // others run join the next tick; finished queries leave and release memory.
+// Mesh construction (ordering, patches, uploads, set-up kernels) runs on
+// builder threads with their own streams, so the worker keeps ticking while
+// new queries are prepared.  The worker uploads the device records of the
+// active meshes when a phase changes and rebuilds the launch lists only when
+// the set of active meshes changes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +24,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <string>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -55,6 +61,8 @@ struct Query {
     int steps = 0;          // steps of the phase
     int done = 0;           // steps done in the phase
     bool cancelled = false;
+    gs_status build_status = GS_OK;
+    std::string build_error;
     // results
     Buf g_dev;              // device gradients
     double* h_stage = nullptr;  // pinned host staging
@@ -85,6 +93,11 @@ struct gs_server {
     bool stop = false;
     uint64_t next_id = 1;
     std::deque<Query*> pending;
+    std::deque<Query*> to_build;     // admitted, waiting for a builder thread
+    std::vector<Query*> built;       // mesh ready, not yet started by the worker
+    int building = 0;                // queries a builder thread holds
+    std::vector<std::thread> builders;
+    std::condition_variable cv_build;  // wakes builder threads
     std::vector<Query*> active;      // admitted, in some phase
     std::map<uint64_t, Query*> all;  // every query not yet collected
     size_t admitted = 0;
@@ -96,9 +109,14 @@ struct gs_server {
     bool ls_dirty = false;  // a query left: rebuild before the next launch
     int tick = 0;
     std::deque<cudaEvent_t> tick_events;
+    std::vector<cudaEvent_t> free_events;
+    // worker-time breakdown (seconds) and counters
+    double t_build = 0, t_start = 0, t_rebuild = 0, t_sync = 0, t_wait = 0;
+    uint64_t n_ticks = 0, n_rebuilds = 0, n_syncs = 0;
 
     void run();
-    void admit_locked(std::vector<Query*>& fresh);
+    void build_loop();
+    void admit_locked();
     gs_status start_query(Query* q);
     void set_phase(Query* q, Phase ph, int chunk);
     gs_status enter_phase(Query* q);
@@ -144,22 +162,60 @@ gs_status gs_server::enter_phase(Query* q) {
     return GS_OK;
 }
 
-gs_status gs_server::start_query(Query* q) {
+// builder thread: the mesh, its state/checkpoint/adjoint buffers and the
+// target, all on the builder's stream, finished before the query is handed on
+static gs_status build_query(gs_ctx* ctx, const gs_server_opts& opts, Query* q, cudaStream_t bs) {
     gs_mesh* m = nullptr;
-    gs_status st = gs_mesh_create(ctx, &q->desc, &m);
-    if (st < 0) return st;
+    GS_TRY(mesh_create(ctx, &q->desc, bs, &m));
     q->mesh = m;
     q->K = opts.K > 0 ? std::min(opts.K, std::max(q->S, 1))
                       : std::max(1, (int)std::ceil(std::sqrt((double)std::max(q->S, 1))));
     q->n_ck = std::max(1, (q->S + q->K - 1) / q->K);
-    GS_TRY(m->ensure_buffers(1 + q->n_ck + q->K + 1, stream));
-    GS_TRY(m->ensure_adjoint(stream));
+    GS_TRY(m->ensure_buffers(1 + q->n_ck + q->K + 1, bs));
+    GS_TRY(m->ensure_adjoint(bs));
     m->rt.g_act = nullptr;  // results carry no actuation gradients
     m->rt.g_hact = nullptr;
-    GS_TRY(m->target.alloc(ctx, q->target.size() * sizeof(float), stream));
-    GS_CUDA(cudaMemcpyAsync(m->target.p, q->target.data(), m->target.bytes, cudaMemcpyHostToDevice, stream));
+    GS_TRY(m->target.alloc(ctx, q->target.size() * sizeof(float), bs));
+    GS_CUDA(cudaMemcpyAsync(m->target.p, q->target.data(), m->target.bytes, cudaMemcpyHostToDevice, bs));
     m->rt.target = (const float*)m->target.p;
     m->rt.dt = q->dt;
+    GS_CUDA(cudaStreamSynchronize(bs));
+    return GS_OK;
+}
+
+void gs_server::build_loop() {
+    cudaSetDevice(ctx->device);
+    cudaStream_t bs = nullptr;
+    const bool have_stream = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) == cudaSuccess;
+    while (true) {
+        Query* q = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_build.wait(lk, [this] { return stop || !to_build.empty(); });
+            if (stop) break;
+            q = to_build.front();
+            to_build.pop_front();
+            building++;
+        }
+        const double t = now_s();
+        gs_status st = have_stream ? build_query(ctx, opts, q, bs) : set_error(GS_ECUDA, "builder stream");
+        const std::string err = st < 0 ? std::string(gs_last_error()) : std::string();
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            q->build_status = st;
+            q->build_error = err;
+            t_build += now_s() - t;
+            building--;
+            built.push_back(q);
+        }
+        cv.notify_all();
+    }
+    if (have_stream) cudaStreamDestroy(bs);
+}
+
+// worker: the query's first phase on the server stream
+gs_status gs_server::start_query(Query* q) {
+    gs_mesh* m = q->mesh;
     // checkpoint 0 = the initial state
     m->rt.cp_src = 0;
     m->rt.cp_dst = 1;
@@ -272,7 +328,7 @@ void gs_server::collect() {
     }
 }
 
-void gs_server::admit_locked(std::vector<Query*>& fresh) {
+void gs_server::admit_locked() {
     while (!pending.empty()) {
         Query* q = pending.front();
         if (q->cancelled) {
@@ -283,12 +339,14 @@ void gs_server::admit_locked(std::vector<Query*>& fresh) {
             cv_done.notify_all();
             continue;
         }
-        const int n_active = (int)(active.size() + fresh.size());
+        const int n_active = (int)(active.size() + to_build.size() + built.size()) + building;
         if (opts.max_active > 0 && n_active >= opts.max_active) break;
         if (opts.hbm_budget_bytes && admitted + q->bytes > opts.hbm_budget_bytes && n_active > 0) break;
         pending.pop_front();
         admitted += q->bytes;
-        fresh.push_back(q);
+        q->t_admit = now_s();
+        to_build.push_back(q);
+        cv_build.notify_one();
     }
 }
 
@@ -296,24 +354,38 @@ void gs_server::run() {
     cudaSetDevice(ctx->device);
     while (true) {
         std::vector<Query*> fresh;
+        bool waiting;  // queries admitted but still being built
         {
             std::unique_lock<std::mutex> lk(mu);
             if (stop) break;
-            admit_locked(fresh);
+            admit_locked();
+            fresh.swap(built);
+            waiting = !to_build.empty() || building > 0;
+            const bool idle = active.empty() && fresh.empty() && !waiting;
+            if (idle && busy_since >= 0) {
+                busy_time += now_s() - busy_since;
+                busy_since = -1.0;
+            }
+            if (!idle && busy_since < 0) busy_since = now_s();
             if (active.empty() && fresh.empty()) {
-                if (busy_since >= 0) {
-                    busy_time += now_s() - busy_since;
-                    busy_since = -1.0;
-                }
-                cv.wait_for(lk, std::chrono::milliseconds(50));
+                cv.wait_for(lk, std::chrono::milliseconds(waiting ? 5 : 50));
                 continue;
             }
-            if (busy_since < 0) busy_since = now_s();
         }
-        bool changed = !fresh.empty();
+        bool members = false, rt_changed = false;
         for (Query* q : fresh) {
-            q->t_admit = now_s();
-            gs_status st = start_query(q);
+            bool c;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                c = q->cancelled;
+            }
+            gs_status st = q->build_status;
+            if (st >= 0 && c) st = GS_ECANCELLED;
+            if (st >= 0) {
+                const double t = now_s();
+                st = start_query(q);
+                t_start += now_s() - t;
+            }
             if (st < 0) {
                 if (q->mesh) gs_mesh_destroy(q->mesh);
                 q->mesh = nullptr;
@@ -327,6 +399,7 @@ void gs_server::run() {
                 continue;
             }
             active.push_back(q);
+            members = true;
         }
         // cancellations of running queries
         for (Query* q : active) {
@@ -341,13 +414,13 @@ void gs_server::run() {
                 q->phase = P_FINISHING;
                 cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming);
                 cudaEventRecord(q->ev, stream);
-                changed = true;
+                rt_changed = true;
             }
         }
         // phase transitions (queries whose phase has run all its steps)
         for (Query* q : active) {
             while (q->phase != P_FINISHING && q->done >= q->steps) {
-                changed = true;
+                rt_changed = true;
                 if (q->phase == P_FWD) {
                     if ((q->chunk + 1) * q->K < q->S) {
                         set_phase(q, P_FWD, q->chunk + 1);
@@ -380,36 +453,62 @@ void gs_server::run() {
                 if (q->phase != P_FINISHING) enter_phase(q);
             }
         }
-        if (changed || ls_dirty || !ls_valid) {
+        // device records: full launch lists when the set of meshes changed,
+        // otherwise only the per-mesh records (phase fields)
+        if (members || ls_dirty || !ls_valid) {
+            const double t = now_s();
             std::vector<gs_mesh*> ms;
             for (Query* q : active) ms.push_back(q->mesh);
             ls_valid = !ms.empty() && ls.build(ctx, ms, stream) == GS_OK;
             ls_dirty = false;
-        } else {
+            t_rebuild += now_s() - t;
+            n_rebuilds++;
+        } else if (rt_changed) {
+            const double t = now_s();
             ls.sync_rt(stream);
+            t_sync += now_s() - t;
+            n_syncs++;
         }
-        // one tick: forward over FWD/REC queries, adjoint over ADJ queries
+        // ticks until the next phase change of any running query, back to back
         bool any_f = false, any_a = false;
+        int run = 1 << 30;
         for (Query* q : active) {
             if (q->phase == P_FWD || q->phase == P_REC) any_f = true;
             if (q->phase == P_ADJ) any_a = true;
+            if (q->phase == P_FWD || q->phase == P_REC || q->phase == P_ADJ) run = std::min(run, q->steps - q->done);
         }
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            // let queries that are arriving or being built join soon
+            if (!pending.empty() || !to_build.empty() || building > 0 || !built.empty()) run = std::min(run, 8);
+        }
+        run = std::max(1, std::min(run, 64));
         if ((any_f || any_a) && ls_valid) {
-            if (any_f) launch_forward_step(ls.launch, tick, stream);
-            if (any_a) launch_adjoint_step(ls.launch, tick, stream);
+            for (int r = 0; r < run; ++r) {
+                if (any_f) launch_forward_step(ls.launch, tick, stream);
+                if (any_a) launch_adjoint_step(ls.launch, tick, stream);
+                tick++;
+            }
+            n_ticks += run;
             for (Query* q : active)
-                if (q->phase == P_FWD || q->phase == P_REC || q->phase == P_ADJ) q->done++;
-            tick++;
-            // bound the work in flight: wait for the tick 8 back
-            cudaEvent_t e;
-            cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-            cudaEventRecord(e, stream);
-            tick_events.push_back(e);
-            if (tick_events.size() > 8) {
+                if (q->phase == P_FWD || q->phase == P_REC || q->phase == P_ADJ) q->done += run;
+            // bound the work in flight: wait for the batch of ticks 4 back
+            if (tick_events.size() >= 4) {
+                const double t = now_s();
                 cudaEventSynchronize(tick_events.front());
-                cudaEventDestroy(tick_events.front());
+                t_wait += now_s() - t;
+                free_events.push_back(tick_events.front());
                 tick_events.pop_front();
             }
+            cudaEvent_t e;
+            if (!free_events.empty()) {
+                e = free_events.back();
+                free_events.pop_back();
+            } else {
+                cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+            }
+            cudaEventRecord(e, stream);
+            tick_events.push_back(e);
             // keep ticks in a range where tick-affine indices stay small
             if (tick > (1 << 28)) {
                 for (Query* q : active) {
@@ -422,15 +521,20 @@ void gs_server::run() {
                     if (r.ck_tick >= 0) r.ck_tick -= sh;
                 }
                 tick = 0;
+                ls.sync_rt(stream);
             }
         } else {
+            const double t = now_s();
             cudaStreamSynchronize(stream);
+            t_wait += now_s() - t;
         }
         collect();
     }
     cudaStreamSynchronize(stream);
     for (cudaEvent_t e : tick_events) cudaEventDestroy(e);
+    for (cudaEvent_t e : free_events) cudaEventDestroy(e);
     tick_events.clear();
+    free_events.clear();
 }
 
 extern "C" gs_status gs_server_create(gs_ctx* ctx, const gs_server_opts* opts, gs_server** out) {
@@ -443,6 +547,8 @@ extern "C" gs_status gs_server_create(gs_ctx* ctx, const gs_server_opts* opts, g
     if (opts) s->opts = *opts;
     GS_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     gs_server* raw = s.get();
+    const int nb = s->opts.build_threads > 0 ? std::min(s->opts.build_threads, 64) : 4;
+    for (int i = 0; i < nb; ++i) s->builders.emplace_back([raw] { raw->build_loop(); });
     s->worker = std::thread([raw] { raw->run(); });
     *out = s.release();
     return GS_OK;
@@ -456,7 +562,12 @@ extern "C" void gs_server_destroy(gs_server* s) {
         for (auto& kv : s->all) kv.second->cancelled = true;
     }
     s->cv.notify_all();
+    s->cv_build.notify_all();
+    for (std::thread& b : s->builders)
+        if (b.joinable()) b.join();
     if (s->worker.joinable()) s->worker.join();
+    for (Query* q : s->built)
+        if (q->mesh) gs_mesh_destroy(q->mesh);
     for (Query* q : s->active) {
         if (q->mesh) gs_mesh_destroy(q->mesh);
         if (q->h_stage) cudaFreeHost(q->h_stage);
@@ -577,6 +688,15 @@ extern "C" gs_status gs_server_stats_get(gs_server* s, gs_server_stats* out) {
     }
     double busy = s->busy_time + (s->busy_since >= 0 ? now_s() - s->busy_since : 0.0);
     out->elem_steps_per_s = busy > 0 ? s->elem_steps / busy : 0.0;
+    out->busy_s = busy;
+    out->build_s = s->t_build;
+    out->start_s = s->t_start;
+    out->rebuild_s = s->t_rebuild;
+    out->rt_sync_s = s->t_sync;
+    out->gpu_wait_s = s->t_wait;
+    out->ticks = s->n_ticks;
+    out->rebuilds = s->n_rebuilds;
+    out->rt_syncs = s->n_syncs;
     return GS_OK;
 }
 

@@ -63,7 +63,7 @@ class gs_allocator(C.Structure):
 
 class gs_server_opts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int), ("K", C.c_int),
-                ("use_graphs", C.c_int)]
+                ("use_graphs", C.c_int), ("build_threads", C.c_int)]
 
 
 class gs_query(C.Structure):
@@ -80,7 +80,10 @@ class gs_result(C.Structure):
 class gs_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
                 ("active", C.c_uint64), ("queued", C.c_uint64), ("p50_latency_s", C.c_double),
-                ("p99_latency_s", C.c_double), ("elem_steps_per_s", C.c_double), ("admitted_bytes", C.c_size_t)]
+                ("p99_latency_s", C.c_double), ("elem_steps_per_s", C.c_double), ("admitted_bytes", C.c_size_t),
+                ("busy_s", C.c_double), ("build_s", C.c_double), ("start_s", C.c_double), ("rebuild_s", C.c_double),
+                ("rt_sync_s", C.c_double), ("gpu_wait_s", C.c_double), ("ticks", C.c_uint64),
+                ("rebuilds", C.c_uint64), ("rt_syncs", C.c_uint64)]
 
 
 class gs_kernel_time(C.Structure):
@@ -390,9 +393,9 @@ class Batch:
 class Server:
     """Continuous-batching gradient-query server (gs_server_*)."""
 
-    def __init__(self, ctx: Context, budget: int = 0, max_active: int = 0, K: int = 0):
+    def __init__(self, ctx: Context, budget: int = 0, max_active: int = 0, K: int = 0, build_threads: int = 0):
         self.ctx = ctx
-        o = gs_server_opts(budget, max_active, K, 0)
+        o = gs_server_opts(budget, max_active, K, 0, build_threads)
         self.h = _vp()
         check(load().gs_server_create(ctx.h, C.byref(o), C.byref(self.h)))
         self._keep = {}
