@@ -49,7 +49,7 @@ struct PatchDesc {
     int lr_begin;          // local CSR row pointers: n_int + n_bnd + 1 entries (16 B aligned)
     int slot_begin;        // local CSR slot list (16 B aligned)
     int mesh;              // index into the launch set's MeshRT array
-    int pad;
+    int n_slots;           // local CSR slots, every row padded to a multiple of 4
 };
 
 struct NodeBlock {  // a run of node indices of one mesh
@@ -68,8 +68,8 @@ struct MeshRT {
     const uint16_t* loc_rowptr;
     const uint16_t* loc_slots;
     const int* bnd_rowptr;   // [n_bnd + 1] over boundary nodes (internal id - n_int)
-    const int* bnd_parts;    // partial slots, in patch order
-    float4* partials;        // one per (patch, boundary local node)
+    const int* part_pos;     // per (patch, boundary local node): index of its partial
+    float4* partials;        // node-major: node b's partials at [bnd_rowptr[b], bnd_rowptr[b+1]), patch order
     const int* node_perm;    // internal node -> caller node
     const int* elem_perm;    // internal element -> caller element
     const int* hinge_perm;   // internal hinge -> caller hinge

@@ -46,9 +46,20 @@ __device__ __forceinline__ uint2 rec_ids(float4 w) { return make_uint2(__float_a
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar)) : "memory");
+// barrier completing a phase after `count` arrivals (and its expected bytes)
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(saddr(bar)) : "memory");
+}
+// arrive on `bar` once all of this thread's earlier cp.async copies have landed
+// (the arrival is one of the barrier's initial count)
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -91,20 +102,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 __host__ __device__ __forceinline__ int r16(int bytes) { return (bytes + 15) & ~15; }
 
-// Shared-memory layout of one pipeline stage (byte offsets, 16 B aligned).
-// The adjoint also holds v_hat for all local nodes, the interior adjoint
-// state and the boundary nodes' raw adjoint state.
+// Shared-memory layout of one pipeline stage (byte offsets, 16 B aligned):
+// the 4 record planes and one zero float4 (the target of padded CSR slots),
+// the local CSR, the partial positions of the boundary nodes, local node
+// state.  The adjoint also holds v_hat for all local nodes, the interior
+// adjoint state and the boundary nodes' raw adjoint state.
 struct Layout {
-    int rec, rp, sl, xs, vh, vs, xb, vb, xbB, vbB, gmu, glam, total;
+    int rec, rp, sl, pos, xs, vh, vs, xb, vb, xbB, vbB, gmu, glam, total;
 };
 
 __host__ __device__ __forceinline__ Layout patch_layout(int n_rec, int n_loc, int n_int, int n_slots, bool adjoint) {
     const int n_bnd = n_loc - n_int;
     Layout L;
     L.rec = 0;
-    L.rp = L.rec + 64 * n_rec;
+    L.rp = L.rec + 64 * n_rec + 16;
     L.sl = L.rp + r16(2 * (n_loc + 1));
-    L.xs = L.sl + r16(2 * n_slots);
+    L.pos = L.sl + r16(2 * n_slots);
+    L.xs = L.pos + r16(4 * n_bnd);
     L.vh = L.xs + 16 * n_loc;
     L.vs = L.vh + (adjoint ? 16 * n_loc : 0);
     L.xb = L.vs + 16 * n_int;
@@ -121,6 +135,9 @@ __host__ __device__ __forceinline__ Layout patch_layout(int n_rec, int n_loc, in
 // cp.async 16 B global -> shared (LDGSTS), groups per thread
 __device__ __forceinline__ void cp16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
@@ -240,6 +257,7 @@ struct Stage {
     float4* rec;  // planes [4][n_rec]
     uint16_t* rp;
     uint16_t* sl;
+    int* pos;     // partial positions of the boundary local nodes
     float4* xs;   // local node state (u, w)
     float4* vh;   // adjoint: v_hat of local nodes
     float4* vs;   // interior v
@@ -254,13 +272,13 @@ struct Stage {
 __device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned char* buf, bool adjoint) {
     const int n_loc = p.n_int + p.n_bnd;
     const int n_rec = p.n_e + p.n_h;
-    const int n_slots = (kind == GS_TET ? 4 : 3) * p.n_e + 4 * p.n_h;
-    const Layout L = patch_layout(n_rec, n_loc, p.n_int, n_slots, adjoint);
+    const Layout L = patch_layout(n_rec, n_loc, p.n_int, p.n_slots, adjoint);
     Stage S;
     S.n_rec = n_rec;
     S.rec = (float4*)(buf + L.rec);
     S.rp = (uint16_t*)(buf + L.rp);
     S.sl = (uint16_t*)(buf + L.sl);
+    S.pos = (int*)(buf + L.pos);
     S.xs = (float4*)(buf + L.xs);
     S.vh = (float4*)(buf + L.vh);
     S.vs = (float4*)(buf + L.vs);
@@ -285,7 +303,7 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT& m, 
     const Stage S = stage_at(p, m.kind, buf, adjoint);
     const int n_loc = p.n_int + p.n_bnd;
     const int n_rec = S.n_rec;
-    const int n_slots = (m.kind == GS_TET ? 4 : 3) * p.n_e + 4 * p.n_h;
+    const int n_slots = p.n_slots;
     const int ib = in_buffer(m, tick, adjoint);
     const float4* X = bufx(m, ib);
     const float4* V = bufv(m, ib);
@@ -316,55 +334,51 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT& m, 
     }
 }
 
-// boundary-node ids held in registers between their load and the gather
-constexpr int kIdsPerThread = 4;
-
-__device__ __forceinline__ void load_ids(const PatchDesc& p, const MeshRT& m, int* ids) {
-#pragma unroll
-    for (int j = 0; j < kIdsPerThread; ++j) {
-        const int k = threadIdx.x + j * blockDim.x;
-        ids[j] = k < p.n_bnd ? m.bnd_ids[p.bnd_begin + k] : 0;
-    }
-}
-
-// all threads: asynchronous gather of the boundary nodes into `buf`
-__device__ __forceinline__ void issue_gather(const PatchDesc& p, const MeshRT& m, int tick, unsigned char* buf,
-                                             bool adjoint, const int* ids) {
+// producer warp: asynchronous gather of the boundary nodes' state (and their
+// partial positions) into `buf`; ids for 4 x 32 nodes are loaded before their
+// copies are issued
+__device__ __forceinline__ void produce_gather(const PatchDesc& p, const MeshRT& m, int tick, unsigned char* buf,
+                                               bool adjoint, int lane) {
     const Stage S = stage_at(p, m.kind, buf, adjoint);
     const float4* X = bufx(m, in_buffer(m, tick, adjoint));
+    const int* ids = m.bnd_ids + p.bnd_begin;
+    const int* pos = m.part_pos + p.bnd_begin;
+    for (int k0 = 0; k0 < p.n_bnd; k0 += 128) {
+        int g[4];
 #pragma unroll
-    for (int j = 0; j < kIdsPerThread; ++j) {
-        const int k = threadIdx.x + j * blockDim.x;
-        if (k < p.n_bnd) {
-            const int g = ids[j];
-            cp16(S.xs + p.n_int + k, X + g);
-            if (adjoint) {
-                cp16(S.xbB + k, m.xb + g);
-                cp16(S.vbB + k, m.vb + g);
+        for (int j = 0; j < 4; ++j) {
+            const int k = k0 + lane + 32 * j;
+            g[j] = k < p.n_bnd ? ids[k] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = k0 + lane + 32 * j;
+            if (k < p.n_bnd) {
+                cp16(S.xs + p.n_int + k, X + g[j]);
+                cp4(S.pos + k, pos + k);
+                if (adjoint) {
+                    cp16(S.xbB + k, m.xb + g[j]);
+                    cp16(S.vbB + k, m.vb + g[j]);
+                }
             }
         }
     }
-    for (int k = threadIdx.x + kIdsPerThread * blockDim.x; k < p.n_bnd; k += blockDim.x) {
-        const int g = m.bnd_ids[p.bnd_begin + k];
-        cp16(S.xs + p.n_int + k, X + g);
-        if (adjoint) {
-            cp16(S.xbB + k, m.xb + g);
-            cp16(S.vbB + k, m.vb + g);
-        }
-    }
 }
 
-// corner result of slot s (record << 2 | corner): plane (s & 3), row (s >> 2)
-__device__ __forceinline__ float4 corner4(const Stage& S, int s) { return S.rec[(s & 3) * S.n_rec + (s >> 2)]; }
-__device__ __forceinline__ float3 corner3(const Stage& S, int s) { return xyz(corner4(S, s)); }
+// corner c of record r is written in place into plane c, row r; a CSR slot is
+// that float4 index (c * n_rec + r), or 4 * n_rec for a padding slot
 __device__ __forceinline__ void put(const Stage& S, int r, int c, float4 f) { S.rec[c * S.n_rec + r] = f; }
+__device__ __forceinline__ void zero_pad_slot(const Stage& S) {
+    if (threadIdx.x == 0) S.rec[4 * S.n_rec] = make_float4(0.f, 0.f, 0.f, 0.f);  // a consumer thread
+}
 
 // ---------------------------------------------------------------------------
 // element phases (one thread per element record)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void tet_elements_fwd(const PatchDesc& p, const Stage& S) {
+__device__ __forceinline__ void tet_elements_fwd(const PatchDesc& p, const Stage& S, int nt) {
     const int nr = S.n_rec;
-    for (int le = threadIdx.x; le < p.n_e; le += blockDim.x) {
+    zero_pad_slot(S);
+    for (int le = threadIdx.x; le < p.n_e; le += nt) {
         const float4 a = S.rec[le], b = S.rec[nr + le], c = S.rec[2 * nr + le], w = S.rec[3 * nr + le];
         const uint2 id = rec_ids(w);
         TetState s;
@@ -379,9 +393,10 @@ __device__ __forceinline__ void tet_elements_fwd(const PatchDesc& p, const Stage
     }
 }
 
-__device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Stage& S) {
+__device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Stage& S, int nt) {
     const int nr = S.n_rec;
-    for (int lr = threadIdx.x; lr < nr; lr += blockDim.x) {
+    zero_pad_slot(S);
+    for (int lr = threadIdx.x; lr < nr; lr += nt) {
         const float4 a = S.rec[lr], b = S.rec[nr + lr], c = S.rec[2 * nr + lr], w = S.rec[3 * nr + lr];
         const uint2 id = rec_ids(w);
         if (lr < p.n_e) {
@@ -408,10 +423,11 @@ __device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Sta
 }
 
 // corner result (dL/du_corner, f_corner . v_hat_node) in place
-__device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshRT& m, const Stage& S) {
+__device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshRT& m, const Stage& S, int nt) {
     const float dt = m.dt;
     const int nr = S.n_rec;
-    for (int le = threadIdx.x; le < p.n_e; le += blockDim.x) {
+    zero_pad_slot(S);
+    for (int le = threadIdx.x; le < p.n_e; le += nt) {
         const float4 a = S.rec[le], b = S.rec[nr + le], c = S.rec[2 * nr + le], w = S.rec[3 * nr + le];
         const uint2 id = rec_ids(w);
         const int i0 = id.x & 0xffff, i1 = id.x >> 16, i2 = id.y & 0xffff, i3 = id.y >> 16;
@@ -436,10 +452,11 @@ __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshR
     }
 }
 
-__device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const MeshRT& m, const Stage& S) {
+__device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const MeshRT& m, const Stage& S, int nt) {
     const float dt = m.dt;
     const int nr = S.n_rec;
-    for (int lr = threadIdx.x; lr < nr; lr += blockDim.x) {
+    zero_pad_slot(S);
+    for (int lr = threadIdx.x; lr < nr; lr += nt) {
         const float4 a = S.rec[lr], b = S.rec[nr + lr], c = S.rec[2 * nr + lr], w = S.rec[3 * nr + lr];
         const uint2 id = rec_ids(w);
         if (lr < p.n_e) {
@@ -483,148 +500,183 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
     }
 }
 
-// Fixed-order sum of the corner results of CSR row [k, k1): four slots at a
-// time with all loads issued before the adds (the adds stay in row order, so
-// the result is the same as a one-by-one walk).
+// Fixed-order sum of the corner results of CSR row [k, k1): rows are padded
+// to a multiple of 4 (padding slots read a zero float4), so four slot indices
+// come in one 8 B load and all four corner loads are issued before the adds;
+// the adds stay in row order.  The forward sums 3 lanes, the adjoint 4.
 __device__ __forceinline__ void add4(float4& acc, float4 q) {
     acc.x += q.x;
     acc.y += q.y;
     acc.z += q.z;
     acc.w += q.w;
 }
-__device__ __forceinline__ float4 row_sum(const Stage& S, int k, int k1) {
+__device__ __forceinline__ void add3(float3& acc, float4 q) {
+    acc.x += q.x;
+    acc.y += q.y;
+    acc.z += q.z;
+}
+__device__ __forceinline__ float4 row_sum4(const Stage& S, int k, int k1) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (; k + 4 <= k1; k += 4) {
-        const int s0 = S.sl[k], s1 = S.sl[k + 1], s2 = S.sl[k + 2], s3 = S.sl[k + 3];
-        const float4 q0 = corner4(S, s0), q1 = corner4(S, s1), q2 = corner4(S, s2), q3 = corner4(S, s3);
+    for (; k < k1; k += 4) {
+        const uint2 q = *reinterpret_cast<const uint2*>(S.sl + k);
+        const float4 q0 = S.rec[q.x & 0xffff], q1 = S.rec[q.x >> 16], q2 = S.rec[q.y & 0xffff], q3 = S.rec[q.y >> 16];
         add4(acc, q0);
         add4(acc, q1);
         add4(acc, q2);
         add4(acc, q3);
     }
-    for (; k < k1; ++k) add4(acc, corner4(S, S.sl[k]));
+    return acc;
+}
+__device__ __forceinline__ float3 row_sum3(const Stage& S, int k, int k1) {
+    float3 acc = make_float3(0.f, 0.f, 0.f);
+    for (; k < k1; k += 4) {
+        const uint2 q = *reinterpret_cast<const uint2*>(S.sl + k);
+        const float4 q0 = S.rec[q.x & 0xffff], q1 = S.rec[q.x >> 16], q2 = S.rec[q.y & 0xffff], q3 = S.rec[q.y >> 16];
+        add3(acc, q0);
+        add3(acc, q1);
+        add3(acc, q2);
+        add3(acc, q3);
+    }
     return acc;
 }
 
 // node phases: fixed-order corner sums, then interior update or partial
-__device__ __forceinline__ void forward_nodes(const PatchDesc& p, const MeshRT& m, int tick, const Stage& S) {
+__device__ __forceinline__ void forward_nodes(const PatchDesc& p, const MeshRT& m, int tick, const Stage& S, int nt) {
     const int n_loc = p.n_int + p.n_bnd;
-    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
-        const float3 f = xyz(row_sum(S, S.rp[l], S.rp[l + 1]));
+    for (int l = threadIdx.x; l < n_loc; l += nt) {
+        const float3 f = row_sum3(S, S.rp[l], S.rp[l + 1]);
         if (l < p.n_int) node_forward(m, tick, p.int_begin + l, S.xs[l], S.vs[l], f);
-        else m.partials[p.bnd_begin + (l - p.n_int)] = f4(f, 0.f);
+        else m.partials[S.pos[l - p.n_int]] = f4(f, 0.f);
     }
 }
 
-__device__ __forceinline__ void adjoint_nodes(const PatchDesc& p, const MeshRT& m, const Stage& S) {
+__device__ __forceinline__ void adjoint_nodes(const PatchDesc& p, const MeshRT& m, const Stage& S, int nt) {
     const int n_loc = p.n_int + p.n_bnd;
-    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
-        const float4 acc = row_sum(S, S.rp[l], S.rp[l + 1]);
+    for (int l = threadIdx.x; l < n_loc; l += nt) {
+        const float4 acc = row_sum4(S, S.rp[l], S.rp[l + 1]);
         if (l < p.n_int) node_adjoint(m, p.int_begin + l, S.xs[l], S.vs[l], S.xb[l], S.vb[l], xyz(acc), acc.w);
-        else m.partials[p.bnd_begin + (l - p.n_int)] = acc;
+        else m.partials[S.pos[l - p.n_int]] = acc;
     }
 }
 
-// boundary nodes: partials of the row in patch order, loads grouped by four
+// boundary nodes: the node's partials (contiguous, in patch order), loads
+// grouped by four
 __device__ __forceinline__ float4 partial_sum(const MeshRT& m, int b) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     int k = m.bnd_rowptr[b];
     const int k1 = m.bnd_rowptr[b + 1];
     for (; k + 4 <= k1; k += 4) {
-        const int s0 = m.bnd_parts[k], s1 = m.bnd_parts[k + 1], s2 = m.bnd_parts[k + 2], s3 = m.bnd_parts[k + 3];
-        const float4 q0 = m.partials[s0], q1 = m.partials[s1], q2 = m.partials[s2], q3 = m.partials[s3];
+        const float4 q0 = m.partials[k], q1 = m.partials[k + 1], q2 = m.partials[k + 2], q3 = m.partials[k + 3];
         add4(acc, q0);
         add4(acc, q1);
         add4(acc, q2);
         add4(acc, q3);
     }
-    for (; k < k1; ++k) add4(acc, m.partials[m.bnd_parts[k]]);
+    for (; k < k1; ++k) add4(acc, m.partials[k]);
     return acc;
 }
 
 // ---------------------------------------------------------------------------
-// the pipeline: a persistent CTA walks patches blockIdx.x, +gridDim.x, ...
-// with two shared-memory stages; while patch i computes, patch i+1's bulk
-// copies and boundary gathers are in flight.
+// The pipeline: a persistent CTA walks the live patches blockIdx.x,
+// +gridDim.x, ... through two shared-memory stages, warp-specialised.  The
+// last warp produces: it finds the next live patch, waits until the
+// consumers released the stage (empty[s]), writes the patch descriptor into
+// the stage header, issues the bulk copies (one elected lane, expect_tx on
+// full[s]) and the boundary gathers (all lanes, each lane's cp.async copies
+// counted on full[s] by a no-increment arrival).  The other warps consume:
+// wait for full[s], run the element phase, sync among themselves (named
+// barrier 1), run the node phase and release the stage.  After the last patch
+// the producer fills one more stage with an end marker.
+// full[s] completes after 33 arrivals (the elected lane's expect_tx + one per
+// producer lane) and the expected bytes; empty[s] after one arrival per
+// consumer warp.
 // ---------------------------------------------------------------------------
+constexpr int kHdr = 64;  // stage header: the patch descriptor
+
+__device__ __forceinline__ void consumer_sync(int nt) { asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory"); }
+
 template <int KIND, bool ADJ>
 __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ patches, int n_patches,
                                                const MeshRT* __restrict__ rts, int tick, int stage_bytes) {
     extern __shared__ __align__(128) unsigned char sm[];
-    uint64_t* bars = (uint64_t*)sm;
+    uint64_t* full = (uint64_t*)sm;
+    uint64_t* empty = full + 2;
     unsigned char* const buf0 = sm + 128;
     const int mask = ADJ ? ACT_ADJ : ACT_FWD;
+    const int nt = (int)blockDim.x - 32;  // consumer threads
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        mbar_init(&bars[0]);
-        mbar_init(&bars[1]);
+        mbar_init(&full[0], 33);
+        mbar_init(&full[1], 33);
+        mbar_init(&empty[0], nt >> 5);
+        mbar_init(&empty[1], nt >> 5);
+        mbar_init_fence();
     }
     __syncthreads();
-    uint32_t parity = 0u;  // bit b: phase parity of buffer b's barrier
-    int ids[kIdsPerThread];
-    // prologue: stage the first patch into buffer 0
-    int pi = blockIdx.x;
-    bool live = pi < n_patches && (rts[patches[pi].mesh].active & mask);
-    if (live) {
-        const PatchDesc p = patches[pi];
-        const MeshRT& m = rts[p.mesh];
-        if (threadIdx.x == 0) issue_bulk(p, m, tick, buf0, &bars[0], ADJ);
-        load_ids(p, m, ids);
-        issue_gather(p, m, tick, buf0, ADJ, ids);
+    if (n_patches <= 0) return;
+    int* const status = rts[patches[blockIdx.x < n_patches ? blockIdx.x : 0].mesh].status;
+    if (warp == (nt >> 5)) {
+        // ---- producer warp ----
+        int pi = blockIdx.x;
+        for (int it = 0;; ++it) {
+            PatchDesc p;
+            p.n_e = -1;
+            for (; pi < n_patches; pi += gridDim.x) {
+                p = patches[pi];
+                if (rts[p.mesh].active & mask) break;
+            }
+            const bool done = pi >= n_patches;
+            const int s = it & 1;
+            unsigned char* const b = buf0 + s * stage_bytes;
+            if (it >= 2 && !mbar_wait_bounded(&empty[s], ((it >> 1) - 1) & 1u, status)) return;
+            if (done) {
+                if (lane == 0) ((PatchDesc*)b)->n_e = -1;  // end marker
+                __syncwarp();
+                mbar_arrive(&full[s]);
+                if (lane == 0) mbar_arrive(&full[s]);
+                return;
+            }
+            const MeshRT& m = rts[p.mesh];
+            if (lane == 0) {
+                *(PatchDesc*)b = p;
+                issue_bulk(p, m, tick, b + kHdr, &full[s], ADJ);
+            }
+            produce_gather(p, m, tick, b + kHdr, ADJ, lane);
+            cp_async_mbar_arrive(&full[s]);
+            pi += gridDim.x;
+        }
     }
-    cp_commit();
-    for (int it = 0; pi < n_patches; ++it, pi += gridDim.x) {
-        const int cur = it & 1, nxt = cur ^ 1;
-        unsigned char* const bcur = buf0 + cur * stage_bytes;
-        unsigned char* const bnxt = buf0 + nxt * stage_bytes;
-        const int pn = pi + gridDim.x;
-        const bool live_n = pn < n_patches && (rts[patches[pn].mesh].active & mask);
-        if (live_n) {
-            const PatchDesc q = patches[pn];
-            const MeshRT& mq = rts[q.mesh];
-            if (threadIdx.x == 0) issue_bulk(q, mq, tick, bnxt, &bars[nxt], ADJ);
-            load_ids(q, mq, ids);
-        }
-        const PatchDesc p = patches[pi];
+    // ---- consumer warps ----
+    for (int it = 0;; ++it) {
+        const int s = it & 1;
+        unsigned char* const b = buf0 + s * stage_bytes;
+        if (!mbar_wait_bounded(&full[s], (it >> 1) & 1u, status)) return;
+        const PatchDesc p = *(const PatchDesc*)b;
+        if (p.n_e < 0) return;
         const MeshRT& m = rts[p.mesh];
-        Stage S = stage_at(p, KIND, bcur, ADJ);
-        if (live) {
-            cp_wait_all();
-            const bool ok = mbar_wait_bounded(&bars[cur], (parity >> cur) & 1u, m.status);
-            parity ^= 1u << cur;
-            if (__syncthreads_or(!ok)) return;
-            if (ADJ) {
-                for (int l = threadIdx.x; l < p.n_int; l += blockDim.x)
-                    S.vh[l] = f4(xyz(S.vb[l]) + m.dt * xyz(S.xb[l]), 0.f);
-                for (int k = threadIdx.x; k < p.n_bnd; k += blockDim.x)
-                    S.vh[p.n_int + k] = f4(xyz(S.vbB[k]) + m.dt * xyz(S.xbB[k]), 0.f);
-                __syncthreads();
-            }
-            if (KIND == GS_TET) {
-                if (ADJ) tet_elements_adj(p, m, S);
-                else tet_elements_fwd(p, S);
-            } else {
-                if (ADJ) cloth_elements_adj(p, m, S);
-                else cloth_elements_fwd(p, S);
-            }
+        const Stage S = stage_at(p, KIND, b + kHdr, ADJ);
+        if (ADJ) {
+            for (int l = threadIdx.x; l < p.n_int; l += nt) S.vh[l] = f4(xyz(S.vb[l]) + m.dt * xyz(S.xb[l]), 0.f);
+            for (int k = threadIdx.x; k < p.n_bnd; k += nt)
+                S.vh[p.n_int + k] = f4(xyz(S.vbB[k]) + m.dt * xyz(S.xbB[k]), 0.f);
+            consumer_sync(nt);
         }
-        // the next patch's boundary gathers, issued before this patch's node phase
-        if (live_n) {
-            const PatchDesc q = patches[pn];
-            issue_gather(q, rts[q.mesh], tick, bnxt, ADJ, ids);
+        if (KIND == GS_TET) {
+            if (ADJ) tet_elements_adj(p, m, S, nt);
+            else tet_elements_fwd(p, S, nt);
+        } else {
+            if (ADJ) cloth_elements_adj(p, m, S, nt);
+            else cloth_elements_fwd(p, S, nt);
         }
-        cp_commit();
-        if (live) {
-            __syncthreads();
-            if (ADJ) adjoint_nodes(p, m, S);
-            else forward_nodes(p, m, tick, S);
-        }
-        // this thread's generic shared writes of buffer `cur` are ordered before
-        // the async-proxy (bulk copy) writes that will refill it
+        consumer_sync(nt);
+        if (ADJ) adjoint_nodes(p, m, S, nt);
+        else forward_nodes(p, m, tick, S, nt);
+        // this warp's generic shared accesses of the stage are ordered before the
+        // async-proxy writes that will refill it
         fence_proxy_async();
-        __syncthreads();  // buffer `cur` is free for the patch after next
-        live = live_n;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
     }
-    cp_wait_all();
 }
 
 }  // namespace
@@ -765,8 +817,9 @@ __global__ void k_setup_patch(const PatchDesc* __restrict__ patches, const MeshR
     const PatchDesc p = patches[blockIdx.x];
     const MeshRT& m = rts[p.mesh];
     const int n_loc = p.n_int + p.n_bnd;
+    const int n_rec = p.n_e + p.n_h;
     double* xs = dsm;               // 3 per local node
-    double* mc = dsm + 3 * n_loc;   // one per slot code (record << 2 | corner)
+    double* mc = dsm + 3 * n_loc;   // one per corner (plane-major, as the CSR slots), + the padding slot
     for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
         const int g = local_gid(p, m, l);
         xs[3 * l] = a.X[3 * g];
@@ -853,10 +906,11 @@ __global__ void k_setup_patch(const PatchDesc* __restrict__ patches, const MeshR
             }
             share = (double)a.rho[e] * area / 3.0;
         }
-        for (int c = 0; c < 4; ++c) mc[4 * le + c] = c < nc ? share : 0.0;
+        for (int c = 0; c < 4; ++c) mc[c * n_rec + le] = c < nc ? share : 0.0;
     }
     // hinge corners carry no mass; hinge rest vectors X1-X3, X2-X3, X4-X3
-    for (int lh = threadIdx.x; lh < 4 * p.n_h; lh += blockDim.x) mc[4 * p.n_e + lh] = 0.0;
+    for (int lh = threadIdx.x; lh < 4 * p.n_h; lh += blockDim.x) mc[(lh & 3) * n_rec + p.n_e + (lh >> 2)] = 0.0;
+    if (threadIdx.x == 0) mc[4 * n_rec] = 0.0;
     if (a.geometry) {
         for (int lh = threadIdx.x; lh < p.n_h; lh += blockDim.x) {
             const int h = p.h_begin + lh;
@@ -886,7 +940,7 @@ __global__ void k_setup_patch(const PatchDesc* __restrict__ patches, const MeshR
         const int k1 = rp[l + 1];
         for (int k = rp[l]; k < k1; ++k) s += mc[sl[k]];
         if (l < p.n_int) a.mass[p.int_begin + l] = s;
-        else a.mass_part[p.bnd_begin + (l - p.n_int)] = s;
+        else a.mass_part[m.part_pos[p.bnd_begin + (l - p.n_int)]] = s;
     }
 }
 
@@ -896,7 +950,7 @@ __global__ void k_mass_boundary(const NodeBlock* __restrict__ blocks, const Mesh
     for (int i = threadIdx.x; i < nb.count; i += blockDim.x) {
         const int b = nb.begin + i;
         double s = 0.0;
-        for (int k = m.bnd_rowptr[b]; k < m.bnd_rowptr[b + 1]; ++k) s += a.mass_part[m.bnd_parts[k]];
+        for (int k = m.bnd_rowptr[b]; k < m.bnd_rowptr[b + 1]; ++k) s += a.mass_part[k];
         a.mass[m.n_int + b] = s;
     }
 }
@@ -1051,7 +1105,7 @@ __global__ void k_elem_grads(const PatchDesc* __restrict__ patches, const MeshRT
 // launchers
 // ===========================================================================
 size_t patch_smem_bytes(int n_rec, int n_loc, int n_int, int n_slots, bool adjoint) {
-    return (size_t)((patch_layout(n_rec, n_loc, n_int, n_slots, adjoint).total + 127) & ~127);
+    return (size_t)((kHdr + patch_layout(n_rec, n_loc, n_int, n_slots, adjoint).total + 127) & ~127);
 }
 
 // persistent grid: resident CTAs per SM x SMs, at most one CTA per patch
@@ -1062,7 +1116,8 @@ int patch_grid(int which, int threads, int stage_bytes, int n_patches, int num_s
                   : which == 2 ? (const void*)k_tet_adj
                                : (const void*)k_cloth_adj;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, 128 + 2 * (size_t)stage_bytes) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads + 32, 128 + 2 * (size_t)stage_bytes) !=
+        cudaSuccess) {
         cudaGetLastError();
         nb = 1;
     }
@@ -1095,20 +1150,20 @@ const char* kernel_name(int kind) {
 
 void launch_forward_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
     if (L.n_tet_patches)
-        GS_TIMED(KT_TET_FWD, (k_tet_fwd<<<L.grid[0], L.threads, 128 + 2 * (size_t)L.stage[0], s>>>(
+        GS_TIMED(KT_TET_FWD, (k_tet_fwd<<<L.grid[0], L.threads + 32, 128 + 2 * (size_t)L.stage[0], s>>>(
                                  L.tet_patches, L.n_tet_patches, L.rt, tick, L.stage[0])));
     if (L.n_cloth_patches)
-        GS_TIMED(KT_CLOTH_FWD, (k_cloth_fwd<<<L.grid[1], L.threads, 128 + 2 * (size_t)L.stage[1], s>>>(
+        GS_TIMED(KT_CLOTH_FWD, (k_cloth_fwd<<<L.grid[1], L.threads + 32, 128 + 2 * (size_t)L.stage[1], s>>>(
                                    L.cloth_patches, L.n_cloth_patches, L.rt, tick, L.stage[1])));
     if (L.n_bnd_blocks) GS_TIMED(KT_FWD_BND, (k_fwd_boundary<<<L.n_bnd_blocks, 256, 0, s>>>(L.bnd_blocks, L.rt, tick)));
 }
 
 void launch_adjoint_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
     if (L.n_tet_patches)
-        GS_TIMED(KT_TET_ADJ, (k_tet_adj<<<L.grid[2], L.threads, 128 + 2 * (size_t)L.stage[2], s>>>(
+        GS_TIMED(KT_TET_ADJ, (k_tet_adj<<<L.grid[2], L.threads + 32, 128 + 2 * (size_t)L.stage[2], s>>>(
                                  L.tet_patches, L.n_tet_patches, L.rt, tick, L.stage[2])));
     if (L.n_cloth_patches)
-        GS_TIMED(KT_CLOTH_ADJ, (k_cloth_adj<<<L.grid[3], L.threads, 128 + 2 * (size_t)L.stage[3], s>>>(
+        GS_TIMED(KT_CLOTH_ADJ, (k_cloth_adj<<<L.grid[3], L.threads + 32, 128 + 2 * (size_t)L.stage[3], s>>>(
                                    L.cloth_patches, L.n_cloth_patches, L.rt, tick, L.stage[3])));
     if (L.n_bnd_blocks) GS_TIMED(KT_ADJ_BND, (k_adj_boundary<<<L.n_bnd_blocks, 256, 0, s>>>(L.bnd_blocks, L.rt, tick)));
 }

@@ -99,7 +99,7 @@ struct Topology {
     std::vector<uint2> eidx, hidx;
     std::vector<int> bnd_ids;
     std::vector<uint16_t> loc_rowptr, loc_slots;
-    std::vector<int> bnd_rowptr, bnd_parts;
+    std::vector<int> bnd_rowptr, part_pos;
     int n_int = 0, n_bnd = 0, max_loc = 0, max_slots = 0, max_rec = 0;
     size_t smem_fwd = 0, smem_adj = 0;
 };
@@ -192,6 +192,13 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
     }
     // 4. internal node numbering: interior nodes patch by patch, then boundary
     //    nodes by (first patch, id), then untouched nodes
+    //    (each patch's interior nodes by descending corner count, so the
+    //    threads of a warp walk CSR rows of similar length)
+    std::vector<int> deg(N, 0);
+    for (int e = 0; e < E; ++e)
+        for (int c = 0; c < nc; ++c) deg[ecorner(e, c)]++;
+    for (int h = 0; h < B; ++h)
+        for (int c = 0; c < 4; ++c) deg[hcorner(h, c)]++;
     std::vector<std::vector<int>> interior(P);
     std::vector<std::pair<int, int>> bnodes;
     std::vector<int> loose;
@@ -200,6 +207,8 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
         else if (cnt[u] > 1) bnodes.push_back({first[u], u});
         else loose.push_back(u);
     }
+    for (auto& v : interior)
+        std::sort(v.begin(), v.end(), [&](int x, int y) { return deg[x] != deg[y] ? deg[x] > deg[y] : x < y; });
     std::sort(bnodes.begin(), bnodes.end());
     T.node_perm.clear();
     T.node_perm.reserve(N);
@@ -217,42 +226,51 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
     // 5. per patch: boundary list, local indices, local CSR
     T.eidx.assign(E, make_uint2(0, 0));
     T.hidx.assign(B, make_uint2(0, 0));
-    std::vector<int> loc(N, -1);
-    std::vector<std::vector<int>> bparts(T.n_bnd);
+    std::vector<int> loc(N, -1), pdeg(N, 0);
+    std::vector<int> bcount(T.n_bnd, 0);   // partials per boundary node so far
+    std::vector<int> entry_node, entry_j;  // per (patch, boundary local node)
     for (int p = 0; p < P; ++p) {
         PatchDesc& q = T.patches[p];
         std::vector<int> bl;  // internal ids of boundary nodes touched by p
         auto note = [&](int u) {
             const int g = T.node_inv[u];
-            if (g >= T.n_int && loc[g] == -1) {
-                loc[g] = -2;
-                bl.push_back(g);
+            if (g >= T.n_int) {
+                if (loc[g] == -1) {
+                    loc[g] = -2;
+                    bl.push_back(g);
+                }
+                pdeg[g]++;
             }
         };
         for (int e = q.e_begin; e < q.e_begin + q.n_e; ++e)
             for (int c = 0; c < nc; ++c) note(ecorner(e, c));
         for (int h = q.h_begin; h < q.h_begin + q.n_h; ++h)
             for (int c = 0; c < 4; ++c) note(hcorner(h, c));
-        std::sort(bl.begin(), bl.end());
+        // descending corner count within the patch (similar row lengths per warp)
+        std::sort(bl.begin(), bl.end(), [&](int x, int y) { return pdeg[x] != pdeg[y] ? pdeg[x] > pdeg[y] : x < y; });
         q.bnd_begin = (int)T.bnd_ids.size();
         q.n_bnd = (int)bl.size();
         for (int k = 0; k < q.n_bnd; ++k) {
             loc[bl[k]] = q.n_int + k;
             T.bnd_ids.push_back(bl[k]);
-            bparts[bl[k] - T.n_int].push_back(q.bnd_begin + k);
+            const int b = bl[k] - T.n_int;
+            entry_node.push_back(b);
+            entry_j.push_back(bcount[b]++);
         }
         for (int l = 0; l < q.n_int; ++l) loc[q.int_begin + l] = l;
         const int n_loc = q.n_int + q.n_bnd;
         const int n_rec = q.n_e + q.n_h;
-        const int n_slots = nc * q.n_e + 4 * q.n_h;
-        if (n_loc > 65535 || 4 * n_rec > 65535)
+        if (n_loc > 65535 || 4 * n_rec + 1 > 65535)
             return set_error(GS_EINVAL, "patch too large for 16-bit local indices; lower patch_elems");
         auto lid = [&](int u) { return (uint32_t)loc[T.node_inv[u]]; };
-        // local ids, and the CSR over slot codes (record << 2 | corner) in
-        // ascending code order (= ascending element order, hinges last)
+        // local ids, and the CSR over corner codes (record << 2 | corner) in
+        // ascending code order (= ascending element order, hinges last); the
+        // stored slot is the corner's float4 index in the staged record planes,
+        // corner * n_rec + record, and rows are padded to a multiple of 4 with
+        // index 4 * n_rec (a zero float4 after the planes)
         std::vector<int> rc(n_loc + 1, 0);
         std::vector<std::pair<int, int>> code_node;  // (code, local node)
-        code_node.reserve(n_slots);
+        code_node.reserve(nc * q.n_e + 4 * q.n_h);
         for (int le = 0; le < q.n_e; ++le) {
             const int e = q.e_begin + le;
             uint32_t l[4] = {0, 0, 0, 0};
@@ -272,23 +290,30 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
             T.hidx[h] = make_uint2(l[0] | l[1] << 16, l[2] | l[3] << 16);
         }
         for (auto& cn : code_node) rc[cn.second + 1]++;
+        for (int l = 0; l < n_loc; ++l) rc[l + 1] = (rc[l + 1] + 3) / 4 * 4;  // padded row lengths
         for (int l = 0; l < n_loc; ++l) rc[l + 1] += rc[l];
+        const int n_slots = rc[n_loc];
+        if (n_slots > 65535) return set_error(GS_EINVAL, "patch has too many corners; lower patch_elems");
+        q.n_slots = n_slots;
         // 16 B aligned starts for the bulk copies
         while (T.loc_rowptr.size() % 8) T.loc_rowptr.push_back(0);
         while (T.loc_slots.size() % 8) T.loc_slots.push_back(0);
         q.lr_begin = (int)T.loc_rowptr.size();
         q.slot_begin = (int)T.loc_slots.size();
         for (int l = 0; l <= n_loc; ++l) T.loc_rowptr.push_back((uint16_t)rc[l]);
-        std::vector<uint16_t> slots(n_slots);
+        std::vector<uint16_t> slots(n_slots, (uint16_t)(4 * n_rec));
         std::vector<int> fill(rc.begin(), rc.end() - 1);
-        for (auto& cn : code_node) slots[fill[cn.second]++] = (uint16_t)cn.first;
+        for (auto& cn : code_node) slots[fill[cn.second]++] = (uint16_t)((cn.first & 3) * n_rec + (cn.first >> 2));
         T.loc_slots.insert(T.loc_slots.end(), slots.begin(), slots.end());
         T.max_loc = std::max(T.max_loc, n_loc);
         T.max_slots = std::max(T.max_slots, n_slots);
         T.max_rec = std::max(T.max_rec, n_rec);
         T.smem_fwd = std::max(T.smem_fwd, patch_smem_bytes(n_rec, n_loc, q.n_int, n_slots, false));
         T.smem_adj = std::max(T.smem_adj, patch_smem_bytes(n_rec, n_loc, q.n_int, n_slots, true));
-        for (int g : bl) loc[g] = -1;
+        for (int g : bl) {
+            loc[g] = -1;
+            pdeg[g] = 0;
+        }
         for (int l = 0; l < q.n_int; ++l) loc[q.int_begin + l] = -1;
         q.mesh = 0;
     }
@@ -297,11 +322,12 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
         T.loc_rowptr.push_back(0);
         T.loc_slots.push_back(0);
     }
-    // 6. boundary CSR (partials in patch order)
+    // 6. boundary CSR: node b's partials at [bnd_rowptr[b], bnd_rowptr[b+1]),
+    //    in patch order; each (patch, boundary local node) knows its position
     T.bnd_rowptr.assign(T.n_bnd + 1, 0);
-    for (int b = 0; b < T.n_bnd; ++b) T.bnd_rowptr[b + 1] = T.bnd_rowptr[b] + (int)bparts[b].size();
-    T.bnd_parts.reserve(T.bnd_rowptr[T.n_bnd]);
-    for (int b = 0; b < T.n_bnd; ++b) T.bnd_parts.insert(T.bnd_parts.end(), bparts[b].begin(), bparts[b].end());
+    for (int b = 0; b < T.n_bnd; ++b) T.bnd_rowptr[b + 1] = T.bnd_rowptr[b] + bcount[b];
+    T.part_pos.resize(entry_node.size());
+    for (size_t i = 0; i < entry_node.size(); ++i) T.part_pos[i] = T.bnd_rowptr[entry_node[i]] + entry_j[i];
     return GS_OK;
 }
 
@@ -464,7 +490,7 @@ gs_status gs_mesh::ensure_adjoint(cudaStream_t s) {
 gs_mesh::~gs_mesh() {
     cudaStream_t s = 0;
     for (Buf* b : {&rec, &hrec, &Xs, &Xp, &v0, &bnd_ids, &loc_rowptr, &loc_slots, &bnd_rowptr,
-                   &bnd_parts, &partials, &node_perm, &elem_perm, &hinge_perm, &w, &X, &rho, &pinned, &st, &xb, &vb,
+                   &part_pos, &partials, &node_perm, &elem_perm, &hinge_perm, &w, &X, &rho, &pinned, &st, &xb, &vb,
                    &wbar, &mbar, &g_mu, &g_lam, &g_act, &g_kb, &g_hact, &status, &target, &scratch})
         b->release(s);
     self.reset();
@@ -514,7 +540,7 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     m->patches = T.patches;
     m->bnd_blocks = make_blocks(0, T.n_bnd, 256, 0);
     m->node_blocks = make_blocks(0, N, 256, 0);
-    const size_t need = std::max(128 + 2 * T.smem_adj, sizeof(double) * (3 * (size_t)T.max_loc + 4 * (size_t)T.max_rec));
+    const size_t need = std::max(128 + 2 * T.smem_adj, sizeof(double) * (3 * (size_t)T.max_loc + 4 * (size_t)T.max_rec + 1));
     if (need > ctx->smem_optin)
         return set_error(GS_EINVAL, "patch needs " + std::to_string(need) + " B of shared memory; lower patch_elems");
     // element records in internal order, 4 planes (geometry filled by the set-up kernel)
@@ -577,7 +603,7 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     GS_TRY(upload(ctx, m->loc_rowptr, T.loc_rowptr, s));
     GS_TRY(upload(ctx, m->loc_slots, T.loc_slots, s));
     GS_TRY(upload(ctx, m->bnd_rowptr, T.bnd_rowptr, s));
-    GS_TRY(upload(ctx, m->bnd_parts, T.bnd_parts, s));
+    GS_TRY(upload(ctx, m->part_pos, T.part_pos, s));
     GS_TRY(m->partials.alloc(ctx, std::max<size_t>(T.bnd_ids.size(), 1) * sizeof(float4), s));
     GS_TRY(upload(ctx, m->node_perm, T.node_perm, s));
     GS_TRY(upload(ctx, m->elem_perm, T.elem_perm, s));
@@ -609,7 +635,7 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     r.loc_rowptr = (const uint16_t*)m->loc_rowptr.p;
     r.loc_slots = (const uint16_t*)m->loc_slots.p;
     r.bnd_rowptr = (const int*)m->bnd_rowptr.p;
-    r.bnd_parts = (const int*)m->bnd_parts.p;
+    r.part_pos = (const int*)m->part_pos.p;
     r.partials = (float4*)m->partials.p;
     r.node_perm = (const int*)m->node_perm.p;
     r.elem_perm = (const int*)m->elem_perm.p;
@@ -649,7 +675,7 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     if (bad) return set_error(GS_EINVAL, "inverted or degenerate rest element (non-positive volume or area)");
     m->info.device_bytes = 0;
     for (Buf* b : {&m->rec, &m->hrec, &m->Xs, &m->Xp, &m->v0, &m->bnd_ids, &m->loc_rowptr,
-                   &m->loc_slots, &m->bnd_rowptr, &m->bnd_parts, &m->partials, &m->node_perm, &m->elem_perm,
+                   &m->loc_slots, &m->bnd_rowptr, &m->part_pos, &m->partials, &m->node_perm, &m->elem_perm,
                    &m->hinge_perm, &m->w, &m->X, &m->rho, &m->pinned, &m->st})
         m->info.device_bytes += b->bytes;
     *out = m.release();
@@ -660,7 +686,7 @@ gs_status gs_mesh::run_setup(int geometry, cudaStream_t s) {
     Buf mass, part;
     GS_TRY(mass.alloc(ctx, (size_t)n_pad * sizeof(double), s));
     GS_TRY(part.alloc(ctx, std::max<size_t>(bnd_ids.bytes / sizeof(int), 1) * sizeof(double), s));
-    const size_t sm = sizeof(double) * (3 * (size_t)max_loc + 4 * (size_t)max_rec);
+    const size_t sm = sizeof(double) * (3 * (size_t)max_loc + 4 * (size_t)max_rec + 1);
     launch_setup_mesh(self->launch, (const double*)X.p, (const float*)rho.p, (double*)mass.p, (double*)part.p,
                       (const uint8_t*)pinned.p, (int*)status.p + 1, geometry, sm, s);
     GS_CUDA(cudaGetLastError());

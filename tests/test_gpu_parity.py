@@ -72,7 +72,7 @@ def test_bar_1b_with_contact(gs, ctx):
     check_grads(out, ref, TET_KEYS)
 
 
-@pytest.mark.parametrize("patch_elems", [300, 1000])
+@pytest.mark.parametrize("patch_elems", [300, 800])
 def test_block_many_patches_ragged(gs, ctx, patch_elems):
     # 8^3 cells (2560 tets) split into several patches with a ragged last one;
     # heterogeneous materials, random velocities, ground contact from step 0
@@ -84,6 +84,16 @@ def test_block_many_patches_ragged(gs, ctx, patch_elems):
     assert out["mesh"].info.n_boundary_nodes > 0
     assert rel_pos(out["x"], ref["x"]) <= POS_CONTACT
     check_grads(out, ref, TET_KEYS)
+
+
+def test_patch_too_large_for_shared_memory_is_rejected(gs, ctx):
+    # two pipeline stages of a 1000-tet adjoint patch exceed the 227 KB of
+    # shared memory a CTA may use: mesh creation fails cleanly with EINVAL
+    p = I.block(n=8, steps=1, seed=3)
+    with pytest.raises(gs.GradsimError) as ei:
+        gs.Mesh(ctx, p, patch_elems=1000)
+    assert ei.value.status == gs.GS_EINVAL
+    assert "shared memory" in str(ei.value)
 
 
 def test_cloth_on_sphere(gs, ctx):
