@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="block: library defaults instead of the autotuner's patch shape and K")
     ap.add_argument("--cpu-steps", type=int, default=1, help="oracle steps in the CPU sample")
     ap.add_argument("--workload", default="block", choices=["block", "bar", "cloth", "batch", "serve"],
                     help="block: the 1.3M-tet solid (default line); the others measure the remaining workloads")
@@ -201,16 +203,20 @@ def throughput(n_ranks, n_elems, steps_per_rollout, bench_steps, total_ms):
 
 
 def launches_per_step(S, K, have_bnd):
-    """Kernels of ours launched by one benchmark step (set_state + rollout +
-    adjoint), counted from the library's launch sequence."""
-    import math
-    K = K if K > 0 else max(1, math.ceil(math.sqrt(max(S, 1))))
+    """Kernels of ours launched by one benchmark step (reset + rollout +
+    adjoint of a tet mesh), counted from the library's launch sequence."""
+    K = mesh_K(K, S)
     n_ck = max(1, -(-S // K))
     per_step = 2 if have_bnd else 1
-    n = 1                           # set_state
+    n = 1                           # reset
     n += 1 + per_step * S + 2       # checkpoint copy, steps, loss + finalize
-    n += 1 + 1 + 3                  # seed, zero w_bar, zero the mu, lambda, kb accumulators
-    n += n_ck + 2 * per_step * S    # per segment copy; recompute + reverse steps
+    if K == 1:
+        n += 1                      # final state back to buffer 0
+    n += 1 + 1 + 2                  # seed, zero w_bar, zero the mu and lambda accumulators
+    if K == 1:
+        n += per_step * S           # reverse steps over the stored states
+    else:
+        n += n_ck + per_step * (S - n_ck) + per_step * S  # per segment: copy, n-1 recomputed, n reverse
     n += 2                          # node and element gradient kernels
     return n
 
@@ -245,6 +251,15 @@ def main():
     p = I.block(n=args.cells, steps=args.rollout, seed=rank)
     E, N, S = p.n_elems, p.n_nodes, args.rollout
     ctx = gs.Context(local)
+    # the autotuner's launch shape and checkpoint interval (untimed)
+    tuned = None
+    if not args.no_autotune:
+        from paper_2104_02646_gb300 import autotune
+        tuned = autotune.tune(ctx, p, steps=10, horizon=S, use_cache=False)
+        if args.patch == 0 and args.threads == 0:
+            args.patch, args.threads = tuned["patch_elems"], tuned["block_threads"]
+        if args.K == 0:
+            args.K = tuned["K"]
     mesh = gs.Mesh(ctx, p, patch_elems=args.patch, block_threads=args.threads)
     dev = torch.device("cuda", local)
     x0 = torch.tensor(p.x0, dtype=torch.float32, device=dev)
@@ -362,7 +377,11 @@ def main():
             "config": {"workload": f"block{args.cells}: {args.cells}^3 hex cells x 5 tets = {E} tets, {N} nodes, "
                                    f"{S}-step rollout at dt {p.dt} + adjoint, K={mesh_K(args.K, S)}",
                        "parallelism": f"replicas x{ws}", "l2": "flushed between timed iterations (512 MiB write)",
-                       "patch_elems": mesh.info.patch_elems, "block_threads": mesh.info.block_threads},
+                       "patch_elems": mesh.info.patch_elems, "block_threads": mesh.info.block_threads,
+                       "autotune": None if tuned is None else {
+                           "K": tuned["K"], "budget": "half the free device memory",
+                           "candidates_ms": {f'{t["patch_elems"]}/{t["block_threads"]}': t["ms"]
+                                             for t in tuned["timings"]}}},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "alg_bytes_per_launch": abytes, "avg_launch_ms": avg_s * 1e3,

@@ -52,6 +52,9 @@ struct PatchDesc {
     int n_slots;           // local CSR slots, every row padded to a multiple of 4
 };
 
+// nodes per NodeBlock (boundary kernels: 2 nodes per thread of a 128-thread CTA)
+constexpr int kNodeBlock = 256;
+
 struct NodeBlock {  // a run of node indices of one mesh
     int mesh, begin, count, pad;
 };
@@ -124,6 +127,7 @@ struct Launch {
     // size and bytes of one of the two shared-memory pipeline stages
     int grid[4] = {0, 0, 0, 0};
     int stage[4] = {0, 0, 0, 0};
+    int bgrid[2] = {0, 0};  // boundary kernels (fwd, adj): CTAs striding over bnd_blocks
 };
 
 // --------------------------------------------------------------------------
@@ -131,6 +135,7 @@ struct Launch {
 // --------------------------------------------------------------------------
 size_t patch_smem_bytes(int n_rec, int n_loc, int n_int, int n_slots, bool adjoint);
 int patch_grid(int which, int threads, int stage_bytes, int n_patches, int num_sms);
+int boundary_grid(int adjoint, int n_blocks, int num_sms);
 void set_kernel_smem_limits(size_t bytes);
 // kernels whose launches can be timed one by one (gs_profile)
 enum { KT_TET_FWD, KT_CLOTH_FWD, KT_FWD_BND, KT_TET_ADJ, KT_CLOTH_ADJ, KT_ADJ_BND, KT_COUNT };

@@ -701,31 +701,103 @@ __global__ void k_cloth_adj(const PatchDesc* __restrict__ patches, int n_patches
     patch_pipeline<GS_CLOTH, true>(patches, n_patches, rts, tick, stage_bytes);
 }
 
-// boundary nodes: sum the per-patch partials in patch order, then finish
-__global__ void k_fwd_boundary(const NodeBlock* __restrict__ blocks, const MeshRT* __restrict__ rts, int tick) {
-    const NodeBlock nb = blocks[blockIdx.x];
-    const MeshRT& m = rts[nb.mesh];
-    if (!(m.active & ACT_FWD)) return;
-    const int ib = m.in_a + m.in_b * tick;
-    for (int i = threadIdx.x; i < nb.count; i += blockDim.x) {
-        const int b = nb.begin + i;
-        const int gid = m.n_int + b;
-        const float4 x4 = bufx(m, ib)[gid], v4 = bufv(m, ib)[gid];
-        node_forward(m, tick, gid, x4, v4, xyz(partial_sum(m, b)));
+// Boundary nodes: sum the node's partials (contiguous, in patch order), then
+// finish the node.  A CTA of 128 threads takes a 256-node block, two nodes
+// per thread, with every independent load of both nodes issued before the
+// dependent ones; CTAs stride over the blocks (grid sized to one wave).
+constexpr int kBndThreads = kNodeBlock / 2;
+
+// fixed-order sums of the partials [k0, k0 + n0) and [k1, k1 + n1), four
+// loads of each row in flight per round (absent terms read as zero)
+__device__ __forceinline__ void partial_sums2(const float4* __restrict__ P, int k0, int n0, int k1, int n1, float4& a0,
+                                              float4& a1) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    a0 = z;
+    a1 = z;
+    const int n = n0 > n1 ? n0 : n1;
+    for (int j = 0; j < n; j += 4) {
+        float4 q0[4], q1[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            q0[t] = j + t < n0 ? P[k0 + j + t] : z;
+            q1[t] = j + t < n1 ? P[k1 + j + t] : z;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            add4(a0, q0[t]);
+            add4(a1, q1[t]);
+        }
     }
 }
 
-__global__ void k_adj_boundary(const NodeBlock* __restrict__ blocks, const MeshRT* __restrict__ rts, int tick) {
-    const NodeBlock nb = blocks[blockIdx.x];
-    const MeshRT& m = rts[nb.mesh];
-    if (!(m.active & ACT_ADJ)) return;
-    const int sb = m.adj_a + m.adj_b * tick;
-    for (int i = threadIdx.x; i < nb.count; i += blockDim.x) {
-        const int b = nb.begin + i;
-        const int gid = m.n_int + b;
-        const float4 x4 = bufx(m, sb)[gid], v4 = bufv(m, sb)[gid], xb4 = m.xb[gid], vb4 = m.vb[gid];
-        const float4 acc = partial_sum(m, b);
-        node_adjoint(m, gid, x4, v4, xb4, vb4, xyz(acc), acc.w);
+__global__ void __launch_bounds__(kBndThreads, 8)
+    k_fwd_boundary(const NodeBlock* __restrict__ blocks, int n_blocks, const MeshRT* __restrict__ rts, int tick) {
+    for (int bi = blockIdx.x; bi < n_blocks; bi += gridDim.x) {
+        const NodeBlock nb = blocks[bi];
+        const MeshRT& m = rts[nb.mesh];
+        if (!(m.active & ACT_FWD)) continue;
+        const int ib = m.in_a + m.in_b * tick;
+        const float4* X = bufx(m, ib);
+        const float4* V = bufv(m, ib);
+        const int i0 = threadIdx.x, i1 = threadIdx.x + kBndThreads;
+        const bool h0 = i0 < nb.count, h1 = i1 < nb.count;
+        const int b0 = nb.begin + i0, b1 = nb.begin + i1;
+        int k0 = 0, e0 = 0, k1 = 0, e1 = 0;
+        float4 x0, v0, x1, v1;
+        if (h0) {
+            k0 = m.bnd_rowptr[b0];
+            e0 = m.bnd_rowptr[b0 + 1];
+            x0 = X[m.n_int + b0];
+            v0 = V[m.n_int + b0];
+        }
+        if (h1) {
+            k1 = m.bnd_rowptr[b1];
+            e1 = m.bnd_rowptr[b1 + 1];
+            x1 = X[m.n_int + b1];
+            v1 = V[m.n_int + b1];
+        }
+        float4 f0, f1;
+        partial_sums2(m.partials, k0, e0 - k0, k1, e1 - k1, f0, f1);
+        if (h0) node_forward(m, tick, m.n_int + b0, x0, v0, xyz(f0));
+        if (h1) node_forward(m, tick, m.n_int + b1, x1, v1, xyz(f1));
+    }
+}
+
+__global__ void __launch_bounds__(kBndThreads, 6)
+    k_adj_boundary(const NodeBlock* __restrict__ blocks, int n_blocks, const MeshRT* __restrict__ rts, int tick) {
+    for (int bi = blockIdx.x; bi < n_blocks; bi += gridDim.x) {
+        const NodeBlock nb = blocks[bi];
+        const MeshRT& m = rts[nb.mesh];
+        if (!(m.active & ACT_ADJ)) continue;
+        const int sb = m.adj_a + m.adj_b * tick;
+        const float4* X = bufx(m, sb);
+        const float4* V = bufv(m, sb);
+        const int i0 = threadIdx.x, i1 = threadIdx.x + kBndThreads;
+        const bool h0 = i0 < nb.count, h1 = i1 < nb.count;
+        const int b0 = nb.begin + i0, b1 = nb.begin + i1;
+        const int g0 = m.n_int + b0, g1 = m.n_int + b1;
+        int k0 = 0, e0 = 0, k1 = 0, e1 = 0;
+        float4 x0, v0, xb0, vb0, x1, v1, xb1, vb1;
+        if (h0) {
+            k0 = m.bnd_rowptr[b0];
+            e0 = m.bnd_rowptr[b0 + 1];
+            x0 = X[g0];
+            v0 = V[g0];
+            xb0 = m.xb[g0];
+            vb0 = m.vb[g0];
+        }
+        if (h1) {
+            k1 = m.bnd_rowptr[b1];
+            e1 = m.bnd_rowptr[b1 + 1];
+            x1 = X[g1];
+            v1 = V[g1];
+            xb1 = m.xb[g1];
+            vb1 = m.vb[g1];
+        }
+        float4 a0, a1;
+        partial_sums2(m.partials, k0, e0 - k0, k1, e1 - k1, a0, a1);
+        if (h0) node_adjoint(m, g0, x0, v0, xb0, vb0, xyz(a0), a0.w);
+        if (h1) node_adjoint(m, g1, x1, v1, xb1, vb1, xyz(a1), a1.w);
     }
 }
 
@@ -1126,6 +1198,20 @@ int patch_grid(int which, int threads, int stage_bytes, int n_patches, int num_s
     return (int)(g < n_patches ? g : n_patches);
 }
 
+// boundary kernels: one wave of CTAs striding over the 256-node blocks
+int boundary_grid(int adjoint, int n_blocks, int num_sms) {
+    if (n_blocks <= 0) return 0;
+    int nb = 0;
+    const void* f = adjoint ? (const void*)k_adj_boundary : (const void*)k_fwd_boundary;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kBndThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    nb = nb < 1 ? 1 : nb;
+    const long long g = (long long)nb * num_sms;
+    return (int)(g < n_blocks ? g : n_blocks);
+}
+
 void set_kernel_smem_limits(size_t bytes) {
     cudaFuncSetAttribute(k_tet_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     cudaFuncSetAttribute(k_cloth_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -1155,7 +1241,8 @@ void launch_forward_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) 
     if (L.n_cloth_patches)
         GS_TIMED(KT_CLOTH_FWD, (k_cloth_fwd<<<L.grid[1], L.threads + 32, 128 + 2 * (size_t)L.stage[1], s>>>(
                                    L.cloth_patches, L.n_cloth_patches, L.rt, tick, L.stage[1])));
-    if (L.n_bnd_blocks) GS_TIMED(KT_FWD_BND, (k_fwd_boundary<<<L.n_bnd_blocks, 256, 0, s>>>(L.bnd_blocks, L.rt, tick)));
+    if (L.n_bnd_blocks)
+        GS_TIMED(KT_FWD_BND, (k_fwd_boundary<<<L.bgrid[0], kBndThreads, 0, s>>>(L.bnd_blocks, L.n_bnd_blocks, L.rt, tick)));
 }
 
 void launch_adjoint_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
@@ -1165,7 +1252,8 @@ void launch_adjoint_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) 
     if (L.n_cloth_patches)
         GS_TIMED(KT_CLOTH_ADJ, (k_cloth_adj<<<L.grid[3], L.threads + 32, 128 + 2 * (size_t)L.stage[3], s>>>(
                                    L.cloth_patches, L.n_cloth_patches, L.rt, tick, L.stage[3])));
-    if (L.n_bnd_blocks) GS_TIMED(KT_ADJ_BND, (k_adj_boundary<<<L.n_bnd_blocks, 256, 0, s>>>(L.bnd_blocks, L.rt, tick)));
+    if (L.n_bnd_blocks)
+        GS_TIMED(KT_ADJ_BND, (k_adj_boundary<<<L.bgrid[1], kBndThreads, 0, s>>>(L.bnd_blocks, L.n_bnd_blocks, L.rt, tick)));
 }
 
 void launch_copy_state(const Launch& L, cudaStream_t s) {

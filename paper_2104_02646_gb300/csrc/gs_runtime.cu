@@ -538,7 +538,7 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     m->smem_fwd = T.smem_fwd;
     m->smem_adj = T.smem_adj;
     m->patches = T.patches;
-    m->bnd_blocks = make_blocks(0, T.n_bnd, 256, 0);
+    m->bnd_blocks = make_blocks(0, T.n_bnd, kNodeBlock, 0);
     m->node_blocks = make_blocks(0, N, 256, 0);
     const size_t need = std::max(128 + 2 * T.smem_adj, sizeof(double) * (3 * (size_t)T.max_loc + 4 * (size_t)T.max_rec + 1));
     if (need > ctx->smem_optin)
@@ -870,6 +870,8 @@ gs_status LaunchSet::build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStrea
     launch.grid[1] = patch_grid(1, threads, launch.stage[1], (int)cp.size(), c->num_sms);
     launch.grid[2] = patch_grid(2, threads, launch.stage[2], (int)tp.size(), c->num_sms);
     launch.grid[3] = patch_grid(3, threads, launch.stage[3], (int)cp.size(), c->num_sms);
+    launch.bgrid[0] = boundary_grid(0, (int)bb.size(), c->num_sms);
+    launch.bgrid[1] = boundary_grid(1, (int)bb.size(), c->num_sms);
     return sync_rt(s);
 }
 
@@ -928,8 +930,12 @@ gs_status LaunchSet::rollout(const std::vector<float>& dts, int S, int K, const 
                              double* loss_dev, cudaStream_t s) {
     if (S < 0) return set_error(GS_EINVAL, "n_steps must be >= 0");
     K = choose_K(S, K);
+    // K = 1 keeps every state (state n in buffer 1 + n): the adjoint then
+    // needs no recomputation.  Otherwise checkpoints 1..n_ck hold the states
+    // c K and K + 1 further buffers hold a recomputed segment.
+    const bool all = K == 1;
     const int n_ck = std::max(1, (S + K - 1) / K);
-    const int n_bufs = 1 + n_ck + K + 1;
+    const int n_bufs = all ? S + 2 : 1 + n_ck + K + 1;
     gs_status warn = GS_OK;
     for (size_t i = 0; i < meshes.size(); ++i) {
         gs_mesh* m = meshes[i];
@@ -952,15 +958,36 @@ gs_status LaunchSet::rollout(const std::vector<float>& dts, int S, int K, const 
     }
     GS_TRY(sync_rt(s));
     launch_copy_state(launch, s);
-    for (int c = 0; c < n_ck; ++c) {
-        const int steps = std::min(K, S - c * K);
+    if (all) {
+        // tick t reads buffer 1 + t and writes 2 + t; the final state is then
+        // copied to buffer 0 (the current state)
         for (gs_mesh* m : meshes) {
-            m->rt.in_a = m->rt.in_b = m->rt.out_a = m->rt.out_b = 0;
-            m->rt.ck_tick = (c + 1 < n_ck) ? steps - 1 : -1;
-            m->rt.ck_buf = 2 + c;
+            m->rt.in_a = 1;
+            m->rt.in_b = 1;
+            m->rt.out_a = 2;
+            m->rt.out_b = 1;
+            m->rt.ck_tick = -1;
         }
         GS_TRY(sync_rt(s));
-        GS_TRY(run(0, steps, s));
+        GS_TRY(run(0, S, s));
+        for (gs_mesh* m : meshes) {
+            m->rt.in_a = m->rt.in_b = m->rt.out_a = m->rt.out_b = 0;
+            m->rt.cp_src = S + 1;
+            m->rt.cp_dst = 0;
+        }
+        GS_TRY(sync_rt(s));
+        launch_copy_state(launch, s);
+    } else {
+        for (int c = 0; c < n_ck; ++c) {
+            const int steps = std::min(K, S - c * K);
+            for (gs_mesh* m : meshes) {
+                m->rt.in_a = m->rt.in_b = m->rt.out_a = m->rt.out_b = 0;
+                m->rt.ck_tick = (c + 1 < n_ck) ? steps - 1 : -1;
+                m->rt.ck_buf = 2 + c;
+            }
+            GS_TRY(sync_rt(s));
+            GS_TRY(run(0, steps, s));
+        }
     }
     for (gs_mesh* m : meshes) m->rt.ck_tick = -1;
     GS_TRY(sync_rt(s));
@@ -982,7 +1009,9 @@ gs_status LaunchSet::rollout(const std::vector<float>& dts, int S, int K, const 
 
 // discrete adjoint over the whole rollout: per segment (last first) restore
 // the checkpoint, recompute and store the segment's states, then run the
-// reverse steps (App. B)
+// reverse steps (App. B).  A segment of n steps needs its states 0..n-1, so
+// n - 1 forward steps are recomputed; with every state kept (K = 1) the
+// reverse steps read the stored states directly.
 gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std::vector<const float*>& seed_v,
                              const std::vector<gs_grads>& grads, int keep, cudaStream_t s) {
     for (gs_mesh* m : meshes)
@@ -1010,7 +1039,17 @@ gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std:
         if (m->rt.g_hact) launch_zero_f64((double*)m->g_hact.p, m->info.n_hinges, s);
     }
     const int seg0 = 1 + n_ck;
-    for (int sg = n_ck - 1; sg >= 0; --sg) {
+    if (K == 1) {
+        // tick t reverses step S-1-t, whose input state is in buffer S - t
+        for (gs_mesh* m : meshes) {
+            m->rt.ck_tick = -1;
+            m->rt.adj_a = S;
+            m->rt.adj_b = -1;
+        }
+        GS_TRY(sync_rt(s));
+        GS_TRY(run(1, S, s));
+    }
+    for (int sg = K == 1 ? -1 : n_ck - 1; sg >= 0; --sg) {
         const int steps = std::min(K, S - sg * K);
         for (gs_mesh* m : meshes) {
             MeshRT& r = m->rt;
@@ -1026,7 +1065,7 @@ gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std:
         }
         GS_TRY(sync_rt(s));
         launch_copy_state(launch, s);
-        GS_TRY(run(0, steps, s));
+        GS_TRY(run(0, steps - 1, s));
         GS_TRY(run(1, steps, s));
     }
     for (size_t i = 0; i < meshes.size(); ++i) {

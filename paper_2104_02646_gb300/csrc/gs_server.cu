@@ -59,6 +59,7 @@ struct Query {
     int chunk = 0;          // forward chunk or segment index
     int t0 = 0;             // tick at which the phase started
     int steps = 0;          // steps of the phase
+    int seg_steps = 0;      // steps of the current reverse segment
     int done = 0;           // steps done in the phase
     bool cancelled = false;
     gs_status build_status = GS_OK;
@@ -143,7 +144,9 @@ gs_status gs_server::enter_phase(Query* q) {
         r.ck_tick = (q->chunk + 1 < q->n_ck) ? q->t0 + q->steps - 1 : -1;
         r.ck_buf = 2 + q->chunk;
     } else if (q->phase == P_REC) {
-        q->steps = std::min(q->K, q->S - q->chunk * q->K);
+        // a segment of n steps needs its states 0..n-1: n - 1 forward steps
+        q->seg_steps = std::min(q->K, q->S - q->chunk * q->K);
+        q->steps = q->seg_steps - 1;
         r.active = ACT_FWD;
         r.cp_src = 1 + q->chunk;
         r.cp_dst = seg0;
@@ -439,9 +442,8 @@ void gs_server::run() {
                         set_phase(q, P_REC, q->n_ck - 1);
                     }
                 } else if (q->phase == P_REC) {
-                    const int st = q->steps;
                     set_phase(q, P_ADJ, q->chunk);
-                    q->steps = st;
+                    q->steps = q->seg_steps;
                 } else if (q->phase == P_ADJ) {
                     if (q->chunk > 0) {
                         set_phase(q, P_REC, q->chunk - 1);

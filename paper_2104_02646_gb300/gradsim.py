@@ -252,6 +252,7 @@ class Context:
 
     def __init__(self, device: int = 0, budget: int = 0, torch_alloc: bool = False):
         self.h = _vp()
+        self.device = int(device)
         self._cb = None
         alloc = None
         if torch_alloc:

@@ -90,3 +90,22 @@ def test_batch_bitwise_equal_to_alone(gs, ctx):
         assert float(loss[i]) == a["loss"]
         for k in grads[i]:
             np.testing.assert_array_equal(grads[i][k].cpu().numpy(), a[k].astype(grads[i][k].cpu().numpy().dtype))
+
+
+@pytest.mark.gpu
+def test_autotune_picks_a_working_shape(gs, ctx, tmp_path):
+    from paper_2104_02646_gb300 import autotune as A
+    p = I.block(n=8, steps=30, seed=4)
+    cache = str(tmp_path / "tune.json")
+    r = A.tune(ctx, p, steps=5, cache=cache, candidates=((256, 128), (128, 64), (100000, 128)))
+    assert (r["patch_elems"], r["block_threads"]) in ((256, 128), (128, 64))
+    assert r["K"] == 1  # a 30-step rollout of 729 nodes fits any budget
+    # the too-large patch is skipped, not fatal
+    assert any(t["ms"] is None for t in r["timings"])
+    again = A.tune(ctx, p, steps=5, cache=cache)
+    assert again["cached"] and again["patch_elems"] == r["patch_elems"]
+    # the tuned shape gives the same gradients as the default one
+    tgt = make_target(p, 30)
+    a = run_gpu(gs, ctx, p, 30, tgt, K=r["K"], patch_elems=r["patch_elems"], block_threads=r["block_threads"])
+    b = run_gpu(gs, ctx, p, 30, tgt)
+    assert rel(a["d_mu"], b["d_mu"]) <= 1e-5

@@ -114,9 +114,11 @@ def test_checkpoint_interval_does_not_change_results(gs, ctx):
     a = run_gpu(gs, ctx, p, 57, tgt, K=1, patch_elems=200)
     b = run_gpu(gs, ctx, p, 57, tgt, K=8, patch_elems=200)
     c = run_gpu(gs, ctx, p, 57, tgt, K=57, patch_elems=200)
-    for k in ("x", "d_mu", "d_lambda", "d_density", "d_v0", "d_x0"):
+    d = run_gpu(gs, ctx, p, 57, tgt, K=2, patch_elems=200)  # last segment of one step
+    for k in ("x", "v", "d_mu", "d_lambda", "d_density", "d_v0", "d_x0"):
         np.testing.assert_array_equal(a[k], b[k])
         np.testing.assert_array_equal(a[k], c[k])
+        np.testing.assert_array_equal(a[k], d[k])
 
 
 def test_deterministic_and_graphs_match_plain_loop(gs, ctx):
