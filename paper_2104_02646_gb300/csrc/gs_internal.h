@@ -61,7 +61,7 @@ struct NodeBlock {  // a run of node indices of one mesh
 
 enum { ACT_FWD = 1, ACT_ADJ = 2 };
 
-struct MeshRT {
+struct alignas(16) MeshRT {  // 16 B aligned: the patch kernels bulk-copy it into shared memory
     // static mesh data
     int kind, n_nodes, n_int, n_bnd;
     int n_elems, n_hinges, active, pad0;

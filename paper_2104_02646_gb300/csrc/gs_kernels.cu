@@ -108,7 +108,7 @@ __host__ __device__ __forceinline__ int r16(int bytes) { return (bytes + 15) & ~
 // state.  The adjoint also holds v_hat for all local nodes, the interior
 // adjoint state and the boundary nodes' raw adjoint state.
 struct Layout {
-    int rec, rp, sl, pos, xs, vh, vs, xb, vb, xbB, vbB, gmu, glam, total;
+    int rec, rp, sl, pos, xs, vh, vs, xb, vb, xbB, vbB, gmu, glam, wb, total;
 };
 
 __host__ __device__ __forceinline__ Layout patch_layout(int n_rec, int n_loc, int n_int, int n_slots, bool adjoint) {
@@ -128,7 +128,9 @@ __host__ __device__ __forceinline__ Layout patch_layout(int n_rec, int n_loc, in
     // adjoint: the patch's FP64 dL/dmu, dL/dlambda accumulators (records 0..n_rec)
     L.gmu = L.vbB + (adjoint ? 16 * n_bnd : 0);
     L.glam = L.gmu + (adjoint ? r16(8 * n_rec) : 0);
-    L.total = L.glam + (adjoint ? r16(8 * n_rec) : 0);
+    // adjoint: dL/dw of the interior nodes
+    L.wb = L.glam + (adjoint ? r16(8 * n_rec) : 0);
+    L.total = L.wb + (adjoint ? r16(8 * n_int) : 0);
     return L;
 }
 
@@ -138,6 +140,9 @@ __device__ __forceinline__ void cp16(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp4(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
@@ -235,10 +240,10 @@ __device__ __forceinline__ void node_forward(const MeshRT& m, int tick, int gid,
 
 // reverse of node_forward for one node.  Inputs: state (u, v) at step n, the
 // adjoint (xb, vb) of step n+1, the gathered element terms xsum = sum of
-// corner dL/du and ssum = sum of corner f . v_hat.  Writes the adjoint of
-// step n and accumulates dL/dw (FP64).
+// corner dL/du and ssum = sum of corner f . v_hat, and dL/dw so far.  Writes
+// the adjoint of step n and the accumulated dL/dw (FP64).
 __device__ __forceinline__ void node_adjoint(const MeshRT& m, int gid, float4 x4, float4 v4, float4 xb4, float4 vb4,
-                                             float3 xsum, float ssum) {
+                                             float3 xsum, float ssum, double wb_old) {
     const float w = x4.w;
     const float3 xbn = xyz(xb4);
     const float3 vh = xyz(vb4) + m.dt * xbn;    // dL/dv+ (total)
@@ -248,7 +253,7 @@ __device__ __forceinline__ void node_adjoint(const MeshRT& m, int gid, float4 x4
     const float3 fc = contact_adjoint(m, gid, xyz(x4), xyz(v4), v4.w, fb, xb, vb);
     m.xb[gid] = f4(xb, 0.0f);
     m.vb[gid] = f4(vb, 0.0f);
-    m.wbar[gid] += (double)(m.dt * (ssum + dot3(fc, vh)));
+    m.wbar[gid] = wb_old + (double)(m.dt * (ssum + dot3(fc, vh)));
 }
 
 // A staged patch in shared memory.
@@ -267,6 +272,7 @@ struct Stage {
     float4* vbB;  // adjoint: boundary v_bar (raw)
     double* gmu;  // adjoint: staged accumulators of the patch's elements
     double* glam;
+    double* wb;   // adjoint: dL/dw of the interior nodes
 };
 
 __device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned char* buf, bool adjoint) {
@@ -288,6 +294,7 @@ __device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned
     S.vbB = (float4*)(buf + L.vbB);
     S.gmu = (double*)(buf + L.gmu);
     S.glam = (double*)(buf + L.glam);
+    S.wb = (double*)(buf + L.wb);
     return S;
 }
 
@@ -296,10 +303,10 @@ __device__ __forceinline__ int in_buffer(const MeshRT& m, int tick, bool adjoint
     return adjoint ? m.adj_a + m.adj_b * tick : m.in_a + m.in_b * tick;
 }
 
-// Elected thread: bulk copies of the patch's records, CSR and interior node
-// data into `buf`, completing on `bar` (called by thread 0 only).
-__device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT& m, int tick, unsigned char* buf,
-                                           uint64_t* bar, bool adjoint) {
+// Elected thread: bulk copies of the mesh record (into `hdr_rt`) and of the
+// patch's records, CSR and interior node data into `buf`, completing on `bar`.
+__device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_global, const MeshRT& m, int tick,
+                                           unsigned char* buf, MeshRT* hdr_rt, uint64_t* bar, bool adjoint) {
     const Stage S = stage_at(p, m.kind, buf, adjoint);
     const int n_loc = p.n_int + p.n_bnd;
     const int n_rec = S.n_rec;
@@ -311,9 +318,11 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT& m, 
     // accumulators are staged for the tet / triangle records (8 B each, the
     // copy rounded up to 16 B into the arrays' tail padding)
     const uint32_t b_g = adjoint ? (uint32_t)r16(8 * p.n_e) : 0u;
-    const uint32_t tx = 64u * n_rec + b_rp + b_sl + (p.n_int ? (adjoint ? 4u : 2u) * b_int : 0u) + 2u * b_g;
+    const uint32_t tx = (uint32_t)sizeof(MeshRT) + 64u * n_rec + b_rp + b_sl +
+                        (p.n_int ? (adjoint ? 4u : 2u) * b_int : 0u) + 2u * b_g;
     fence_proxy_async();
     mbar_expect_tx(bar, tx);
+    bulk_g2s(hdr_rt, rt_global, (uint32_t)sizeof(MeshRT), bar);
     for (int k = 0; k < 4; ++k) {
         if (p.n_e) bulk_g2s(S.rec + k * n_rec, m.rec + (size_t)k * m.n_elems + p.e_begin, 16u * p.n_e, bar);
         if (p.n_h) bulk_g2s(S.rec + k * n_rec + p.n_e, m.hrec + (size_t)k * m.n_hinges + p.h_begin, 16u * p.n_h, bar);
@@ -335,34 +344,58 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT& m, 
 }
 
 // producer warp: asynchronous gather of the boundary nodes' state (and their
-// partial positions) into `buf`; ids for 4 x 32 nodes are loaded before their
-// copies are issued
-__device__ __forceinline__ void produce_gather(const PatchDesc& p, const MeshRT& m, int tick, unsigned char* buf,
-                                               bool adjoint, int lane) {
-    const Stage S = stage_at(p, m.kind, buf, adjoint);
-    const float4* X = bufx(m, in_buffer(m, tick, adjoint));
-    const int* ids = m.bnd_ids + p.bnd_begin;
-    const int* pos = m.part_pos + p.bnd_begin;
-    for (int k0 = 0; k0 < p.n_bnd; k0 += 128) {
-        int g[4];
+// partial positions) into `buf`; the ids of the first 128 boundary nodes
+// (`g`, lane + 32 j) and the state pointer X were loaded ahead.  The adjoint
+// also stages dL/dw of the interior nodes.
+constexpr int kPrefetchIds = 4;
+
+__device__ __forceinline__ void prefetch_ids(const PatchDesc& p, const MeshRT& m, int lane, int* g) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kPrefetchIds; ++j) {
+        const int k = lane + 32 * j;
+        g[j] = k < p.n_bnd ? m.bnd_ids[p.bnd_begin + k] : 0;
+    }
+}
+
+__device__ __forceinline__ void produce_gather(const PatchDesc& p, const MeshRT& m, const float4* X, const int* g,
+                                               unsigned char* buf, bool adjoint, int lane) {
+    const Stage S = stage_at(p, m.kind, buf, adjoint);
+    const int* pos = m.part_pos + p.bnd_begin;
+#pragma unroll
+    for (int j = 0; j < kPrefetchIds; ++j) {
+        const int k = lane + 32 * j;
+        if (k < p.n_bnd) {
+            cp16(S.xs + p.n_int + k, X + g[j]);
+            cp4(S.pos + k, pos + k);
+            if (adjoint) {
+                cp16(S.xbB + k, m.xb + g[j]);
+                cp16(S.vbB + k, m.vb + g[j]);
+            }
+        }
+    }
+    const int* ids = m.bnd_ids + p.bnd_begin;
+    for (int k0 = 32 * kPrefetchIds; k0 < p.n_bnd; k0 += 32 * kPrefetchIds) {
+        int h[kPrefetchIds];
+#pragma unroll
+        for (int j = 0; j < kPrefetchIds; ++j) {
             const int k = k0 + lane + 32 * j;
-            g[j] = k < p.n_bnd ? ids[k] : 0;
+            h[j] = k < p.n_bnd ? ids[k] : 0;
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < kPrefetchIds; ++j) {
             const int k = k0 + lane + 32 * j;
             if (k < p.n_bnd) {
-                cp16(S.xs + p.n_int + k, X + g[j]);
+                cp16(S.xs + p.n_int + k, X + h[j]);
                 cp4(S.pos + k, pos + k);
                 if (adjoint) {
-                    cp16(S.xbB + k, m.xb + g[j]);
-                    cp16(S.vbB + k, m.vb + g[j]);
+                    cp16(S.xbB + k, m.xb + h[j]);
+                    cp16(S.vbB + k, m.vb + h[j]);
                 }
             }
         }
     }
+    if (adjoint)
+        for (int l = lane; l < p.n_int; l += 32) cp8(S.wb + l, m.wbar + p.int_begin + l);
 }
 
 // corner c of record r is written in place into plane c, row r; a CSR slot is
@@ -554,7 +587,8 @@ __device__ __forceinline__ void adjoint_nodes(const PatchDesc& p, const MeshRT& 
     const int n_loc = p.n_int + p.n_bnd;
     for (int l = threadIdx.x; l < n_loc; l += nt) {
         const float4 acc = row_sum4(S, S.rp[l], S.rp[l + 1]);
-        if (l < p.n_int) node_adjoint(m, p.int_begin + l, S.xs[l], S.vs[l], S.xb[l], S.vb[l], xyz(acc), acc.w);
+        if (l < p.n_int)
+            node_adjoint(m, p.int_begin + l, S.xs[l], S.vs[l], S.xb[l], S.vb[l], xyz(acc), acc.w, S.wb[l]);
         else m.partials[S.pos[l - p.n_int]] = acc;
     }
 }
@@ -591,9 +625,19 @@ __device__ __forceinline__ float4 partial_sum(const MeshRT& m, int b) {
 // producer lane) and the expected bytes; empty[s] after one arrival per
 // consumer warp.
 // ---------------------------------------------------------------------------
-constexpr int kHdr = 64;  // stage header: the patch descriptor
+// stage header: the patch descriptor at 0, the mesh record at kHdrRt
+constexpr int kHdrRt = 64;
+constexpr int kHdr = kHdrRt + (int)((sizeof(MeshRT) + 63) / 64 * 64);
 
 __device__ __forceinline__ void consumer_sync(int nt) { asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory"); }
+
+// first live patch at or after `pi` in steps of gridDim.x
+__device__ __forceinline__ int next_live(const PatchDesc* __restrict__ patches, int n_patches,
+                                         const MeshRT* __restrict__ rts, int pi, int mask) {
+    for (; pi < n_patches; pi += gridDim.x)
+        if (rts[patches[pi].mesh].active & mask) break;
+    return pi;
+}
 
 template <int KIND, bool ADJ>
 __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ patches, int n_patches,
@@ -616,20 +660,22 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
     if (n_patches <= 0) return;
     int* const status = rts[patches[blockIdx.x < n_patches ? blockIdx.x : 0].mesh].status;
     if (warp == (nt >> 5)) {
-        // ---- producer warp ----
-        int pi = blockIdx.x;
+        // ---- producer warp: the next patch's descriptor, boundary ids and
+        // state pointer are loaded while waiting for its stage ----
+        int pi = next_live(patches, n_patches, rts, blockIdx.x, mask);
+        PatchDesc p;
+        int g[kPrefetchIds];
+        const float4* X = nullptr;
+        if (pi < n_patches) {
+            p = patches[pi];
+            prefetch_ids(p, rts[p.mesh], lane, g);
+            X = bufx(rts[p.mesh], in_buffer(rts[p.mesh], tick, ADJ));
+        }
         for (int it = 0;; ++it) {
-            PatchDesc p;
-            p.n_e = -1;
-            for (; pi < n_patches; pi += gridDim.x) {
-                p = patches[pi];
-                if (rts[p.mesh].active & mask) break;
-            }
-            const bool done = pi >= n_patches;
             const int s = it & 1;
             unsigned char* const b = buf0 + s * stage_bytes;
             if (it >= 2 && !mbar_wait_bounded(&empty[s], ((it >> 1) - 1) & 1u, status)) return;
-            if (done) {
+            if (pi >= n_patches) {
                 if (lane == 0) ((PatchDesc*)b)->n_e = -1;  // end marker
                 __syncwarp();
                 mbar_arrive(&full[s]);
@@ -639,21 +685,26 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
             const MeshRT& m = rts[p.mesh];
             if (lane == 0) {
                 *(PatchDesc*)b = p;
-                issue_bulk(p, m, tick, b + kHdr, &full[s], ADJ);
+                issue_bulk(p, &rts[p.mesh], m, tick, b + kHdr, (MeshRT*)(b + kHdrRt), &full[s], ADJ);
             }
-            produce_gather(p, m, tick, b + kHdr, ADJ, lane);
+            produce_gather(p, m, X, g, b + kHdr, ADJ, lane);
             cp_async_mbar_arrive(&full[s]);
-            pi += gridDim.x;
+            pi = next_live(patches, n_patches, rts, pi + gridDim.x, mask);
+            if (pi < n_patches) {
+                p = patches[pi];
+                prefetch_ids(p, rts[p.mesh], lane, g);
+                X = bufx(rts[p.mesh], in_buffer(rts[p.mesh], tick, ADJ));
+            }
         }
     }
-    // ---- consumer warps ----
+    // ---- consumer warps: descriptor and mesh record from the stage header ----
     for (int it = 0;; ++it) {
         const int s = it & 1;
         unsigned char* const b = buf0 + s * stage_bytes;
         if (!mbar_wait_bounded(&full[s], (it >> 1) & 1u, status)) return;
         const PatchDesc p = *(const PatchDesc*)b;
         if (p.n_e < 0) return;
-        const MeshRT& m = rts[p.mesh];
+        const MeshRT& m = *(const MeshRT*)(b + kHdrRt);
         const Stage S = stage_at(p, KIND, b + kHdr, ADJ);
         if (ADJ) {
             for (int l = threadIdx.x; l < p.n_int; l += nt) S.vh[l] = f4(xyz(S.vb[l]) + m.dt * xyz(S.xb[l]), 0.f);
@@ -778,6 +829,7 @@ __global__ void __launch_bounds__(kBndThreads, 6)
         const int g0 = m.n_int + b0, g1 = m.n_int + b1;
         int k0 = 0, e0 = 0, k1 = 0, e1 = 0;
         float4 x0, v0, xb0, vb0, x1, v1, xb1, vb1;
+        double w0 = 0.0, w1 = 0.0;
         if (h0) {
             k0 = m.bnd_rowptr[b0];
             e0 = m.bnd_rowptr[b0 + 1];
@@ -785,6 +837,7 @@ __global__ void __launch_bounds__(kBndThreads, 6)
             v0 = V[g0];
             xb0 = m.xb[g0];
             vb0 = m.vb[g0];
+            w0 = m.wbar[g0];
         }
         if (h1) {
             k1 = m.bnd_rowptr[b1];
@@ -793,11 +846,12 @@ __global__ void __launch_bounds__(kBndThreads, 6)
             v1 = V[g1];
             xb1 = m.xb[g1];
             vb1 = m.vb[g1];
+            w1 = m.wbar[g1];
         }
         float4 a0, a1;
         partial_sums2(m.partials, k0, e0 - k0, k1, e1 - k1, a0, a1);
-        if (h0) node_adjoint(m, g0, x0, v0, xb0, vb0, xyz(a0), a0.w);
-        if (h1) node_adjoint(m, g1, x1, v1, xb1, vb1, xyz(a1), a1.w);
+        if (h0) node_adjoint(m, g0, x0, v0, xb0, vb0, xyz(a0), a0.w, w0);
+        if (h1) node_adjoint(m, g1, x1, v1, xb1, vb1, xyz(a1), a1.w, w1);
     }
 }
 
