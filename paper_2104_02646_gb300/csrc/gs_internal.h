@@ -45,7 +45,7 @@ struct PatchDesc {
     int e_begin, n_e;      // elements (tets or triangles), internal order
     int h_begin, n_h;      // hinges (cloth)
     int int_begin, n_int;  // interior nodes: internal ids [int_begin, int_begin + n_int)
-    int bnd_begin, n_bnd;  // boundary local nodes: bnd_ids / partials [bnd_begin, +n_bnd), 16 B aligned
+    int bnd_begin, n_bnd;  // boundary local nodes: bnd_ids / part_pos [bnd_begin, +n_bnd); bnd_begin % 4 == 0
     int lr_begin;          // local CSR row pointers: n_int + n_bnd + 1 entries (16 B aligned)
     int slot_begin;        // local CSR slot list (16 B aligned)
     int mesh;              // index into the launch set's MeshRT array

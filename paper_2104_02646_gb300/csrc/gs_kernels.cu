@@ -318,7 +318,8 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
     // accumulators are staged for the tet / triangle records (8 B each, the
     // copy rounded up to 16 B into the arrays' tail padding)
     const uint32_t b_g = adjoint ? (uint32_t)r16(8 * p.n_e) : 0u;
-    const uint32_t tx = (uint32_t)sizeof(MeshRT) + 64u * n_rec + b_rp + b_sl +
+    const uint32_t b_pos = (uint32_t)r16(4 * p.n_bnd);
+    const uint32_t tx = (uint32_t)sizeof(MeshRT) + 64u * n_rec + b_rp + b_sl + b_pos +
                         (p.n_int ? (adjoint ? 4u : 2u) * b_int : 0u) + 2u * b_g;
     fence_proxy_async();
     mbar_expect_tx(bar, tx);
@@ -329,6 +330,7 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
     }
     bulk_g2s(S.rp, m.loc_rowptr + p.lr_begin, b_rp, bar);
     bulk_g2s(S.sl, m.loc_slots + p.slot_begin, b_sl, bar);
+    if (b_pos) bulk_g2s(S.pos, m.part_pos + p.bnd_begin, b_pos, bar);
     if (p.n_int) {
         bulk_g2s(S.xs, X + p.int_begin, b_int, bar);
         bulk_g2s(S.vs, V + p.int_begin, b_int, bar);
@@ -343,8 +345,8 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
     }
 }
 
-// producer warp: asynchronous gather of the boundary nodes' state (and their
-// partial positions) into `buf`; the ids of the first 128 boundary nodes
+// producer warp: asynchronous gather of the boundary nodes' state into `buf`;
+// the ids of the first 128 boundary nodes
 // (`g`, lane + 32 j) and the state pointer X were loaded ahead.  The adjoint
 // also stages dL/dw of the interior nodes.
 constexpr int kPrefetchIds = 4;
@@ -360,13 +362,11 @@ __device__ __forceinline__ void prefetch_ids(const PatchDesc& p, const MeshRT& m
 __device__ __forceinline__ void produce_gather(const PatchDesc& p, const MeshRT& m, const float4* X, const int* g,
                                                unsigned char* buf, bool adjoint, int lane) {
     const Stage S = stage_at(p, m.kind, buf, adjoint);
-    const int* pos = m.part_pos + p.bnd_begin;
 #pragma unroll
     for (int j = 0; j < kPrefetchIds; ++j) {
         const int k = lane + 32 * j;
         if (k < p.n_bnd) {
             cp16(S.xs + p.n_int + k, X + g[j]);
-            cp4(S.pos + k, pos + k);
             if (adjoint) {
                 cp16(S.xbB + k, m.xb + g[j]);
                 cp16(S.vbB + k, m.vb + g[j]);
@@ -386,7 +386,6 @@ __device__ __forceinline__ void produce_gather(const PatchDesc& p, const MeshRT&
             const int k = k0 + lane + 32 * j;
             if (k < p.n_bnd) {
                 cp16(S.xs + p.n_int + k, X + h[j]);
-                cp4(S.pos + k, pos + k);
                 if (adjoint) {
                     cp16(S.xbB + k, m.xb + h[j]);
                     cp16(S.vbB + k, m.vb + h[j]);
@@ -548,30 +547,39 @@ __device__ __forceinline__ void add3(float3& acc, float4 q) {
     acc.y += q.y;
     acc.z += q.z;
 }
-__device__ __forceinline__ float4 row_sum4(const Stage& S, int k, int k1) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (; k < k1; k += 4) {
-        const uint2 q = *reinterpret_cast<const uint2*>(S.sl + k);
-        const float4 q0 = S.rec[q.x & 0xffff], q1 = S.rec[q.x >> 16], q2 = S.rec[q.y & 0xffff], q3 = S.rec[q.y >> 16];
-        add4(acc, q0);
-        add4(acc, q1);
-        add4(acc, q2);
-        add4(acc, q3);
-    }
+// software-pipelined: the next group's slot and corner loads are issued
+// before the current group's adds
+#define GS_ROW_SUM(T, ADD, ZERO)                                                                            \
+    T acc = ZERO;                                                                                           \
+    if (k >= k1) return acc;                                                                                \
+    uint2 q = *reinterpret_cast<const uint2*>(S.sl + k);                                                    \
+    float4 c0 = S.rec[q.x & 0xffff], c1 = S.rec[q.x >> 16], c2 = S.rec[q.y & 0xffff], c3 = S.rec[q.y >> 16]; \
+    for (k += 4; k < k1; k += 4) {                                                                          \
+        q = *reinterpret_cast<const uint2*>(S.sl + k);                                                      \
+        const float4 n0 = S.rec[q.x & 0xffff], n1 = S.rec[q.x >> 16], n2 = S.rec[q.y & 0xffff],              \
+                     n3 = S.rec[q.y >> 16];                                                                 \
+        ADD(acc, c0);                                                                                       \
+        ADD(acc, c1);                                                                                       \
+        ADD(acc, c2);                                                                                       \
+        ADD(acc, c3);                                                                                       \
+        c0 = n0;                                                                                            \
+        c1 = n1;                                                                                            \
+        c2 = n2;                                                                                            \
+        c3 = n3;                                                                                            \
+    }                                                                                                       \
+    ADD(acc, c0);                                                                                           \
+    ADD(acc, c1);                                                                                           \
+    ADD(acc, c2);                                                                                           \
+    ADD(acc, c3);                                                                                           \
     return acc;
+
+__device__ __forceinline__ float4 row_sum4(const Stage& S, int k, int k1) {
+    GS_ROW_SUM(float4, add4, make_float4(0.f, 0.f, 0.f, 0.f))
 }
 __device__ __forceinline__ float3 row_sum3(const Stage& S, int k, int k1) {
-    float3 acc = make_float3(0.f, 0.f, 0.f);
-    for (; k < k1; k += 4) {
-        const uint2 q = *reinterpret_cast<const uint2*>(S.sl + k);
-        const float4 q0 = S.rec[q.x & 0xffff], q1 = S.rec[q.x >> 16], q2 = S.rec[q.y & 0xffff], q3 = S.rec[q.y >> 16];
-        add3(acc, q0);
-        add3(acc, q1);
-        add3(acc, q2);
-        add3(acc, q3);
-    }
-    return acc;
+    GS_ROW_SUM(float3, add3, make_float3(0.f, 0.f, 0.f))
 }
+#undef GS_ROW_SUM
 
 // node phases: fixed-order corner sums, then interior update or partial
 __device__ __forceinline__ void forward_nodes(const PatchDesc& p, const MeshRT& m, int tick, const Stage& S, int nt) {

@@ -248,6 +248,12 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
             for (int c = 0; c < 4; ++c) note(hcorner(h, c));
         // descending corner count within the patch (similar row lengths per warp)
         std::sort(bl.begin(), bl.end(), [&](int x, int y) { return pdeg[x] != pdeg[y] ? pdeg[x] > pdeg[y] : x < y; });
+        // each patch's list starts 16 B aligned (its partial positions are bulk-copied)
+        while (T.bnd_ids.size() % 4) {
+            T.bnd_ids.push_back(0);
+            entry_node.push_back(-1);
+            entry_j.push_back(0);
+        }
         q.bnd_begin = (int)T.bnd_ids.size();
         q.n_bnd = (int)bl.size();
         for (int k = 0; k < q.n_bnd; ++k) {
@@ -326,8 +332,12 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
     //    in patch order; each (patch, boundary local node) knows its position
     T.bnd_rowptr.assign(T.n_bnd + 1, 0);
     for (int b = 0; b < T.n_bnd; ++b) T.bnd_rowptr[b + 1] = T.bnd_rowptr[b] + bcount[b];
-    T.part_pos.resize(entry_node.size());
-    for (size_t i = 0; i < entry_node.size(); ++i) T.part_pos[i] = T.bnd_rowptr[entry_node[i]] + entry_j[i];
+    // (padding entries point at partial 0 and are never used; 4 entries of
+    // tail padding keep a rounded-up copy of the last list in bounds)
+    T.part_pos.assign(entry_node.size() + 4, 0);
+    for (size_t i = 0; i < entry_node.size(); ++i)
+        if (entry_node[i] >= 0) T.part_pos[i] = T.bnd_rowptr[entry_node[i]] + entry_j[i];
+    for (int k = 0; k < 4; ++k) T.bnd_ids.push_back(0);
     return GS_OK;
 }
 
