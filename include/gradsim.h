@@ -215,8 +215,10 @@ GS_API gs_status gs_mesh_set_state(gs_mesh* mesh, const float* x, const float* v
  * held as the displacement from X), v = v0.  Enqueued on `stream`. */
 GS_API gs_status gs_mesh_reset(gs_mesh* mesh, void* stream);
 GS_API gs_status gs_mesh_get_state(gs_mesh* mesh, float* x, float* v, int mem_space, void* stream);
-/* Sticky per-mesh status from the device: GS_OK or GS_ENONFINITE (a NaN/Inf
- * appeared in the state since the last reset).  Synchronises the stream. */
+/* Sticky per-mesh status from the device since the last reset: GS_OK,
+ * GS_ETIMEOUT (a bounded wait inside a step kernel ran out: the kernel gave
+ * up on its shared-memory copies and returned; the results are invalid) or
+ * GS_ENONFINITE (a NaN/Inf appeared in the state).  Synchronises the stream. */
 GS_API gs_status gs_mesh_check(gs_mesh* mesh, int reset, void* stream);
 
 /* ---- forward (App. B semi-implicit Euler) --------------------------------- */
@@ -334,6 +336,16 @@ GS_API gs_status gs_query_poll(gs_server* server, uint64_t ticket, gs_result* ou
 GS_API gs_status gs_query_cancel(gs_server* server, uint64_t ticket);
 GS_API gs_status gs_server_stats_get(gs_server* server, gs_server_stats* out);
 GS_API void gs_result_free(gs_result* r);
+
+/* ---- self-test of the kernels' failure path (no paper counterpart) --------
+ * Every wait inside the step kernels (for shared-memory copies, or for a
+ * stage to be released) is bounded; when it runs out the kernel sets status
+ * bit 2, waits once more (bounded) and returns, so that the context stays
+ * usable.  This launches one CTA whose thread waits on a shared-memory
+ * barrier that nothing arrives at, with `iterations` polls (1..1e6), and
+ * writes the status word to *status_out (HOST): 2 when the wait ran out as
+ * designed.  Synchronises the stream.  GS_EINVAL on bad arguments. */
+GS_API gs_status gs_selftest_bounded_wait(int iterations, int* status_out, void* stream);
 
 #ifdef __cplusplus
 }

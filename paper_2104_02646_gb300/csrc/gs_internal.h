@@ -136,6 +136,7 @@ struct Launch {
 size_t patch_smem_bytes(int n_rec, int n_loc, int n_int, int n_slots, bool adjoint);
 int patch_grid(int which, int threads, int stage_bytes, int n_patches, int num_sms);
 int boundary_grid(int adjoint, int n_blocks, int num_sms);
+gs_status selftest_bounded_wait(int iterations, int* status_host, cudaStream_t s);
 void set_kernel_smem_limits(size_t bytes);
 // kernels whose launches can be timed one by one (gs_profile)
 enum { KT_TET_FWD, KT_CLOTH_FWD, KT_FWD_BND, KT_TET_ADJ, KT_CLOTH_ADJ, KT_ADJ_BND, KT_COUNT };

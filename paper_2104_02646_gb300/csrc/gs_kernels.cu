@@ -91,13 +91,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // any real transfer; on expiry the kernel reports GS error bit 2 and, after
 // a second bounded wait for its own copies, the caller returns.
 constexpr int kWaitLimit = 1 << 22;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
-    for (int i = 0; i < kWaitLimit; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status,
+                                                  int limit = kWaitLimit) {
+    for (int i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     atomicOr(status, 2);
-    for (int i = 0; i < kWaitLimit; ++i)
+    for (int i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) break;
     return false;
+}
+
+// one thread waits on a barrier that nothing arrives at, `limit` polls
+__global__ void k_selftest_wait(int limit, int* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        mbar_wait_bounded(&bar, 0u, status, limit);
+    }
 }
 
 __host__ __device__ __forceinline__ int r16(int bytes) { return (bytes + 15) & ~15; }
@@ -1332,6 +1343,21 @@ void launch_loss_finalize(const double* block_partials, int begin, int count, do
 
 void launch_zero_adjoint(const Launch& L, cudaStream_t s) {
     if (L.n_node_blocks) k_zero_adjoint<<<L.n_node_blocks, 256, 0, s>>>(L.node_blocks, L.rt);
+}
+
+gs_status selftest_bounded_wait(int iterations, int* status_host, cudaStream_t s) {
+    int* d = nullptr;
+    GS_CUDA(cudaMallocAsync((void**)&d, sizeof(int), s));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        k_selftest_wait<<<1, 32, 0, s>>>(iterations, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status_host, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "gs_selftest_bounded_wait");
+    return GS_OK;
 }
 
 void launch_zero_f64(double* p, long long n, cudaStream_t s) {

@@ -814,8 +814,16 @@ extern "C" gs_status gs_mesh_check(gs_mesh* m, int reset, void* stream) {
     GS_CUDA(cudaMemcpyAsync(&st, m->status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     GS_CUDA(cudaStreamSynchronize(s));
     if (reset) GS_CUDA(cudaMemsetAsync(m->status.p, 0, sizeof(int), s));
+    if (st & 2) return set_error(GS_ETIMEOUT, "a bounded wait in a step kernel ran out; results are invalid");
     if (st & 1) return set_error(GS_ENONFINITE, "non-finite state");
     return GS_OK;
+}
+
+extern "C" gs_status gs_selftest_bounded_wait(int iterations, int* status_out, void* stream) {
+    clear_error();
+    if (!status_out || iterations < 1 || iterations > 1000000)
+        return set_error(GS_EINVAL, "gs_selftest_bounded_wait: iterations in 1..1e6 and status_out required");
+    return selftest_bounded_wait(iterations, status_out, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------

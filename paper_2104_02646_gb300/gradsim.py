@@ -124,6 +124,7 @@ _PROTOS = {
     "gs_query_cancel": (C.c_int, [_vp, C.c_uint64]),
     "gs_server_stats_get": (C.c_int, [_vp, C.POINTER(gs_server_stats)]),
     "gs_result_free": (None, [C.POINTER(gs_result)]),
+    "gs_selftest_bounded_wait": (C.c_int, [C.c_int, C.POINTER(C.c_int), _vp]),
 }
 
 _lib = None

@@ -249,8 +249,11 @@ def block(n: int = 64, steps: int = 200, seed: int = 0, h: float = 0.025) -> Pro
                    rho=np.full(E, 1000.0), v0=v0, contact=Contact(), dt=5.0e-5, steps=steps)
 
 
-def cloth(variant: str = "3s", n: int = 256, steps: int = 500, grid_scaled: bool = False) -> Problem:
-    """n x n cloth over [0,1]^2 at y = 0.305 draped on a sphere (r 0.3 at (0.5, 0, 0.5)).
+def cloth(variant: str = "3s", n: int = 256, steps: int = 500, grid_scaled: bool = False,
+          height: float = 0.305) -> Problem:
+    """n x n cloth over [0,1]^2 at y = `height` (0.305: 5 mm above the top of
+    the sphere, which it reaches near step 320; below 0.3 the sphere touches
+    it from step 0) draped on a sphere (r 0.3 at (0.5, 0, 0.5)).
 
     "3": mu = 5e3, lambda = 1e4, kb = 1e-2, areal density 0.2, ke = 1e4,
     kd = 10, kf = 1 -- explicitly unstable at dt = 1e-4 (tiny node masses).
@@ -258,7 +261,7 @@ def cloth(variant: str = "3s", n: int = 256, steps: int = 500, grid_scaled: bool
     ``grid_scaled`` multiplies the stiffnesses by ((255/(n-1))^2), the ratio
     of node masses, so a coarser grid keeps the 256^2 grid's time scales.
     """
-    X, tris, hinges = cloth_grid(n, 1.0, 0.305)
+    X, tris, hinges = cloth_grid(n, 1.0, height)
     T, B = tris.shape[0], hinges.shape[0]
     sc = (255.0 / (n - 1)) ** 2 if grid_scaled else 1.0
     if variant == "3":

@@ -11,6 +11,21 @@ CLOTH_KEYS = {"tri_mu": "d_mu", "tri_lam": "d_lambda", "tri_rho": "d_density", "
               "x0": "d_x0", "v0": "d_v0"}
 
 
+# FP32 GPU vs FP64 oracle: positions rel-L2 (centroid-removed norm) <= 1e-4
+# contact-free, <= 1e-3 with contact; gradients rel-L2 <= 1e-3, cosine >= 0.9999
+POS_FREE, POS_CONTACT, GRAD_REL, GRAD_COS = 1e-4, 1e-3, 1e-3, 0.9999
+
+
+def check_grads(g_gpu, g_ref, keys, skip=()):
+    for ok, gk in keys.items():
+        if ok in skip:
+            continue
+        a, b = g_gpu[gk], g_ref[ok]
+        assert np.all(np.isfinite(a)), gk
+        assert rel(a, b) <= GRAD_REL, (gk, rel(a, b))
+        assert cosine(a, b) >= GRAD_COS, (gk, cosine(a, b))
+
+
 def rel_pos(x, ref):
     """C19 position norm: |x - ref|_2 / |ref - centroid(ref)|_2."""
     return float(np.linalg.norm(x - ref) / np.linalg.norm(ref - ref.mean(axis=0)))

@@ -10,26 +10,15 @@ import pytest
 
 from paper_2104_02646_gb300 import inputs as I
 
-from gpu_util import CLOTH_KEYS, TET_KEYS, cosine, make_target, rel, rel_pos, run_gpu, run_oracle
+from gpu_util import (CLOTH_KEYS, GRAD_COS, GRAD_REL, POS_CONTACT, POS_FREE, TET_KEYS, check_grads, cosine,
+                      make_target, rel, rel_pos, run_gpu, run_oracle)
 
 pytestmark = pytest.mark.gpu
-
-POS_FREE, POS_CONTACT, GRAD_REL, GRAD_COS = 1e-4, 1e-3, 1e-3, 0.9999
 
 
 @pytest.fixture(scope="module")
 def ctx(gs):
     return gs.Context(0)
-
-
-def check_grads(g_gpu, g_ref, keys, skip=()):
-    for ok, gk in keys.items():
-        if ok in skip:
-            continue
-        a, b = g_gpu[gk], g_ref[ok]
-        assert np.all(np.isfinite(a)), gk
-        assert rel(a, b) <= GRAD_REL, (gk, rel(a, b))
-        assert cosine(a, b) >= GRAD_COS, (gk, cosine(a, b))
 
 
 def test_bar_1a_contact_free_forward_and_gradients(gs, ctx):
