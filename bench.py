@@ -436,15 +436,22 @@ def _single_mesh_line(args, name, problem, extra_cfg):
     gs.load()
     dev = torch.device("cuda", 0)
     ctx = gs.Context(0)
-    mesh = gs.Mesh(ctx, problem, patch_elems=args.patch, block_threads=args.threads)
     S = problem.steps
+    pe, bt, K = args.patch, args.threads, args.K
+    tuned = None
+    if not args.no_autotune and pe == 0 and bt == 0:
+        from paper_2104_02646_gb300 import autotune
+        tuned = autotune.tune(ctx, problem, steps=min(S, 20), horizon=S, use_cache=False)
+        pe, bt = tuned["patch_elems"], tuned["block_threads"]
+        K = tuned["K"] if K == 0 else K
+    mesh = gs.Mesh(ctx, problem, patch_elems=pe, block_threads=bt)
     target = torch.tensor(problem.X + 1e-3, dtype=torch.float32, device=dev)
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
     g = _grads(problem, dev)
 
     def fwd():
         mesh.reset()
-        mesh.rollout(problem.dt, S, args.K, target, loss)
+        mesh.rollout(problem.dt, S, K, target, loss)
 
     def both():
         fwd()
@@ -464,7 +471,10 @@ def _single_mesh_line(args, name, problem, extra_cfg):
             "us_per_step_fwd_adj": 1e3 * t_all / S, "plain_loop_value": E * S / (t_plain / 1e3),
             "finite": mesh.check_finite() == 0, "dtype": "f32", "data": "synthetic",
             "config": dict(extra_cfg, elems=E, nodes=problem.n_nodes, hinges=problem.n_hinges, steps=S,
-                           dt=problem.dt, patch_elems=mesh.info.patch_elems)}
+                           dt=problem.dt, patch_elems=mesh.info.patch_elems,
+                           block_threads=mesh.info.block_threads, K=mesh_K(K, S),
+                           autotune=None if tuned is None else {
+                               f'{t["patch_elems"]}/{t["block_threads"]}': t["ms"] for t in tuned["timings"]})}
     print(json.dumps(line), flush=True)
 
 
@@ -498,6 +508,10 @@ def workload_batch(args):
     batch = gs.Batch(ctx, meshes)
     S = 300
     E = sum(p.n_elems for p in probs)
+    K = args.K
+    if K == 0 and not args.no_autotune:
+        from paper_2104_02646_gb300 import autotune
+        K = autotune.choose_K(sum(p.n_nodes for p in probs), S, autotune.default_budget())
     targets = [torch.tensor(p.X + 1e-3, dtype=torch.float32, device=dev) for p in probs]
     loss = torch.zeros(len(probs), dtype=torch.float64, device=dev)
     grads = [_grads(p, dev) for p in probs]
@@ -506,7 +520,7 @@ def workload_batch(args):
     def batched():
         for m in meshes:
             m.reset()
-        batch.rollout(dts, S, args.K, targets, loss)
+        batch.rollout(dts, S, K, targets, loss)
         batch.adjoint(grads)
 
     losses = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in probs]
@@ -514,7 +528,7 @@ def workload_batch(args):
     def plain():
         for m, p, t, l, g in zip(meshes, probs, targets, losses, grads):
             m.reset()
-            m.rollout(p.dt, S, args.K, t, l)
+            m.rollout(p.dt, S, K, t, l)
             m.adjoint(g)
 
     batched()
@@ -528,7 +542,7 @@ def workload_batch(args):
             "plain_loop_value": E * S / (t_p / 1e3), "speedup_vs_plain": t_p / t_b,
             "ms_batched": t_b, "ms_plain": t_p, "dtype": "f32", "data": "synthetic",
             "config": {"meshes": len(probs), "tets": E, "nodes": sum(p.n_nodes for p in probs), "steps": S,
-                       "dt": 1e-4, "mesh_create_s": t_create}}
+                       "dt": 1e-4, "K": mesh_K(K, S), "mesh_create_s": t_create}}
     print(json.dumps(line), flush=True)
 
 

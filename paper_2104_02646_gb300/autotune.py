@@ -26,7 +26,7 @@ import time
 STATE_BYTES = 32  # one stored state per node: (u, w) and (v, plane offset) as float4
 
 # (elements per patch, consumer threads per CTA)
-DEFAULT_CANDIDATES = ((256, 128), (128, 128), (256, 256), (384, 128), (512, 256))
+DEFAULT_CANDIDATES = ((256, 128), (128, 128), (256, 256), (384, 128), (512, 256), (128, 64), (64, 64))
 
 
 def state_buffers(S: int, K: int) -> int:

@@ -74,6 +74,16 @@ struct Query {
     double t_submit = 0, t_admit = 0, t_done = 0;
 };
 
+// Checkpoint interval of a query: the server's fixed K, else K = 1 (every
+// state kept: one forward phase and one reverse phase, no recomputation)
+// when those states take at most 1/32 of the budget, else about sqrt(S).
+size_t estimate_bytes(const gs_mesh_desc& d, int S, int K);
+int query_K(const gs_server_opts& o, const gs_mesh_desc& d, int S) {
+    if (o.K > 0) return std::min(o.K, std::max(S, 1));
+    if (o.hbm_budget_bytes == 0 || estimate_bytes(d, S, 1) <= o.hbm_budget_bytes / 32) return 1;
+    return std::max(1, (int)std::ceil(std::sqrt((double)std::max(S, 1))));
+}
+
 size_t estimate_bytes(const gs_mesh_desc& d, int S, int K) {
     const size_t N = d.n_nodes, E = d.n_elems, B = d.kind == GS_CLOTH ? d.n_hinges : 0;
     const int n_ck = std::max(1, (S + K - 1) / K);
@@ -137,7 +147,16 @@ gs_status gs_server::enter_phase(Query* q) {
     gs_mesh* m = q->mesh;
     MeshRT& r = m->rt;
     const int seg0 = 1 + q->n_ck;
-    if (q->phase == P_FWD) {
+    if (q->phase == P_FWD && q->K == 1) {
+        // every state kept: step n reads buffer 1 + n and writes 2 + n
+        q->steps = q->S;
+        r.active = ACT_FWD;
+        r.in_a = 1 - q->t0;
+        r.in_b = 1;
+        r.out_a = 2 - q->t0;
+        r.out_b = 1;
+        r.ck_tick = -1;
+    } else if (q->phase == P_FWD) {
         q->steps = std::min(q->K, q->S - q->chunk * q->K);
         r.active = ACT_FWD;
         r.in_a = r.in_b = r.out_a = r.out_b = 0;
@@ -159,7 +178,9 @@ gs_status gs_server::enter_phase(Query* q) {
         r.ck_tick = -1;
     } else if (q->phase == P_ADJ) {
         r.active = ACT_ADJ;
-        r.adj_a = seg0 + q->steps - 1 + q->t0;
+        // reverse step of step n reads its input state: the stored state n
+        // (K = 1: buffer 1 + n) or the recomputed segment
+        r.adj_a = (q->K == 1 ? q->S : seg0 + q->steps - 1) + q->t0;
         r.adj_b = -1;
     }
     return GS_OK;
@@ -171,8 +192,6 @@ static gs_status build_query(gs_ctx* ctx, const gs_server_opts& opts, Query* q, 
     gs_mesh* m = nullptr;
     GS_TRY(mesh_create(ctx, &q->desc, bs, &m));
     q->mesh = m;
-    q->K = opts.K > 0 ? std::min(opts.K, std::max(q->S, 1))
-                      : std::max(1, (int)std::ceil(std::sqrt((double)std::max(q->S, 1))));
     q->n_ck = std::max(1, (q->S + q->K - 1) / q->K);
     GS_TRY(m->ensure_buffers(1 + q->n_ck + q->K + 1, bs));
     GS_TRY(m->ensure_adjoint(bs));
@@ -425,11 +444,18 @@ void gs_server::run() {
             while (q->phase != P_FINISHING && q->done >= q->steps) {
                 rt_changed = true;
                 if (q->phase == P_FWD) {
-                    if ((q->chunk + 1) * q->K < q->S) {
+                    if (q->K > 1 && (q->chunk + 1) * q->K < q->S) {
                         set_phase(q, P_FWD, q->chunk + 1);
                     } else {
                         // forward done: seed dL/dx(S) from the target, zero the accumulators
                         gs_mesh* m = q->mesh;
+                        if (q->K == 1) {  // the final state (buffer S + 1) becomes the current one
+                            m->rt.cp_src = q->S + 1;
+                            m->rt.cp_dst = 0;
+                            m->rt.active = ACT_FWD;
+                            m->self->sync_rt(stream);
+                            launch_copy_state(m->self->launch, stream);
+                        }
                         m->rt.active = ACT_FWD | ACT_ADJ;
                         m->self->sync_rt(stream);
                         launch_seed_loss(m->self->launch, (double*)m->self->d_loss.p, 1, stream);
@@ -439,7 +465,12 @@ void gs_server::run() {
                         launch_zero_f64((double*)m->g_act.p, m->info.n_elems, stream);
                         launch_zero_f64((double*)m->g_kb.p, m->info.n_hinges, stream);
                         launch_zero_f64((double*)m->g_hact.p, m->info.n_hinges, stream);
-                        set_phase(q, P_REC, q->n_ck - 1);
+                        if (q->K == 1) {
+                            set_phase(q, P_ADJ, 0);
+                            q->steps = q->S;
+                        } else {
+                            set_phase(q, P_REC, q->n_ck - 1);
+                        }
                     }
                 } else if (q->phase == P_REC) {
                     set_phase(q, P_ADJ, q->chunk);
@@ -619,8 +650,8 @@ extern "C" gs_status gs_query_submit(gs_server* s, const gs_query* q, uint64_t* 
     Q->desc.pinned = nullptr;
     Q->dt = q->dt;
     Q->S = q->n_steps;
-    const int K = s->opts.K > 0 ? s->opts.K : std::max(1, (int)std::ceil(std::sqrt((double)std::max(Q->S, 1))));
-    Q->bytes = estimate_bytes(d, Q->S, K);
+    Q->K = query_K(s->opts, d, Q->S);
+    Q->bytes = estimate_bytes(d, Q->S, Q->K);
     Q->t_submit = now_s();
     std::lock_guard<std::mutex> lk(s->mu);
     s->submitted++;

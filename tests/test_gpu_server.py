@@ -26,12 +26,15 @@ def _alone(gs, ctx, p, tgt):
     return run_gpu(gs, ctx, p, p.steps, tgt)
 
 
-def test_server_results_equal_alone_and_overlap(gs):
+@pytest.mark.parametrize("server_K", [0, 7])
+def test_server_results_equal_alone_and_overlap(gs, server_K):
+    # server_K = 0: every query keeps all its states (K = 1: one forward and one
+    # reverse phase); 7: checkpoints and segment recompute
     qs = _queries()
     ctx_alone = gs.Context(0)
     alone = [_alone(gs, ctx_alone, p, t) for p, t in qs]
     ctx = gs.Context(0)
-    server = gs.Server(ctx, budget=8 << 30)
+    server = gs.Server(ctx, budget=8 << 30, K=server_K)
     tickets = [server.submit(p, t) for p, t in qs]
     res = []
     for t in tickets:
