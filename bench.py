@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="block: library defaults instead of the autotuner's patch shape and K")
-    ap.add_argument("--cpu-steps", type=int, default=1, help="oracle steps in the CPU sample")
+    ap.add_argument("--cpu-steps", type=int, default=4,
+                    help="oracle steps in the CPU sample (about 3 s each on one core for block64)")
     ap.add_argument("--workload", default="block", choices=["block", "bar", "cloth", "batch", "serve"],
                     help="block: the 1.3M-tet solid (default line); the others measure the remaining workloads")
     ap.add_argument("--meshes", type=int, default=512, help="batch: number of meshes")
