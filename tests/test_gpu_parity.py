@@ -76,11 +76,11 @@ def test_block_many_patches_ragged(gs, ctx, patch_elems):
 
 
 def test_patch_too_large_for_shared_memory_is_rejected(gs, ctx):
-    # two pipeline stages of a 1000-tet adjoint patch exceed the 227 KB of
-    # shared memory a CTA may use: mesh creation fails cleanly with EINVAL
+    # two pipeline stages of a 2000-tet patch exceed the 227 KB of shared
+    # memory a CTA may use: mesh creation fails cleanly with EINVAL
     p = I.block(n=8, steps=1, seed=3)
     with pytest.raises(gs.GradsimError) as ei:
-        gs.Mesh(ctx, p, patch_elems=1000)
+        gs.Mesh(ctx, p, patch_elems=2000)
     assert ei.value.status == gs.GS_EINVAL
     assert "shared memory" in str(ei.value)
 
