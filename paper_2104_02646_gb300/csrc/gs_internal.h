@@ -50,7 +50,20 @@ struct PatchDesc {
     int slot_begin;        // local CSR slot list (16 B aligned)
     int mesh;              // index into the launch set's MeshRT array
     int n_slots;           // local CSR slots, every row padded to a multiple of 4
+    int topo;              // the patch's topology block in MeshRT::topo (16 B units)
 };
+
+// shared-memory pipeline stages of the patch kernels
+constexpr int kStages = 2;
+
+// Element records are patch-contiguous: the patch of elements [b, b + n)
+// (b = p * pe, n = min(pe, E - b)) holds its 4 planes of n float4 at 4 b, so
+// one bulk copy stages the whole patch.  Index of plane k of element e:
+__host__ __device__ __forceinline__ size_t rec_at(int E, int pe, int k, int e) {
+    const int b = (e / pe) * pe;
+    const int n = (E - b < pe) ? (E - b) : pe;
+    return 4 * (size_t)b + (size_t)k * (size_t)n + (size_t)(e - b);
+}
 
 // nodes per NodeBlock (boundary kernels: 2 nodes per thread of a 128-thread CTA)
 constexpr int kNodeBlock = 256;
@@ -64,14 +77,15 @@ enum { ACT_FWD = 1, ACT_ADJ = 2 };
 struct alignas(16) MeshRT {  // 16 B aligned: the patch kernels bulk-copy it into shared memory
     // static mesh data
     int kind, n_nodes, n_int, n_bnd;
-    int n_elems, n_hinges, active, pad0;
-    float4* rec;             // [4][E] element records as 4 planes of float4 (layout below)
+    int n_elems, n_hinges, active, pe;  // pe: elements per patch
+    float4* rec;             // element records, patch-contiguous (rec_at), 4 float4 planes per patch
     float4* hrec;            // [4][B] hinge records
     const int* bnd_ids;      // per-patch boundary lists (internal node ids)
     const uint16_t* loc_rowptr;
     const uint16_t* loc_slots;
     const int* bnd_rowptr;   // [n_bnd + 1] over boundary nodes (internal id - n_int)
     const int* part_pos;     // per (patch, boundary local node): index of its partial
+    const uint4* topo;       // per patch, 16 B aligned: CSR row pointers, CSR slots, partial positions
     float4* partials;        // node-major: node b's partials at [bnd_rowptr[b], bnd_rowptr[b+1]), patch order
     const int* node_perm;    // internal node -> caller node
     const int* elem_perm;    // internal element -> caller element

@@ -269,7 +269,7 @@ __device__ __forceinline__ void node_adjoint(const MeshRT& m, int gid, float4 x4
 
 // A staged patch in shared memory.
 struct Stage {
-    int n_rec;
+    int n_rec, n_e, n_h;
     float4* rec;  // planes [4][n_rec]
     uint16_t* rp;
     uint16_t* sl;
@@ -292,6 +292,8 @@ __device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned
     const Layout L = patch_layout(n_rec, n_loc, p.n_int, p.n_slots, adjoint);
     Stage S;
     S.n_rec = n_rec;
+    S.n_e = p.n_e;
+    S.n_h = p.n_h;
     S.rec = (float4*)(buf + L.rec);
     S.rp = (uint16_t*)(buf + L.rp);
     S.sl = (uint16_t*)(buf + L.sl);
@@ -314,10 +316,13 @@ __device__ __forceinline__ int in_buffer(const MeshRT& m, int tick, bool adjoint
     return adjoint ? m.adj_a + m.adj_b * tick : m.in_a + m.in_b * tick;
 }
 
-// Elected thread: bulk copies of the mesh record (into `hdr_rt`) and of the
-// patch's records, CSR and interior node data into `buf`, completing on `bar`.
+// Elected thread: bulk copies of the mesh record (into `hdr_rt`, unless the
+// stage holds it already) and of the patch's records (one copy: they are
+// patch-contiguous; hinges plane by plane), topology block (one copy) and
+// interior node data into `buf`, completing on `bar`.
 __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_global, const MeshRT& m, int tick,
-                                           unsigned char* buf, MeshRT* hdr_rt, uint64_t* bar, bool adjoint) {
+                                           unsigned char* buf, MeshRT* hdr_rt, bool copy_rt, uint64_t* bar,
+                                           bool adjoint) {
     const Stage S = stage_at(p, m.kind, buf, adjoint);
     const int n_loc = p.n_int + p.n_bnd;
     const int n_rec = S.n_rec;
@@ -330,18 +335,15 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
     // copy rounded up to 16 B into the arrays' tail padding)
     const uint32_t b_g = adjoint ? (uint32_t)r16(8 * p.n_e) : 0u;
     const uint32_t b_pos = (uint32_t)r16(4 * p.n_bnd);
-    const uint32_t tx = (uint32_t)sizeof(MeshRT) + 64u * n_rec + b_rp + b_sl + b_pos +
+    const uint32_t tx = (copy_rt ? (uint32_t)sizeof(MeshRT) : 0u) + 64u * n_rec + b_rp + b_sl + b_pos +
                         (p.n_int ? (adjoint ? 4u : 2u) * b_int : 0u) + 2u * b_g;
     fence_proxy_async();
     mbar_expect_tx(bar, tx);
-    bulk_g2s(hdr_rt, rt_global, (uint32_t)sizeof(MeshRT), bar);
-    for (int k = 0; k < 4; ++k) {
-        if (p.n_e) bulk_g2s(S.rec + k * n_rec, m.rec + (size_t)k * m.n_elems + p.e_begin, 16u * p.n_e, bar);
-        if (p.n_h) bulk_g2s(S.rec + k * n_rec + p.n_e, m.hrec + (size_t)k * m.n_hinges + p.h_begin, 16u * p.n_h, bar);
-    }
-    bulk_g2s(S.rp, m.loc_rowptr + p.lr_begin, b_rp, bar);
-    bulk_g2s(S.sl, m.loc_slots + p.slot_begin, b_sl, bar);
-    if (b_pos) bulk_g2s(S.pos, m.part_pos + p.bnd_begin, b_pos, bar);
+    if (copy_rt) bulk_g2s(hdr_rt, rt_global, (uint32_t)sizeof(MeshRT), bar);
+    if (p.n_e) bulk_g2s(S.rec, m.rec + 4 * (size_t)p.e_begin, 64u * p.n_e, bar);
+    for (int k = 0; k < 4 && p.n_h; ++k)
+        bulk_g2s(S.rec + 4 * p.n_e + k * p.n_h, m.hrec + (size_t)k * m.n_hinges + p.h_begin, 16u * p.n_h, bar);
+    bulk_g2s(S.rp, m.topo + p.topo, b_rp + b_sl + b_pos, bar);  // S.rp, S.sl, S.pos are consecutive
     if (p.n_int) {
         bulk_g2s(S.xs, X + p.int_begin, b_int, bar);
         bulk_g2s(S.vs, V + p.int_begin, b_int, bar);
@@ -408,9 +410,17 @@ __device__ __forceinline__ void produce_gather(const PatchDesc& p, const MeshRT&
         for (int l = lane; l < p.n_int; l += 32) cp8(S.wb + l, m.wbar + p.int_begin + l);
 }
 
-// corner c of record r is written in place into plane c, row r; a CSR slot is
-// that float4 index (c * n_rec + r), or 4 * n_rec for a padding slot
-__device__ __forceinline__ void put(const Stage& S, int r, int c, float4 f) { S.rec[c * S.n_rec + r] = f; }
+// Staged records: the element planes [4][n_e], then the hinge planes
+// [4][n_h].  Corner c of a record is written in place into its plane c; a CSR
+// slot is that float4 index, or 4 * n_rec for a padding slot.
+struct RecAt {
+    int base, stride;  // plane k of the record at base + k * stride
+};
+__device__ __forceinline__ RecAt rec_slot(const Stage& S, int lr) {
+    return lr < S.n_e ? RecAt{lr, S.n_e} : RecAt{4 * S.n_e + (lr - S.n_e), S.n_h};
+}
+__device__ __forceinline__ void put(const Stage& S, int r, int c, float4 f) { S.rec[c * S.n_e + r] = f; }  // elements
+__device__ __forceinline__ void put(const Stage& S, RecAt q, int c, float4 f) { S.rec[q.base + c * q.stride] = f; }
 __device__ __forceinline__ void zero_pad_slot(const Stage& S) {
     if (threadIdx.x == 0) S.rec[4 * S.n_rec] = make_float4(0.f, 0.f, 0.f, 0.f);  // a consumer thread
 }
@@ -440,7 +450,9 @@ __device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Sta
     const int nr = S.n_rec;
     zero_pad_slot(S);
     for (int lr = threadIdx.x; lr < nr; lr += nt) {
-        const float4 a = S.rec[lr], b = S.rec[nr + lr], c = S.rec[2 * nr + lr], w = S.rec[3 * nr + lr];
+        const RecAt q = rec_slot(S, lr);
+        const float4 a = S.rec[q.base], b = S.rec[q.base + q.stride], c = S.rec[q.base + 2 * q.stride],
+                     w = S.rec[q.base + 3 * q.stride];
         const uint2 id = rec_ids(w);
         if (lr < p.n_e) {
             TriState s;
@@ -448,19 +460,19 @@ __device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Sta
                       make_float3(c.x, c.y, c.z), make_float3(c.w, w.z, w.w), s);
             float3 f0, f1, f2;
             tri_forces(s, a, b, f0, f1, f2);
-            put(S, lr, 0, f4(f0, 0.f));
-            put(S, lr, 1, f4(f1, 0.f));
-            put(S, lr, 2, f4(f2, 0.f));
+            put(S, q, 0, f4(f0, 0.f));
+            put(S, q, 1, f4(f1, 0.f));
+            put(S, q, 2, f4(f2, 0.f));
         } else {
             HingeState s;
             hinge_state(xyz(S.xs[id.x & 0xffff]), xyz(S.xs[id.x >> 16]), xyz(S.xs[id.y & 0xffff]),
                         xyz(S.xs[id.y >> 16]), xyz(a), xyz(b), xyz(c), b.w, s);
             float3 f1, f2, f3, f4_;
             hinge_forces(s, a.w, f1, f2, f3, f4_);
-            put(S, lr, 0, f4(f1, 0.f));
-            put(S, lr, 1, f4(f2, 0.f));
-            put(S, lr, 2, f4(f3, 0.f));
-            put(S, lr, 3, f4(f4_, 0.f));
+            put(S, q, 0, f4(f1, 0.f));
+            put(S, q, 1, f4(f2, 0.f));
+            put(S, q, 2, f4(f3, 0.f));
+            put(S, q, 3, f4(f4_, 0.f));
         }
     }
 }
@@ -500,7 +512,9 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
     const int nr = S.n_rec;
     zero_pad_slot(S);
     for (int lr = threadIdx.x; lr < nr; lr += nt) {
-        const float4 a = S.rec[lr], b = S.rec[nr + lr], c = S.rec[2 * nr + lr], w = S.rec[3 * nr + lr];
+        const RecAt q = rec_slot(S, lr);
+        const float4 a = S.rec[q.base], b = S.rec[q.base + q.stride], c = S.rec[q.base + 2 * q.stride],
+                     w = S.rec[q.base + 3 * q.stride];
         const uint2 id = rec_ids(w);
         if (lr < p.n_e) {
             const int i0 = id.x & 0xffff, i1 = id.x >> 16, i2 = id.y & 0xffff;
@@ -513,9 +527,9 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             float3 xb0, xb1, xb2;
             float gmu, glam, gact;
             tri_adjoint(s, a, b, (dt * x0.w) * v0, (dt * x1.w) * v1, (dt * x2.w) * v2, xb0, xb1, xb2, gmu, glam, gact);
-            put(S, lr, 0, f4(xb0, dot3(f0, v0)));
-            put(S, lr, 1, f4(xb1, dot3(f1, v1)));
-            put(S, lr, 2, f4(xb2, dot3(f2, v2)));
+            put(S, q, 0, f4(xb0, dot3(f0, v0)));
+            put(S, q, 1, f4(xb1, dot3(f1, v1)));
+            put(S, q, 2, f4(xb2, dot3(f2, v2)));
             const int t = p.e_begin + lr;
             m.g_mu[t] = S.gmu[lr] + (double)gmu;
             m.g_lam[t] = S.glam[lr] + (double)glam;
@@ -532,10 +546,10 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             float gkb, gact;
             hinge_adjoint(s, a.w, (dt * x1.w) * v1, (dt * x2.w) * v2, (dt * x3.w) * v3, (dt * x4.w) * v4, xb1, xb2,
                           xb3, xb4, gkb, gact);
-            put(S, lr, 0, f4(xb1, dot3(f1, v1)));
-            put(S, lr, 1, f4(xb2, dot3(f2, v2)));
-            put(S, lr, 2, f4(xb3, dot3(f3, v3)));
-            put(S, lr, 3, f4(xb4, dot3(f4_, v4)));
+            put(S, q, 0, f4(xb1, dot3(f1, v1)));
+            put(S, q, 1, f4(xb2, dot3(f2, v2)));
+            put(S, q, 2, f4(xb3, dot3(f3, v3)));
+            put(S, q, 3, f4(xb4, dot3(f4_, v4)));
             const int h = p.h_begin + (lr - p.n_e);
             m.g_kb[h] += (double)gkb;
             if (m.g_hact) m.g_hact[h] += (double)gact;
@@ -631,7 +645,7 @@ __device__ __forceinline__ float4 partial_sum(const MeshRT& m, int b) {
 
 // ---------------------------------------------------------------------------
 // The pipeline: a persistent CTA walks the live patches blockIdx.x,
-// +gridDim.x, ... through two shared-memory stages, warp-specialised.  The
+// +gridDim.x, ... through kStages shared-memory stages, warp-specialised.  The
 // last warp produces: it finds the next live patch, waits until the
 // consumers released the stage (empty[s]), writes the patch descriptor into
 // the stage header, issues the bulk copies (one elected lane, expect_tx on
@@ -663,16 +677,17 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
                                                const MeshRT* __restrict__ rts, int tick, int stage_bytes) {
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* full = (uint64_t*)sm;
-    uint64_t* empty = full + 2;
+    uint64_t* empty = full + kStages;
     unsigned char* const buf0 = sm + 128;
     const int mask = ADJ ? ACT_ADJ : ACT_FWD;
     const int nt = (int)blockDim.x - 32;  // consumer threads
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        mbar_init(&full[0], 33);
-        mbar_init(&full[1], 33);
-        mbar_init(&empty[0], nt >> 5);
-        mbar_init(&empty[1], nt >> 5);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 33);
+            mbar_init(&empty[s], nt >> 5);
+            ((PatchDesc*)(buf0 + s * stage_bytes))->mesh = -1;  // no mesh record staged yet
+        }
         mbar_init_fence();
     }
     __syncthreads();
@@ -691,9 +706,9 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
             X = bufx(rts[p.mesh], in_buffer(rts[p.mesh], tick, ADJ));
         }
         for (int it = 0;; ++it) {
-            const int s = it & 1;
+            const int s = it % kStages;
             unsigned char* const b = buf0 + s * stage_bytes;
-            if (it >= 2 && !mbar_wait_bounded(&empty[s], ((it >> 1) - 1) & 1u, status)) return;
+            if (it >= kStages && !mbar_wait_bounded(&empty[s], (it / kStages - 1) & 1u, status)) return;
             if (pi >= n_patches) {
                 if (lane == 0) ((PatchDesc*)b)->n_e = -1;  // end marker
                 __syncwarp();
@@ -703,8 +718,10 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
             }
             const MeshRT& m = rts[p.mesh];
             if (lane == 0) {
+                // the stage keeps its mesh record from the last patch it held
+                const bool copy_rt = ((const PatchDesc*)b)->mesh != p.mesh;
                 *(PatchDesc*)b = p;
-                issue_bulk(p, &rts[p.mesh], m, tick, b + kHdr, (MeshRT*)(b + kHdrRt), &full[s], ADJ);
+                issue_bulk(p, &rts[p.mesh], m, tick, b + kHdr, (MeshRT*)(b + kHdrRt), copy_rt, &full[s], ADJ);
             }
             produce_gather(p, m, X, g, b + kHdr, ADJ, lane);
             cp_async_mbar_arrive(&full[s]);
@@ -718,9 +735,9 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
     }
     // ---- consumer warps: descriptor and mesh record from the stage header ----
     for (int it = 0;; ++it) {
-        const int s = it & 1;
+        const int s = it % kStages;
         unsigned char* const b = buf0 + s * stage_bytes;
-        if (!mbar_wait_bounded(&full[s], (it >> 1) & 1u, status)) return;
+        if (!mbar_wait_bounded(&full[s], (it / kStages) & 1u, status)) return;
         const PatchDesc p = *(const PatchDesc*)b;
         if (p.n_e < 0) return;
         const MeshRT& m = *(const MeshRT*)(b + kHdrRt);
@@ -964,7 +981,7 @@ __global__ void k_setup_patch(const PatchDesc* __restrict__ patches, const MeshR
     const int n_loc = p.n_int + p.n_bnd;
     const int n_rec = p.n_e + p.n_h;
     double* xs = dsm;               // 3 per local node
-    double* mc = dsm + 3 * n_loc;   // one per corner (plane-major, as the CSR slots), + the padding slot
+    double* mc = dsm + 3 * n_loc;   // one per corner, indexed as the CSR slots, + the padding slot
     for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
         const int g = local_gid(p, m, l);
         xs[3 * l] = a.X[3 * g];
@@ -975,7 +992,8 @@ __global__ void k_setup_patch(const PatchDesc* __restrict__ patches, const MeshR
     const int nc = m.kind == GS_TET ? 4 : 3;
     for (int le = threadIdx.x; le < p.n_e; le += blockDim.x) {
         const int e = p.e_begin + le;
-        const uint2 id = rec_ids(m.rec[3 * (size_t)m.n_elems + e]);
+        float4* const R = m.rec + 4 * (size_t)p.e_begin;  // the patch's planes of p.n_e records
+        const uint2 id = rec_ids(R[3 * p.n_e + le]);
         const int li[4] = {(int)(id.x & 0xffff), (int)(id.x >> 16), (int)(id.y & 0xffff), (int)(id.y >> 16)};
         double share;
         if (m.kind == GS_TET) {
@@ -998,13 +1016,13 @@ __global__ void k_setup_patch(const PatchDesc* __restrict__ patches, const MeshR
             const double i22 = (D[0][0] * D[1][1] - D[0][1] * D[1][0]) * id_;
             const double V = det / 6.0;
             if (a.geometry) {
-                const size_t E = m.n_elems;
-                m.rec[e] = make_float4((float)i00, (float)i01, (float)i02, (float)i10);
-                m.rec[E + e] = make_float4((float)i11, (float)i12, (float)i20, (float)i21);
-                float4 c = m.rec[2 * E + e];
+                const int n = p.n_e;
+                R[le] = make_float4((float)i00, (float)i01, (float)i02, (float)i10);
+                R[n + le] = make_float4((float)i11, (float)i12, (float)i20, (float)i21);
+                float4 c = R[2 * n + le];
                 c.x = (float)i22;
                 c.y = (float)V;
-                m.rec[2 * E + e] = c;
+                R[2 * n + le] = c;
             }
             share = (double)a.rho[e] * V / 4.0;
         } else {
@@ -1032,29 +1050,30 @@ __global__ void k_setup_patch(const PatchDesc* __restrict__ patches, const MeshR
             const double area = 0.5 * ln;
             if (a.geometry) {
                 const double d00 = A22 / det, d01 = -A12 / det, d10 = -A21 / det, d11 = A11 / det;
-                const size_t E = m.n_elems;
-                m.rec[e] = make_float4((float)d00, (float)d01, (float)d10, (float)d11);
-                float4 b = m.rec[E + e];
+                const int n = p.n_e;
+                R[le] = make_float4((float)d00, (float)d01, (float)d10, (float)d11);
+                float4 b = R[n + le];
                 b.x = (float)area;
-                m.rec[E + e] = b;
+                R[n + le] = b;
                 // rest frame R0 = Ds_rest Dm^-1 (orthonormal columns)
                 double r0[3], r1[3];
                 for (int r = 0; r < 3; ++r) {
                     r0[r] = e1[r] * d00 + e2[r] * d10;
                     r1[r] = e1[r] * d01 + e2[r] * d11;
                 }
-                m.rec[2 * E + e] = make_float4((float)r0[0], (float)r0[1], (float)r0[2], (float)r1[0]);
-                float4 w = m.rec[3 * E + e];
+                R[2 * n + le] = make_float4((float)r0[0], (float)r0[1], (float)r0[2], (float)r1[0]);
+                float4 w = R[3 * n + le];
                 w.z = (float)r1[1];
                 w.w = (float)r1[2];
-                m.rec[3 * E + e] = w;
+                R[3 * n + le] = w;
             }
             share = (double)a.rho[e] * area / 3.0;
         }
-        for (int c = 0; c < 4; ++c) mc[c * n_rec + le] = c < nc ? share : 0.0;
+        for (int c = 0; c < 4; ++c) mc[c * p.n_e + le] = c < nc ? share : 0.0;
     }
-    // hinge corners carry no mass; hinge rest vectors X1-X3, X2-X3, X4-X3
-    for (int lh = threadIdx.x; lh < 4 * p.n_h; lh += blockDim.x) mc[(lh & 3) * n_rec + p.n_e + (lh >> 2)] = 0.0;
+    // hinge corners carry no mass (staged after the element planes); hinge
+    // rest vectors X1-X3, X2-X3, X4-X3
+    for (int lh = threadIdx.x; lh < 4 * p.n_h; lh += blockDim.x) mc[4 * p.n_e + (lh & 3) * p.n_h + (lh >> 2)] = 0.0;
     if (threadIdx.x == 0) mc[4 * n_rec] = 0.0;
     if (a.geometry) {
         for (int lh = threadIdx.x; lh < p.n_h; lh += blockDim.x) {
@@ -1123,19 +1142,19 @@ __global__ void k_scatter_params(const MeshRT* __restrict__ rts, const float* mu
     const MeshRT& m = rts[0];
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m.n_elems; e += gridDim.x * blockDim.x) {
         const int u = m.elem_perm[e];
-        const size_t E = m.n_elems;
+        const int E = m.n_elems;
         if (m.kind == GS_TET) {
-            float4 c = m.rec[2 * E + e];
+            float4 c = m.rec[rec_at(E, m.pe, 2, e)];
             if (mu) c.z = mu[u];
             if (lam) c.w = lam[u];
-            m.rec[2 * E + e] = c;
-            if (act) m.rec[3 * E + e].z = act[u];
+            m.rec[rec_at(E, m.pe, 2, e)] = c;
+            if (act) m.rec[rec_at(E, m.pe, 3, e)].z = act[u];
         } else {
-            float4 b = m.rec[E + e];
+            float4 b = m.rec[rec_at(E, m.pe, 1, e)];
             if (mu) b.y = mu[u];
             if (lam) b.z = lam[u];
             if (act) b.w = act[u];
-            m.rec[E + e] = b;
+            m.rec[rec_at(E, m.pe, 1, e)] = b;
         }
     }
     if (kb && m.kind == GS_CLOTH) {
@@ -1223,15 +1242,15 @@ __global__ void k_elem_grads(const PatchDesc* __restrict__ patches, const MeshRT
     for (int le = threadIdx.x; le < p.n_e; le += blockDim.x) {
         const int e = p.e_begin + le;
         const int u = m.elem_perm[e];
-        const size_t E = m.n_elems;
-        const uint2 id = rec_ids(m.rec[3 * E + e]);
+        const float4* R = m.rec + 4 * (size_t)p.e_begin;  // the patch's planes of p.n_e records
+        const uint2 id = rec_ids(R[3 * p.n_e + le]);
         if (d_rho) {
             if (m.kind == GS_TET) {
                 const double s = msm[id.x & 0xffff] + msm[id.x >> 16] + msm[id.y & 0xffff] + msm[id.y >> 16];
-                d_rho[u] = s * ((double)m.rec[2 * E + e].y / 4.0);
+                d_rho[u] = s * ((double)R[2 * p.n_e + le].y / 4.0);
             } else {
                 const double s = msm[id.x & 0xffff] + msm[id.x >> 16] + msm[id.y & 0xffff];
-                d_rho[u] = s * ((double)m.rec[E + e].x / 3.0);
+                d_rho[u] = s * ((double)R[p.n_e + le].x / 3.0);
             }
         }
         if (d_mu) d_mu[u] = m.g_mu[e];
@@ -1261,7 +1280,7 @@ int patch_grid(int which, int threads, int stage_bytes, int n_patches, int num_s
                   : which == 2 ? (const void*)k_tet_adj
                                : (const void*)k_cloth_adj;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads + 32, 128 + 2 * (size_t)stage_bytes) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads + 32, 128 + kStages * (size_t)stage_bytes) !=
         cudaSuccess) {
         cudaGetLastError();
         nb = 1;
@@ -1309,10 +1328,10 @@ const char* kernel_name(int kind) {
 
 void launch_forward_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
     if (L.n_tet_patches)
-        GS_TIMED(KT_TET_FWD, (k_tet_fwd<<<L.grid[0], L.threads + 32, 128 + 2 * (size_t)L.stage[0], s>>>(
+        GS_TIMED(KT_TET_FWD, (k_tet_fwd<<<L.grid[0], L.threads + 32, 128 + kStages * (size_t)L.stage[0], s>>>(
                                  L.tet_patches, L.n_tet_patches, L.rt, tick, L.stage[0])));
     if (L.n_cloth_patches)
-        GS_TIMED(KT_CLOTH_FWD, (k_cloth_fwd<<<L.grid[1], L.threads + 32, 128 + 2 * (size_t)L.stage[1], s>>>(
+        GS_TIMED(KT_CLOTH_FWD, (k_cloth_fwd<<<L.grid[1], L.threads + 32, 128 + kStages * (size_t)L.stage[1], s>>>(
                                    L.cloth_patches, L.n_cloth_patches, L.rt, tick, L.stage[1])));
     if (L.n_bnd_blocks)
         GS_TIMED(KT_FWD_BND, (k_fwd_boundary<<<L.bgrid[0], kBndThreads, 0, s>>>(L.bnd_blocks, L.n_bnd_blocks, L.rt, tick)));
@@ -1320,10 +1339,10 @@ void launch_forward_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) 
 
 void launch_adjoint_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
     if (L.n_tet_patches)
-        GS_TIMED(KT_TET_ADJ, (k_tet_adj<<<L.grid[2], L.threads + 32, 128 + 2 * (size_t)L.stage[2], s>>>(
+        GS_TIMED(KT_TET_ADJ, (k_tet_adj<<<L.grid[2], L.threads + 32, 128 + kStages * (size_t)L.stage[2], s>>>(
                                  L.tet_patches, L.n_tet_patches, L.rt, tick, L.stage[2])));
     if (L.n_cloth_patches)
-        GS_TIMED(KT_CLOTH_ADJ, (k_cloth_adj<<<L.grid[3], L.threads + 32, 128 + 2 * (size_t)L.stage[3], s>>>(
+        GS_TIMED(KT_CLOTH_ADJ, (k_cloth_adj<<<L.grid[3], L.threads + 32, 128 + kStages * (size_t)L.stage[3], s>>>(
                                    L.cloth_patches, L.n_cloth_patches, L.rt, tick, L.stage[3])));
     if (L.n_bnd_blocks)
         GS_TIMED(KT_ADJ_BND, (k_adj_boundary<<<L.bgrid[1], kBndThreads, 0, s>>>(L.bnd_blocks, L.n_bnd_blocks, L.rt, tick)));

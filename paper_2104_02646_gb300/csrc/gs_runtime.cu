@@ -100,6 +100,7 @@ struct Topology {
     std::vector<int> bnd_ids;
     std::vector<uint16_t> loc_rowptr, loc_slots;
     std::vector<int> bnd_rowptr, part_pos;
+    std::vector<uint4> topo;  // per patch: row pointers, slots, partial positions (16 B aligned pieces)
     int n_int = 0, n_bnd = 0, max_loc = 0, max_slots = 0, max_rec = 0;
     size_t smem_fwd = 0, smem_adj = 0;
 };
@@ -309,7 +310,12 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
         for (int l = 0; l <= n_loc; ++l) T.loc_rowptr.push_back((uint16_t)rc[l]);
         std::vector<uint16_t> slots(n_slots, (uint16_t)(4 * n_rec));
         std::vector<int> fill(rc.begin(), rc.end() - 1);
-        for (auto& cn : code_node) slots[fill[cn.second]++] = (uint16_t)((cn.first & 3) * n_rec + (cn.first >> 2));
+        // staged planes: elements [4][n_e], then hinges [4][n_h]
+        auto slot_of = [&](int code) {
+            const int r = code >> 2, c = code & 3;
+            return r < q.n_e ? c * q.n_e + r : 4 * q.n_e + c * q.n_h + (r - q.n_e);
+        };
+        for (auto& cn : code_node) slots[fill[cn.second]++] = (uint16_t)slot_of(cn.first);
         T.loc_slots.insert(T.loc_slots.end(), slots.begin(), slots.end());
         T.max_loc = std::max(T.max_loc, n_loc);
         T.max_slots = std::max(T.max_slots, n_slots);
@@ -338,6 +344,19 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
     for (size_t i = 0; i < entry_node.size(); ++i)
         if (entry_node[i] >= 0) T.part_pos[i] = T.bnd_rowptr[entry_node[i]] + entry_j[i];
     for (int k = 0; k < 4; ++k) T.bnd_ids.push_back(0);
+    // 7. per patch topology blocks for the one-copy staging
+    auto append = [&](const void* src, size_t bytes) {
+        const size_t n16 = (bytes + 15) / 16, at = T.topo.size();
+        T.topo.resize(at + n16, make_uint4(0, 0, 0, 0));
+        if (bytes) std::memcpy(&T.topo[at], src, bytes);
+    };
+    for (PatchDesc& q : T.patches) {
+        const int n_loc = q.n_int + q.n_bnd;
+        q.topo = (int)T.topo.size();
+        append(&T.loc_rowptr[q.lr_begin], 2 * (size_t)(n_loc + 1));
+        append(&T.loc_slots[q.slot_begin], 2 * (size_t)q.n_slots);
+        append(&T.part_pos[q.bnd_begin], 4 * (size_t)q.n_bnd);
+    }
     return GS_OK;
 }
 
@@ -550,7 +569,7 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     m->patches = T.patches;
     m->bnd_blocks = make_blocks(0, T.n_bnd, kNodeBlock, 0);
     m->node_blocks = make_blocks(0, N, 256, 0);
-    const size_t need = std::max(128 + 2 * T.smem_adj, sizeof(double) * (3 * (size_t)T.max_loc + 4 * (size_t)T.max_rec + 1));
+    const size_t need = std::max(128 + kStages * T.smem_adj, sizeof(double) * (3 * (size_t)T.max_loc + 4 * (size_t)T.max_rec + 1));
     if (need > ctx->smem_optin)
         return set_error(GS_EINVAL, "patch needs " + std::to_string(need) + " B of shared memory; lower patch_elems");
     // element records in internal order, 4 planes (geometry filled by the set-up kernel)
@@ -566,11 +585,11 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
         rho[e] = (float)d.density[u];
         const float act = d.act ? (float)d.act[u] : 0.0f;
         if (d.kind == GS_TET) {
-            rec[2 * (size_t)E + e] = make_float4(0.f, 0.f, (float)d.mu[u], (float)d.lambda[u]);
-            rec[3 * (size_t)E + e] = make_float4(bits(T.eidx[e].x), bits(T.eidx[e].y), act, 0.f);
+            rec[rec_at(E, pe, 2, e)] = make_float4(0.f, 0.f, (float)d.mu[u], (float)d.lambda[u]);
+            rec[rec_at(E, pe, 3, e)] = make_float4(bits(T.eidx[e].x), bits(T.eidx[e].y), act, 0.f);
         } else {
-            rec[(size_t)E + e] = make_float4(0.f, (float)d.mu[u], (float)d.lambda[u], act);
-            rec[3 * (size_t)E + e] = make_float4(bits(T.eidx[e].x), bits(T.eidx[e].y), 0.f, 0.f);
+            rec[rec_at(E, pe, 1, e)] = make_float4(0.f, (float)d.mu[u], (float)d.lambda[u], act);
+            rec[rec_at(E, pe, 3, e)] = make_float4(bits(T.eidx[e].x), bits(T.eidx[e].y), 0.f, 0.f);
         }
     }
     std::vector<float4> hrec(4 * (size_t)B, make_float4(0.f, 0.f, 0.f, 0.f));
@@ -614,6 +633,7 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     GS_TRY(upload(ctx, m->loc_slots, T.loc_slots, s));
     GS_TRY(upload(ctx, m->bnd_rowptr, T.bnd_rowptr, s));
     GS_TRY(upload(ctx, m->part_pos, T.part_pos, s));
+    GS_TRY(upload(ctx, m->topo, T.topo, s));
     GS_TRY(m->partials.alloc(ctx, std::max<size_t>(T.bnd_ids.size(), 1) * sizeof(float4), s));
     GS_TRY(upload(ctx, m->node_perm, T.node_perm, s));
     GS_TRY(upload(ctx, m->elem_perm, T.elem_perm, s));
@@ -644,6 +664,8 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     r.bnd_ids = (const int*)m->bnd_ids.p;
     r.loc_rowptr = (const uint16_t*)m->loc_rowptr.p;
     r.loc_slots = (const uint16_t*)m->loc_slots.p;
+    r.topo = (const uint4*)m->topo.p;
+    r.pe = pe;
     r.bnd_rowptr = (const int*)m->bnd_rowptr.p;
     r.part_pos = (const int*)m->part_pos.p;
     r.partials = (float4*)m->partials.p;
@@ -685,7 +707,7 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     if (bad) return set_error(GS_EINVAL, "inverted or degenerate rest element (non-positive volume or area)");
     m->info.device_bytes = 0;
     for (Buf* b : {&m->rec, &m->hrec, &m->Xs, &m->Xp, &m->v0, &m->bnd_ids, &m->loc_rowptr,
-                   &m->loc_slots, &m->bnd_rowptr, &m->part_pos, &m->partials, &m->node_perm, &m->elem_perm,
+                   &m->loc_slots, &m->bnd_rowptr, &m->part_pos, &m->topo, &m->partials, &m->node_perm, &m->elem_perm,
                    &m->hinge_perm, &m->w, &m->X, &m->rho, &m->pinned, &m->st})
         m->info.device_bytes += b->bytes;
     *out = m.release();
