@@ -107,8 +107,7 @@ struct alignas(16) MeshRT {  // 16 B aligned: the patch kernels bulk-copy it int
     float4* xb;
     float4* vb;
     double* wbar;            // [N]
-    double* g_mu;            // [E]
-    double* g_lam;
+    double2* g_ml;           // [E]: (dL/dmu, dL/dlambda) per element
     double* g_act;           // nullable
     double* g_kb;            // [B]
     double* g_hact;          // nullable

@@ -119,7 +119,7 @@ __host__ __device__ __forceinline__ int r16(int bytes) { return (bytes + 15) & ~
 // state.  The adjoint also holds v_hat for all local nodes, the interior
 // adjoint state and the boundary nodes' raw adjoint state.
 struct Layout {
-    int rec, rp, sl, pos, xs, vh, vs, xb, vb, xbB, vbB, gmu, glam, wb, total;
+    int rec, rp, sl, pos, xs, vh, vs, xb, vb, xbB, vbB, gml, wb, total;
 };
 
 __host__ __device__ __forceinline__ Layout patch_layout(int n_rec, int n_loc, int n_int, int n_slots, bool adjoint) {
@@ -137,10 +137,9 @@ __host__ __device__ __forceinline__ Layout patch_layout(int n_rec, int n_loc, in
     L.xbB = L.vb + (adjoint ? 16 * n_int : 0);
     L.vbB = L.xbB + (adjoint ? 16 * n_bnd : 0);
     // adjoint: the patch's FP64 dL/dmu, dL/dlambda accumulators (records 0..n_rec)
-    L.gmu = L.vbB + (adjoint ? 16 * n_bnd : 0);
-    L.glam = L.gmu + (adjoint ? r16(8 * n_rec) : 0);
+    L.gml = L.vbB + (adjoint ? 16 * n_bnd : 0);
     // adjoint: dL/dw of the interior nodes
-    L.wb = L.glam + (adjoint ? r16(8 * n_rec) : 0);
+    L.wb = L.gml + (adjoint ? 16 * n_rec : 0);
     L.total = L.wb + (adjoint ? r16(8 * n_int) : 0);
     return L;
 }
@@ -281,8 +280,7 @@ struct Stage {
     float4* vb;   // adjoint: interior v_bar
     float4* xbB;  // adjoint: boundary x_bar (raw)
     float4* vbB;  // adjoint: boundary v_bar (raw)
-    double* gmu;  // adjoint: staged accumulators of the patch's elements
-    double* glam;
+    double2* gml;  // adjoint: staged (dL/dmu, dL/dlambda) of the patch's elements
     double* wb;   // adjoint: dL/dw of the interior nodes
 };
 
@@ -305,8 +303,7 @@ __device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned
     S.vb = (float4*)(buf + L.vb);
     S.xbB = (float4*)(buf + L.xbB);
     S.vbB = (float4*)(buf + L.vbB);
-    S.gmu = (double*)(buf + L.gmu);
-    S.glam = (double*)(buf + L.glam);
+    S.gml = (double2*)(buf + L.gml);
     S.wb = (double*)(buf + L.wb);
     return S;
 }
@@ -331,12 +328,11 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
     const float4* X = bufx(m, ib);
     const float4* V = bufv(m, ib);
     const uint32_t b_rp = r16(2 * (n_loc + 1)), b_sl = r16(2 * n_slots), b_int = 16 * p.n_int;
-    // accumulators are staged for the tet / triangle records (8 B each, the
-    // copy rounded up to 16 B into the arrays' tail padding)
-    const uint32_t b_g = adjoint ? (uint32_t)r16(8 * p.n_e) : 0u;
+    // (dL/dmu, dL/dlambda) of the tet / triangle records, 16 B each
+    const uint32_t b_g = adjoint ? 16u * p.n_e : 0u;
     const uint32_t b_pos = (uint32_t)r16(4 * p.n_bnd);
     const uint32_t tx = (copy_rt ? (uint32_t)sizeof(MeshRT) : 0u) + 64u * n_rec + b_rp + b_sl + b_pos +
-                        (p.n_int ? (adjoint ? 4u : 2u) * b_int : 0u) + 2u * b_g;
+                        (p.n_int ? (adjoint ? 4u : 2u) * b_int : 0u) + b_g;
     fence_proxy_async();
     mbar_expect_tx(bar, tx);
     if (copy_rt) bulk_g2s(hdr_rt, rt_global, (uint32_t)sizeof(MeshRT), bar);
@@ -353,8 +349,7 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
         }
     }
     if (b_g) {
-        bulk_g2s(S.gmu, m.g_mu + p.e_begin, b_g, bar);
-        bulk_g2s(S.glam, m.g_lam + p.e_begin, b_g, bar);
+        bulk_g2s(S.gml, m.g_ml + p.e_begin, b_g, bar);
     }
 }
 
@@ -501,8 +496,8 @@ __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshR
         put(S, le, 2, f4(xb2, dot3(f2, v2)));
         put(S, le, 3, f4(xb3, dot3(f3, v3)));
         const int e = p.e_begin + le;
-        m.g_mu[e] = S.gmu[le] + (double)gmu;
-        m.g_lam[e] = S.glam[le] + (double)glam;
+        const double2 g0 = S.gml[le];
+        m.g_ml[e] = make_double2(g0.x + (double)gmu, g0.y + (double)glam);
         if (m.g_act) m.g_act[e] += (double)gact;
     }
 }
@@ -531,8 +526,8 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             put(S, q, 1, f4(xb1, dot3(f1, v1)));
             put(S, q, 2, f4(xb2, dot3(f2, v2)));
             const int t = p.e_begin + lr;
-            m.g_mu[t] = S.gmu[lr] + (double)gmu;
-            m.g_lam[t] = S.glam[lr] + (double)glam;
+            const double2 g0 = S.gml[lr];
+            m.g_ml[t] = make_double2(g0.x + (double)gmu, g0.y + (double)glam);
             if (m.g_act) m.g_act[t] += (double)gact;
         } else {
             const int i1 = id.x & 0xffff, i2 = id.x >> 16, i3 = id.y & 0xffff, i4 = id.y >> 16;
@@ -1253,8 +1248,8 @@ __global__ void k_elem_grads(const PatchDesc* __restrict__ patches, const MeshRT
                 d_rho[u] = s * ((double)R[p.n_e + le].x / 3.0);
             }
         }
-        if (d_mu) d_mu[u] = m.g_mu[e];
-        if (d_lam) d_lam[u] = m.g_lam[e];
+        if (d_mu) d_mu[u] = m.g_ml[e].x;
+        if (d_lam) d_lam[u] = m.g_ml[e].y;
         if (d_act && m.g_act) d_act[u] = m.g_act[e];
     }
     for (int lh = threadIdx.x; lh < p.n_h; lh += blockDim.x) {

@@ -475,8 +475,7 @@ gs_status gs_mesh::refresh_rt() {
     r.xb = (float4*)xb.p;
     r.vb = (float4*)vb.p;
     r.wbar = (double*)wbar.p;
-    r.g_mu = (double*)g_mu.p;
-    r.g_lam = (double*)g_lam.p;
+    r.g_ml = (double2*)g_ml.p;
     r.g_act = (double*)g_act.p;
     r.g_kb = (double*)g_kb.p;
     r.g_hact = (double*)g_hact.p;
@@ -506,8 +505,7 @@ gs_status gs_mesh::ensure_adjoint(cudaStream_t s) {
     GS_TRY(wbar.alloc(ctx, (size_t)n_pad * sizeof(double), s));
     GS_TRY(mbar.alloc(ctx, (size_t)n_pad * sizeof(double), s));
     // +2: tail padding for the rounded-up bulk copy of the last patch
-    GS_TRY(g_mu.alloc(ctx, ((size_t)info.n_elems + 2) * sizeof(double), s));
-    GS_TRY(g_lam.alloc(ctx, ((size_t)info.n_elems + 2) * sizeof(double), s));
+    GS_TRY(g_ml.alloc(ctx, ((size_t)info.n_elems + 1) * sizeof(double2), s));
     GS_TRY(g_act.alloc(ctx, (size_t)info.n_elems * sizeof(double), s));
     if (info.n_hinges) {
         GS_TRY(g_kb.alloc(ctx, (size_t)info.n_hinges * sizeof(double), s));
@@ -520,7 +518,7 @@ gs_mesh::~gs_mesh() {
     cudaStream_t s = 0;
     for (Buf* b : {&rec, &hrec, &Xs, &Xp, &v0, &bnd_ids, &loc_rowptr, &loc_slots, &bnd_rowptr,
                    &part_pos, &partials, &node_perm, &elem_perm, &hinge_perm, &w, &X, &rho, &pinned, &st, &xb, &vb,
-                   &wbar, &mbar, &g_mu, &g_lam, &g_act, &g_kb, &g_hact, &status, &target, &scratch})
+                   &wbar, &mbar, &g_ml, &g_act, &g_kb, &g_hact, &status, &target, &scratch})
         b->release(s);
     self.reset();
     cudaStreamSynchronize(s);
@@ -1072,8 +1070,7 @@ gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std:
     launch_seed_loss(launch, (double*)d_loss.p, 1, s);
     launch_zero_adjoint(launch, s);
     for (gs_mesh* m : meshes) {
-        launch_zero_f64((double*)m->g_mu.p, m->info.n_elems, s);
-        launch_zero_f64((double*)m->g_lam.p, m->info.n_elems, s);
+        launch_zero_f64((double*)m->g_ml.p, 2 * (long long)m->info.n_elems, s);
         if (m->rt.g_act) launch_zero_f64((double*)m->g_act.p, m->info.n_elems, s);
         launch_zero_f64((double*)m->g_kb.p, m->info.n_hinges, s);
         if (m->rt.g_hact) launch_zero_f64((double*)m->g_hact.p, m->info.n_hinges, s);

@@ -460,8 +460,7 @@ void gs_server::run() {
                         m->self->sync_rt(stream);
                         launch_seed_loss(m->self->launch, (double*)m->self->d_loss.p, 1, stream);
                         launch_zero_adjoint(m->self->launch, stream);
-                        launch_zero_f64((double*)m->g_mu.p, m->info.n_elems, stream);
-                        launch_zero_f64((double*)m->g_lam.p, m->info.n_elems, stream);
+                        launch_zero_f64((double*)m->g_ml.p, 2 * (long long)m->info.n_elems, stream);
                         launch_zero_f64((double*)m->g_act.p, m->info.n_elems, stream);
                         launch_zero_f64((double*)m->g_kb.p, m->info.n_hinges, stream);
                         launch_zero_f64((double*)m->g_hact.p, m->info.n_hinges, stream);
