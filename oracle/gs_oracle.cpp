@@ -462,7 +462,11 @@ void total_force(const orc_model* m, const Rest& r, const T* x, const T* v,
 template <class T>
 struct Inputs {
     std::vector<T> tmu, tlam, tact, trho, rmu, rlam, ract, rrho, kb, hact, cp;
+    std::vector<T> tseq, rseq, hseq;  // per-step actuation rows (empty if none)
+    int n_seq = 0;
     void load(const orc_model* m, const orc_dirs* d);
+    // actuation in effect during step n: static value + row n of the sequence
+    void step_act(const orc_model* m, int n, std::vector<T>& ta, std::vector<T>& ra, std::vector<T>& ha) const;
 };
 
 template <class T> void seed(T& t, double v, const double* dir, int i) { (void)dir; (void)i; t = T(v); }
@@ -489,6 +493,23 @@ void Inputs<T>::load(const orc_model* m, const orc_dirs* d) {
     fill(hact, m->n_hinges, m->hinge_act, 0.0, d ? d->hinge_act : nullptr);
     const double c4[4] = {m->ke, m->kd, m->kf, m->mu_f};
     fill(cp, 4, c4, 0.0, d ? d->contact : nullptr);
+    n_seq = m->n_act_steps > 0 ? m->n_act_steps : 0;
+    if (n_seq && m->tet_act_seq) fill(tseq, n_seq * m->n_tets, m->tet_act_seq, 0.0, d ? d->tet_act_seq : nullptr);
+    if (n_seq && m->tri_act_seq) fill(rseq, n_seq * m->n_tris, m->tri_act_seq, 0.0, d ? d->tri_act_seq : nullptr);
+    if (n_seq && m->hinge_act_seq)
+        fill(hseq, n_seq * m->n_hinges, m->hinge_act_seq, 0.0, d ? d->hinge_act_seq : nullptr);
+}
+
+template <class T>
+void Inputs<T>::step_act(const orc_model* m, int n, std::vector<T>& ta, std::vector<T>& ra,
+                         std::vector<T>& ha) const {
+    ta = tact;
+    ra = ract;
+    ha = hact;
+    if (n >= n_seq) return;
+    if (!tseq.empty()) for (int e = 0; e < m->n_tets; ++e) ta[e] += tseq[(size_t)n * m->n_tets + e];
+    if (!rseq.empty()) for (int t = 0; t < m->n_tris; ++t) ra[t] += rseq[(size_t)n * m->n_tris + t];
+    if (!hseq.empty()) for (int h = 0; h < m->n_hinges; ++h) ha[h] += hseq[(size_t)n * m->n_hinges + h];
 }
 
 // Inverse masses w_i = 1/m_i; pinned nodes (and nodes without mass) are
@@ -510,9 +531,11 @@ void inverse_masses(const orc_model* m, const Rest& r, const Inputs<T>& in, std:
 // w > 0 and leaves kinematic nodes alone; forces are all taken at s-.
 template <class T>
 void step(const orc_model* m, const Rest& r, const Inputs<T>& in, const std::vector<T>& w,
-          double dt, std::vector<T>& x, std::vector<T>& v, std::vector<T>& f) {
-    total_force(m, r, x.data(), v.data(), in.tmu.data(), in.tlam.data(), in.tact.data(),
-                in.rmu.data(), in.rlam.data(), in.ract.data(), in.kb.data(), in.hact.data(),
+          double dt, int n, std::vector<T>& x, std::vector<T>& v, std::vector<T>& f) {
+    std::vector<T> ta, ra, ha;
+    in.step_act(m, n, ta, ra, ha);
+    total_force(m, r, x.data(), v.data(), in.tmu.data(), in.tlam.data(), ta.data(),
+                in.rmu.data(), in.rlam.data(), ra.data(), in.kb.data(), ha.data(),
                 in.cp.data(), f.data());
     for (int i = 0; i < m->n_nodes; ++i) {
         const bool dyn = val(w[i]) > 0.0;
@@ -559,7 +582,7 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
     std::memcpy(&X[0], x.data(), 3 * N * sizeof(double));
     std::memcpy(&V[0], v.data(), 3 * N * sizeof(double));
     for (int n = 0; n < S; ++n) {
-        step(m, r, in, w, dt, x, v, f);
+        step(m, r, in, w, dt, n, x, v, f);
         std::memcpy(&X[(size_t)(n + 1) * 3 * N], x.data(), 3 * N * sizeof(double));
         std::memcpy(&V[(size_t)(n + 1) * 3 * N], v.data(), 3 * N * sizeof(double));
     }
@@ -579,15 +602,21 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
     if (loss) *loss = L;
 
     std::vector<double> tmu_b(m->n_tets, 0.0), tlam_b(m->n_tets, 0.0), tact_b(m->n_tets, 0.0);
+    // per-step actuation gradients, written when requested
+    double* tseq_b = g ? g->tet_act_seq : nullptr;
+    double* rseq_b = g ? g->tri_act_seq : nullptr;
+    double* hseq_b = g ? g->hinge_act_seq : nullptr;
     std::vector<double> rmu_b(m->n_tris, 0.0), rlam_b(m->n_tris, 0.0), ract_b(m->n_tris, 0.0);
     std::vector<double> kb_b(m->n_hinges, 0.0), hact_b(m->n_hinges, 0.0);
     double cp_b[4] = {0, 0, 0, 0};
     std::vector<double> w_b(N, 0.0);
     std::vector<double> cq(3 * N), cu(3 * N), y(3 * N), lq_new(3 * N), lu_new(3 * N);
 
+    std::vector<double> ta, ra, ha;
     for (int n = S - 1; n >= 0; --n) {
         const double* xn = &X[(size_t)n * 3 * N];
         const double* vn = &V[(size_t)n * 3 * N];
+        in.step_act(m, n, ta, ra, ha);  // the actuation in effect during step n
         // (dg/ds+)^T c = -(dl/ds+)^T with dg/ds+ = [[0, I], [I, -dt I]] over
         // s+ = (q+, u+) and g = (g_u, g_q):  c_q = -dl/dq+,  c_u = -dl/du+ - dt dl/dq+
         for (size_t i = 0; i < 3 * N; ++i) {
@@ -606,7 +635,7 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
             const int* t = &m->tets[4 * e];
             for (int c = 0; c < 4; ++c)
                 for (int k = 0; k < 3; ++k) { xe[3 * c + k] = xn[3 * (size_t)t[c] + k]; ye[3 * c + k] = y[3 * (size_t)t[c] + k]; }
-            const double pe[3] = {in.tmu[e], in.tlam[e], in.tact[e]};
+            const double pe[3] = {in.tmu[e], in.tlam[e], ta[e]};
             const double* Dmi = &r.tet_Dminv[9 * (size_t)e];
             const double Ve = r.tet_V[e];
             element_vjp<12, 3>(xe, pe, ye, xb, pb, [&](auto* xd, auto* pd, auto* fd) {
@@ -615,13 +644,14 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
             for (int c = 0; c < 4; ++c)
                 for (int k = 0; k < 3; ++k) lq_new[3 * (size_t)t[c] + k] += xb[3 * c + k];
             tmu_b[e] += pb[0]; tlam_b[e] += pb[1]; tact_b[e] += pb[2];
+            if (tseq_b) tseq_b[(size_t)n * m->n_tets + e] = pb[2];
         }
         for (int e = 0; e < m->n_tris; ++e) {
             double xe[9], ye[9], xb[9] = {0}, pb[3] = {0, 0, 0};
             const int* t = &m->tris[3 * e];
             for (int c = 0; c < 3; ++c)
                 for (int k = 0; k < 3; ++k) { xe[3 * c + k] = xn[3 * (size_t)t[c] + k]; ye[3 * c + k] = y[3 * (size_t)t[c] + k]; }
-            const double pe[3] = {in.rmu[e], in.rlam[e], in.ract[e]};
+            const double pe[3] = {in.rmu[e], in.rlam[e], ra[e]};
             const double* Dmi = &r.tri_Dminv[4 * (size_t)e];
             const double Ae = r.tri_A[e];
             element_vjp<9, 3>(xe, pe, ye, xb, pb, [&](auto* xd, auto* pd, auto* fd) {
@@ -630,19 +660,21 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
             for (int c = 0; c < 3; ++c)
                 for (int k = 0; k < 3; ++k) lq_new[3 * (size_t)t[c] + k] += xb[3 * c + k];
             rmu_b[e] += pb[0]; rlam_b[e] += pb[1]; ract_b[e] += pb[2];
+            if (rseq_b) rseq_b[(size_t)n * m->n_tris + e] = pb[2];
         }
         for (int h = 0; h < m->n_hinges; ++h) {
             double xe[12], ye[12], xb[12] = {0}, pb[2] = {0, 0};
             const int* t = &m->hinges[4 * h];
             for (int c = 0; c < 4; ++c)
                 for (int k = 0; k < 3; ++k) { xe[3 * c + k] = xn[3 * (size_t)t[c] + k]; ye[3 * c + k] = y[3 * (size_t)t[c] + k]; }
-            const double pe[2] = {in.kb[h], in.hact[h]};
+            const double pe[2] = {in.kb[h], ha[h]};
             element_vjp<12, 2>(xe, pe, ye, xb, pb, [&](auto* xd, auto* pd, auto* fd) {
                 hinge_forces_t(xd, pd[0], pd[1], fd);
             });
             for (int c = 0; c < 4; ++c)
                 for (int k = 0; k < 3; ++k) lq_new[3 * (size_t)t[c] + k] += xb[3 * c + k];
             kb_b[h] += pb[0]; hact_b[h] += pb[1];
+            if (hseq_b) hseq_b[(size_t)n * m->n_hinges + h] = pb[1];
         }
         if (m->plane_on || m->sphere_on) {
             for (size_t i = 0; i < N; ++i) {
@@ -661,8 +693,8 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
         // dl/dw_i: the step uses w_i f_i(s-) (gravity does not depend on w)
         {
             std::vector<double> f_n(3 * N), xx(xn, xn + 3 * N), vv(vn, vn + 3 * N);
-            total_force(m, r, xx.data(), vv.data(), in.tmu.data(), in.tlam.data(), in.tact.data(),
-                        in.rmu.data(), in.rlam.data(), in.ract.data(), in.kb.data(), in.hact.data(),
+            total_force(m, r, xx.data(), vv.data(), in.tmu.data(), in.tlam.data(), ta.data(),
+                        in.rmu.data(), in.rlam.data(), ra.data(), in.kb.data(), ha.data(),
                         in.cp.data(), f_n.data());
             for (size_t i = 0; i < N; ++i)
                 for (int k = 0; k < 3; ++k) w_b[i] += -dt * cu[3 * i + k] * f_n[3 * i + k];
@@ -773,7 +805,7 @@ int orc_rollout(const orc_model* m, const double* x0, const double* v0, double d
     std::vector<double> x(x0, x0 + 3 * N), v(v0, v0 + 3 * N), f(3 * N);
     if (traj) std::memcpy(traj, x.data(), 3 * N * sizeof(double));
     for (int n = 0; n < S; ++n) {
-        step(m, r, in, w, dt, x, v, f);
+        step(m, r, in, w, dt, n, x, v, f);
         if (traj) std::memcpy(traj + (size_t)(n + 1) * 3 * N, x.data(), 3 * N * sizeof(double));
     }
     if (xS) std::memcpy(xS, x.data(), 3 * N * sizeof(double));
@@ -803,7 +835,7 @@ int orc_loss_dir(const orc_model* m, const double* x0, const double* v0, double 
         seed<T>(x[i], x0[i], d ? d->x0 : nullptr, (int)i);
         seed<T>(v[i], v0[i], d ? d->v0 : nullptr, (int)i);
     }
-    for (int n = 0; n < S; ++n) step(m, r, in, w, dt, x, v, f);
+    for (int n = 0; n < S; ++n) step(m, r, in, w, dt, n, x, v, f);
     T L(0.0);
     for (size_t i = 0; i < 3 * N; ++i) {
         const T dd = x[i] - target[i];

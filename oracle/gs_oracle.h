@@ -67,6 +67,13 @@ typedef struct orc_model {
     int sphere_on;
     double sphere_c[3];
     double sphere_r;
+    /* time-varying actuation (the control input of Sec. 3 "visuomotor
+     * control"): row n of each [n_act_steps][n] array is added to the
+     * element's actuation during step n < n_act_steps; nullable */
+    int n_act_steps;
+    const double* tet_act_seq;
+    const double* tri_act_seq;
+    const double* hinge_act_seq;
 } orc_model;
 
 /* Gradient outputs; every pointer nullable. */
@@ -85,6 +92,10 @@ typedef struct orc_grads {
     double* hinge_act;
     double* contact;   /* [4]: ke, kd, kf, mu_f */
     double* node_mass; /* [N]: dL/dm_i */
+    /* [S][n]: dL/d(actuation of the element during step n), every step */
+    double* tet_act_seq;
+    double* tri_act_seq;
+    double* hinge_act_seq;
 } orc_grads;
 
 /* Directions for the forward-mode (dual number) rollout; every pointer nullable (= 0). */
@@ -102,6 +113,9 @@ typedef struct orc_dirs {
     const double* hinge_kb;
     const double* hinge_act;
     const double* contact; /* [4] */
+    const double* tet_act_seq;   /* [n_act_steps][n] */
+    const double* tri_act_seq;
+    const double* hinge_act_seq;
 } orc_dirs;
 
 /* ---- rest-state set-up ------------------------------------------------- */

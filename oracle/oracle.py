@@ -30,13 +30,17 @@ class _Model(C.Structure):
         ("ke", C.c_double), ("kd", C.c_double), ("kf", C.c_double), ("mu_f", C.c_double),
         ("plane_on", C.c_int), ("plane_n", C.c_double * 3), ("plane_h", C.c_double),
         ("sphere_on", C.c_int), ("sphere_c", C.c_double * 3), ("sphere_r", C.c_double),
+        ("n_act_steps", C.c_int), ("tet_act_seq", _dp), ("tri_act_seq", _dp), ("hinge_act_seq", _dp),
     ]
 
 
 _GRAD_FIELDS = ["x0", "v0", "tet_mu", "tet_lam", "tet_rho", "tet_act", "tri_mu", "tri_lam",
-                "tri_rho", "tri_act", "hinge_kb", "hinge_act", "contact", "node_mass"]
+                "tri_rho", "tri_act", "hinge_kb", "hinge_act", "contact", "node_mass",
+                "tet_act_seq", "tri_act_seq", "hinge_act_seq"]
 _DIR_FIELDS = ["x0", "v0", "tet_mu", "tet_lam", "tet_rho", "tet_act", "tri_mu", "tri_lam",
-               "tri_rho", "tri_act", "hinge_kb", "hinge_act", "contact"]
+               "tri_rho", "tri_act", "hinge_kb", "hinge_act", "contact",
+               "tet_act_seq", "tri_act_seq", "hinge_act_seq"]
+_SEQ = ("tet_act_seq", "tri_act_seq", "hinge_act_seq")
 
 
 class _Grads(C.Structure):
@@ -100,8 +104,12 @@ class Model:
     def __init__(self, problem=None, *, X=None, tets=None, tet_mu=None, tet_lam=None,
                  tet_rho=None, tet_act=None, tris=None, tri_mu=None, tri_lam=None,
                  tri_rho=None, tri_act=None, hinges=None, kb=None, hinge_act=None,
-                 pinned=None, contact=None, gravity=(0.0, -9.81, 0.0)):
+                 pinned=None, contact=None, gravity=(0.0, -9.81, 0.0), act_seq=None, hinge_act_seq=None):
+        # act_seq [n_steps][n_elements] (tets or triangles) and hinge_act_seq
+        # [n_steps][n_hinges]: actuation added during each step
         if problem is not None:
+            act_seq = getattr(problem, "act_seq", None) if act_seq is None else act_seq
+            hinge_act_seq = getattr(problem, "hinge_act_seq", None) if hinge_act_seq is None else hinge_act_seq
             X = problem.X
             contact = problem.contact
             gravity = problem.gravity
@@ -152,6 +160,20 @@ class Model:
             pn = keep(pinned, np.uint8)
             m.pinned = pn.ctypes.data_as(C.POINTER(C.c_ubyte))
         m.gravity = (C.c_double * 3)(*gravity)
+        self.n_act_steps = 0
+        if act_seq is not None or hinge_act_seq is not None:
+            rows = [np.asarray(a).shape[0] for a in (act_seq, hinge_act_seq) if a is not None]
+            if len(set(rows)) != 1:
+                raise ValueError("actuation sequences need the same number of steps")
+            m.n_act_steps = self.n_act_steps = rows[0]
+            if act_seq is not None:
+                a = keep(act_seq)
+                if m.n_tets:
+                    m.tet_act_seq = _p(a)
+                else:
+                    m.tri_act_seq = _p(a)
+            if hinge_act_seq is not None:
+                m.hinge_act_seq = _p(keep(hinge_act_seq))
         if contact is not None:
             m.ke, m.kd, m.kf, m.mu_f = contact.ke, contact.kd, contact.kf, contact.mu_f
             m.plane_on = int(contact.plane_on)
@@ -188,8 +210,10 @@ class Model:
         lib().orc_rollout(C.byref(self.c), _p(x0), _p(v0), dt, steps, _p(xS), _p(vS), _p(tr))
         return (xS, vS, tr) if traj else (xS, vS)
 
-    def loss_grad(self, x0, v0, dt, steps, target=None, xbar=None, vbar=None):
-        """Loss sum |x(S) - target|^2 and every gradient, by the discrete adjoint."""
+    def loss_grad(self, x0, v0, dt, steps, target=None, xbar=None, vbar=None, act_seq_grad=False):
+        """Loss sum |x(S) - target|^2 and every gradient, by the discrete adjoint.
+        With ``act_seq_grad`` also the per-step actuation gradients
+        (``tet_act_seq`` / ``tri_act_seq`` [S][n], ``hinge_act_seq`` [S][n_hinges])."""
         x0, v0, target, xbar, vbar = _d(x0), _d(v0), _d(target), _d(xbar), _d(vbar)
         N = self.n_nodes
         out = {
@@ -201,6 +225,8 @@ class Model:
             "hinge_kb": np.zeros(self.n_hinges), "hinge_act": np.zeros(self.n_hinges),
             "contact": np.zeros(4), "node_mass": np.zeros(N),
         }
+        for k, n in zip(_SEQ, (self.n_tets, self.n_tris, self.n_hinges)):
+            out[k] = np.zeros((steps, n)) if act_seq_grad else np.zeros(0)
         g = _Grads(**{k: (_p(out[k]) if out[k].size else None) for k in _GRAD_FIELDS})
         L = C.c_double(0.0)
         lib().orc_loss_grad(C.byref(self.c), _p(x0), _p(v0), dt, steps, _p(target), _p(xbar),
