@@ -57,7 +57,7 @@ def parse():
                     help="block: library defaults instead of the autotuner's patch shape and K")
     ap.add_argument("--cpu-steps", type=int, default=4,
                     help="oracle steps in the CPU sample (about 3 s each on one core for block64)")
-    ap.add_argument("--workload", default="block", choices=["block", "bar", "cloth", "batch", "serve"],
+    ap.add_argument("--workload", default="block", choices=["block", "bar", "cloth", "batch", "serve", "control"],
                     help="block: the 1.3M-tet solid (default line); the others measure the remaining workloads")
     ap.add_argument("--meshes", type=int, default=512, help="batch: number of meshes")
     ap.add_argument("--rates", default="10,20,50,100,200,500", help="serve: arrival rates (req/s)")
@@ -612,7 +612,83 @@ def workload_serve(args):
         print(json.dumps(line), flush=True)
 
 
-WORKLOADS = {"bar": workload_bar, "cloth": workload_cloth, "batch": workload_batch, "serve": workload_serve}
+def workload_control(args):
+    """Time-varying actuation (the visuomotor control input, Sec. 3) driven by
+    the App. D controller: (1) a 1,080-tet block, the size of the paper's
+    control-fem object, one controller training iteration = controller
+    forward, actuated rollout, adjoint with per-step actuation gradients,
+    controller backward; (2) the 1.3M-tet block with every element actuated
+    every step, against the same rollout + adjoint without actuation."""
+    import torch
+    from paper_2104_02646_gb300 import autograd as A
+    from paper_2104_02646_gb300 import control
+    from paper_2104_02646_gb300 import gradsim as gs
+    from paper_2104_02646_gb300 import inputs as I
+    gs.load()
+    dev = torch.device("cuda", 0)
+    ctx = gs.Context(0)
+    # (1) controller training iteration on a small object
+    S1 = 1000
+    p = I.block(n=6, steps=S1, seed=3)
+    mesh = gs.Mesh(ctx, p)
+    x0 = torch.tensor(p.x0, dtype=torch.float32, device=dev)
+    v0 = torch.tensor(p.v0, dtype=torch.float32, device=dev)
+    t = torch.arange(S1, dtype=torch.float32, device=dev) * p.dt
+    ctrl = control.SinusoidController(p.n_elems, omega=2 * 3.14159265 * 20, generator=torch.Generator().manual_seed(0)).to(dev)
+    xT = x0 + 0.01
+    opt = torch.optim.Adam(ctrl.parameters(), lr=0.05)
+
+    def iteration():
+        opt.zero_grad()
+        xS, _ = A.actuated_rollout(mesh, p.dt, S1, ctrl(t), x0, v0, K=1)
+        loss = ((xS - xT) ** 2).sum()
+        loss.backward()
+        opt.step()
+        return loss
+
+    for _ in range(args.warmup):
+        iteration()
+    t_it = min(_events_ms(iteration) for _ in range(args.steps))
+    line = {"metric": "controller training iterations/s", "workload": "control1080", "value": 1e3 / t_it,
+            "unit": "iterations/s", "ms_per_iteration": t_it,
+            "fwd_adj_elem_steps_per_s": p.n_elems * S1 / (t_it / 1e3), "dtype": "f32", "data": "synthetic",
+            "config": {"tets": p.n_elems, "steps": S1, "dt": p.dt, "controller": "8 sinusoids -> FC (no bias) -> tanh",
+                       "actuated": "every element, every step", "K": 1}}
+    print(json.dumps(line), flush=True)
+    mesh.close()
+    # (2) actuation overhead at scale
+    S2 = 200
+    q = I.block(n=64, steps=S2)
+    m2 = gs.Mesh(ctx, q)
+    E, N = q.n_elems, q.n_nodes
+    seq = (0.05 * torch.sin(torch.arange(S2, device=dev, dtype=torch.float32)[:, None] * 0.1
+                            + torch.linspace(0, 6.28, E, device=dev)[None, :])).contiguous()
+    tgt = torch.tensor(q.X, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = _grads(q, dev)
+    g_act = dict(g, d_act_seq=torch.zeros(S2, E, device=dev))
+
+    def run(actuated):
+        m2.set_act_seq(seq if actuated else None)
+        m2.reset()
+        m2.rollout(q.dt, S2, 1, tgt, loss)
+        m2.adjoint(g_act if actuated else g)
+
+    res = {}
+    for actuated in (False, True):
+        for _ in range(args.warmup):
+            run(actuated)
+        res[actuated] = min(_events_ms(lambda: run(actuated)) for _ in range(args.steps))
+    line = {"metric": "fwd+adjoint element-steps/s", "workload": "control_block64", "value": E * S2 / (res[True] / 1e3),
+            "unit": "element-steps/s", "unactuated_value": E * S2 / (res[False] / 1e3),
+            "ms_actuated": res[True], "ms_unactuated": res[False], "dtype": "f32", "data": "synthetic",
+            "config": {"tets": E, "steps": S2, "actuated": "every element, every step; per-step actuation gradients out",
+                       "K": 1}}
+    print(json.dumps(line), flush=True)
+
+
+WORKLOADS = {"bar": workload_bar, "cloth": workload_cloth, "batch": workload_batch, "serve": workload_serve,
+             "control": workload_control}
 
 if __name__ == "__main__":
     main()

@@ -164,6 +164,11 @@ typedef struct gs_grads {
     double* d_mass;
     float* d_x0;
     float* d_v0;
+    /* [S][n_elems] / [S][n_hinges], caller order, FP32: dL/d(the actuation
+     * an element / hinge has during step n) of the time-varying actuation
+     * (gs_mesh_set_act_seq), for every step of the rollout (S = its length) */
+    float* d_act_seq;
+    float* d_hinge_act_seq;
 } gs_grads;
 
 /* ---- library ------------------------------------------------------------ */
@@ -209,6 +214,19 @@ GS_API gs_status gs_mesh_info_get(const gs_mesh* mesh, gs_mesh_info* out);
 GS_API gs_status gs_mesh_set_params(gs_mesh* mesh, const float* mu, const float* lambda,
                              const float* density, const float* act, const float* kb,
                              int mem_space, void* stream);
+/* Time-varying actuation, the control input of the paper's visuomotor
+ * control experiments (Sec. 3; the controller of App. D drives per-element
+ * activations): during step n < n_steps, row n of act_seq [n_steps][n_elems]
+ * (caller order) is added to each element's actuation a_e in the energy
+ * (alpha = 1 + 3 mu/(4 lambda) + a_e, App. A) and row n of hinge_act_seq
+ * [n_steps][n_hinges] to each hinge's rest-angle actuation; later steps add
+ * nothing.  Rollouts count steps from 0; gs_step applies rows 0..n-1 on each
+ * call.  Both arrays nullable; n_steps = 0 (or both NULL) clears.  Copied
+ * (DEVICE or HOST per mem_space).  GS_EINVAL for n_steps < 0 or (HOST)
+ * non-finite values.  The adjoint's per-step gradients come out in
+ * gs_grads.d_act_seq / d_hinge_act_seq. */
+GS_API gs_status gs_mesh_set_act_seq(gs_mesh* mesh, const float* act_seq, const float* hinge_act_seq, int n_steps,
+                                     int mem_space, void* stream);
 /* Current state (x, v) [n_nodes][3] in caller order; nullable = unchanged. */
 GS_API gs_status gs_mesh_set_state(gs_mesh* mesh, const float* x, const float* v, int mem_space, void* stream);
 /* Back to the description's initial state: x = X exactly (the state is

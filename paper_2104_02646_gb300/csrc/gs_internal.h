@@ -122,6 +122,15 @@ struct alignas(16) MeshRT {  // 16 B aligned: the patch kernels bulk-copy it int
     float pnx, pny, pnz, ph;
     float scx, scy, scz, sr;
     int* status;             // bit 0: non-finite state
+    // time-varying actuation (nullable): during step n = st_a + st_b * tick,
+    // row n < n_act of act_seq [n_act][E] (hact_seq [n_act][B]) is added to
+    // the element's (hinge's) actuation; the adjoint writes dL/d(that
+    // actuation) into row n < n_dact of d_act_seq [n_dact][E] (d_hact_seq)
+    const float* act_seq;
+    const float* hact_seq;
+    float* d_act_seq;
+    float* d_hact_seq;
+    int n_act, n_dact, st_a, st_b;
 };
 
 // Everything one kernel launch over a launch set needs.
@@ -150,6 +159,10 @@ size_t patch_smem_bytes(int n_rec, int n_loc, int n_int, int n_slots, bool adjoi
 int patch_grid(int which, int threads, int stage_bytes, int n_patches, int num_sms);
 int boundary_grid(int adjoint, int n_blocks, int num_sms);
 gs_status selftest_bounded_wait(int iterations, int* status_host, cudaStream_t s);
+// rows x count floats between caller order and internal order: to_internal:
+// dst[r][i] = src[r][perm[i]]; else dst[r][perm[i]] = src[r][i]
+void launch_permute_rows(const float* src, float* dst, int rows, int count, const int* perm, int to_internal,
+                         cudaStream_t s);
 void set_kernel_smem_limits(size_t bytes);
 // kernels whose launches can be timed one by one (gs_profile)
 enum { KT_TET_FWD, KT_CLOTH_FWD, KT_FWD_BND, KT_TET_ADJ, KT_CLOTH_ADJ, KT_ADJ_BND, KT_COUNT };

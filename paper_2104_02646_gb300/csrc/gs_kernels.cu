@@ -40,6 +40,19 @@ __device__ __forceinline__ ContactParams cparams(const MeshRT& m) {
 
 __device__ __forceinline__ uint2 rec_ids(float4 w) { return make_uint2(__float_as_uint(w.x), __float_as_uint(w.y)); }
 
+// actuation added during the current step by a time-varying sequence (0 without one)
+__device__ __forceinline__ float act_step(const MeshRT& m, const float* seq, int count, int tick, int i) {
+    if (!seq) return 0.f;
+    const int n = m.st_a + m.st_b * tick;
+    return (n >= 0 && n < m.n_act) ? seq[(size_t)n * count + i] : 0.f;
+}
+// dL/d(actuation during the current step), when per-step gradients are requested
+__device__ __forceinline__ void act_grad_step(const MeshRT& m, float* dseq, int count, int tick, int i, float g) {
+    if (!dseq) return;
+    const int n = m.st_a + m.st_b * tick;
+    if (n >= 0 && n < m.n_dact) dseq[(size_t)n * count + i] = g;
+}
+
 
 // ---------------------------------------------------------------------------
 // TMA bulk copies global -> shared completing on an mbarrier
@@ -423,7 +436,8 @@ __device__ __forceinline__ void zero_pad_slot(const Stage& S) {
 // ---------------------------------------------------------------------------
 // element phases (one thread per element record)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void tet_elements_fwd(const PatchDesc& p, const Stage& S, int nt) {
+__device__ __forceinline__ void tet_elements_fwd(const PatchDesc& p, const MeshRT& m, int tick, const Stage& S,
+                                                 int nt) {
     const int nr = S.n_rec;
     zero_pad_slot(S);
     for (int le = threadIdx.x; le < p.n_e; le += nt) {
@@ -431,7 +445,7 @@ __device__ __forceinline__ void tet_elements_fwd(const PatchDesc& p, const Stage
         const uint2 id = rec_ids(w);
         TetState s;
         tet_state(xyz(S.xs[id.x & 0xffff]), xyz(S.xs[id.x >> 16]), xyz(S.xs[id.y & 0xffff]), xyz(S.xs[id.y >> 16]), a,
-                  b, c, w.z, s);
+                  b, c, w.z + act_step(m, m.act_seq, m.n_elems, tick, p.e_begin + le), s);
         float3 f0, f1, f2, f3;
         tet_forces(s, a, b, c, f0, f1, f2, f3);
         put(S, le, 0, f4(f0, 0.f));
@@ -441,16 +455,18 @@ __device__ __forceinline__ void tet_elements_fwd(const PatchDesc& p, const Stage
     }
 }
 
-__device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Stage& S, int nt) {
+__device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const MeshRT& m, int tick, const Stage& S,
+                                                   int nt) {
     const int nr = S.n_rec;
     zero_pad_slot(S);
     for (int lr = threadIdx.x; lr < nr; lr += nt) {
         const RecAt q = rec_slot(S, lr);
-        const float4 a = S.rec[q.base], b = S.rec[q.base + q.stride], c = S.rec[q.base + 2 * q.stride],
-                     w = S.rec[q.base + 3 * q.stride];
+        const float4 a = S.rec[q.base], c = S.rec[q.base + 2 * q.stride], w = S.rec[q.base + 3 * q.stride];
+        float4 b = S.rec[q.base + q.stride];
         const uint2 id = rec_ids(w);
         if (lr < p.n_e) {
             TriState s;
+            b.w += act_step(m, m.act_seq, m.n_elems, tick, p.e_begin + lr);  // actuation (b.w)
             tri_state(xyz(S.xs[id.x & 0xffff]), xyz(S.xs[id.x >> 16]), xyz(S.xs[id.y & 0xffff]), a, b,
                       make_float3(c.x, c.y, c.z), make_float3(c.w, w.z, w.w), s);
             float3 f0, f1, f2;
@@ -461,7 +477,8 @@ __device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Sta
         } else {
             HingeState s;
             hinge_state(xyz(S.xs[id.x & 0xffff]), xyz(S.xs[id.x >> 16]), xyz(S.xs[id.y & 0xffff]),
-                        xyz(S.xs[id.y >> 16]), xyz(a), xyz(b), xyz(c), b.w, s);
+                        xyz(S.xs[id.y >> 16]), xyz(a), xyz(b), xyz(c),
+                        b.w + act_step(m, m.hact_seq, m.n_hinges, tick, p.h_begin + (lr - p.n_e)), s);
             float3 f1, f2, f3, f4_;
             hinge_forces(s, a.w, f1, f2, f3, f4_);
             put(S, q, 0, f4(f1, 0.f));
@@ -473,7 +490,8 @@ __device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Sta
 }
 
 // corner result (dL/du_corner, f_corner . v_hat_node) in place
-__device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshRT& m, const Stage& S, int nt) {
+__device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshRT& m, int tick, const Stage& S,
+                                                 int nt) {
     const float dt = m.dt;
     const int nr = S.n_rec;
     zero_pad_slot(S);
@@ -484,7 +502,8 @@ __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshR
         const float4 x0 = S.xs[i0], x1 = S.xs[i1], x2 = S.xs[i2], x3 = S.xs[i3];
         const float3 v0 = xyz(S.vh[i0]), v1 = xyz(S.vh[i1]), v2 = xyz(S.vh[i2]), v3 = xyz(S.vh[i3]);
         TetState s;
-        tet_state(xyz(x0), xyz(x1), xyz(x2), xyz(x3), a, b, c, w.z, s);
+        tet_state(xyz(x0), xyz(x1), xyz(x2), xyz(x3), a, b, c, w.z + act_step(m, m.act_seq, m.n_elems, tick, p.e_begin + le),
+                  s);
         float3 f0, f1, f2, f3;
         tet_forces(s, a, b, c, f0, f1, f2, f3);
         float3 xb0, xb1, xb2, xb3;
@@ -499,10 +518,12 @@ __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshR
         const double2 g0 = S.gml[le];
         m.g_ml[e] = make_double2(g0.x + (double)gmu, g0.y + (double)glam);
         if (m.g_act) m.g_act[e] += (double)gact;
+        act_grad_step(m, m.d_act_seq, m.n_elems, tick, e, gact);
     }
 }
 
-__device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const MeshRT& m, const Stage& S, int nt) {
+__device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const MeshRT& m, int tick, const Stage& S,
+                                                   int nt) {
     const float dt = m.dt;
     const int nr = S.n_rec;
     zero_pad_slot(S);
@@ -516,12 +537,14 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             const float4 x0 = S.xs[i0], x1 = S.xs[i1], x2 = S.xs[i2];
             const float3 v0 = xyz(S.vh[i0]), v1 = xyz(S.vh[i1]), v2 = xyz(S.vh[i2]);
             TriState s;
-            tri_state(xyz(x0), xyz(x1), xyz(x2), a, b, make_float3(c.x, c.y, c.z), make_float3(c.w, w.z, w.w), s);
+            float4 bt = b;
+            bt.w += act_step(m, m.act_seq, m.n_elems, tick, p.e_begin + lr);  // actuation (b.w)
+            tri_state(xyz(x0), xyz(x1), xyz(x2), a, bt, make_float3(c.x, c.y, c.z), make_float3(c.w, w.z, w.w), s);
             float3 f0, f1, f2;
             tri_forces(s, a, b, f0, f1, f2);
             float3 xb0, xb1, xb2;
             float gmu, glam, gact;
-            tri_adjoint(s, a, b, (dt * x0.w) * v0, (dt * x1.w) * v1, (dt * x2.w) * v2, xb0, xb1, xb2, gmu, glam, gact);
+            tri_adjoint(s, a, bt, (dt * x0.w) * v0, (dt * x1.w) * v1, (dt * x2.w) * v2, xb0, xb1, xb2, gmu, glam, gact);
             put(S, q, 0, f4(xb0, dot3(f0, v0)));
             put(S, q, 1, f4(xb1, dot3(f1, v1)));
             put(S, q, 2, f4(xb2, dot3(f2, v2)));
@@ -529,12 +552,14 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             const double2 g0 = S.gml[lr];
             m.g_ml[t] = make_double2(g0.x + (double)gmu, g0.y + (double)glam);
             if (m.g_act) m.g_act[t] += (double)gact;
+            act_grad_step(m, m.d_act_seq, m.n_elems, tick, t, gact);
         } else {
             const int i1 = id.x & 0xffff, i2 = id.x >> 16, i3 = id.y & 0xffff, i4 = id.y >> 16;
             const float4 x1 = S.xs[i1], x2 = S.xs[i2], x3 = S.xs[i3], x4 = S.xs[i4];
             const float3 v1 = xyz(S.vh[i1]), v2 = xyz(S.vh[i2]), v3 = xyz(S.vh[i3]), v4 = xyz(S.vh[i4]);
             HingeState s;
-            hinge_state(xyz(x1), xyz(x2), xyz(x3), xyz(x4), xyz(a), xyz(b), xyz(c), b.w, s);
+            hinge_state(xyz(x1), xyz(x2), xyz(x3), xyz(x4), xyz(a), xyz(b), xyz(c),
+                        b.w + act_step(m, m.hact_seq, m.n_hinges, tick, p.h_begin + (lr - p.n_e)), s);
             float3 f1, f2, f3, f4_;
             hinge_forces(s, a.w, f1, f2, f3, f4_);
             float3 xb1, xb2, xb3, xb4;
@@ -548,6 +573,7 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             const int h = p.h_begin + (lr - p.n_e);
             m.g_kb[h] += (double)gkb;
             if (m.g_hact) m.g_hact[h] += (double)gact;
+            act_grad_step(m, m.d_hact_seq, m.n_hinges, tick, h, gact);
         }
     }
 }
@@ -744,11 +770,11 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
             consumer_sync(nt);
         }
         if (KIND == GS_TET) {
-            if (ADJ) tet_elements_adj(p, m, S, nt);
-            else tet_elements_fwd(p, S, nt);
+            if (ADJ) tet_elements_adj(p, m, tick, S, nt);
+            else tet_elements_fwd(p, m, tick, S, nt);
         } else {
-            if (ADJ) cloth_elements_adj(p, m, S, nt);
-            else cloth_elements_fwd(p, S, nt);
+            if (ADJ) cloth_elements_adj(p, m, tick, S, nt);
+            else cloth_elements_fwd(p, m, tick, S, nt);
         }
         consumer_sync(nt);
         if (ADJ) adjoint_nodes(p, m, S, nt);
@@ -1372,6 +1398,25 @@ gs_status selftest_bounded_wait(int iterations, int* status_host, cudaStream_t s
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "gs_selftest_bounded_wait");
     return GS_OK;
+}
+
+__global__ void k_permute_rows(const float* __restrict__ src, float* __restrict__ dst, int rows, int count,
+                               const int* __restrict__ perm, int to_internal) {
+    const long long total = (long long)rows * count;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const long long r = k / count;
+        const int i = (int)(k - r * count);
+        if (to_internal) dst[k] = src[r * count + perm[i]];
+        else dst[r * count + perm[i]] = src[k];
+    }
+}
+
+void launch_permute_rows(const float* src, float* dst, int rows, int count, const int* perm, int to_internal,
+                         cudaStream_t s) {
+    const long long total = (long long)rows * count;
+    if (total <= 0) return;
+    const long long blocks = (total + 255) / 256;
+    k_permute_rows<<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(src, dst, rows, count, perm, to_internal);
 }
 
 void launch_zero_f64(double* p, long long n, cudaStream_t s) {

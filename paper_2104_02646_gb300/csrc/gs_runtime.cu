@@ -1005,6 +1005,8 @@ gs_status LaunchSet::rollout(const std::vector<float>& dts, int S, int K, const 
             m->rt.out_a = 2;
             m->rt.out_b = 1;
             m->rt.ck_tick = -1;
+            m->rt.st_a = 0;  // tick t is step t
+            m->rt.st_b = 1;
         }
         GS_TRY(sync_rt(s));
         GS_TRY(run(0, S, s));
@@ -1022,6 +1024,8 @@ gs_status LaunchSet::rollout(const std::vector<float>& dts, int S, int K, const 
                 m->rt.in_a = m->rt.in_b = m->rt.out_a = m->rt.out_b = 0;
                 m->rt.ck_tick = (c + 1 < n_ck) ? steps - 1 : -1;
                 m->rt.ck_buf = 2 + c;
+                m->rt.st_a = c * K;  // tick t is step c K + t
+                m->rt.st_b = 1;
             }
             GS_TRY(sync_rt(s));
             GS_TRY(run(0, steps, s));
@@ -1065,6 +1069,19 @@ gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std:
         // actuation gradients only when asked for (saves an FP64 read-modify-write per element-step)
         m->rt.g_act = grads[i].d_act ? (double*)m->g_act.p : nullptr;
         m->rt.g_hact = grads[i].d_hinge_act ? (double*)m->g_hact.p : nullptr;
+        // per-step actuation gradients (internal order), every step written
+        m->rt.d_act_seq = m->rt.d_hact_seq = nullptr;
+        m->rt.n_dact = 0;
+        if (grads[i].d_act_seq && S > 0) {
+            GS_TRY(m->dact_seq.alloc(ctx, (size_t)S * m->info.n_elems * sizeof(float), s));
+            m->rt.d_act_seq = (float*)m->dact_seq.p;
+            m->rt.n_dact = S;
+        }
+        if (grads[i].d_hinge_act_seq && S > 0 && m->info.n_hinges > 0) {
+            GS_TRY(m->dhact_seq.alloc(ctx, (size_t)S * m->info.n_hinges * sizeof(float), s));
+            m->rt.d_hact_seq = (float*)m->dhact_seq.p;
+            m->rt.n_dact = S;
+        }
     }
     GS_TRY(sync_rt(s));
     launch_seed_loss(launch, (double*)d_loss.p, 1, s);
@@ -1082,6 +1099,8 @@ gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std:
             m->rt.ck_tick = -1;
             m->rt.adj_a = S;
             m->rt.adj_b = -1;
+            m->rt.st_a = S - 1;
+            m->rt.st_b = -1;
         }
         GS_TRY(sync_rt(s));
         GS_TRY(run(1, S, s));
@@ -1099,14 +1118,29 @@ gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std:
             r.ck_tick = -1;
             r.adj_a = seg0 + steps - 1;
             r.adj_b = -1;
+            r.st_a = sg * K;  // recompute: tick t is step sg K + t
+            r.st_b = 1;
         }
         GS_TRY(sync_rt(s));
         launch_copy_state(launch, s);
         GS_TRY(run(0, steps - 1, s));
+        for (gs_mesh* m : meshes) {
+            m->rt.st_a = sg * K + steps - 1;  // reverse: tick t is step sg K + steps - 1 - t
+            m->rt.st_b = -1;
+        }
+        GS_TRY(sync_rt(s));
         GS_TRY(run(1, steps, s));
     }
     for (size_t i = 0; i < meshes.size(); ++i) {
         gs_mesh* m = meshes[i];
+        if (m->rt.d_act_seq)
+            launch_permute_rows((const float*)m->dact_seq.p, grads[i].d_act_seq, S, m->info.n_elems,
+                                (const int*)m->elem_perm.p, 0, s);
+        if (m->rt.d_hact_seq)
+            launch_permute_rows((const float*)m->dhact_seq.p, grads[i].d_hinge_act_seq, S, m->info.n_hinges,
+                                (const int*)m->hinge_perm.p, 0, s);
+        m->rt.d_act_seq = m->rt.d_hact_seq = nullptr;
+        m->rt.n_dact = 0;
         m->rt.seed_x = m->rt.seed_v = nullptr;
         const size_t sm = std::max(sizeof(double) * (size_t)m->max_loc, (size_t)16);
         GS_TRY(m->self->sync_rt(s));
@@ -1130,9 +1164,15 @@ gs_status LaunchSet::step(const std::vector<float>& dts, int n, cudaStream_t s) 
         m->rt.active = ACT_FWD | ACT_ADJ;
         m->ro.valid = false;
     }
-    GS_TRY(sync_rt(s));
     const int chunk = 64;
-    for (int done = 0; done < n; done += chunk) GS_TRY(run(0, std::min(chunk, n - done), s));
+    for (int done = 0; done < n; done += chunk) {
+        for (gs_mesh* m : meshes) {
+            m->rt.st_a = done;  // actuation rows done, done + 1, ...
+            m->rt.st_b = 1;
+        }
+        GS_TRY(sync_rt(s));
+        GS_TRY(run(0, std::min(chunk, n - done), s));
+    }
     return warn;
 }
 
@@ -1257,6 +1297,49 @@ extern "C" gs_status gs_set_graphs(gs_ctx* c, int enable) {
     return GS_OK;
 }
 
+extern "C" gs_status gs_mesh_set_act_seq(gs_mesh* m, const float* act, const float* hact, int n_steps, int mem,
+                                         void* stream) {
+    clear_error();
+    if (!m) return set_error(GS_EINVAL, "null mesh");
+    if (n_steps < 0) return set_error(GS_EINVAL, "n_steps must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t E = m->info.n_elems, B = m->info.n_hinges;
+    if (mem == GS_MEM_HOST && n_steps > 0) {
+        auto finite = [](const float* a, size_t n) {
+            for (size_t i = 0; i < n; ++i)
+                if (!std::isfinite(a[i])) return false;
+            return true;
+        };
+        if ((act && !finite(act, (size_t)n_steps * E)) || (hact && !finite(hact, (size_t)n_steps * B)))
+            return set_error(GS_EINVAL, "non-finite actuation sequence");
+    }
+    m->rt.act_seq = m->rt.hact_seq = nullptr;
+    m->rt.n_act = 0;
+    m->act_seq.release(s);
+    m->hact_seq.release(s);
+    if (n_steps == 0 || (!act && !hact)) return GS_OK;
+    Buf tmp;
+    const float* src = nullptr;
+    if (act) {
+        GS_TRY(stage_in(m->ctx, tmp, act, (size_t)n_steps * E, mem, s, &src));
+        GS_TRY(m->act_seq.alloc(m->ctx, (size_t)n_steps * E * sizeof(float), s));
+        launch_permute_rows(src, (float*)m->act_seq.p, n_steps, (int)E, (const int*)m->elem_perm.p, 1, s);
+        m->rt.act_seq = (const float*)m->act_seq.p;
+    }
+    if (hact && B > 0) {
+        Buf tmp2;
+        GS_TRY(stage_in(m->ctx, tmp2, hact, (size_t)n_steps * B, mem, s, &src));
+        GS_TRY(m->hact_seq.alloc(m->ctx, (size_t)n_steps * B * sizeof(float), s));
+        launch_permute_rows(src, (float*)m->hact_seq.p, n_steps, (int)B, (const int*)m->hinge_perm.p, 1, s);
+        m->rt.hact_seq = (const float*)m->hact_seq.p;
+        tmp2.release(s);
+    }
+    m->rt.n_act = n_steps;
+    tmp.release(s);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
 extern "C" gs_status gs_step(gs_mesh* m, float dt, int n, void* stream) {
     clear_error();
     if (!m) return set_error(GS_EINVAL, "null mesh");
@@ -1311,8 +1394,10 @@ extern "C" gs_status gs_adjoint(gs_mesh* m, const float* dLdx, const float* dLdv
     }
     // host gradients: compute into device scratch, then copy back
     const size_t E = m->info.n_elems, B = m->info.n_hinges, N = m->info.n_nodes;
+    const size_t S = m->ro.valid ? (size_t)m->ro.S : 0;
     Buf hb;
-    const size_t bytes = sizeof(double) * (4 * E + 2 * B + N) + sizeof(float) * 2 * n3;
+    const size_t bytes = sizeof(double) * (4 * E + 2 * B + N) + sizeof(float) * 2 * n3 +
+                         sizeof(float) * S * ((g.d_act_seq ? E : 0) + (g.d_hinge_act_seq ? B : 0));
     GS_TRY(hb.alloc(m->ctx, bytes, s));
     char* p = (char*)hb.p;
     gs_grads dg{};
@@ -1330,6 +1415,8 @@ extern "C" gs_status gs_adjoint(gs_mesh* m, const float* dLdx, const float* dLdv
     dg.d_mass = g.d_mass ? (double*)take(8 * N) : nullptr;
     dg.d_x0 = g.d_x0 ? (float*)take(4 * n3) : nullptr;
     dg.d_v0 = g.d_v0 ? (float*)take(4 * n3) : nullptr;
+    dg.d_act_seq = g.d_act_seq ? (float*)take(4 * S * E) : nullptr;
+    dg.d_hinge_act_seq = g.d_hinge_act_seq ? (float*)take(4 * S * B) : nullptr;
     GS_TRY(m->self->adjoint({sx}, {sv}, {dg}, keep, s));
     auto back = [&](void* dst, const void* src, size_t nbytes) -> gs_status {
         if (dst && src) GS_CUDA(cudaMemcpyAsync(dst, src, nbytes, cudaMemcpyDeviceToHost, s));
@@ -1344,6 +1431,8 @@ extern "C" gs_status gs_adjoint(gs_mesh* m, const float* dLdx, const float* dLdv
     GS_TRY(back(g.d_mass, dg.d_mass, 8 * N));
     GS_TRY(back(g.d_x0, dg.d_x0, 4 * n3));
     GS_TRY(back(g.d_v0, dg.d_v0, 4 * n3));
+    GS_TRY(back(g.d_act_seq, dg.d_act_seq, 4 * S * E));
+    GS_TRY(back(g.d_hinge_act_seq, dg.d_hinge_act_seq, 4 * S * B));
     GS_CUDA(cudaStreamSynchronize(s));
     hb.release(s);
     t1.release(s);

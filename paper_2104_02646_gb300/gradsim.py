@@ -50,7 +50,8 @@ class gs_mesh_info(C.Structure):
 
 class gs_grads(C.Structure):
     _fields_ = [("d_mu", _vp), ("d_lambda", _vp), ("d_density", _vp), ("d_act", _vp), ("d_kb", _vp),
-                ("d_hinge_act", _vp), ("d_mass", _vp), ("d_x0", _vp), ("d_v0", _vp)]
+                ("d_hinge_act", _vp), ("d_mass", _vp), ("d_x0", _vp), ("d_v0", _vp), ("d_act_seq", _vp),
+                ("d_hinge_act_seq", _vp)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(_vp, C.c_size_t, _vp, _vp)
@@ -105,6 +106,7 @@ _PROTOS = {
     "gs_mesh_info_get": (C.c_int, [_vp, C.POINTER(gs_mesh_info)]),
     "gs_mesh_set_params": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
     "gs_mesh_set_state": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
+    "gs_mesh_set_act_seq": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
     "gs_mesh_get_state": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
     "gs_mesh_reset": (C.c_int, [_vp, _vp]),
     "gs_mesh_check": (C.c_int, [_vp, C.c_int, _vp]),
@@ -314,6 +316,17 @@ class Mesh:
     def set_state(self, x=None, v=None, host=False, stream=None):
         check(load().gs_mesh_set_state(self.h, _ptr(x), _ptr(v), GS_MEM_HOST if host else GS_MEM_DEVICE,
                                        _stream(stream)))
+
+    def set_act_seq(self, act_seq=None, hinge_act_seq=None, host=False, stream=None):
+        """Time-varying actuation: row n of act_seq [n_steps][n_elems] (and
+        hinge_act_seq [n_steps][n_hinges]) is added during step n; None for
+        both clears.  FP32 arrays (device tensors, or host arrays with host=True)."""
+        rows = [a.shape[0] for a in (act_seq, hinge_act_seq) if a is not None]
+        if len(set(rows)) > 1:
+            raise ValueError("actuation sequences need the same number of steps")
+        n = rows[0] if rows else 0
+        check(load().gs_mesh_set_act_seq(self.h, _ptr(act_seq), _ptr(hinge_act_seq), int(n),
+                                         GS_MEM_HOST if host else GS_MEM_DEVICE, _stream(stream)))
 
     def reset(self, stream=None):
         check(load().gs_mesh_reset(self.h, _stream(stream)))
