@@ -78,9 +78,11 @@ typedef struct gs_mesh gs_mesh;
 typedef struct gs_batch gs_batch;
 typedef struct gs_server gs_server;
 
-/* Device-memory provider.  alloc returns NULL on failure; free receives the
- * pointer and size given by alloc.  Both are called on the thread making the
- * library call, with the stream the memory will first be used on. */
+/* Device-memory provider.  alloc returns NULL on failure, else memory
+ * aligned to 256 bytes (as cudaMalloc's; an unaligned block is handed back
+ * to free and the call fails with GS_EINVAL); free receives the pointer and
+ * size given by alloc.  Both are called on the thread making the library
+ * call, with the stream the memory will first be used on. */
 typedef struct gs_allocator {
     void* (*alloc)(size_t bytes, void* stream, void* user);
     void (*free)(void* ptr, size_t bytes, void* stream, void* user);

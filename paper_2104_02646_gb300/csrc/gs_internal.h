@@ -118,14 +118,16 @@ struct alignas(16) MeshRT {  // 16 B aligned: the patch kernels bulk-copy it int
     // constants
     float dt, gx, gy, gz;
     float ke, kd, kf, mu_f;
-    int plane_on, sphere_on, pad1, pad2;
+    int plane_on, sphere_on;
+    int act_ld, hact_ld;     // row strides of act_seq / d_act_seq and hact_seq / d_hact_seq (multiples of 4)
     float pnx, pny, pnz, ph;
     float scx, scy, scz, sr;
     int* status;             // bit 0: non-finite state
     // time-varying actuation (nullable): during step n = st_a + st_b * tick,
-    // row n < n_act of act_seq [n_act][E] (hact_seq [n_act][B]) is added to
-    // the element's (hinge's) actuation; the adjoint writes dL/d(that
-    // actuation) into row n < n_dact of d_act_seq [n_dact][E] (d_hact_seq)
+    // row n < n_act of act_seq [n_act][act_ld] (hact_seq [n_act][hact_ld]),
+    // internal element (hinge) order, is added to the element's (hinge's)
+    // actuation; the adjoint writes dL/d(that actuation) into row n < n_dact
+    // of d_act_seq [n_dact][act_ld] (d_hact_seq [n_dact][hact_ld])
     const float* act_seq;
     const float* hact_seq;
     float* d_act_seq;
@@ -155,13 +157,13 @@ struct Launch {
 // --------------------------------------------------------------------------
 // kernels (gs_kernels.cu)
 // --------------------------------------------------------------------------
-size_t patch_smem_bytes(int n_rec, int n_loc, int n_int, int n_slots, bool adjoint);
+size_t patch_smem_bytes(int n_e, int n_h, int n_loc, int n_int, int n_slots, bool adjoint);
 int patch_grid(int which, int threads, int stage_bytes, int n_patches, int num_sms);
 int boundary_grid(int adjoint, int n_blocks, int num_sms);
 gs_status selftest_bounded_wait(int iterations, int* status_host, cudaStream_t s);
 // rows x count floats between caller order and internal order: to_internal:
 // dst[r][i] = src[r][perm[i]]; else dst[r][perm[i]] = src[r][i]
-void launch_permute_rows(const float* src, float* dst, int rows, int count, const int* perm, int to_internal,
+void launch_permute_rows(const float* src, float* dst, int rows, int count, int ld, const int* perm, int to_internal,
                          cudaStream_t s);
 void set_kernel_smem_limits(size_t bytes);
 // kernels whose launches can be timed one by one (gs_profile)

@@ -40,18 +40,22 @@ __device__ __forceinline__ ContactParams cparams(const MeshRT& m) {
 
 __device__ __forceinline__ uint2 rec_ids(float4 w) { return make_uint2(__float_as_uint(w.x), __float_as_uint(w.y)); }
 
-// actuation added during the current step by a time-varying sequence (0 without one)
-__device__ __forceinline__ float act_step(const MeshRT& m, const float* seq, int count, int tick, int i) {
-    if (!seq) return 0.f;
+// row of the time-varying actuation applied during the current step, or -1
+// (no sequence, or the step lies past its end: no extra actuation)
+__device__ __forceinline__ int act_row(const MeshRT& m, const float* seq, int tick) {
     const int n = m.st_a + m.st_b * tick;
-    return (n >= 0 && n < m.n_act) ? seq[(size_t)n * count + i] : 0.f;
+    return (seq && n >= 0 && n < m.n_act) ? n : -1;
 }
 // dL/d(actuation during the current step), when per-step gradients are requested
-__device__ __forceinline__ void act_grad_step(const MeshRT& m, float* dseq, int count, int tick, int i, float g) {
+__device__ __forceinline__ void act_grad_step(const MeshRT& m, float* dseq, int ld, int tick, int i, float g) {
     if (!dseq) return;
     const int n = m.st_a + m.st_b * tick;
-    if (n >= 0 && n < m.n_dact) dseq[(size_t)n * count + i] = g;
+    if (n >= 0 && n < m.n_dact) dseq[(size_t)n * ld + i] = g;
 }
+// the slice [r4down(begin), r4up(begin + n)) of a sequence row that holds a
+// patch's n entries from `begin`: 16 B aligned ends for one bulk copy
+__host__ __device__ __forceinline__ int act_slice_lo(int begin) { return begin & ~3; }
+__host__ __device__ __forceinline__ int act_slice_n(int begin, int n) { return ((begin + n + 3) & ~3) - (begin & ~3); }
 
 
 // ---------------------------------------------------------------------------
@@ -132,10 +136,12 @@ __host__ __device__ __forceinline__ int r16(int bytes) { return (bytes + 15) & ~
 // state.  The adjoint also holds v_hat for all local nodes, the interior
 // adjoint state and the boundary nodes' raw adjoint state.
 struct Layout {
-    int rec, rp, sl, pos, xs, vh, vs, xb, vb, xbB, vbB, gml, wb, total;
+    int rec, rp, sl, pos, xs, vh, vs, xb, vb, xbB, vbB, gml, wb, act, hact, total;
 };
 
-__host__ __device__ __forceinline__ Layout patch_layout(int n_rec, int n_loc, int n_int, int n_slots, bool adjoint) {
+__host__ __device__ __forceinline__ Layout patch_layout(int n_e, int n_h, int n_loc, int n_int, int n_slots,
+                                                        bool adjoint) {
+    const int n_rec = n_e + n_h;
     const int n_bnd = n_loc - n_int;
     Layout L;
     L.rec = 0;
@@ -153,7 +159,11 @@ __host__ __device__ __forceinline__ Layout patch_layout(int n_rec, int n_loc, in
     L.gml = L.vbB + (adjoint ? 16 * n_bnd : 0);
     // adjoint: dL/dw of the interior nodes
     L.wb = L.gml + (adjoint ? 16 * n_rec : 0);
-    L.total = L.wb + (adjoint ? r16(8 * n_int) : 0);
+    // the step's row slices of a time-varying actuation (elements, hinges);
+    // up to 3 entries of slack on each side for the aligned slice ends
+    L.act = L.wb + (adjoint ? r16(8 * n_int) : 0);
+    L.hact = L.act + r16(4 * (n_e + 6));
+    L.total = L.hact + (n_h ? r16(4 * (n_h + 6)) : 0);
     return L;
 }
 
@@ -295,12 +305,14 @@ struct Stage {
     float4* vbB;  // adjoint: boundary v_bar (raw)
     double2* gml;  // adjoint: staged (dL/dmu, dL/dlambda) of the patch's elements
     double* wb;   // adjoint: dL/dw of the interior nodes
+    const float* act;   // this step's actuation of the patch's elements [n_e], or null
+    const float* hact;  // this step's actuation of the patch's hinges [n_h], or null
 };
 
 __device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned char* buf, bool adjoint) {
     const int n_loc = p.n_int + p.n_bnd;
     const int n_rec = p.n_e + p.n_h;
-    const Layout L = patch_layout(n_rec, n_loc, p.n_int, p.n_slots, adjoint);
+    const Layout L = patch_layout(p.n_e, p.n_h, n_loc, p.n_int, p.n_slots, adjoint);
     Stage S;
     S.n_rec = n_rec;
     S.n_e = p.n_e;
@@ -318,8 +330,17 @@ __device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned
     S.vbB = (float4*)(buf + L.vbB);
     S.gml = (double2*)(buf + L.gml);
     S.wb = (double*)(buf + L.wb);
+    S.act = (const float*)(buf + L.act) + (p.e_begin & 3);
+    S.hact = (const float*)(buf + L.hact) + (p.h_begin & 3);
     return S;
 }
+
+// staged actuation of the current step, if the producer copied one
+__device__ __forceinline__ void bind_act(Stage& S, const PatchDesc& p, const MeshRT& m, int tick) {
+    if (act_row(m, m.act_seq, tick) < 0 || p.n_e == 0) S.act = nullptr;
+    if (act_row(m, m.hact_seq, tick) < 0 || p.n_h == 0) S.hact = nullptr;
+}
+__device__ __forceinline__ float act_of(const float* a, int i) { return a ? a[i] : 0.f; }
 
 // state buffers a patch reads
 __device__ __forceinline__ int in_buffer(const MeshRT& m, int tick, bool adjoint) {
@@ -344,8 +365,13 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
     // (dL/dmu, dL/dlambda) of the tet / triangle records, 16 B each
     const uint32_t b_g = adjoint ? 16u * p.n_e : 0u;
     const uint32_t b_pos = (uint32_t)r16(4 * p.n_bnd);
+    // this step's actuation rows, aligned slices around the patch's entries
+    const int ra = p.n_e ? act_row(m, m.act_seq, tick) : -1;
+    const int rh = p.n_h ? act_row(m, m.hact_seq, tick) : -1;
+    const uint32_t b_act = ra >= 0 ? 4u * act_slice_n(p.e_begin, p.n_e) : 0u;
+    const uint32_t b_hact = rh >= 0 ? 4u * act_slice_n(p.h_begin, p.n_h) : 0u;
     const uint32_t tx = (copy_rt ? (uint32_t)sizeof(MeshRT) : 0u) + 64u * n_rec + b_rp + b_sl + b_pos +
-                        (p.n_int ? (adjoint ? 4u : 2u) * b_int : 0u) + b_g;
+                        (p.n_int ? (adjoint ? 4u : 2u) * b_int : 0u) + b_g + b_act + b_hact;
     fence_proxy_async();
     mbar_expect_tx(bar, tx);
     if (copy_rt) bulk_g2s(hdr_rt, rt_global, (uint32_t)sizeof(MeshRT), bar);
@@ -364,6 +390,11 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
     if (b_g) {
         bulk_g2s(S.gml, m.g_ml + p.e_begin, b_g, bar);
     }
+    if (b_act)
+        bulk_g2s((void*)(S.act - (p.e_begin & 3)), m.act_seq + (size_t)ra * m.act_ld + act_slice_lo(p.e_begin), b_act, bar);
+    if (b_hact)
+        bulk_g2s((void*)(S.hact - (p.h_begin & 3)), m.hact_seq + (size_t)rh * m.hact_ld + act_slice_lo(p.h_begin), b_hact,
+                 bar);
 }
 
 // producer warp: asynchronous gather of the boundary nodes' state into `buf`;
@@ -445,7 +476,7 @@ __device__ __forceinline__ void tet_elements_fwd(const PatchDesc& p, const MeshR
         const uint2 id = rec_ids(w);
         TetState s;
         tet_state(xyz(S.xs[id.x & 0xffff]), xyz(S.xs[id.x >> 16]), xyz(S.xs[id.y & 0xffff]), xyz(S.xs[id.y >> 16]), a,
-                  b, c, w.z + act_step(m, m.act_seq, m.n_elems, tick, p.e_begin + le), s);
+                  b, c, w.z + act_of(S.act, le), s);
         float3 f0, f1, f2, f3;
         tet_forces(s, a, b, c, f0, f1, f2, f3);
         put(S, le, 0, f4(f0, 0.f));
@@ -466,7 +497,7 @@ __device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Mes
         const uint2 id = rec_ids(w);
         if (lr < p.n_e) {
             TriState s;
-            b.w += act_step(m, m.act_seq, m.n_elems, tick, p.e_begin + lr);  // actuation (b.w)
+            b.w += act_of(S.act, lr);  // actuation (b.w)
             tri_state(xyz(S.xs[id.x & 0xffff]), xyz(S.xs[id.x >> 16]), xyz(S.xs[id.y & 0xffff]), a, b,
                       make_float3(c.x, c.y, c.z), make_float3(c.w, w.z, w.w), s);
             float3 f0, f1, f2;
@@ -478,7 +509,7 @@ __device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Mes
             HingeState s;
             hinge_state(xyz(S.xs[id.x & 0xffff]), xyz(S.xs[id.x >> 16]), xyz(S.xs[id.y & 0xffff]),
                         xyz(S.xs[id.y >> 16]), xyz(a), xyz(b), xyz(c),
-                        b.w + act_step(m, m.hact_seq, m.n_hinges, tick, p.h_begin + (lr - p.n_e)), s);
+                        b.w + act_of(S.hact, lr - p.n_e), s);
             float3 f1, f2, f3, f4_;
             hinge_forces(s, a.w, f1, f2, f3, f4_);
             put(S, q, 0, f4(f1, 0.f));
@@ -502,8 +533,7 @@ __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshR
         const float4 x0 = S.xs[i0], x1 = S.xs[i1], x2 = S.xs[i2], x3 = S.xs[i3];
         const float3 v0 = xyz(S.vh[i0]), v1 = xyz(S.vh[i1]), v2 = xyz(S.vh[i2]), v3 = xyz(S.vh[i3]);
         TetState s;
-        tet_state(xyz(x0), xyz(x1), xyz(x2), xyz(x3), a, b, c, w.z + act_step(m, m.act_seq, m.n_elems, tick, p.e_begin + le),
-                  s);
+        tet_state(xyz(x0), xyz(x1), xyz(x2), xyz(x3), a, b, c, w.z + act_of(S.act, le), s);
         float3 f0, f1, f2, f3;
         tet_forces(s, a, b, c, f0, f1, f2, f3);
         float3 xb0, xb1, xb2, xb3;
@@ -518,7 +548,7 @@ __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshR
         const double2 g0 = S.gml[le];
         m.g_ml[e] = make_double2(g0.x + (double)gmu, g0.y + (double)glam);
         if (m.g_act) m.g_act[e] += (double)gact;
-        act_grad_step(m, m.d_act_seq, m.n_elems, tick, e, gact);
+        act_grad_step(m, m.d_act_seq, m.act_ld, tick, e, gact);
     }
 }
 
@@ -538,7 +568,7 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             const float3 v0 = xyz(S.vh[i0]), v1 = xyz(S.vh[i1]), v2 = xyz(S.vh[i2]);
             TriState s;
             float4 bt = b;
-            bt.w += act_step(m, m.act_seq, m.n_elems, tick, p.e_begin + lr);  // actuation (b.w)
+            bt.w += act_of(S.act, lr);  // actuation (b.w)
             tri_state(xyz(x0), xyz(x1), xyz(x2), a, bt, make_float3(c.x, c.y, c.z), make_float3(c.w, w.z, w.w), s);
             float3 f0, f1, f2;
             tri_forces(s, a, b, f0, f1, f2);
@@ -552,14 +582,14 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             const double2 g0 = S.gml[lr];
             m.g_ml[t] = make_double2(g0.x + (double)gmu, g0.y + (double)glam);
             if (m.g_act) m.g_act[t] += (double)gact;
-            act_grad_step(m, m.d_act_seq, m.n_elems, tick, t, gact);
+            act_grad_step(m, m.d_act_seq, m.act_ld, tick, t, gact);
         } else {
             const int i1 = id.x & 0xffff, i2 = id.x >> 16, i3 = id.y & 0xffff, i4 = id.y >> 16;
             const float4 x1 = S.xs[i1], x2 = S.xs[i2], x3 = S.xs[i3], x4 = S.xs[i4];
             const float3 v1 = xyz(S.vh[i1]), v2 = xyz(S.vh[i2]), v3 = xyz(S.vh[i3]), v4 = xyz(S.vh[i4]);
             HingeState s;
             hinge_state(xyz(x1), xyz(x2), xyz(x3), xyz(x4), xyz(a), xyz(b), xyz(c),
-                        b.w + act_step(m, m.hact_seq, m.n_hinges, tick, p.h_begin + (lr - p.n_e)), s);
+                        b.w + act_of(S.hact, lr - p.n_e), s);
             float3 f1, f2, f3, f4_;
             hinge_forces(s, a.w, f1, f2, f3, f4_);
             float3 xb1, xb2, xb3, xb4;
@@ -573,7 +603,7 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             const int h = p.h_begin + (lr - p.n_e);
             m.g_kb[h] += (double)gkb;
             if (m.g_hact) m.g_hact[h] += (double)gact;
-            act_grad_step(m, m.d_hact_seq, m.n_hinges, tick, h, gact);
+            act_grad_step(m, m.d_hact_seq, m.hact_ld, tick, h, gact);
         }
     }
 }
@@ -762,7 +792,8 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
         const PatchDesc p = *(const PatchDesc*)b;
         if (p.n_e < 0) return;
         const MeshRT& m = *(const MeshRT*)(b + kHdrRt);
-        const Stage S = stage_at(p, KIND, b + kHdr, ADJ);
+        Stage S = stage_at(p, KIND, b + kHdr, ADJ);
+        bind_act(S, p, m, tick);
         if (ADJ) {
             for (int l = threadIdx.x; l < p.n_int; l += nt) S.vh[l] = f4(xyz(S.vb[l]) + m.dt * xyz(S.xb[l]), 0.f);
             for (int k = threadIdx.x; k < p.n_bnd; k += nt)
@@ -1289,8 +1320,8 @@ __global__ void k_elem_grads(const PatchDesc* __restrict__ patches, const MeshRT
 // ===========================================================================
 // launchers
 // ===========================================================================
-size_t patch_smem_bytes(int n_rec, int n_loc, int n_int, int n_slots, bool adjoint) {
-    return (size_t)((kHdr + patch_layout(n_rec, n_loc, n_int, n_slots, adjoint).total + 127) & ~127);
+size_t patch_smem_bytes(int n_e, int n_h, int n_loc, int n_int, int n_slots, bool adjoint) {
+    return (size_t)((kHdr + patch_layout(n_e, n_h, n_loc, n_int, n_slots, adjoint).total + 127) & ~127);
 }
 
 // persistent grid: resident CTAs per SM x SMs, at most one CTA per patch
@@ -1400,23 +1431,25 @@ gs_status selftest_bounded_wait(int iterations, int* status_host, cudaStream_t s
     return GS_OK;
 }
 
-__global__ void k_permute_rows(const float* __restrict__ src, float* __restrict__ dst, int rows, int count,
+// rows of `count` entries between caller order (row stride count) and
+// internal order (row stride ld >= count; the padding is written as 0)
+__global__ void k_permute_rows(const float* __restrict__ src, float* __restrict__ dst, int rows, int count, int ld,
                                const int* __restrict__ perm, int to_internal) {
-    const long long total = (long long)rows * count;
+    const long long total = (long long)rows * ld;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
-        const long long r = k / count;
-        const int i = (int)(k - r * count);
-        if (to_internal) dst[k] = src[r * count + perm[i]];
-        else dst[r * count + perm[i]] = src[k];
+        const long long r = k / ld;
+        const int i = (int)(k - r * ld);
+        if (to_internal) dst[k] = i < count ? src[r * count + perm[i]] : 0.f;
+        else if (i < count) dst[r * count + perm[i]] = src[k];
     }
 }
 
-void launch_permute_rows(const float* src, float* dst, int rows, int count, const int* perm, int to_internal,
+void launch_permute_rows(const float* src, float* dst, int rows, int count, int ld, const int* perm, int to_internal,
                          cudaStream_t s) {
-    const long long total = (long long)rows * count;
+    const long long total = (long long)rows * ld;
     if (total <= 0) return;
     const long long blocks = (total + 255) / 256;
-    k_permute_rows<<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(src, dst, rows, count, perm, to_internal);
+    k_permute_rows<<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(src, dst, rows, count, ld, perm, to_internal);
 }
 
 void launch_zero_f64(double* p, long long n, cudaStream_t s) {

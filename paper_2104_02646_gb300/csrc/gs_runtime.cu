@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <memory>
 #include <numeric>
@@ -57,6 +58,12 @@ gs_status Buf::alloc(gs_ctx* c, size_t nbytes, cudaStream_t s) {
             c->used.fetch_sub(nbytes);
             return set_error(GS_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
         }
+    }
+    if (((uintptr_t)q & 255) != 0) {  // bulk copies need 16 B; the library assumes cudaMalloc's 256 B
+        if (c->has_alloc) c->alloc.free(q, nbytes, (void*)s, c->alloc.user);
+        else cudaFreeAsync(q, s);
+        c->used.fetch_sub(nbytes);
+        return set_error(GS_EINVAL, "device allocation is not 256-byte aligned");
     }
     ctx = c;
     p = q;
@@ -320,8 +327,8 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
         T.max_loc = std::max(T.max_loc, n_loc);
         T.max_slots = std::max(T.max_slots, n_slots);
         T.max_rec = std::max(T.max_rec, n_rec);
-        T.smem_fwd = std::max(T.smem_fwd, patch_smem_bytes(n_rec, n_loc, q.n_int, n_slots, false));
-        T.smem_adj = std::max(T.smem_adj, patch_smem_bytes(n_rec, n_loc, q.n_int, n_slots, true));
+        T.smem_fwd = std::max(T.smem_fwd, patch_smem_bytes(q.n_e, q.n_h, n_loc, q.n_int, n_slots, false));
+        T.smem_adj = std::max(T.smem_adj, patch_smem_bytes(q.n_e, q.n_h, n_loc, q.n_int, n_slots, true));
         for (int g : bl) {
             loc[g] = -1;
             pdeg[g] = 0;
@@ -653,6 +660,8 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     r.n_bnd = T.n_bnd;
     r.n_elems = E;
     r.n_hinges = B;
+    r.act_ld = (E + 3) & ~3;  // 16 B rows: a patch's slice of a row is one bulk copy
+    r.hact_ld = (B + 3) & ~3;
     r.active = ACT_FWD | ACT_ADJ;
     r.rec = (float4*)m->rec.p;
     r.hrec = (float4*)m->hrec.p;
@@ -1073,12 +1082,12 @@ gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std:
         m->rt.d_act_seq = m->rt.d_hact_seq = nullptr;
         m->rt.n_dact = 0;
         if (grads[i].d_act_seq && S > 0) {
-            GS_TRY(m->dact_seq.alloc(ctx, (size_t)S * m->info.n_elems * sizeof(float), s));
+            GS_TRY(m->dact_seq.alloc(ctx, (size_t)S * m->rt.act_ld * sizeof(float), s));
             m->rt.d_act_seq = (float*)m->dact_seq.p;
             m->rt.n_dact = S;
         }
         if (grads[i].d_hinge_act_seq && S > 0 && m->info.n_hinges > 0) {
-            GS_TRY(m->dhact_seq.alloc(ctx, (size_t)S * m->info.n_hinges * sizeof(float), s));
+            GS_TRY(m->dhact_seq.alloc(ctx, (size_t)S * m->rt.hact_ld * sizeof(float), s));
             m->rt.d_hact_seq = (float*)m->dhact_seq.p;
             m->rt.n_dact = S;
         }
@@ -1134,11 +1143,11 @@ gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std:
     for (size_t i = 0; i < meshes.size(); ++i) {
         gs_mesh* m = meshes[i];
         if (m->rt.d_act_seq)
-            launch_permute_rows((const float*)m->dact_seq.p, grads[i].d_act_seq, S, m->info.n_elems,
+            launch_permute_rows((const float*)m->dact_seq.p, grads[i].d_act_seq, S, m->info.n_elems, m->rt.act_ld,
                                 (const int*)m->elem_perm.p, 0, s);
         if (m->rt.d_hact_seq)
             launch_permute_rows((const float*)m->dhact_seq.p, grads[i].d_hinge_act_seq, S, m->info.n_hinges,
-                                (const int*)m->hinge_perm.p, 0, s);
+                                m->rt.hact_ld, (const int*)m->hinge_perm.p, 0, s);
         m->rt.d_act_seq = m->rt.d_hact_seq = nullptr;
         m->rt.n_dact = 0;
         m->rt.seed_x = m->rt.seed_v = nullptr;
@@ -1322,15 +1331,17 @@ extern "C" gs_status gs_mesh_set_act_seq(gs_mesh* m, const float* act, const flo
     const float* src = nullptr;
     if (act) {
         GS_TRY(stage_in(m->ctx, tmp, act, (size_t)n_steps * E, mem, s, &src));
-        GS_TRY(m->act_seq.alloc(m->ctx, (size_t)n_steps * E * sizeof(float), s));
-        launch_permute_rows(src, (float*)m->act_seq.p, n_steps, (int)E, (const int*)m->elem_perm.p, 1, s);
+        GS_TRY(m->act_seq.alloc(m->ctx, (size_t)n_steps * m->rt.act_ld * sizeof(float), s));
+        launch_permute_rows(src, (float*)m->act_seq.p, n_steps, (int)E, m->rt.act_ld, (const int*)m->elem_perm.p, 1,
+                            s);
         m->rt.act_seq = (const float*)m->act_seq.p;
     }
     if (hact && B > 0) {
         Buf tmp2;
         GS_TRY(stage_in(m->ctx, tmp2, hact, (size_t)n_steps * B, mem, s, &src));
-        GS_TRY(m->hact_seq.alloc(m->ctx, (size_t)n_steps * B * sizeof(float), s));
-        launch_permute_rows(src, (float*)m->hact_seq.p, n_steps, (int)B, (const int*)m->hinge_perm.p, 1, s);
+        GS_TRY(m->hact_seq.alloc(m->ctx, (size_t)n_steps * m->rt.hact_ld * sizeof(float), s));
+        launch_permute_rows(src, (float*)m->hact_seq.p, n_steps, (int)B, m->rt.hact_ld, (const int*)m->hinge_perm.p,
+                            1, s);
         m->rt.hact_seq = (const float*)m->hact_seq.p;
         tmp2.release(s);
     }
