@@ -6,7 +6,8 @@
 // Layout of this file, in the order the method is described:
 //   1. dual numbers (exact forward-mode derivatives; no hand derivation)
 //   2. rest-state set-up: Dm^-1, volume / area, lumped masses
-//   3. element physics: neo-Hookean tet, membrane triangle, dihedral bending
+//   3. element physics: neo-Hookean tet, membrane triangle, air on a triangle,
+//      dihedral bending
 //   4. contact and friction
 //   5. the semi-implicit Euler step and the rollout
 //   6. the discrete adjoint of App. B and the loss
@@ -306,6 +307,42 @@ T tri_energy_t(const T* x, const double* Dminv, double A, T mu, T lam, T act) {
     return A * (0.5 * mu * (Ic - 2.0) + 0.5 * lam * (J - alpha) * (J - alpha) - 0.5 * mu * flog(Ic + 1.0));
 }
 
+// Air on a triangle (App. A.1 "Deformable Thin-Shells" adds a lift/drag model
+// of the surrounding air but prints no formula).  Reading, a flat plate in a
+// uniform wind:
+//   v_r = (v_0 + v_1 + v_2)/3 - wind        velocity of the plate through the air
+//   N   = (x_1 - x_0) x (x_2 - x_0) / 2     vector area, |N| = A, N/A = n
+//   s   = N . v_r = A |v_r| cos(theta)
+//   drag  F_D = -k_drag |s| v_r              along -v_r, size k_drag A |cos theta| |v_r|^2
+//   lift  F_L = -k_lift s/(A |v_r|) (|v_r|^2 N - s v_r)
+//             = -k_lift A |v_r|^2 cos(theta) (n - cos(theta) v_r/|v_r|)
+//                                            perpendicular to v_r, size k_lift A |v_r|^2 |sin 2 theta|/2
+// and each corner takes F/3.  Both terms are unchanged when the winding (the
+// sign of n) flips; the lift does no work, the drag only removes energy
+// (zero wind).  The lift is taken as 0 when v_r = 0 or A = 0.
+template <class T>
+void air_forces_t(const T* x, const T* v, double k_drag, double k_lift, const double* wind, T* f) {
+    T e1[3], e2[3], N[3], vr[3];
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = x[3 + k] - x[k];
+        e2[k] = x[6 + k] - x[k];
+        vr[k] = (v[k] + v[3 + k] + v[6 + k]) / 3.0 - wind[k];
+    }
+    vcross(e1, e2, N);
+    for (int k = 0; k < 3; ++k) N[k] = 0.5 * N[k];
+    const T s = vdot(N, vr);
+    const T abs_s = val(s) < 0.0 ? -s : s;
+    T F[3];
+    for (int k = 0; k < 3; ++k) F[k] = -k_drag * abs_s * vr[k];
+    const T q = vdot(vr, vr), A2 = vdot(N, N);
+    if (k_lift != 0.0 && val(q) > 0.0 && val(A2) > 0.0) {
+        const T c = k_lift * s / (fsqrt(A2) * fsqrt(q));
+        for (int k = 0; k < 3; ++k) F[k] = F[k] - c * (q * N[k] - s * vr[k]);
+    }
+    for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 3; ++k) f[3 * c + k] = F[k] / 3.0;
+}
+
 // Dihedral angle of a hinge (x1, x2 wing tips; edge x3 -> x4):
 // N1 = (x1 - x3) x (x1 - x4), N2 = (x2 - x4) x (x2 - x3), E = x4 - x3,
 // phi = atan2((n1 x n2) . E/|E|, n1 . n2)   (0 when flat).
@@ -439,6 +476,19 @@ void total_force(const orc_model* m, const Rest& r, const T* x, const T* v,
         tri_forces_t(xe, &r.tri_Dminv[4 * (size_t)t], r.tri_A[t], rmu[t], rlam[t], ract[t], fe);
         for (int c = 0; c < 3; ++c)
             for (int k = 0; k < 3; ++k) f[3 * (size_t)m->tris[3 * t + c] + k] += fe[3 * c + k];
+    }
+    if (m->air_on) {
+        for (int t = 0; t < m->n_tris; ++t) {
+            T xe[9], ve[9], fe[9];
+            for (int c = 0; c < 3; ++c)
+                for (int k = 0; k < 3; ++k) {
+                    xe[3 * c + k] = x[3 * (size_t)m->tris[3 * t + c] + k];
+                    ve[3 * c + k] = v[3 * (size_t)m->tris[3 * t + c] + k];
+                }
+            air_forces_t(xe, ve, m->k_drag, m->k_lift, m->wind, fe);
+            for (int c = 0; c < 3; ++c)
+                for (int k = 0; k < 3; ++k) f[3 * (size_t)m->tris[3 * t + c] + k] += fe[3 * c + k];
+        }
     }
     for (int h = 0; h < m->n_hinges; ++h) {
         T xe[12], fe[12];
@@ -676,6 +726,29 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
             kb_b[h] += pb[0]; hact_b[h] += pb[1];
             if (hseq_b) hseq_b[(size_t)n * m->n_hinges + h] = pb[1];
         }
+        if (m->air_on) {
+            // air force of a triangle as a function of its corners' (x, v):
+            // 18 inputs, 9 force outputs (y padded with zeros)
+            for (int e = 0; e < m->n_tris; ++e) {
+                double xv[18], ye[18] = {0}, xb[18] = {0}, pb[1] = {0};
+                const int* t = &m->tris[3 * e];
+                for (int c = 0; c < 3; ++c)
+                    for (int k = 0; k < 3; ++k) {
+                        xv[3 * c + k] = xn[3 * (size_t)t[c] + k];
+                        xv[9 + 3 * c + k] = vn[3 * (size_t)t[c] + k];
+                        ye[3 * c + k] = y[3 * (size_t)t[c] + k];
+                    }
+                element_vjp<18, 0>(xv, nullptr, ye, xb, pb, [&](auto* xd, auto* pd, auto* fd) {
+                    (void)pd;
+                    air_forces_t(xd, xd + 9, m->k_drag, m->k_lift, m->wind, fd);
+                });
+                for (int c = 0; c < 3; ++c)
+                    for (int k = 0; k < 3; ++k) {
+                        lq_new[3 * (size_t)t[c] + k] += xb[3 * c + k];
+                        lu_new[3 * (size_t)t[c] + k] += xb[9 + 3 * c + k];
+                    }
+            }
+        }
         if (m->plane_on || m->sphere_on) {
             for (size_t i = 0; i < N; ++i) {
                 double xv[6], yi[6] = {0}, xb[6] = {0, 0, 0, 0, 0, 0}, pb[4] = {0, 0, 0, 0};
@@ -780,6 +853,10 @@ void orc_hinge_angle_grad(const double x[12], double g[12]) {
     for (int i = 0; i < 12; ++i) { xd[i] = Dual<12>(x[i]); xd[i].d[i] = 1.0; }
     const Dual<12> phi = hinge_angle_t(xd);
     for (int i = 0; i < 12; ++i) g[i] = phi.d[i];
+}
+void orc_air_forces(const double x[9], const double v[9], double k_drag, double k_lift, const double wind[3],
+                    double f[9]) {
+    air_forces_t<double>(x, v, k_drag, k_lift, wind, f);
 }
 void orc_contact_force(const orc_model* m, const double x[3], const double v[3], double f[3]) {
     contact_t<double>(m, x, v, m->ke, m->kd, m->kf, m->mu_f, f);

@@ -15,6 +15,8 @@
  *   - constant-strain triangles with the same energy in the plane
  *     (I_C - 2 offset), and Bridson's dihedral bending force
  *     f_b = k_b sin(phi/2 + alpha) d                         [App. A.1]
+ *   - a lift/drag air model on the cloth surface (flat-plate reading)
+ *                                                          [App. A.1]
  *   - compliant contact f_n = n (k_e C + k_d dC/dt) with relaxed Coulomb
  *     friction against a ground plane and a sphere          [App. A.1, App. C.2]
  *   - semi-implicit Euler u+ = u- + dt M^-1 f(s-), q+ = q- + dt u+  [App. B]
@@ -74,6 +76,13 @@ typedef struct orc_model {
     const double* tet_act_seq;
     const double* tri_act_seq;
     const double* hinge_act_seq;
+    /* air on the cloth surface (App. A.1 "Deformable Thin-Shells": a
+     * lift/drag model of the surrounding air; the paper gives no formula,
+     * the reading is stated at air_forces_t): per triangle, drag and lift
+     * coefficients k_drag, k_lift (kg/m^3) against a uniform wind (m/s) */
+    int air_on;
+    double k_drag, k_lift;
+    double wind[3];
 } orc_model;
 
 /* Gradient outputs; every pointer nullable. */
@@ -121,6 +130,9 @@ typedef struct orc_dirs {
 /* ---- rest-state set-up ------------------------------------------------- */
 void orc_tet_rest(const double X[12], double Dminv[9], double* V);
 void orc_tri_rest(const double X[9], double Dminv[4], double* A);
+/* air force on one triangle's corners (x, v: 3 corners x 3) */
+void orc_air_forces(const double x[9], const double v[9], double k_drag, double k_lift, const double wind[3],
+                    double f[9]);
 /* lumped node masses m_i (pinned nodes included) */
 int orc_node_masses(const orc_model* m, double* mass);
 

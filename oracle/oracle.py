@@ -31,6 +31,7 @@ class _Model(C.Structure):
         ("plane_on", C.c_int), ("plane_n", C.c_double * 3), ("plane_h", C.c_double),
         ("sphere_on", C.c_int), ("sphere_c", C.c_double * 3), ("sphere_r", C.c_double),
         ("n_act_steps", C.c_int), ("tet_act_seq", _dp), ("tri_act_seq", _dp), ("hinge_act_seq", _dp),
+        ("air_on", C.c_int), ("k_drag", C.c_double), ("k_lift", C.c_double), ("wind", C.c_double * 3),
     ]
 
 
@@ -72,6 +73,7 @@ def lib():
         L.orc_hinge_angle.restype = C.c_double
         L.orc_hinge_angle_grad.argtypes = [_dp, _dp]
         L.orc_contact_force.argtypes = [C.POINTER(_Model), _dp, _dp, _dp]
+        L.orc_air_forces.argtypes = [_dp, _dp, C.c_double, C.c_double, _dp, _dp]
         L.orc_forces.argtypes = [C.POINTER(_Model), _dp, _dp, _dp]
         L.orc_rollout.argtypes = [C.POINTER(_Model), _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp]
         L.orc_loss_grad.argtypes = [C.POINTER(_Model), _dp, _dp, C.c_double, C.c_int, _dp, _dp,
@@ -104,10 +106,13 @@ class Model:
     def __init__(self, problem=None, *, X=None, tets=None, tet_mu=None, tet_lam=None,
                  tet_rho=None, tet_act=None, tris=None, tri_mu=None, tri_lam=None,
                  tri_rho=None, tri_act=None, hinges=None, kb=None, hinge_act=None,
-                 pinned=None, contact=None, gravity=(0.0, -9.81, 0.0), act_seq=None, hinge_act_seq=None):
+                 pinned=None, contact=None, gravity=(0.0, -9.81, 0.0), act_seq=None, hinge_act_seq=None,
+                 air=None):
         # act_seq [n_steps][n_elements] (tets or triangles) and hinge_act_seq
-        # [n_steps][n_hinges]: actuation added during each step
+        # [n_steps][n_hinges]: actuation added during each step; air: an
+        # object with k_drag, k_lift, wind (the triangles' air model)
         if problem is not None:
+            air = getattr(problem, "air", None) if air is None else air
             act_seq = getattr(problem, "act_seq", None) if act_seq is None else act_seq
             hinge_act_seq = getattr(problem, "hinge_act_seq", None) if hinge_act_seq is None else hinge_act_seq
             X = problem.X
@@ -174,6 +179,10 @@ class Model:
                     m.tri_act_seq = _p(a)
             if hinge_act_seq is not None:
                 m.hinge_act_seq = _p(keep(hinge_act_seq))
+        if air is not None:
+            m.air_on = 1
+            m.k_drag, m.k_lift = float(air.k_drag), float(air.k_lift)
+            m.wind = (C.c_double * 3)(*air.wind)
         if contact is not None:
             m.ke, m.kd, m.kf, m.mu_f = contact.ke, contact.kd, contact.kf, contact.mu_f
             m.plane_on = int(contact.plane_on)
@@ -308,3 +317,14 @@ def hinge_angle_grad(x):
     g = np.zeros(12)
     lib().orc_hinge_angle_grad(_p(x), _p(g))
     return g.reshape(4, 3)
+
+
+def air_forces(x, v, k_drag, k_lift, wind=(0.0, 0.0, 0.0)):
+    """Air force on the corners of one triangle ([3, 3] positions and
+    velocities) under the oracle's flat-plate reading of the lift/drag model."""
+    x = _d(np.asarray(x).reshape(9))
+    v = _d(np.asarray(v).reshape(9))
+    w = _d(np.asarray(wind).reshape(3))
+    f = np.zeros(9)
+    lib().orc_air_forces(_p(x), _p(v), float(k_drag), float(k_lift), _p(w), _p(f))
+    return f.reshape(3, 3)

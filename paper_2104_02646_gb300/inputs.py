@@ -24,6 +24,8 @@ missing mesh datasets):
 * ``cloth``    256^2 node grid over a 1 m square at y = 0.305 draped on a
                sphere of radius 0.3 centred at (0.5, 0, 0.5); "3" keeps the
                stated (explicitly unstable) materials, "3s" the stable variant.
+* ``cloth_throw`` a small cloth (64-2048 triangles) thrown through air with
+               lift/drag over the ground: the cloth-control episode.
 * ``batch``    512 seeded a x b x c hex blocks, 1e3-1e5 tets each.
 * ``queries``  a Poisson stream of tet-block / cloth-grid gradient queries.
 """
@@ -176,6 +178,15 @@ class Contact:
 
 
 @dataclasses.dataclass
+class Air:
+    """Air on the cloth surface: drag and lift coefficients (kg/m^3, the
+    factor 1/2 rho_air C of a flat plate) against a uniform wind (m/s)."""
+    k_drag: float = 0.6
+    k_lift: float = 0.4
+    wind: tuple = (0.0, 0.0, 0.0)
+
+
+@dataclasses.dataclass
 class Problem:
     """One simulation instance: mesh, parameters, initial state, run length."""
     name: str
@@ -196,6 +207,7 @@ class Problem:
     gravity: tuple = (0.0, -9.81, 0.0)
     dt: float = 1.0e-4
     steps: int = 100
+    air: Optional[Air] = None             # cloth only: lift/drag air model
 
     def __post_init__(self):
         if self.x0 is None:
@@ -277,6 +289,33 @@ def cloth(variant: str = "3s", n: int = 256, steps: int = 500, grid_scaled: bool
     return Problem(name=f"cloth{variant}_{n}", kind=CLOTH, X=X, elems=tris,
                    mu=np.full(T, mu), lam=np.full(T, lam), rho=np.full(T, 0.2),
                    hinges=hinges, kb=np.full(B, kb), contact=con, dt=1.0e-4, steps=steps)
+
+
+def cloth_throw(n: int = 12, steps: int = 400, seed: int = 0, air: Optional["Air"] = None,
+                side: float = 0.5) -> Problem:
+    """The cloth-control episode of Sec. 3 (a cloth of 64-2048 triangles sent
+    towards a goal by its initial velocity, under lift/drag): an n x n grid
+    (2 (n-1)^2 triangles, n in 7..33) of side ``side`` at 0.4 m, tilted by a
+    seeded angle, thrown with a seeded common velocity plus a small per-node
+    spread, over the ground plane.  Materials of "3s" scaled to the grid.
+    """
+    rng = np.random.default_rng(seed)
+    X, tris, hinges = cloth_grid(n, side, 0.0)
+    # tilt about the x axis through the centre, then lift to 0.4 m
+    a = rng.uniform(-0.5, 0.5)
+    c0 = X.mean(axis=0)
+    R = np.array([[1.0, 0.0, 0.0], [0.0, math.cos(a), -math.sin(a)], [0.0, math.sin(a), math.cos(a)]])
+    X = (X - c0) @ R.T + np.array([0.5, 0.4, 0.5])
+    T, B = tris.shape[0], hinges.shape[0]
+    sc = (255.0 / (n - 1)) ** 2 * side ** 2  # node masses relative to the 256^2 unit cloth
+    mu, lam, kb = 10.0 * sc, 20.0 * sc, 1.0e-6 * sc
+    con = Contact(ke=100.0 * sc, kd=1.0e-3 * sc, kf=1.0e-3 * sc, mu_f=0.5)
+    v_common = np.array([rng.uniform(-1.0, 1.0), rng.uniform(0.5, 1.5), rng.uniform(-1.0, 1.0)])
+    v0 = v_common + rng.normal(0.0, 0.05, X.shape)
+    return Problem(name=f"cloth_throw{n}", kind=CLOTH, X=X, elems=tris,
+                   mu=np.full(T, mu), lam=np.full(T, lam), rho=np.full(T, 0.2),
+                   hinges=hinges, kb=np.full(B, kb), v0=v0, contact=con, dt=1.0e-4, steps=steps,
+                   air=Air() if air is None else air)
 
 
 def block_dims(n_tets_target: float, rng) -> tuple:
