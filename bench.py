@@ -17,6 +17,7 @@ the host cores on a bounded sample of the same workload.
 """
 import argparse
 import hashlib
+import dataclasses
 import json
 import os
 import statistics
@@ -57,7 +58,7 @@ def parse():
                     help="block: library defaults instead of the autotuner's patch shape and K")
     ap.add_argument("--cpu-steps", type=int, default=4,
                     help="oracle steps in the CPU sample (about 3 s each on one core for block64)")
-    ap.add_argument("--workload", default="block", choices=["block", "bar", "cloth", "batch", "serve", "control"],
+    ap.add_argument("--workload", default="block", choices=["block", "bar", "cloth", "batch", "serve", "control", "cloth_air"],
                     help="block: the 1.3M-tet solid (default line); the others measure the remaining workloads")
     ap.add_argument("--meshes", type=int, default=512, help="batch: number of meshes")
     ap.add_argument("--rates", default="10,20,50,100,200,500", help="serve: arrival rates (req/s)")
@@ -687,8 +688,76 @@ def workload_control(args):
     print(json.dumps(line), flush=True)
 
 
+def workload_cloth_air(args):
+    """The air model on cloth (App. A.1 lift/drag) and the cloth-control
+    workload of Sec. 3: (1) one system-identification iteration on a thrown
+    2,048-triangle cloth (the largest of the paper's 64-2048) = rollout of
+    1,000 steps with air + adjoint + Adam on the per-node initial velocity;
+    (2) the 256^2 cloth ("3s") rollout + adjoint with and without air."""
+    import torch
+    from paper_2104_02646_gb300 import autograd as A
+    from paper_2104_02646_gb300 import gradsim as gs
+    from paper_2104_02646_gb300 import inputs as I
+    gs.load()
+    dev = torch.device("cuda", 0)
+    ctx = gs.Context(0)
+    S1 = 1000
+    p = I.cloth_throw(n=33, steps=S1, seed=0)
+    mesh = gs.Mesh(ctx, p)
+    f32 = dict(dtype=torch.float32, device=dev)
+    mu, lam, rho = (torch.tensor(a, **f32) for a in (p.mu, p.lam, p.rho))
+    x0 = torch.tensor(p.x0, **f32)
+    v_ref = torch.tensor(p.v0, **f32)
+    with torch.no_grad():
+        xT, _ = A.rollout(mesh, p.dt, S1, mu, lam, rho, x0, v_ref, K=1)
+    v = (v_ref + 0.3).requires_grad_(True)
+    opt = torch.optim.Adam([v], lr=0.05)
+
+    def iteration():
+        opt.zero_grad()
+        xS, _ = A.rollout(mesh, p.dt, S1, mu, lam, rho, x0, v, K=1)
+        loss = ((xS - xT) ** 2).sum()
+        loss.backward()
+        opt.step()
+
+    for _ in range(args.warmup):
+        iteration()
+    t_it = min(_events_ms(iteration) for _ in range(args.steps))
+    line = {"metric": "cloth v0 system-ID iterations/s", "workload": "cloth_throw33", "value": 1e3 / t_it,
+            "unit": "iterations/s", "ms_per_iteration": t_it,
+            "fwd_adj_tri_steps_per_s": p.n_elems * S1 / (t_it / 1e3), "dtype": "f32", "data": "synthetic",
+            "config": {"triangles": p.n_elems, "hinges": p.n_hinges, "steps": S1, "dt": p.dt,
+                       "air": dataclasses.asdict(p.air), "optimised": "per-node initial velocity (Adam)", "K": 1}}
+    print(json.dumps(line), flush=True)
+    mesh.close()
+    S2 = 500
+    q = I.cloth("3s", n=256, steps=S2)
+    m2 = gs.Mesh(ctx, q)
+    tgt = torch.tensor(q.X, **f32)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = _grads(q, dev)
+    res = {}
+    for air in (None, I.Air(wind=(0.5, 0.0, 0.2))):
+        m2.set_air(air)
+
+        def run():
+            m2.reset()
+            m2.rollout(q.dt, S2, 1, tgt, loss)
+            m2.adjoint(g)
+
+        for _ in range(args.warmup):
+            run()
+        res[air is not None] = min(_events_ms(run) for _ in range(args.steps))
+    line = {"metric": "fwd+adjoint element-steps/s", "workload": "cloth3s_air", "value": q.n_elems * S2 / (res[True] / 1e3),
+            "unit": "element-steps/s", "no_air_value": q.n_elems * S2 / (res[False] / 1e3),
+            "ms_air": res[True], "ms_no_air": res[False], "dtype": "f32", "data": "synthetic",
+            "config": {"grid": "256x256", "triangles": q.n_elems, "hinges": q.n_hinges, "steps": S2, "K": 1,
+                       "air": "k_drag 0.6, k_lift 0.4, wind (0.5, 0, 0.2)"}}
+    print(json.dumps(line), flush=True)
+
+
 WORKLOADS = {"bar": workload_bar, "cloth": workload_cloth, "batch": workload_batch, "serve": workload_serve,
-             "control": workload_control}
+             "control": workload_control, "cloth_air": workload_cloth_air}
 
 if __name__ == "__main__":
     main()

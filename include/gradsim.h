@@ -229,6 +229,22 @@ GS_API gs_status gs_mesh_set_params(gs_mesh* mesh, const float* mu, const float*
  * gs_grads.d_act_seq / d_hinge_act_seq. */
 GS_API gs_status gs_mesh_set_act_seq(gs_mesh* mesh, const float* act_seq, const float* hinge_act_seq, int n_steps,
                                      int mem_space, void* stream);
+/* Air on the cloth surface (App. A.1 "Deformable Thin-Shells": a lift/drag
+ * model of the surrounding air; the paper prints no formula).  Flat-plate
+ * reading, per triangle with deformed vector area N (|N| = A), mean corner
+ * velocity minus the wind v_r, s = N . v_r:
+ *   drag F_D = -k_drag |s| v_r,
+ *   lift F_L = -k_lift s/(A |v_r|) (|v_r|^2 N - s v_r)  (perpendicular to v_r),
+ * a third of F_D + F_L on each corner; coefficients in kg/m^3 (1/2 rho_air C
+ * of a flat plate), wind in m/s.  Both enter the forward step and the
+ * adjoint (dL/dx, dL/dv through the air).  GS_CLOTH meshes only (GS_EINVAL
+ * otherwise); coefficients finite and >= 0, wind finite (GS_EINVAL).  NULL
+ * turns the air off.  Takes effect at the next launch. */
+typedef struct gs_air {
+    float k_drag, k_lift;
+    float wind[3];
+} gs_air;
+GS_API gs_status gs_mesh_set_air(gs_mesh* mesh, const gs_air* air, void* stream);
 /* Current state (x, v) [n_nodes][3] in caller order; nullable = unchanged. */
 GS_API gs_status gs_mesh_set_state(gs_mesh* mesh, const float* x, const float* v, int mem_space, void* stream);
 /* Back to the description's initial state: x = X exactly (the state is

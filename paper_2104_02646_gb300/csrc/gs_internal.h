@@ -133,6 +133,11 @@ struct alignas(16) MeshRT {  // 16 B aligned: the patch kernels bulk-copy it int
     float* d_act_seq;
     float* d_hact_seq;
     int n_act, n_dact, st_a, st_b;
+    // air on the triangles (cloth, when air_on): drag / lift coefficients,
+    // wind; the adjoint's boundary partials of dL/dv from it
+    float k_drag, k_lift, wx, wy, wz;
+    int air_on;
+    float4* partials_v;
 };
 
 // Everything one kernel launch over a launch set needs.
@@ -152,12 +157,13 @@ struct Launch {
     int grid[4] = {0, 0, 0, 0};
     int stage[4] = {0, 0, 0, 0};
     int bgrid[2] = {0, 0};  // boundary kernels (fwd, adj): CTAs striding over bnd_blocks
+    int air = 0;            // some cloth mesh of the set has air on: the adjoint step adds k_adj_boundary_air
 };
 
 // --------------------------------------------------------------------------
 // kernels (gs_kernels.cu)
 // --------------------------------------------------------------------------
-size_t patch_smem_bytes(int n_e, int n_h, int n_loc, int n_int, int n_slots, bool adjoint);
+size_t patch_smem_bytes(int kind, int n_e, int n_h, int n_loc, int n_int, int n_slots, bool adjoint);
 int patch_grid(int which, int threads, int stage_bytes, int n_patches, int num_sms);
 int boundary_grid(int adjoint, int n_blocks, int num_sms);
 gs_status selftest_bounded_wait(int iterations, int* status_host, cudaStream_t s);

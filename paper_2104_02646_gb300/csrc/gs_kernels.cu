@@ -136,11 +136,11 @@ __host__ __device__ __forceinline__ int r16(int bytes) { return (bytes + 15) & ~
 // state.  The adjoint also holds v_hat for all local nodes, the interior
 // adjoint state and the boundary nodes' raw adjoint state.
 struct Layout {
-    int rec, rp, sl, pos, xs, vh, vs, xb, vb, xbB, vbB, gml, wb, act, hact, total;
+    int rec, rp, sl, pos, xs, vh, vs, xb, vb, xbB, vbB, gml, wb, act, hact, vB, total;
 };
 
-__host__ __device__ __forceinline__ Layout patch_layout(int n_e, int n_h, int n_loc, int n_int, int n_slots,
-                                                        bool adjoint) {
+__host__ __device__ __forceinline__ Layout patch_layout(int kind, int n_e, int n_h, int n_loc, int n_int,
+                                                        int n_slots, bool adjoint) {
     const int n_rec = n_e + n_h;
     const int n_bnd = n_loc - n_int;
     Layout L;
@@ -163,7 +163,10 @@ __host__ __device__ __forceinline__ Layout patch_layout(int n_e, int n_h, int n_
     // up to 3 entries of slack on each side for the aligned slice ends
     L.act = L.wb + (adjoint ? r16(8 * n_int) : 0);
     L.hact = L.act + r16(4 * (n_e + 6));
-    L.total = L.hact + (n_h ? r16(4 * (n_h + 6)) : 0);
+    // cloth: v of the boundary nodes (the air on the triangles needs every
+    // corner's velocity)
+    L.vB = L.hact + (n_h ? r16(4 * (n_h + 6)) : 0);
+    L.total = L.vB + (kind == GS_CLOTH ? 16 * (n_loc - n_int) : 0);
     return L;
 }
 
@@ -276,7 +279,7 @@ __device__ __forceinline__ void node_forward(const MeshRT& m, int tick, int gid,
 // corner dL/du and ssum = sum of corner f . v_hat, and dL/dw so far.  Writes
 // the adjoint of step n and the accumulated dL/dw (FP64).
 __device__ __forceinline__ void node_adjoint(const MeshRT& m, int gid, float4 x4, float4 v4, float4 xb4, float4 vb4,
-                                             float3 xsum, float ssum, double wb_old) {
+                                             float3 xsum, float ssum, double wb_old, float3 vsum) {
     const float w = x4.w;
     const float3 xbn = xyz(xb4);
     const float3 vh = xyz(vb4) + m.dt * xbn;    // dL/dv+ (total)
@@ -284,6 +287,7 @@ __device__ __forceinline__ void node_adjoint(const MeshRT& m, int gid, float4 x4
     float3 xb = xbn + xsum;
     float3 vb = vh;
     const float3 fc = contact_adjoint(m, gid, xyz(x4), xyz(v4), v4.w, fb, xb, vb);
+    vb += vsum;  // the elements' velocity-dependent forces (air), added last
     m.xb[gid] = f4(xb, 0.0f);
     m.vb[gid] = f4(vb, 0.0f);
     m.wbar[gid] = wb_old + (double)(m.dt * (ssum + dot3(fc, vh)));
@@ -307,12 +311,13 @@ struct Stage {
     double* wb;   // adjoint: dL/dw of the interior nodes
     const float* act;   // this step's actuation of the patch's elements [n_e], or null
     const float* hact;  // this step's actuation of the patch's hinges [n_h], or null
+    float4* vB;         // cloth with air: boundary v
 };
 
 __device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned char* buf, bool adjoint) {
     const int n_loc = p.n_int + p.n_bnd;
     const int n_rec = p.n_e + p.n_h;
-    const Layout L = patch_layout(p.n_e, p.n_h, n_loc, p.n_int, p.n_slots, adjoint);
+    const Layout L = patch_layout(kind, p.n_e, p.n_h, n_loc, p.n_int, p.n_slots, adjoint);
     Stage S;
     S.n_rec = n_rec;
     S.n_e = p.n_e;
@@ -332,6 +337,7 @@ __device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned
     S.wb = (double*)(buf + L.wb);
     S.act = (const float*)(buf + L.act) + (p.e_begin & 3);
     S.hact = (const float*)(buf + L.hact) + (p.h_begin & 3);
+    S.vB = (float4*)(buf + L.vB);
     return S;
 }
 
@@ -341,6 +347,17 @@ __device__ __forceinline__ void bind_act(Stage& S, const PatchDesc& p, const Mes
     if (act_row(m, m.hact_seq, tick) < 0 || p.n_h == 0) S.hact = nullptr;
 }
 __device__ __forceinline__ float act_of(const float* a, int i) { return a ? a[i] : 0.f; }
+
+// velocity of local node l (cloth with air: interior staged in vs, boundary in vB)
+__device__ __forceinline__ float3 local_v(const Stage& S, const PatchDesc& p, int l) {
+    return xyz(l < p.n_int ? S.vs[l] : S.vB[l - p.n_int]);
+}
+// air: the triangle's velocity through the air and its deformed vector area
+// N = A (F0 x F1) (A the rest area: the rest frame has det Dm > 0)
+__device__ __forceinline__ float3 air_vr(const MeshRT& m, const Stage& S, const PatchDesc& p, int i0, int i1, int i2) {
+    return (local_v(S, p, i0) + local_v(S, p, i1) + local_v(S, p, i2)) * (1.0f / 3.0f) -
+           make_float3(m.wx, m.wy, m.wz);
+}
 
 // state buffers a patch reads
 __device__ __forceinline__ int in_buffer(const MeshRT& m, int tick, bool adjoint) {
@@ -411,14 +428,16 @@ __device__ __forceinline__ void prefetch_ids(const PatchDesc& p, const MeshRT& m
     }
 }
 
-__device__ __forceinline__ void produce_gather(const PatchDesc& p, const MeshRT& m, const float4* X, const int* g,
-                                               unsigned char* buf, bool adjoint, int lane) {
+__device__ __forceinline__ void produce_gather(const PatchDesc& p, const MeshRT& m, const float4* X, const float4* V,
+                                               const int* g, unsigned char* buf, bool adjoint, int lane) {
     const Stage S = stage_at(p, m.kind, buf, adjoint);
+    const bool gv = m.kind == GS_CLOTH && m.air_on;  // boundary v for the air
 #pragma unroll
     for (int j = 0; j < kPrefetchIds; ++j) {
         const int k = lane + 32 * j;
         if (k < p.n_bnd) {
             cp16(S.xs + p.n_int + k, X + g[j]);
+            if (gv) cp16(S.vB + k, V + g[j]);
             if (adjoint) {
                 cp16(S.xbB + k, m.xb + g[j]);
                 cp16(S.vbB + k, m.vb + g[j]);
@@ -438,6 +457,7 @@ __device__ __forceinline__ void produce_gather(const PatchDesc& p, const MeshRT&
             const int k = k0 + lane + 32 * j;
             if (k < p.n_bnd) {
                 cp16(S.xs + p.n_int + k, X + h[j]);
+                if (gv) cp16(S.vB + k, V + h[j]);
                 if (adjoint) {
                     cp16(S.xbB + k, m.xb + h[j]);
                     cp16(S.vbB + k, m.vb + h[j]);
@@ -502,6 +522,13 @@ __device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Mes
                       make_float3(c.x, c.y, c.z), make_float3(c.w, w.z, w.w), s);
             float3 f0, f1, f2;
             tri_forces(s, a, b, f0, f1, f2);
+            if (m.air_on) {
+                const float3 vr = air_vr(m, S, p, id.x & 0xffff, id.x >> 16, id.y & 0xffff);
+                const float3 Fa = air_force(b.x * cross3(s.F0, s.F1), vr, m.k_drag, m.k_lift) * (1.0f / 3.0f);
+                f0 += Fa;
+                f1 += Fa;
+                f2 += Fa;
+            }
             put(S, q, 0, f4(f0, 0.f));
             put(S, q, 1, f4(f1, 0.f));
             put(S, q, 2, f4(f2, 0.f));
@@ -574,7 +601,26 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             tri_forces(s, a, b, f0, f1, f2);
             float3 xb0, xb1, xb2;
             float gmu, glam, gact;
-            tri_adjoint(s, a, bt, (dt * x0.w) * v0, (dt * x1.w) * v1, (dt * x2.w) * v2, xb0, xb1, xb2, gmu, glam, gact);
+            const float3 y0 = (dt * x0.w) * v0, y1 = (dt * x1.w) * v1, y2 = (dt * x2.w) * v2;
+            tri_adjoint(s, a, bt, y0, y1, y2, xb0, xb1, xb2, gmu, glam, gact);
+            if (m.air_on) {
+                // F on each corner F/3: dL/dF = (y0 + y1 + y2)/3; N = A (F0 x F1)
+                const float3 vr = air_vr(m, S, p, i0, i1, i2);
+                const float3 N = b.x * cross3(s.F0, s.F1);
+                const float3 Fa = air_force(N, vr, m.k_drag, m.k_lift) * (1.0f / 3.0f);
+                f0 += Fa;
+                f1 += Fa;
+                f2 += Fa;
+                float3 Nb = make_float3(0.f, 0.f, 0.f), vrb = make_float3(0.f, 0.f, 0.f);
+                air_adjoint(N, vr, m.k_drag, m.k_lift, (y0 + y1 + y2) * (1.0f / 3.0f), Nb, vrb);
+                const float3 F0b = b.x * cross3(s.F1, Nb), F1b = b.x * cross3(Nb, s.F0);
+                const float3 d1 = F0b * a.x + F1b * a.y, d2 = F0b * a.z + F1b * a.w;
+                xb1 += d1;
+                xb2 += d2;
+                xb0 -= d1 + d2;
+                // the same dL/dv for each corner, summed per node by the node phase
+                put(S, q, 3, f4(vrb * (1.0f / 3.0f), 0.f));
+            }
             put(S, q, 0, f4(xb0, dot3(f0, v0)));
             put(S, q, 1, f4(xb1, dot3(f1, v1)));
             put(S, q, 2, f4(xb2, dot3(f2, v2)));
@@ -667,13 +713,35 @@ __device__ __forceinline__ void forward_nodes(const PatchDesc& p, const MeshRT& 
     }
 }
 
+// cloth with air: fixed-order sum over the node's triangle corners of the
+// triangles' dL/dv (plane 3 of a triangle record; slot c n_e + r with c < 3
+// is corner c of triangle r, hinge and padding slots add nothing)
+__device__ __forceinline__ float3 row_sum_air_v(const Stage& S, int k, int k1) {
+    float3 acc = make_float3(0.f, 0.f, 0.f);
+    const int ne = S.n_e;
+    for (; k < k1; ++k) {
+        const int s = S.sl[k];
+        if (s < 3 * ne) {
+            const int r = s - ne * ((s >= ne) + (s >= 2 * ne));
+            add3(acc, S.rec[3 * ne + r]);
+        }
+    }
+    return acc;
+}
+
+template <int KIND>
 __device__ __forceinline__ void adjoint_nodes(const PatchDesc& p, const MeshRT& m, const Stage& S, int nt) {
     const int n_loc = p.n_int + p.n_bnd;
+    const bool air = KIND == GS_CLOTH && m.air_on;
     for (int l = threadIdx.x; l < n_loc; l += nt) {
         const float4 acc = row_sum4(S, S.rp[l], S.rp[l + 1]);
-        if (l < p.n_int)
-            node_adjoint(m, p.int_begin + l, S.xs[l], S.vs[l], S.xb[l], S.vb[l], xyz(acc), acc.w, S.wb[l]);
-        else m.partials[S.pos[l - p.n_int]] = acc;
+        const float3 va = air ? row_sum_air_v(S, S.rp[l], S.rp[l + 1]) : make_float3(0.f, 0.f, 0.f);
+        if (l < p.n_int) {
+            node_adjoint(m, p.int_begin + l, S.xs[l], S.vs[l], S.xb[l], S.vb[l], xyz(acc), acc.w, S.wb[l], va);
+        } else {
+            m.partials[S.pos[l - p.n_int]] = acc;
+            if (air) m.partials_v[S.pos[l - p.n_int]] = f4(va, 0.f);
+        }
     }
 }
 
@@ -751,10 +819,12 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
         PatchDesc p;
         int g[kPrefetchIds];
         const float4* X = nullptr;
+        const float4* V = nullptr;
         if (pi < n_patches) {
             p = patches[pi];
             prefetch_ids(p, rts[p.mesh], lane, g);
             X = bufx(rts[p.mesh], in_buffer(rts[p.mesh], tick, ADJ));
+            V = bufv(rts[p.mesh], in_buffer(rts[p.mesh], tick, ADJ));
         }
         for (int it = 0;; ++it) {
             const int s = it % kStages;
@@ -774,13 +844,14 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
                 *(PatchDesc*)b = p;
                 issue_bulk(p, &rts[p.mesh], m, tick, b + kHdr, (MeshRT*)(b + kHdrRt), copy_rt, &full[s], ADJ);
             }
-            produce_gather(p, m, X, g, b + kHdr, ADJ, lane);
+            produce_gather(p, m, X, V, g, b + kHdr, ADJ, lane);
             cp_async_mbar_arrive(&full[s]);
             pi = next_live(patches, n_patches, rts, pi + gridDim.x, mask);
             if (pi < n_patches) {
                 p = patches[pi];
                 prefetch_ids(p, rts[p.mesh], lane, g);
                 X = bufx(rts[p.mesh], in_buffer(rts[p.mesh], tick, ADJ));
+                V = bufv(rts[p.mesh], in_buffer(rts[p.mesh], tick, ADJ));
             }
         }
     }
@@ -808,7 +879,7 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
             else cloth_elements_fwd(p, m, tick, S, nt);
         }
         consumer_sync(nt);
-        if (ADJ) adjoint_nodes(p, m, S, nt);
+        if (ADJ) adjoint_nodes<KIND>(p, m, S, nt);
         else forward_nodes(p, m, tick, S, nt);
         // this warp's generic shared accesses of the stage are ordered before the
         // async-proxy writes that will refill it
@@ -938,8 +1009,27 @@ __global__ void __launch_bounds__(kBndThreads, 6)
         }
         float4 a0, a1;
         partial_sums2(m.partials, k0, e0 - k0, k1, e1 - k1, a0, a1);
-        if (h0) node_adjoint(m, g0, x0, v0, xb0, vb0, xyz(a0), a0.w, w0);
-        if (h1) node_adjoint(m, g1, x1, v1, xb1, vb1, xyz(a1), a1.w, w1);
+        const float3 z = make_float3(0.f, 0.f, 0.f);
+        if (h0) node_adjoint(m, g0, x0, v0, xb0, vb0, xyz(a0), a0.w, w0, z);
+        if (h1) node_adjoint(m, g1, x1, v1, xb1, vb1, xyz(a1), a1.w, w1, z);
+    }
+}
+
+// Cloth with air, after k_adj_boundary: each boundary node's dL/dv from the
+// triangles' air forces (partials at the node's partial positions), added
+// last to v_bar as node_adjoint does for interior nodes.
+__global__ void __launch_bounds__(kBndThreads)
+    k_adj_boundary_air(const NodeBlock* __restrict__ blocks, int n_blocks, const MeshRT* __restrict__ rts) {
+    for (int bi = blockIdx.x; bi < n_blocks; bi += gridDim.x) {
+        const NodeBlock nb = blocks[bi];
+        const MeshRT& m = rts[nb.mesh];
+        if (!(m.active & ACT_ADJ) || !m.air_on) continue;
+        for (int i = threadIdx.x; i < nb.count; i += kBndThreads) {
+            const int b = nb.begin + i, g = m.n_int + b;
+            float3 c = make_float3(0.f, 0.f, 0.f);
+            for (int k = m.bnd_rowptr[b], k1 = m.bnd_rowptr[b + 1]; k < k1; ++k) add3(c, m.partials_v[k]);
+            m.vb[g] = f4(xyz(m.vb[g]) + c, 0.0f);
+        }
     }
 }
 
@@ -1320,8 +1410,8 @@ __global__ void k_elem_grads(const PatchDesc* __restrict__ patches, const MeshRT
 // ===========================================================================
 // launchers
 // ===========================================================================
-size_t patch_smem_bytes(int n_e, int n_h, int n_loc, int n_int, int n_slots, bool adjoint) {
-    return (size_t)((kHdr + patch_layout(n_e, n_h, n_loc, n_int, n_slots, adjoint).total + 127) & ~127);
+size_t patch_smem_bytes(int kind, int n_e, int n_h, int n_loc, int n_int, int n_slots, bool adjoint) {
+    return (size_t)((kHdr + patch_layout(kind, n_e, n_h, n_loc, n_int, n_slots, adjoint).total + 127) & ~127);
 }
 
 // persistent grid: resident CTAs per SM x SMs, at most one CTA per patch
@@ -1398,6 +1488,8 @@ void launch_adjoint_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) 
                                    L.cloth_patches, L.n_cloth_patches, L.rt, tick, L.stage[3])));
     if (L.n_bnd_blocks)
         GS_TIMED(KT_ADJ_BND, (k_adj_boundary<<<L.bgrid[1], kBndThreads, 0, s>>>(L.bnd_blocks, L.n_bnd_blocks, L.rt, tick)));
+    if (L.air && L.n_bnd_blocks)
+        GS_TIMED(KT_ADJ_BND, (k_adj_boundary_air<<<L.bgrid[1], kBndThreads, 0, s>>>(L.bnd_blocks, L.n_bnd_blocks, L.rt)));
 }
 
 void launch_copy_state(const Launch& L, cudaStream_t s) {

@@ -417,4 +417,50 @@ __device__ __forceinline__ void contact_one_adjoint(float3 v, float3 n, float C,
     nb += vnb * v;
 }
 
+// ---------------------------------------------------------------------------
+// Air on a triangle (App. A.1: a lift/drag model of the surrounding air on
+// the cloth surface; no formula is given).  Flat-plate reading, with N the
+// deformed vector area (|N| = A) and v_r the triangle's mean velocity minus
+// the wind, s = N . v_r:
+//   drag  F_D = -k_D |s| v_r
+//   lift  F_L = -k_L s / (A |v_r|) (|v_r|^2 N - s v_r)   (0 when v_r = 0 or A = 0)
+// F is the whole triangle's force; each corner takes F/3.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 air_force(float3 N, float3 vr, float kd, float kl) {
+    const float s = dot3(N, vr);
+    float3 F = (-kd * fabsf(s)) * vr;
+    const float q = dot3(vr, vr), A2 = dot3(N, N);
+    if (kl != 0.0f && q > 0.0f && A2 > 0.0f) {
+        const float c = kl * s / (sqrtf(A2) * sqrtf(q));
+        F -= c * (q * N - s * vr);
+    }
+    return F;
+}
+
+// reverse of air_force: yb = dL/dF; adds dL/dN and dL/dv_r
+__device__ __forceinline__ void air_adjoint(float3 N, float3 vr, float kd, float kl, float3 yb, float3& Nb,
+                                            float3& vrb) {
+    const float s = dot3(N, vr);
+    const float yv = dot3(yb, vr);
+    // drag: yb . F_D = -k_D |s| (yb . v_r)
+    const float sg = s < 0.0f ? -1.0f : 1.0f;
+    vrb += (-kd) * ((sg * yv) * N + fabsf(s) * yb);
+    Nb += (-kd * sg * yv) * vr;
+    const float q = dot3(vr, vr), A2 = dot3(N, N);
+    if (kl != 0.0f && q > 0.0f && A2 > 0.0f) {
+        // yb . F_L = -phi psi,  phi = k_L s / (A r),  psi = q (yb . N) - s (yb . v_r)
+        const float A = sqrtf(A2), r = sqrtf(q);
+        const float iAr = 1.0f / (A * r);
+        const float phi = kl * s * iAr;
+        const float yN = dot3(yb, N);
+        const float psi = q * yN - s * yv;
+        const float3 dphi_dv = (kl * iAr) * (N - (s / q) * vr);
+        const float3 dphi_dN = (kl * iAr) * (vr - (s / A2) * N);
+        const float3 dpsi_dv = (2.0f * yN) * vr - yv * N - s * yb;
+        const float3 dpsi_dN = q * yb - yv * vr;
+        vrb -= psi * dphi_dv + phi * dpsi_dv;
+        Nb -= psi * dphi_dN + phi * dpsi_dN;
+    }
+}
+
 }  // namespace gs

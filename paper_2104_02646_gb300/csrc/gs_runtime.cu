@@ -327,8 +327,8 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
         T.max_loc = std::max(T.max_loc, n_loc);
         T.max_slots = std::max(T.max_slots, n_slots);
         T.max_rec = std::max(T.max_rec, n_rec);
-        T.smem_fwd = std::max(T.smem_fwd, patch_smem_bytes(q.n_e, q.n_h, n_loc, q.n_int, n_slots, false));
-        T.smem_adj = std::max(T.smem_adj, patch_smem_bytes(q.n_e, q.n_h, n_loc, q.n_int, n_slots, true));
+        T.smem_fwd = std::max(T.smem_fwd, patch_smem_bytes(d.kind, q.n_e, q.n_h, n_loc, q.n_int, n_slots, false));
+        T.smem_adj = std::max(T.smem_adj, patch_smem_bytes(d.kind, q.n_e, q.n_h, n_loc, q.n_int, n_slots, true));
         for (int g : bl) {
             loc[g] = -1;
             pdeg[g] = 0;
@@ -923,7 +923,11 @@ gs_status LaunchSet::build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStrea
 }
 
 gs_status LaunchSet::sync_rt(cudaStream_t s) {
-    for (size_t i = 0; i < meshes.size(); ++i) host_rt[i] = meshes[i]->rt;
+    launch.air = 0;
+    for (size_t i = 0; i < meshes.size(); ++i) {
+        host_rt[i] = meshes[i]->rt;
+        if (host_rt[i].kind == GS_CLOTH && host_rt[i].air_on) launch.air = 1;
+    }
     GS_CUDA(cudaMemcpyAsync(d_rt.p, host_rt.data(), host_rt.size() * sizeof(MeshRT), cudaMemcpyHostToDevice, s));
     return GS_OK;
 }
@@ -944,7 +948,7 @@ gs_status LaunchSet::run(int phase, int steps, cudaStream_t s) {
         GS_CUDA(cudaGetLastError());
         return GS_OK;
     }
-    const std::pair<int, int> key{phase, steps};
+    const std::pair<int, int> key{phase + 2 * launch.air, steps};  // the air adds a kernel to adjoint steps
     auto it = graphs.find(key);
     if (it == graphs.end()) {
         cudaStream_t cs = ctx->capture_stream;
@@ -1348,6 +1352,30 @@ extern "C" gs_status gs_mesh_set_act_seq(gs_mesh* m, const float* act, const flo
     m->rt.n_act = n_steps;
     tmp.release(s);
     GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+extern "C" gs_status gs_mesh_set_air(gs_mesh* m, const gs_air* air, void* stream) {
+    clear_error();
+    if (!m) return set_error(GS_EINVAL, "null mesh");
+    if (!air) {
+        m->rt.air_on = 0;
+        return GS_OK;
+    }
+    if (m->info.kind != GS_CLOTH) return set_error(GS_EINVAL, "the air model acts on cloth triangles (GS_CLOTH)");
+    const float vals[5] = {air->k_drag, air->k_lift, air->wind[0], air->wind[1], air->wind[2]};
+    for (float v : vals)
+        if (!std::isfinite(v)) return set_error(GS_EINVAL, "non-finite air parameter");
+    if (air->k_drag < 0.f || air->k_lift < 0.f) return set_error(GS_EINVAL, "air coefficients must be >= 0");
+    // the adjoint's boundary partials of dL/dv: one per (boundary node, patch)
+    if (!m->partials_v.p) GS_TRY(m->partials_v.alloc(m->ctx, m->partials.bytes, (cudaStream_t)stream));
+    m->rt.partials_v = (float4*)m->partials_v.p;
+    m->rt.k_drag = air->k_drag;
+    m->rt.k_lift = air->k_lift;
+    m->rt.wx = air->wind[0];
+    m->rt.wy = air->wind[1];
+    m->rt.wz = air->wind[2];
+    m->rt.air_on = (air->k_drag > 0.f || air->k_lift > 0.f) ? 1 : 0;
     return GS_OK;
 }
 

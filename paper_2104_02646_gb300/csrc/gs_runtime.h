@@ -112,7 +112,7 @@ struct gs_mesh {
     std::vector<gs::NodeBlock> bnd_blocks, node_blocks;
     gs::Buf rec, hrec, Xs, Xp, v0, bnd_ids, loc_rowptr, loc_slots, bnd_rowptr, part_pos, topo, partials,
         node_perm, elem_perm, hinge_perm, w, X, rho, pinned, st, xb, vb, wbar, mbar, g_ml, g_act, g_kb,
-        g_hact, status, target, scratch, act_seq, hact_seq, dact_seq, dhact_seq;
+        g_hact, status, target, scratch, act_seq, hact_seq, dact_seq, dhact_seq, partials_v;
     gs::MeshRT rt{};
     struct {
         bool valid = false;

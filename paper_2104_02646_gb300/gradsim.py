@@ -48,6 +48,10 @@ class gs_mesh_info(C.Structure):
                 ("block_threads", C.c_int), ("dt_stable", C.c_double), ("device_bytes", C.c_size_t)]
 
 
+class gs_air(C.Structure):
+    _fields_ = [("k_drag", C.c_float), ("k_lift", C.c_float), ("wind", C.c_float * 3)]
+
+
 class gs_grads(C.Structure):
     _fields_ = [("d_mu", _vp), ("d_lambda", _vp), ("d_density", _vp), ("d_act", _vp), ("d_kb", _vp),
                 ("d_hinge_act", _vp), ("d_mass", _vp), ("d_x0", _vp), ("d_v0", _vp), ("d_act_seq", _vp),
@@ -107,6 +111,7 @@ _PROTOS = {
     "gs_mesh_set_params": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
     "gs_mesh_set_state": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
     "gs_mesh_set_act_seq": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
+    "gs_mesh_set_air": (C.c_int, [_vp, _vp, _vp]),
     "gs_mesh_get_state": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
     "gs_mesh_reset": (C.c_int, [_vp, _vp]),
     "gs_mesh_check": (C.c_int, [_vp, C.c_int, _vp]),
@@ -304,6 +309,8 @@ class Mesh:
         self.info = gs_mesh_info()
         check(load().gs_mesh_info_get(self.h, C.byref(self.info)))
         self.status = GS_OK
+        if getattr(problem, "air", None) is not None:
+            self.set_air(problem.air)
 
     @property
     def n_nodes(self):
@@ -316,6 +323,15 @@ class Mesh:
     def set_state(self, x=None, v=None, host=False, stream=None):
         check(load().gs_mesh_set_state(self.h, _ptr(x), _ptr(v), GS_MEM_HOST if host else GS_MEM_DEVICE,
                                        _stream(stream)))
+
+    def set_air(self, air=None, stream=None):
+        """Air on the cloth surface (an object with k_drag, k_lift, wind), or
+        None to turn it off."""
+        if air is None:
+            check(load().gs_mesh_set_air(self.h, None, _stream(stream)))
+            return
+        a = gs_air(float(air.k_drag), float(air.k_lift), (C.c_float * 3)(*[float(w) for w in air.wind]))
+        check(load().gs_mesh_set_air(self.h, C.byref(a), _stream(stream)))
 
     def set_act_seq(self, act_seq=None, hinge_act_seq=None, host=False, stream=None):
         """Time-varying actuation: row n of act_seq [n_steps][n_elems] (and
@@ -416,6 +432,8 @@ class Server:
         self._keep = {}
 
     def submit(self, problem, target, dt=None, steps=None) -> int:
+        if getattr(problem, "air", None) is not None:
+            raise ValueError("served queries carry no air model; run a Mesh or Batch instead")
         d, keep = mesh_desc(problem)
         t = np.ascontiguousarray(target, dtype=np.float32)
         q = gs_query(d, float(problem.dt if dt is None else dt), int(problem.steps if steps is None else steps),
