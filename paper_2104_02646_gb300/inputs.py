@@ -318,6 +318,77 @@ def cloth_throw(n: int = 12, steps: int = 400, seed: int = 0, air: Optional["Air
                    air=Air() if air is None else air)
 
 
+# ---------------------------------------------------------------------------
+# rendering inputs: cameras, surface triangles, vertex colours
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Camera:
+    """Pinhole camera: x_cam = R x + t (camera looks along +z_cam, y_cam down
+    the image), pixel (u, v) = (fx x_cam/z_cam + cx, fy y_cam/z_cam + cy);
+    pixel (i, j) has its centre at (i + 0.5, j + 0.5).  Depths are normalised
+    over [z_near, z_far]."""
+    R: np.ndarray          # [3, 3] world -> camera rotation
+    t: np.ndarray          # [3]
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    width: int
+    height: int
+    z_near: float = 0.05
+    z_far: float = 10.0
+
+
+def look_at(eye, target, up=(0.0, 1.0, 0.0), width=256, height=256, fov_deg=40.0, z_near=0.05,
+            z_far=10.0) -> Camera:
+    """Camera at `eye` looking at `target` with `up` towards the image top."""
+    eye, target, up = (np.asarray(a, dtype=np.float64) for a in (eye, target, up))
+    f = target - eye
+    f /= np.linalg.norm(f)
+    r = np.cross(f, up)
+    r /= np.linalg.norm(r)
+    d = np.cross(f, r)  # image down
+    R = np.stack([r, d, f])
+    t = -R @ eye
+    fl = 0.5 * width / math.tan(math.radians(fov_deg) / 2)
+    return Camera(R=R, t=t, fx=fl, fy=fl, cx=width / 2, cy=height / 2, width=width, height=height,
+                  z_near=z_near, z_far=z_far)
+
+
+def surface_faces(tets: np.ndarray) -> np.ndarray:
+    """Boundary triangles of a tet mesh (faces used by one tet), oriented
+    with the outward normal by the right-hand rule, in a fixed order (sorted
+    by owning tet, then face)."""
+    tets = np.asarray(tets, dtype=np.int64)
+    loc = np.array([[1, 2, 3], [0, 3, 2], [0, 1, 3], [0, 2, 1]])  # outward for positively oriented tets
+    faces = tets[:, loc].reshape(-1, 3)
+    key = np.sort(faces, axis=1)
+    _, inv, cnt = np.unique(key, axis=0, return_inverse=True, return_counts=True)
+    return faces[cnt[inv.ravel()] == 1].astype(np.int32)
+
+
+def vertex_colours(X: np.ndarray, seed: int = 0) -> np.ndarray:
+    """Seeded smooth per-vertex RGB in [0.1, 0.9] (a colour field over the
+    rest shape, so that shading carries positional information)."""
+    rng = np.random.default_rng(seed)
+    W = rng.normal(size=(3, 3))
+    ph = rng.uniform(0.0, 2.0 * math.pi, 3)
+    span = np.ptp(X, axis=0).max() or 1.0
+    return 0.5 + 0.4 * np.sin(((X - X.min(axis=0)) / span) @ W * 3.0 + ph)
+
+
+@dataclasses.dataclass
+class RenderSpec:
+    """Soft rasteriser settings: sigma (pixel^2) sets the width of the soft
+    edges, gamma the depth softmax temperature, eps the background's
+    normalised depth, bg its colour."""
+    sigma: float = 0.5
+    gamma: float = 1.0e-3
+    eps: float = 1.0e-3
+    bg: tuple = (1.0, 1.0, 1.0)
+
+
 def block_dims(n_tets_target: float, rng) -> tuple:
     """Integer a x b x c (>= 1) with aspect ratios in [0.5, 2] and 5abc ~ target."""
     r1, r2 = np.exp(rng.uniform(math.log(0.5), math.log(2.0), 2))
