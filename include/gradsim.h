@@ -245,6 +245,56 @@ typedef struct gs_air {
     float wind[3];
 } gs_air;
 GS_API gs_status gs_mesh_set_air(gs_mesh* mesh, const gs_air* air, void* stream);
+/* ---- differentiable soft rasteriser ------------------------------------
+ * The rendering stage of Sec. 2 ("Differentiable rendering engine"): the
+ * simulated surface becomes an image through SoftRas-style sigmoid edges and
+ * DIB-R-style barycentric interpolation, so that a loss on pixels reaches the
+ * vertex positions.  The paper prints no formulas; reading, per pixel p with
+ * centre (i + 0.5, j + 0.5) and triangle t with projected corners a, b, c:
+ *   projection: x_cam = R x + t, u = fx x_cam/z_cam + cx, v = fy y_cam/z_cam + cy,
+ *     depth z_cam; a triangle with a corner at z_cam <= z_near or zero
+ *     projected area is skipped;
+ *   coverage D = sigmoid(+-d^2/sigma) with d the distance from p to the
+ *     triangle's boundary (+ inside); 1 - D is kept >= 1e-6; outside pixels
+ *     with D < 1e-5 are not covered;
+ *   silhouette A = 1 - prod_t (1 - D_t);
+ *   colour: clamped barycentrics interpolate the vertex colours and,
+ *     perspective-correct, 1/z; zh = (z_far - z)/(z_far - z_near);
+ *     I = (sum_t D_t e^{zh_t/gamma} C_t + e^{eps/gamma} bg) / (sum_t D_t e^{zh_t/gamma} + e^{eps/gamma}).
+ * Output image [height][width][4] = (I, A), FP32, row-major. */
+typedef struct gs_camera {
+    float R[9];          /* world -> camera rotation, row-major */
+    float t[3];
+    float fx, fy, cx, cy; /* pixels */
+    int width, height;   /* 1..16384 */
+    float z_near, z_far; /* 0 < z_near < z_far */
+} gs_camera;
+typedef struct gs_raster_desc {
+    int n_vertices;
+    int n_faces;
+    const int* faces;    /* HOST [n_faces][3] vertex indices (copied) */
+    gs_camera camera;
+    float sigma;         /* edge softness, pixel^2 (> 0) */
+    float gamma;         /* depth softmax temperature (> 0) */
+    float eps;           /* normalised depth of the background */
+    float bg[3];         /* background colour */
+} gs_raster_desc;
+typedef struct gs_raster gs_raster;
+/* GS_EINVAL for a face index outside [0, n_vertices), a bad camera or
+ * non-positive sigma / gamma. */
+GS_API gs_status gs_raster_create(gs_ctx* ctx, const gs_raster_desc* desc, gs_raster** out);
+GS_API void gs_raster_destroy(gs_raster* r);
+/* New pose / intrinsics, same image size (GS_EINVAL otherwise). */
+GS_API gs_status gs_raster_set_camera(gs_raster* r, const gs_camera* camera);
+/* image [H][W][4] from DEVICE x [n_vertices][3] and colours [n_vertices][3];
+ * keeps copies of x, colours and the per-pixel values the backward needs.
+ * Deterministic (no atomics).  Enqueued on `stream`. */
+GS_API gs_status gs_raster_forward(gs_raster* r, const float* x, const float* colours, float* image, void* stream);
+/* dL/dx and dL/dcolours (DEVICE [n_vertices][3], each nullable) of a loss
+ * with DEVICE dL/dimage [H][W][4], at the last forward's inputs
+ * (GS_ESTATE without one).  Deterministic.  Enqueued on `stream`. */
+GS_API gs_status gs_raster_backward(gs_raster* r, const float* dL_dimage, float* dL_dx, float* dL_dcolours,
+                                    void* stream);
 /* Current state (x, v) [n_nodes][3] in caller order; nullable = unchanged. */
 GS_API gs_status gs_mesh_set_state(gs_mesh* mesh, const float* x, const float* v, int mem_space, void* stream);
 /* Back to the description's initial state: x = X exactly (the state is

@@ -16,26 +16,49 @@ import torch
 from . import gradsim as gs
 
 
+def _claim(mesh):
+    """A token for the rollout a forward is about to store on `mesh`; a
+    later forward on the same mesh replaces the stored rollout."""
+    tok = getattr(mesh, "_rollout_seq", 0) + 1
+    mesh._rollout_seq = tok
+    mesh._rollout_token = tok
+    return tok
+
+
 class Rollout(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, mesh, dt, steps, K, mu, lam, rho, x0, v0):
-        dev = x0.device
-        f32 = dict(dtype=torch.float32, device=dev)
-        mu_, lam_, rho_ = (t.detach().to(**f32).contiguous() for t in (mu, lam, rho))
-        mesh.set_params(mu=mu_, lam=lam_, rho=rho_)
-        mesh.set_state(x=x0.detach().to(**f32).contiguous(), v=v0.detach().to(**f32).contiguous())
+    def _run(mesh, dt, steps, K, mu, lam, rho, x0, v0):
+        f32 = dict(dtype=torch.float32, device=x0.device)
+        mesh.set_params(mu=mu, lam=lam, rho=rho)
+        mesh.set_state(x=x0, v=v0)
         mesh.rollout(dt, steps, K)
         N = mesh.n_nodes
         xS = torch.empty(N, 3, **f32)
         vS = torch.empty(N, 3, **f32)
         mesh.get_state(xS, vS)
+        return xS, vS
+
+    @staticmethod
+    def forward(ctx, mesh, dt, steps, K, mu, lam, rho, x0, v0):
+        dev = x0.device
+        f32 = dict(dtype=torch.float32, device=dev)
+        args = [t.detach().to(**f32).contiguous() for t in (mu, lam, rho, x0, v0)]
+        xS, vS = Rollout._run(mesh, dt, steps, K, *args)
         ctx.mesh = mesh
+        ctx.token = _claim(mesh)
+        ctx.replay = (dt, steps, K, args)
         ctx.shapes = (mu.dtype, lam.dtype, rho.dtype, x0.dtype, v0.dtype)
         return xS, vS
 
     @staticmethod
     def backward(ctx, gx, gv):
         mesh = ctx.mesh
+        if getattr(mesh, "_rollout_token", None) != ctx.token:
+            # a later rollout on this mesh (e.g. the next segment between two
+            # rendered frames) replaced the stored states: recompute them
+            dt, steps, K, args = ctx.replay
+            Rollout._run(mesh, dt, steps, K, *args)
+        mesh._rollout_token = None  # the adjoint consumes the stored rollout
         dev = gx.device if gx is not None else gv.device
         E, N = mesh.info.n_elems, mesh.n_nodes
         f64 = dict(dtype=torch.float64, device=dev)
@@ -76,6 +99,7 @@ class ActuatedRollout(torch.autograd.Function):
         xS = torch.empty(N, 3, **f32)
         vS = torch.empty(N, 3, **f32)
         mesh.get_state(xS, vS)
+        _claim(mesh)
         ctx.mesh = mesh
         ctx.steps = steps
         ctx.has = (act_seq is not None, hinge_act_seq is not None)
@@ -104,3 +128,40 @@ class ActuatedRollout(torch.autograd.Function):
 def actuated_rollout(mesh: "gs.Mesh", dt: float, steps: int, act_seq, x0, v0, hinge_act_seq=None, K: int = 0):
     """Differentiable rollout under a time-varying actuation; see ActuatedRollout."""
     return ActuatedRollout.apply(mesh, dt, steps, K, act_seq, hinge_act_seq, x0, v0)
+
+
+class Render(torch.autograd.Function):
+    """The soft rasteriser (Sec. 2 "Differentiable rendering engine") as an
+    autograd operation: image [H, W, 4] from vertex positions [N, 3] and
+    colours [N, 3]; backward runs gs_raster_backward."""
+
+    @staticmethod
+    def forward(ctx, raster, x, colours):
+        f32 = dict(dtype=torch.float32, device=x.device)
+        xs = x.detach().to(**f32).contiguous()
+        cs = colours.detach().to(**f32).contiguous()
+        img = torch.empty(raster.height, raster.width, 4, **f32)
+        raster.forward(xs, cs, img)
+        ctx.raster = raster
+        ctx.token = _claim(raster)
+        ctx.saved = (xs, cs)
+        ctx.dtypes = (x.dtype, colours.dtype)
+        return img
+
+    @staticmethod
+    def backward(ctx, gimg):
+        r = ctx.raster
+        xs, cs = ctx.saved
+        if getattr(r, "_rollout_token", None) != ctx.token:
+            # another frame was rendered since: restore this frame's state
+            r.forward(xs, cs, torch.empty(r.height, r.width, 4, dtype=torch.float32, device=xs.device))
+            r._rollout_token = ctx.token
+        dx = torch.empty_like(xs)
+        dc = torch.empty_like(cs)
+        r.backward(gimg.detach().to(torch.float32).contiguous(), dx, dc)
+        return None, dx.to(ctx.dtypes[0]), dc.to(ctx.dtypes[1])
+
+
+def render(raster, x, colours):
+    """Differentiable image [H, W, 4] (RGB, silhouette) of `raster`'s triangles."""
+    return Render.apply(raster, x, colours)

@@ -48,6 +48,18 @@ class gs_mesh_info(C.Structure):
                 ("block_threads", C.c_int), ("dt_stable", C.c_double), ("device_bytes", C.c_size_t)]
 
 
+class gs_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int), ("height", C.c_int),
+                ("z_near", C.c_float), ("z_far", C.c_float)]
+
+
+class gs_raster_desc(C.Structure):
+    _fields_ = [("n_vertices", C.c_int), ("n_faces", C.c_int), ("faces", C.POINTER(C.c_int)),
+                ("camera", gs_camera), ("sigma", C.c_float), ("gamma", C.c_float), ("eps", C.c_float),
+                ("bg", C.c_float * 3)]
+
+
 class gs_air(C.Structure):
     _fields_ = [("k_drag", C.c_float), ("k_lift", C.c_float), ("wind", C.c_float * 3)]
 
@@ -132,6 +144,11 @@ _PROTOS = {
     "gs_server_stats_get": (C.c_int, [_vp, C.POINTER(gs_server_stats)]),
     "gs_result_free": (None, [C.POINTER(gs_result)]),
     "gs_selftest_bounded_wait": (C.c_int, [C.c_int, C.POINTER(C.c_int), _vp]),
+    "gs_raster_create": (C.c_int, [_vp, C.POINTER(gs_raster_desc), C.POINTER(_vp)]),
+    "gs_raster_destroy": (None, [_vp]),
+    "gs_raster_set_camera": (C.c_int, [_vp, C.POINTER(gs_camera)]),
+    "gs_raster_forward": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "gs_raster_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -418,6 +435,57 @@ class Batch:
         try:
             self.close()
         except Exception:  # noqa: BLE001
+            pass
+
+
+def camera_struct(cam) -> gs_camera:
+    """gs_camera from an ``inputs.Camera``."""
+    c = gs_camera()
+    c.R = (C.c_float * 9)(*[float(v) for v in np.asarray(cam.R, dtype=np.float64).ravel()])
+    c.t = (C.c_float * 3)(*[float(v) for v in np.asarray(cam.t, dtype=np.float64).ravel()])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.z_near, c.z_far = float(cam.z_near), float(cam.z_far)
+    return c
+
+
+class Raster:
+    """A gs_raster: the soft rasteriser over a fixed triangle list (faces
+    [F, 3] into n_vertices vertices), camera and settings
+    (``inputs.RenderSpec``)."""
+
+    def __init__(self, ctx: Context, n_vertices: int, faces, camera, spec):
+        self.ctx = ctx
+        f = np.ascontiguousarray(faces, dtype=np.int32).reshape(-1, 3)
+        self._faces = f
+        d = gs_raster_desc()
+        d.n_vertices, d.n_faces = int(n_vertices), int(f.shape[0])
+        d.faces = f.ctypes.data_as(C.POINTER(C.c_int)) if f.size else None
+        d.camera = camera_struct(camera)
+        d.sigma, d.gamma, d.eps = float(spec.sigma), float(spec.gamma), float(spec.eps)
+        d.bg = (C.c_float * 3)(*[float(b) for b in spec.bg])
+        self.h = _vp()
+        check(load().gs_raster_create(ctx.h, C.byref(d), C.byref(self.h)))
+        self.n_vertices, self.width, self.height = int(n_vertices), int(camera.width), int(camera.height)
+
+    def set_camera(self, camera):
+        check(load().gs_raster_set_camera(self.h, C.byref(camera_struct(camera))))
+
+    def forward(self, x, colours, image, stream=None):
+        check(load().gs_raster_forward(self.h, _ptr(x), _ptr(colours), _ptr(image), _stream(stream)))
+
+    def backward(self, dimage, dx=None, dcolours=None, stream=None):
+        check(load().gs_raster_backward(self.h, _ptr(dimage), _ptr(dx), _ptr(dcolours), _stream(stream)))
+
+    def close(self):
+        if self.h:
+            load().gs_raster_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
             pass
 
 
