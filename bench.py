@@ -26,6 +26,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -58,7 +60,7 @@ def parse():
                     help="block: library defaults instead of the autotuner's patch shape and K")
     ap.add_argument("--cpu-steps", type=int, default=4,
                     help="oracle steps in the CPU sample (about 3 s each on one core for block64)")
-    ap.add_argument("--workload", default="block", choices=["block", "bar", "cloth", "batch", "serve", "control", "cloth_air"],
+    ap.add_argument("--workload", default="block", choices=["block", "bar", "cloth", "batch", "serve", "control", "cloth_air", "render"],
                     help="block: the 1.3M-tet solid (default line); the others measure the remaining workloads")
     ap.add_argument("--meshes", type=int, default=512, help="batch: number of meshes")
     ap.add_argument("--rates", default="10,20,50,100,200,500", help="serve: arrival rates (req/s)")
@@ -756,8 +758,109 @@ def workload_cloth_air(args):
     print(json.dumps(line), flush=True)
 
 
+def workload_render(args):
+    """The soft rasteriser (Sec. 2 "Differentiable rendering engine"): (1) one
+    frame of the 256^2 cloth (130,050 triangles) at 512^2 and 1024^2, forward
+    and backward; (2) the image-loss identification iteration: a thrown
+    2,048-triangle cloth, 1,000 steps with air, 4 rendered frames at 128^2
+    against target frames, backward through renderer and simulator, Adam on
+    the initial velocity."""
+    import torch
+    from paper_2104_02646_gb300 import autograd as A
+    from paper_2104_02646_gb300 import gradsim as gs
+    from paper_2104_02646_gb300 import inputs as I
+    gs.load()
+    dev = torch.device("cuda", 0)
+    ctx = gs.Context(0)
+    f32 = dict(dtype=torch.float32, device=dev)
+    q = I.cloth("3s", n=256, steps=1)
+    x = torch.tensor(q.X, **f32)
+    col = torch.tensor(I.vertex_colours(q.X, seed=0), **f32)
+    spec = I.RenderSpec()
+    for res in (512, 1024):
+        cam = I.look_at((1.3, 1.2, -0.6), (0.5, 0.3, 0.5), width=res, height=res, fov_deg=50.0)
+        r = gs.Raster(ctx, q.n_nodes, q.elems, cam, spec)
+        img = torch.empty(res, res, 4, **f32)
+        gimg = torch.randn(res, res, 4, generator=torch.Generator().manual_seed(0)).to(dev)
+        dx, dc = torch.empty_like(x), torch.empty_like(col)
+        for _ in range(args.warmup):
+            r.forward(x, col, img)
+            r.backward(gimg, dx, dc)
+        t_f = min(_events_ms(lambda: r.forward(x, col, img), reps=5) for _ in range(args.steps))
+        t_b = min(_events_ms(lambda: r.backward(gimg, dx, dc), reps=5) for _ in range(args.steps))
+        # (pixel, triangle) pairs the kernels evaluate: each triangle's clipped box
+        u, v, z = _project_np(q.X, cam)
+        boxes = _pair_count(u[q.elems], v[q.elems], z[q.elems], cam, spec)
+        line = {"metric": "rendered frames/s (forward + backward)", "workload": f"render_cloth256_{res}",
+                "value": 1e3 / (t_f + t_b), "unit": "frames/s", "ms_forward": t_f, "ms_backward": t_b,
+                "pair_evals_per_frame": boxes, "pair_evals_per_s_forward": boxes / (t_f / 1e3),
+                "dtype": "f32", "data": "synthetic",
+                "config": {"triangles": q.n_elems, "image": f"{res}x{res}", "sigma_px2": spec.sigma,
+                           "gamma": spec.gamma}}
+        print(json.dumps(line), flush=True)
+        r.close()
+    # image-loss identification iteration
+    S, n_frames, res = 1000, 4, 128
+    p = I.cloth_throw(n=33, steps=S, seed=0)
+    mesh = gs.Mesh(ctx, p)
+    mu, lam, rho = (torch.tensor(a, **f32) for a in (p.mu, p.lam, p.rho))
+    x0 = torch.tensor(p.x0, **f32)
+    colp = torch.tensor(I.vertex_colours(p.X, seed=1), **f32)
+    cam = I.look_at((1.6, 1.0, -0.8), (0.45, 0.35, 0.45), width=res, height=res, fov_deg=50.0)
+    raster = gs.Raster(ctx, p.n_nodes, p.elems, cam, I.RenderSpec(sigma=1.0, gamma=1e-2))
+
+    def frames(v0):
+        xx, vv, out = x0, v0, []
+        for _ in range(n_frames):
+            xx, vv = A.rollout(mesh, p.dt, S // n_frames, mu, lam, rho, xx, vv, K=1)
+            out.append(A.render(raster, xx, colp))
+        return out
+
+    v_ref = torch.tensor(p.v0, **f32)
+    with torch.no_grad():
+        target = [f.clone() for f in frames(v_ref)]
+    vv0 = (v_ref + 0.3).requires_grad_(True)
+    opt = torch.optim.Adam([vv0], lr=0.03)
+
+    def iteration():
+        opt.zero_grad()
+        loss = sum(((f - t) ** 2).sum() for f, t in zip(frames(vv0), target))
+        loss.backward()
+        opt.step()
+
+    for _ in range(args.warmup):
+        iteration()
+    t_it = min(_events_ms(iteration) for _ in range(args.steps))
+    line = {"metric": "image-loss v0 identification iterations/s", "workload": "render_cloth_throw33",
+            "value": 1e3 / t_it, "unit": "iterations/s", "ms_per_iteration": t_it, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"triangles": p.n_elems, "steps": S, "frames": n_frames, "image": f"{res}x{res}",
+                       "air": "on", "recompute": "each frame's segment is re-run in backward", "K": 1}}
+    print(json.dumps(line), flush=True)
+    raster.close()
+    mesh.close()
+
+
+def _project_np(X, cam):
+    xc = X @ cam.R.T + cam.t
+    return cam.fx * xc[:, 0] / xc[:, 2] + cam.cx, cam.fy * xc[:, 1] / xc[:, 2] + cam.cy, xc[:, 2]
+
+
+def _pair_count(u, v, z, cam, spec):
+    """(pixel, triangle) pairs in the triangles' clipped pixel boxes."""
+    import math as _m
+    r = _m.sqrt(spec.sigma * _m.log((1 - 1e-5) / 1e-5))
+    ok = (z > cam.z_near).all(axis=1)
+    x0 = np.clip(np.ceil(u.min(axis=1) - r - 0.5), 0, cam.width)
+    x1 = np.clip(np.floor(u.max(axis=1) + r - 0.5), -1, cam.width - 1)
+    y0 = np.clip(np.ceil(v.min(axis=1) - r - 0.5), 0, cam.height)
+    y1 = np.clip(np.floor(v.max(axis=1) + r - 0.5), -1, cam.height - 1)
+    n = np.maximum(x1 - x0 + 1, 0) * np.maximum(y1 - y0 + 1, 0)
+    return int(n[ok].sum())
+
+
 WORKLOADS = {"bar": workload_bar, "cloth": workload_cloth, "batch": workload_batch, "serve": workload_serve,
-             "control": workload_control, "cloth_air": workload_cloth_air}
+             "control": workload_control, "cloth_air": workload_cloth_air, "render": workload_render}
 
 if __name__ == "__main__":
     main()

@@ -11,11 +11,18 @@
 // Kernels:
 //   k_rs_setup    one thread per triangle: project the corners (pinhole),
 //                 twice the signed area, the pixel box its coverage can reach;
-//   k_rs_forward  one CTA per 16x16 tile, one thread per pixel: the CTA
-//                 culls triangles by box against its tile in rounds of 256
-//                 (ballot compaction keeps triangle order), stages the
-//                 survivors in shared memory, and each pixel accumulates them
-//                 in triangle order (product of 1 - D, online depth softmax);
+//   k_rs_bin_*    one CTA per (64x64 super-tile, chunk of triangles): test
+//                 the chunk's 8-byte boxes against the super-tile's 16 tiles,
+//                 count per tile, scan the counts (tile-major, chunks in
+//                 order), then write every tile's list of triangle ids in
+//                 ascending order (block scans keep the order);
+//   k_rs_forward  one CTA per 16x16 tile, one warp per 8x4 pixel block, one
+//                 thread per pixel, no block barrier: each warp culls its
+//                 tile's ordered list against its block 32 entries at a time
+//                 (8-byte boxes, ballot), and every pixel accumulates the hits
+//                 in triangle order (product of 1 - D, online depth
+//                 softmax); if the lists overflowed their buffer, the warp
+//                 scans every triangle instead;
 //   k_rs_backward one warp per triangle: its lanes walk the triangle's pixel
 //                 box, recompute the pair exactly as the forward did, and
 //                 accumulate dL/d(corner u, v, z, colour); a fixed xor tree
@@ -38,6 +45,8 @@ using gs::Buf;
 
 constexpr int kTile = 16;             // tile side (pixels); 256 threads per tile CTA
 constexpr int kTileThreads = kTile * kTile;
+constexpr int kSuper = 64;            // super-tile side (pixels): 4 x 4 tiles
+constexpr int kSub = (kSuper / kTile) * (kSuper / kTile);
 constexpr float kTau = 1.0e-5f;       // outside coverage below this is none
 constexpr float kQmin = 1.0e-6f;      // 1 - coverage is kept >= kQmin
 
@@ -76,7 +85,7 @@ __device__ __forceinline__ void cam_point(const Cam& c, const float* x, float& X
 }
 
 __global__ void k_rs_setup(const float* __restrict__ x, const int* __restrict__ faces, int F, Cam cam, Spec sp,
-                           TriScr* __restrict__ out) {
+                           TriScr* __restrict__ out, short4* __restrict__ boxes) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= F) return;
     TriScr T;
@@ -120,6 +129,140 @@ __global__ void k_rs_setup(const float* __restrict__ x, const int* __restrict__ 
         }
     }
     out[f] = T;
+    boxes[f] = make_short4((short)T.x0, (short)T.y0, (short)T.x1, (short)T.y1);
+}
+
+__device__ __forceinline__ bool box_hits(short4 b, int x0, int y0, int x1, int y1) {
+    return b.z >= x0 && b.x <= x1 && b.w >= y0 && b.y <= y1;
+}
+
+// Binning rounds: 256 threads x kPer consecutive triangles, so a thread's
+// triangles are contiguous and threads follow triangle order.
+constexpr int kPer = 8;
+constexpr int kRound = 256 * kPer;
+
+// block-wide exclusive scan of one int per thread (thread order); returns the total
+__device__ __forceinline__ int block_exclusive_scan(int v, int& excl, int* s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < 8; ++w) {
+        before += w < warp ? s_warp[w] : 0;
+        total += s_warp[w];
+    }
+    excl = before + inc - v;
+    __syncthreads();
+    return total;
+}
+
+// tile t (0..15, row-major) of super-tile (x0, y0)
+__device__ __forceinline__ bool tile_hits(short4 b, int x0, int y0, int t) {
+    const int tx = x0 + kTile * (t % (kSuper / kTile)), ty = y0 + kTile * (t / (kSuper / kTile));
+    return box_hits(b, tx, ty, tx + kTile - 1, ty + kTile - 1);
+}
+
+// CTA (super-tile blockIdx.x, triangle chunk blockIdx.y): per tile of the
+// super-tile, how many of the chunk's triangle boxes overlap it; counts are
+// indexed ((super-tile * 16 + tile) * chunks + chunk)
+__global__ void __launch_bounds__(256) k_rs_bin_count(const short4* __restrict__ boxes, int F, int chunk, int nsx,
+                                                      int W, int H, int* __restrict__ counts) {
+    __shared__ int s_warp[8];
+    const int x0 = (blockIdx.x % nsx) * kSuper, y0 = (blockIdx.x / nsx) * kSuper;
+    const int x1 = min(x0 + kSuper, W) - 1, y1 = min(y0 + kSuper, H) - 1;
+    const int fb = blockIdx.y * chunk, fe = min(fb + chunk, F);
+    int n[kSub];
+#pragma unroll
+    for (int t = 0; t < kSub; ++t) n[t] = 0;
+    for (int f = fb + threadIdx.x; f < fe; f += 256) {
+        const short4 b = boxes[f];
+        if (!box_hits(b, x0, y0, x1, y1)) continue;
+#pragma unroll
+        for (int t = 0; t < kSub; ++t) n[t] += tile_hits(b, x0, y0, t) ? 1 : 0;
+    }
+#pragma unroll 1
+    for (int t = 0; t < kSub; ++t) {
+        int excl;
+        const int total = block_exclusive_scan(n[t], excl, s_warp);
+        if (threadIdx.x == 0) counts[(blockIdx.x * kSub + t) * gridDim.y + blockIdx.y] = total;
+    }
+}
+
+// exclusive scan of the super-tile counts (one CTA, fixed order); flags an
+// overflow of the list buffer
+__global__ void __launch_bounds__(256) k_rs_bin_scan(const int* __restrict__ counts, int n, long long cap,
+                                                     int* __restrict__ offsets, int* __restrict__ overflow) {
+    __shared__ long long part[256];
+    const int per = (n + 255) / 256;
+    const int b = threadIdx.x * per, e = min(b + per, n);
+    long long s = 0;
+    for (int i = b; i < e; ++i) s += counts[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long run = 0;
+        for (int t = 0; t < 256; ++t) {
+            const long long v = part[t];
+            part[t] = run;
+            run += v;
+        }
+        *overflow = run > cap ? 1 : 0;
+    }
+    __syncthreads();
+    long long run = part[threadIdx.x];
+    for (int i = b; i < e; ++i) {
+        offsets[i] = (int)(run < cap ? run : cap);
+        run += counts[i];
+    }
+}
+
+// every tile's list: the chunk's triangle ids overlapping it, ascending;
+// a tile's chunks are adjacent, so its list is ascending as a whole
+__global__ void __launch_bounds__(256) k_rs_bin_fill(const short4* __restrict__ boxes, int F, int chunk, int nsx,
+                                                     int W, int H, const int* __restrict__ offsets,
+                                                     const int* __restrict__ overflow, int* __restrict__ lists) {
+    __shared__ int s_warp[8];
+    if (*overflow) return;
+    const int x0 = (blockIdx.x % nsx) * kSuper, y0 = (blockIdx.x / nsx) * kSuper;
+    const int x1 = min(x0 + kSuper, W) - 1, y1 = min(y0 + kSuper, H) - 1;
+    const int fb = blockIdx.y * chunk, fe = min(fb + chunk, F);
+    int written[kSub];
+#pragma unroll
+    for (int t = 0; t < kSub; ++t) written[t] = 0;
+    for (int base = fb; base < fe; base += kRound) {
+        const int f0 = base + threadIdx.x * kPer;
+        unsigned hm[kPer];  // per candidate: bit t = overlaps tile t
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            hm[k] = 0;
+            if (f0 + k < fe) {
+                const short4 b = boxes[f0 + k];
+                if (box_hits(b, x0, y0, x1, y1)) {
+#pragma unroll
+                    for (int t = 0; t < kSub; ++t) hm[k] |= tile_hits(b, x0, y0, t) ? (1u << t) : 0u;
+                }
+            }
+        }
+#pragma unroll 1
+        for (int t = 0; t < kSub; ++t) {
+            int c = 0;
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) c += (hm[k] >> t) & 1u;
+            int excl;
+            const int total = block_exclusive_scan(c, excl, s_warp);
+            int* o = lists + offsets[(blockIdx.x * kSub + t) * gridDim.y + blockIdx.y] + written[t] + excl;
+#pragma unroll
+            for (int k = 0; k < kPer; ++k)
+                if ((hm[k] >> t) & 1u) *o++ = f0 + k;
+            written[t] += total;
+        }
+    }
 }
 
 __device__ __forceinline__ float seg_d2(float px, float py, float ex, float ey, float fx, float fy, float& t,
@@ -187,58 +330,59 @@ __device__ __forceinline__ void eval_pair(const TriScr& T, float px, float py, c
 }
 
 __global__ void __launch_bounds__(kTileThreads)
-    k_rs_forward(const TriScr* __restrict__ tris, int F, const float* __restrict__ col, Cam cam, Spec sp,
-                 float4* __restrict__ image, float4* __restrict__ image_keep, float4* __restrict__ aux) {
-    __shared__ TriScr s_tri[kTileThreads];
-    __shared__ int s_cnt[kTileThreads / 32];
+    k_rs_forward(const TriScr* __restrict__ tris, const short4* __restrict__ boxes, int F,
+                 const int* __restrict__ counts, const int* __restrict__ offsets, const int* __restrict__ overflow,
+                 const int* __restrict__ lists, int n_super_x, int nch, const float* __restrict__ col, Cam cam,
+                 Spec sp, float4* __restrict__ image, float4* __restrict__ image_keep, float4* __restrict__ aux) {
+    // warp w owns the 8 x 4 pixel block (w % 2, w / 2) of the 16 x 16 tile;
+    // warps run independently (no block barrier)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tx0 = blockIdx.x * kTile, ty0 = blockIdx.y * kTile;
-    const int tx1 = min(tx0 + kTile, cam.W) - 1, ty1 = min(ty0 + kTile, cam.H) - 1;
-    const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
-    const int px = tx0 + lx, py = ty0 + ly;
+    const int bx0 = tx0 + 8 * (warp & 1), by0 = ty0 + 4 * (warp >> 1);
+    const int bx1 = min(bx0 + 7, cam.W - 1), by1 = min(by0 + 3, cam.H - 1);
+    if (bx0 > bx1 || by0 > by1) return;  // the block lies off a ragged edge
+    const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
     const bool active = px < cam.W && py < cam.H;
     const float fx = px + 0.5f, fy = py + 0.5f;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the tile's ordered list, or every triangle after an overflow
+    const int st = (ty0 / kSuper) * n_super_x + tx0 / kSuper;
+    const int sub = ((ty0 % kSuper) / kTile) * (kSuper / kTile) + (tx0 % kSuper) / kTile;
+    const bool all = *overflow != 0;
+    const int first = (st * kSub + sub) * nch, last = first + nch - 1;
+    const int n_cand = all ? F : offsets[last] + counts[last] - offsets[first];
+    const int* cand = all ? nullptr : lists + offsets[first];
     // running union and softmax, starting from the background at depth eps
     float Pq = 1.f, m = sp.eps, Z = 1.f;
     float N[3] = {sp.bg[0], sp.bg[1], sp.bg[2]};
-    for (int base = 0; base < F; base += kTileThreads) {
-        const int f = base + threadIdx.x;
-        bool keep = false;
-        TriScr T;
-        if (f < F) {
-            T = tris[f];
-            keep = T.x1 >= tx0 && T.x0 <= tx1 && T.y1 >= ty0 && T.y0 <= ty1;
+    for (int base = 0; base < n_cand; base += 32) {
+        const int c = base + lane;
+        int f = -1;
+        bool h = false;
+        if (c < n_cand) {
+            f = all ? c : cand[c];
+            h = box_hits(boxes[f], bx0, by0, bx1, by1);
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) s_cnt[warp] = __popc(bal);
-        __syncthreads();
-        int off = 0, total = 0;
-        for (int w = 0; w < kTileThreads / 32; ++w) {
-            off += w < warp ? s_cnt[w] : 0;
-            total += s_cnt[w];
-        }
-        if (keep) s_tri[off + __popc(bal & ((1u << lane) - 1u))] = T;
-        __syncthreads();
-        if (active) {
-            for (int k = 0; k < total; ++k) {
-                const TriScr& S = s_tri[k];
-                if (px < S.x0 || px > S.x1 || py < S.y0 || py > S.y1) continue;
-                Pair P;
-                eval_pair(S, fx, fy, sp, cam, col, P);
-                if (!P.cover) continue;
-                Pq *= P.q;
-                if (P.zh > m) {
-                    const float sc = expf((m - P.zh) * sp.inv_gamma);
-                    Z *= sc;
-                    for (int c = 0; c < 3; ++c) N[c] *= sc;
-                    m = P.zh;
-                }
-                const float wgt = P.D * expf((P.zh - m) * sp.inv_gamma);
-                Z += wgt;
-                for (int c = 0; c < 3; ++c) N[c] += wgt * P.C[c];
+        unsigned bal = __ballot_sync(0xffffffffu, h);
+        while (bal) {  // the hits in list order
+            const int src = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const int fk = __shfl_sync(0xffffffffu, f, src);
+            const TriScr S = tris[fk];
+            if (!active || px < S.x0 || px > S.x1 || py < S.y0 || py > S.y1) continue;
+            Pair P;
+            eval_pair(S, fx, fy, sp, cam, col, P);
+            if (!P.cover) continue;
+            Pq *= P.q;
+            if (P.zh > m) {
+                const float sc = expf((m - P.zh) * sp.inv_gamma);
+                Z *= sc;
+                for (int k = 0; k < 3; ++k) N[k] *= sc;
+                m = P.zh;
             }
+            const float wgt = P.D * expf((P.zh - m) * sp.inv_gamma);
+            Z += wgt;
+            for (int k = 0; k < 3; ++k) N[k] += wgt * P.C[k];
         }
-        __syncthreads();
     }
     if (active) {
         const float iZ = 1.0f / Z;
@@ -383,6 +527,9 @@ struct gs_raster {
     Cam cam{};
     Spec sp{};
     Buf faces, tri, tgrad, rowptr, entries, img, aux, x, col;
+    Buf boxes, bin_counts, bin_offsets, bin_flag, bin_lists;
+    int nsx = 0, nsy = 0, nch = 1, chunk = 1;
+    long long bin_cap = 0;
     bool have_forward = false;
 };
 
@@ -467,6 +614,22 @@ extern "C" gs_status gs_raster_create(gs_ctx* ctx, const gs_raster_desc* d, gs_r
         delete r;
         return st;
     }
+    // tile lists: 8 entries per triangle (at least 1 M) before the tiles fall back to scanning every triangle
+    r->nsx = (r->cam.W + kSuper - 1) / kSuper;
+    r->nsy = (r->cam.H + kSuper - 1) / kSuper;
+    r->bin_cap = std::max<long long>(8LL * F, 1 << 20);
+    // triangle chunks per super-tile: about four CTAs per SM in the binning kernels
+    const int n_super = r->nsx * r->nsy;
+    r->nch = std::max(1, std::min(64, (4 * std::max(ctx->num_sms, 1)) / n_super));
+    r->chunk = std::max(kRound, ((F + r->nch - 1) / r->nch + kRound - 1) / kRound * kRound);
+    r->nch = std::max(1, (F + r->chunk - 1) / r->chunk);
+    if ((st = r->boxes.alloc(ctx, std::max<size_t>(8 * (size_t)F, 16), s)) < 0 ||
+        (st = r->bin_counts.alloc(ctx, 4 * (size_t)n_super * kSub * r->nch, s)) < 0 ||
+        (st = r->bin_offsets.alloc(ctx, 4 * (size_t)n_super * kSub * r->nch, s)) < 0 ||
+        (st = r->bin_flag.alloc(ctx, 16, s)) < 0 || (st = r->bin_lists.alloc(ctx, 4 * (size_t)r->bin_cap, s)) < 0) {
+        delete r;
+        return st;
+    }
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         delete r;
@@ -501,10 +664,21 @@ extern "C" gs_status gs_raster_forward(gs_raster* r, const float* x, const float
     GS_CUDA(cudaMemcpyAsync(r->col.p, colours, 12 * (size_t)r->N, cudaMemcpyDeviceToDevice, s));
     if (r->F > 0)
         k_rs_setup<<<(r->F + 127) / 128, 128, 0, s>>>((const float*)r->x.p, (const int*)r->faces.p, r->F, r->cam,
-                                                      r->sp, (TriScr*)r->tri.p);
+                                                      r->sp, (TriScr*)r->tri.p, (short4*)r->boxes.p);
+    const dim3 sgrid(r->nsx * r->nsy, r->nch);
+    int* counts = (int*)r->bin_counts.p;
+    int* offsets = (int*)r->bin_offsets.p;
+    int* flag = (int*)r->bin_flag.p;
+    k_rs_bin_count<<<sgrid, 256, 0, s>>>((const short4*)r->boxes.p, r->F, r->chunk, r->nsx, r->cam.W, r->cam.H,
+                                         counts);
+    k_rs_bin_scan<<<1, 256, 0, s>>>(counts, r->nsx * r->nsy * kSub * r->nch, r->bin_cap, offsets, flag);
+    k_rs_bin_fill<<<sgrid, 256, 0, s>>>((const short4*)r->boxes.p, r->F, r->chunk, r->nsx, r->cam.W, r->cam.H,
+                                        offsets, flag, (int*)r->bin_lists.p);
     const dim3 grid((r->cam.W + kTile - 1) / kTile, (r->cam.H + kTile - 1) / kTile);
-    k_rs_forward<<<grid, kTileThreads, 0, s>>>((const TriScr*)r->tri.p, r->F, (const float*)r->col.p, r->cam, r->sp,
-                                               (float4*)image, (float4*)r->img.p, (float4*)r->aux.p);
+    k_rs_forward<<<grid, kTileThreads, 0, s>>>((const TriScr*)r->tri.p, (const short4*)r->boxes.p, r->F, counts,
+                                               offsets, flag,
+                                               (const int*)r->bin_lists.p, r->nsx, r->nch, (const float*)r->col.p,
+                                               r->cam, r->sp, (float4*)image, (float4*)r->img.p, (float4*)r->aux.p);
     GS_CUDA(cudaGetLastError());
     r->have_forward = true;
     return GS_OK;
