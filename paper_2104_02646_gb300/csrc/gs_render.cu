@@ -228,14 +228,20 @@ __global__ void __launch_bounds__(256) k_rs_bin_fill(const short4* __restrict__ 
                                                      int W, int H, const int* __restrict__ offsets,
                                                      const int* __restrict__ overflow, int* __restrict__ lists) {
     __shared__ int s_warp[8];
+    // tiles hit in a round: OR of the threads' masks, rotating over three
+    // words so that clearing the next one never races with a reader
+    __shared__ unsigned s_any[3];
     if (*overflow) return;
     const int x0 = (blockIdx.x % nsx) * kSuper, y0 = (blockIdx.x / nsx) * kSuper;
     const int x1 = min(x0 + kSuper, W) - 1, y1 = min(y0 + kSuper, H) - 1;
     const int fb = blockIdx.y * chunk, fe = min(fb + chunk, F);
+    if (threadIdx.x < 3) s_any[threadIdx.x] = 0u;
+    __syncthreads();
     int written[kSub];
 #pragma unroll
     for (int t = 0; t < kSub; ++t) written[t] = 0;
-    for (int base = fb; base < fe; base += kRound) {
+    int round = 0;
+    for (int base = fb; base < fe; base += kRound, ++round) {
         const int f0 = base + threadIdx.x * kPer;
         unsigned hm[kPer];  // per candidate: bit t = overlaps tile t
 #pragma unroll
@@ -249,8 +255,16 @@ __global__ void __launch_bounds__(256) k_rs_bin_fill(const short4* __restrict__ 
                 }
             }
         }
+        unsigned mine = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) mine |= hm[k];
+        if (threadIdx.x == 0) s_any[(round + 1) % 3] = 0u;
+        if (mine) atomicOr(&s_any[round % 3], mine);
+        __syncthreads();
+        const unsigned any = s_any[round % 3];
 #pragma unroll 1
         for (int t = 0; t < kSub; ++t) {
+            if (!((any >> t) & 1u)) continue;  // uniform: no thread hit tile t
             int c = 0;
 #pragma unroll
             for (int k = 0; k < kPer; ++k) c += (hm[k] >> t) & 1u;
