@@ -812,6 +812,117 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
     return 0;
 }
 
+// ---------------------------------------------------------------------------
+// 8. rigid bodies (App. A.1 "Rigid Bodies"): Newton-Euler with the contact
+// model at the body's contact points, semi-implicit Euler (App. B)
+// ---------------------------------------------------------------------------
+// Readings: the quaternion r = (w, x, y, z) maps body to world; the contact
+// law is the particles' (section 4) at X_k = x + R p_k with velocity
+// V_k = v + omega x (R p_k); the world inertia is R I_b R^T; the step is
+//   v+ = v + dt (g + F/m),  omega+ = omega + dt I_w^-1 (tau - omega x I_w omega),
+//   x+ = x + dt v+,  r+ = normalise(r + dt/2 (0, omega+) (x) r)
+// (velocities first, then positions with the new velocities, as App. B's
+// g(s-, s+, theta); the quaternion derivative is 1/2 omega (x) r).
+template <class T>
+void quat_rot(const T* r, T R[3][3]) {
+    const T w = r[0], x = r[1], y = r[2], z = r[3];
+    R[0][0] = 1.0 - 2.0 * (y * y + z * z); R[0][1] = 2.0 * (x * y - w * z); R[0][2] = 2.0 * (x * z + w * y);
+    R[1][0] = 2.0 * (x * y + w * z); R[1][1] = 1.0 - 2.0 * (x * x + z * z); R[1][2] = 2.0 * (y * z - w * x);
+    R[2][0] = 2.0 * (x * z - w * y); R[2][1] = 2.0 * (y * z + w * x); R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+template <class T>
+void mat3_solve(const T A[3][3], const T* b, T* out) {  // Cramer's rule
+    T c[3][3];
+    c[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+    c[0][1] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+    c[0][2] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+    c[1][0] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+    c[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+    c[1][2] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+    c[2][0] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+    c[2][1] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+    c[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    const T det = A[0][0] * c[0][0] + A[0][1] * c[0][1] + A[0][2] * c[0][2];
+    for (int i = 0; i < 3; ++i) out[i] = (c[0][i] * b[0] + c[1][i] * b[1] + c[2][i] * b[2]) / det;
+}
+
+// one step of one body; s [13] -> o [13]; p = (m, I6, ke, kd, kf, mu)
+template <class T>
+void rigid_step_t(const orc_rigid* b, const T* s, const T* p, double dt, T* o) {
+    const orc_model* sc = b->scene;
+    const T* x = s; const T* r = s + 3; const T* v = s + 7; const T* w = s + 10;
+    const T m = p[0];
+    T Ib[3][3] = {{p[1], p[4], p[5]}, {p[4], p[2], p[6]}, {p[5], p[6], p[3]}};
+    T R[3][3];
+    quat_rot(r, R);
+    T F[3] = {T(0.0), T(0.0), T(0.0)}, tau[3] = {T(0.0), T(0.0), T(0.0)};
+    for (int k = 0; k < b->n_points; ++k) {
+        const double* pk = b->points + 3 * k;
+        T d[3], X[3], V[3], wd[3], fc[3], td[3];
+        for (int i = 0; i < 3; ++i) d[i] = R[i][0] * pk[0] + R[i][1] * pk[1] + R[i][2] * pk[2];
+        vcross(w, d, wd);
+        for (int i = 0; i < 3; ++i) { X[i] = x[i] + d[i]; V[i] = v[i] + wd[i]; }
+        contact_t(sc, X, V, p[7], p[8], p[9], p[10], fc);
+        vcross(d, fc, td);
+        for (int i = 0; i < 3; ++i) { F[i] += fc[i]; tau[i] += td[i]; }
+    }
+    // I_w = R I_b R^T;  alpha = I_w^-1 (tau - omega x I_w omega)
+    T Iw[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            T acc(0.0);
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c) acc += R[i][a] * Ib[a][c] * R[j][c];
+            Iw[i][j] = acc;
+        }
+    T L[3], wL[3], h[3], alpha[3];
+    for (int i = 0; i < 3; ++i) L[i] = Iw[i][0] * w[0] + Iw[i][1] * w[1] + Iw[i][2] * w[2];
+    vcross(w, L, wL);
+    for (int i = 0; i < 3; ++i) h[i] = tau[i] - wL[i];
+    mat3_solve(Iw, h, alpha);
+    T* xo = o; T* ro = o + 3; T* vo = o + 7; T* wo = o + 10;
+    for (int i = 0; i < 3; ++i) {
+        vo[i] = v[i] + dt * (sc->gravity[i] + F[i] / m);
+        wo[i] = w[i] + dt * alpha[i];
+        xo[i] = x[i] + dt * vo[i];
+    }
+    // r + dt/2 (0, omega+) (x) r:  (0, a) (x) (rw, rv) = (-a.rv, rw a + a x rv)
+    T ax[3];
+    vcross(wo, r + 1, ax);
+    T q[4];
+    q[0] = r[0] - 0.5 * dt * vdot(wo, r + 1);
+    for (int i = 0; i < 3; ++i) q[1 + i] = r[1 + i] + 0.5 * dt * (r[0] * wo[i] + ax[i]);
+    const T qn = fsqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int i = 0; i < 4; ++i) ro[i] = q[i] / qn;
+}
+
+template <class T>
+T rigid_points_loss(const orc_rigid* b, const T* s, const double* target, const double* seed) {
+    T R[3][3];
+    quat_rot(s + 3, R);
+    T L(0.0);
+    if (target) {
+        for (int k = 0; k < b->n_points; ++k) {
+            const double* pk = b->points + 3 * k;
+            for (int i = 0; i < 3; ++i) {
+                const T X = s[i] + R[i][0] * pk[0] + R[i][1] * pk[1] + R[i][2] * pk[2];
+                const T d = X - target[3 * k + i];
+                L += d * d;
+            }
+        }
+    }
+    if (seed)
+        for (int i = 0; i < 13; ++i) L += seed[i] * s[i];
+    return L;
+}
+
+void rigid_params(const orc_rigid* b, double* p) {
+    p[0] = b->mass;
+    for (int i = 0; i < 6; ++i) p[1 + i] = b->inertia[i];
+    for (int i = 0; i < 4; ++i) p[7 + i] = b->contact[i];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -860,6 +971,82 @@ void orc_air_forces(const double x[9], const double v[9], double k_drag, double 
 }
 void orc_contact_force(const orc_model* m, const double x[3], const double v[3], double f[3]) {
     contact_t<double>(m, x, v, m->ke, m->kd, m->kf, m->mu_f, f);
+}
+
+int orc_rigid_rollout(const orc_rigid* b, const double* state0, double dt, int S, double* stateS, double* traj) {
+    double p[11], s[13], o[13];
+    rigid_params(b, p);
+    std::memcpy(s, state0, sizeof s);
+    if (traj) std::memcpy(traj, s, sizeof s);
+    for (int n = 0; n < S; ++n) {
+        rigid_step_t<double>(b, s, p, dt, o);
+        std::memcpy(s, o, sizeof s);
+        if (traj) std::memcpy(traj + 13 * (size_t)(n + 1), s, sizeof s);
+    }
+    if (stateS) std::memcpy(stateS, s, sizeof s);
+    return 0;
+}
+
+// Reverse mode through the stored trajectory: each step's exact Jacobian
+// with respect to (state, parameters) from Dual<24>, applied transposed.
+int orc_rigid_loss_grad(const orc_rigid* b, const double* state0, double dt, int S, const double* target,
+                        const double* seed, double* loss, double* d_state0, double* d_mass, double* d_inertia,
+                        double* d_contact) {
+    double p[11];
+    rigid_params(b, p);
+    std::vector<double> traj(13 * (size_t)(S + 1));
+    orc_rigid_rollout(b, state0, dt, S, nullptr, traj.data());
+    const double* sS = &traj[13 * (size_t)S];
+    // seed: dL/ds(S)
+    typedef Dual<13> D13;
+    D13 sd[13];
+    for (int i = 0; i < 13; ++i) { sd[i] = D13(sS[i]); sd[i].d[i] = 1.0; }
+    const D13 Ld = rigid_points_loss(b, sd, target, seed);
+    if (loss) *loss = Ld.v;
+    double lam[13], pb[11] = {0};
+    for (int i = 0; i < 13; ++i) lam[i] = Ld.d[i];
+    typedef Dual<24> D;
+    for (int n = S - 1; n >= 0; --n) {
+        const double* sn = &traj[13 * (size_t)n];
+        D si[13], pi[11], so[13];
+        for (int i = 0; i < 13; ++i) { si[i] = D(sn[i]); si[i].d[i] = 1.0; }
+        for (int j = 0; j < 11; ++j) { pi[j] = D(p[j]); pi[j].d[13 + j] = 1.0; }
+        rigid_step_t(b, si, pi, dt, so);
+        double nl[13] = {0};
+        for (int k = 0; k < 24; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i < 13; ++i) acc += lam[i] * so[i].d[k];
+            if (k < 13) nl[k] = acc; else pb[k - 13] += acc;
+        }
+        std::memcpy(lam, nl, sizeof lam);
+    }
+    if (d_state0) std::memcpy(d_state0, lam, sizeof lam);
+    if (d_mass) *d_mass = pb[0];
+    if (d_inertia) for (int i = 0; i < 6; ++i) d_inertia[i] = pb[1 + i];
+    if (d_contact) for (int i = 0; i < 4; ++i) d_contact[i] = pb[7 + i];
+    return 0;
+}
+
+int orc_rigid_loss_dir(const orc_rigid* b, const double* state0, double dt, int S, const double* target,
+                       const double* seed, const double* dir_state0, double dir_mass, const double* dir_inertia,
+                       const double* dir_contact, double* loss, double* dloss) {
+    typedef Dual<1> D;
+    double p[11];
+    rigid_params(b, p);
+    D s[13], pp[11], o[13];
+    for (int i = 0; i < 13; ++i) { s[i] = D(state0[i]); s[i].d[0] = dir_state0 ? dir_state0[i] : 0.0; }
+    for (int j = 0; j < 11; ++j) pp[j] = D(p[j]);
+    pp[0].d[0] = dir_mass;
+    for (int j = 0; j < 6; ++j) pp[1 + j].d[0] = dir_inertia ? dir_inertia[j] : 0.0;
+    for (int j = 0; j < 4; ++j) pp[7 + j].d[0] = dir_contact ? dir_contact[j] : 0.0;
+    for (int n = 0; n < S; ++n) {
+        rigid_step_t(b, s, pp, dt, o);
+        for (int i = 0; i < 13; ++i) s[i] = o[i];
+    }
+    const D L = rigid_points_loss(b, s, target, seed);
+    if (loss) *loss = L.v;
+    if (dloss) *dloss = L.d[0];
+    return 0;
 }
 
 int orc_forces(const orc_model* m, const double* x, const double* v, double* f) {

@@ -127,6 +127,34 @@ typedef struct orc_dirs {
     const double* hinge_act_seq;
 } orc_dirs;
 
+/* ---- rigid bodies (App. A.1 "Rigid Bodies") ----------------------------
+ * State of a body: x (centre of mass), r = (w, x, y, z) unit quaternion
+ * (world from body), v, omega (world frame): 13 doubles in that order.
+ * Design parameters: mass m, body-frame inertia about the centre of mass
+ * (Ixx, Iyy, Izz, Ixy, Ixz, Iyz) and the contact parameters (ke, kd, kf, mu)
+ * of the compliant contact model, applied at every body-frame contact point
+ * with the particles' contact law against the scene's plane / sphere. */
+typedef struct orc_rigid {
+    int n_points;
+    const double* points;   /* [n_points][3] body frame, about the centre of mass */
+    double mass;
+    double inertia[6];      /* Ixx, Iyy, Izz, Ixy, Ixz, Iyz */
+    double contact[4];      /* ke, kd, kf, mu */
+    const orc_model* scene; /* plane / sphere and gravity (mesh fields unused) */
+} orc_rigid;
+/* rollout of S steps: state0 [13] -> stateS [13]; traj [(S+1)][13] nullable */
+int orc_rigid_rollout(const orc_rigid* b, const double* state0, double dt, int S, double* stateS, double* traj);
+/* L = sum_k |X_k(S) - target_k|^2 over the world positions of the points at
+ * step S, plus dot(seed, state(S)) for a nullable seed [13]; gradients:
+ * d_state0 [13], d_mass [1], d_inertia [6], d_contact [4] (each nullable) */
+int orc_rigid_loss_grad(const orc_rigid* b, const double* state0, double dt, int S, const double* target,
+                        const double* seed, double* loss, double* d_state0, double* d_mass, double* d_inertia,
+                        double* d_contact);
+/* the same loss and its derivative along (d_state0 [13], d_mass, d_inertia [6], d_contact [4]) by forward mode */
+int orc_rigid_loss_dir(const orc_rigid* b, const double* state0, double dt, int S, const double* target,
+                       const double* seed, const double* dir_state0, double dir_mass, const double* dir_inertia,
+                       const double* dir_contact, double* loss, double* dloss);
+
 /* ---- rest-state set-up ------------------------------------------------- */
 void orc_tet_rest(const double X[12], double Dminv[9], double* V);
 void orc_tri_rest(const double X[9], double Dminv[4], double* A);

@@ -44,6 +44,11 @@ _DIR_FIELDS = ["x0", "v0", "tet_mu", "tet_lam", "tet_rho", "tet_act", "tri_mu", 
 _SEQ = ("tet_act_seq", "tri_act_seq", "hinge_act_seq")
 
 
+class _Rigid(C.Structure):
+    _fields_ = [("n_points", C.c_int), ("points", _dp), ("mass", C.c_double), ("inertia", C.c_double * 6),
+                ("contact", C.c_double * 4), ("scene", C.POINTER(_Model))]
+
+
 class _Grads(C.Structure):
     _fields_ = [(f, _dp) for f in _GRAD_FIELDS]
 
@@ -74,6 +79,11 @@ def lib():
         L.orc_hinge_angle_grad.argtypes = [_dp, _dp]
         L.orc_contact_force.argtypes = [C.POINTER(_Model), _dp, _dp, _dp]
         L.orc_air_forces.argtypes = [_dp, _dp, C.c_double, C.c_double, _dp, _dp]
+        L.orc_rigid_rollout.argtypes = [C.POINTER(_Rigid), _dp, C.c_double, C.c_int, _dp, _dp]
+        L.orc_rigid_loss_grad.argtypes = [C.POINTER(_Rigid), _dp, C.c_double, C.c_int, _dp, _dp, _dp, _dp, _dp,
+                                          _dp, _dp]
+        L.orc_rigid_loss_dir.argtypes = [C.POINTER(_Rigid), _dp, C.c_double, C.c_int, _dp, _dp, _dp, C.c_double,
+                                         _dp, _dp, _dp, _dp]
         L.orc_forces.argtypes = [C.POINTER(_Model), _dp, _dp, _dp]
         L.orc_rollout.argtypes = [C.POINTER(_Model), _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp]
         L.orc_loss_grad.argtypes = [C.POINTER(_Model), _dp, _dp, C.c_double, C.c_int, _dp, _dp,
@@ -328,3 +338,47 @@ def air_forces(x, v, k_drag, k_lift, wind=(0.0, 0.0, 0.0)):
     f = np.zeros(9)
     lib().orc_air_forces(_p(x), _p(v), float(k_drag), float(k_lift), _p(w), _p(f))
     return f.reshape(3, 3)
+
+
+class Rigid:
+    """One rigid body (an ``inputs.RigidBody``) in the oracle's layout: points,
+    mass, inertia, contact parameters and the scene (plane / sphere, gravity)."""
+
+    def __init__(self, body, mass=None, inertia=None, contact=None):
+        self._pts = np.ascontiguousarray(body.points, dtype=np.float64)
+        self._scene = Model(X=np.zeros((1, 3)), contact=body.scene, gravity=body.gravity)
+        r = _Rigid()
+        r.n_points = self._pts.shape[0]
+        r.points = _p(self._pts)
+        r.mass = float(body.mass if mass is None else mass)
+        r.inertia = (C.c_double * 6)(*(body.inertia if inertia is None else inertia))
+        r.contact = (C.c_double * 4)(*(body.contact if contact is None else contact))
+        r.scene = C.pointer(self._scene.c)
+        self.c = r
+
+    def rollout(self, state0, dt, steps, traj=False):
+        s0 = _d(state0)
+        sS = np.zeros(13)
+        tr = np.zeros((steps + 1, 13)) if traj else None
+        lib().orc_rigid_rollout(C.byref(self.c), _p(s0), dt, steps, _p(sS), _p(tr))
+        return (sS, tr) if traj else sS
+
+    def loss_grad(self, state0, dt, steps, target=None, seed=None):
+        """(L, {"state0" [13], "mass", "inertia" [6], "contact" [4]}) for
+        L = sum_k |X_k(S) - target_k|^2 + seed . state(S)."""
+        s0, tg, sd = _d(state0), _d(target), _d(seed)
+        L = C.c_double(0.0)
+        g = {"state0": np.zeros(13), "mass": np.zeros(1), "inertia": np.zeros(6), "contact": np.zeros(4)}
+        lib().orc_rigid_loss_grad(C.byref(self.c), _p(s0), dt, steps, _p(tg), _p(sd), C.byref(L),
+                                  _p(g["state0"]), _p(g["mass"]), _p(g["inertia"]), _p(g["contact"]))
+        g["mass"] = float(g["mass"][0])
+        return L.value, g
+
+    def loss_dir(self, state0, dt, steps, target=None, seed=None, d_state0=None, d_mass=0.0, d_inertia=None,
+                 d_contact=None):
+        s0, tg, sd = _d(state0), _d(target), _d(seed)
+        ds, di, dc = _d(d_state0), _d(d_inertia), _d(d_contact)
+        L, dL = C.c_double(0.0), C.c_double(0.0)
+        lib().orc_rigid_loss_dir(C.byref(self.c), _p(s0), dt, steps, _p(tg), _p(sd), _p(ds), float(d_mass),
+                                 _p(di), _p(dc), C.byref(L), C.byref(dL))
+        return L.value, dL.value

@@ -389,6 +389,91 @@ class RenderSpec:
     bg: tuple = (1.0, 1.0, 1.0)
 
 
+# ---------------------------------------------------------------------------
+# rigid bodies
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class RigidBody:
+    """A rigid body: contact points and surface triangles in the body frame
+    (about the centre of mass), mass, body-frame inertia (Ixx, Iyy, Izz, Ixy,
+    Ixz, Iyz), contact parameters (ke, kd, kf, mu), the initial state
+    (x, quaternion (w, x, y, z), v, omega) and the scene it moves in."""
+    name: str
+    points: np.ndarray
+    faces: np.ndarray
+    mass: float
+    inertia: tuple
+    contact: tuple
+    state0: np.ndarray
+    scene: Contact = dataclasses.field(default_factory=lambda: Contact(plane_on=True))
+    gravity: tuple = (0.0, -9.81, 0.0)
+    dt: float = 1.0e-3
+    steps: int = 200
+
+
+def box_points(size, n: int = 2):
+    """Points of an n x n x n lattice on the surface of a box of `size` centred
+    at the origin (n = 2: the 8 corners), and the box's 12 surface triangles
+    over its corners (indices into the first 8 points, which are the
+    corners)."""
+    a = np.asarray(size, dtype=np.float64) / 2
+    corners = np.array([[sx, sy, sz] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)], dtype=np.float64) * a
+    pts = [corners]
+    if n > 2:
+        g = np.linspace(-1.0, 1.0, n)
+        lat = np.array([[i, j, k] for i in g for j in g for k in g])
+        on_surface = np.isclose(np.abs(lat), 1.0).any(axis=1)
+        is_corner = np.isclose(np.abs(lat), 1.0).all(axis=1)
+        pts.append(lat[on_surface & ~is_corner] * a)
+    # corner index = 4 (x > 0) + 2 (y > 0) + (z > 0); outward-wound faces
+    quads = [(0, 1, 3, 2), (4, 6, 7, 5), (0, 4, 5, 1), (2, 3, 7, 6), (0, 2, 6, 4), (1, 5, 7, 3)]
+    faces = np.array([t for q in quads for t in ((q[0], q[1], q[2]), (q[0], q[2], q[3]))], dtype=np.int32)
+    return np.vstack(pts), faces
+
+
+def box_body(size=(0.2, 0.2, 0.2), density=125.0, n: int = 2, contact=(1.0e4, 10.0, 100.0, 0.5),
+             x0=(0.0, 0.5, 0.0), q0=(1.0, 0.0, 0.0, 0.0), v0=(0.0, 0.0, 0.0), w0=(0.0, 0.0, 0.0),
+             dt: float = 1.0e-3, steps: int = 200, name: str = "box") -> RigidBody:
+    """A solid box: mass = density x volume, inertia m/12 (b^2 + c^2, ...)
+    about its centre."""
+    pts, faces = box_points(size, n)
+    a, b, c = size
+    m = density * a * b * c
+    I = (m / 12 * (b * b + c * c), m / 12 * (a * a + c * c), m / 12 * (a * a + b * b), 0.0, 0.0, 0.0)
+    q = np.asarray(q0, dtype=np.float64)
+    q = q / np.linalg.norm(q)
+    state0 = np.concatenate([x0, q, v0, w0]).astype(np.float64)
+    return RigidBody(name=name, points=pts, faces=faces, mass=m, inertia=I, contact=tuple(contact), state0=state0,
+                     dt=dt, steps=steps)
+
+
+def rigid_batch(n_bodies: int = 1024, seed: int = 0, n: int = 5, steps: int = 300) -> List[RigidBody]:
+    """Seeded boxes in the ranges of the paper's rigid experiments (App. E:
+    densities 2-12 kg/m^3 of boxes up to ~2 m, friction 0.2-1.0, random
+    poses and velocities; contact stiffness chosen per body so the resting
+    penetration is ~1 mm at dt 1e-3), n x n x n surface lattice points."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_bodies):
+        size = tuple(rng.uniform(0.5, 2.0, 3))
+        dens = rng.uniform(2.0, 12.0)
+        m = dens * size[0] * size[1] * size[2]
+        ke = m * 9.81 / 4 / 1e-3
+        kd = 2.0 * math.sqrt(ke * m / 4) * 0.3
+        kf = rng.uniform(1.0, 500.0) * m
+        mu = rng.uniform(0.2, 1.0)
+        ax = rng.normal(size=3)
+        ang = rng.uniform(0, math.pi)
+        q0 = np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * ax / np.linalg.norm(ax)])
+        x0 = (rng.uniform(-6.5, 6.5), rng.uniform(1.5, 3.0), rng.uniform(-6.5, 6.5))
+        v0 = rng.uniform(-2.0, 2.0, 3)
+        w0 = rng.uniform(-3.0, 3.0, 3)
+        out.append(box_body(size, dens, n=n, contact=(ke, kd, kf, mu), x0=x0, q0=q0, v0=v0, w0=w0, steps=steps,
+                            name=f"box{i}"))
+    return out
+
+
 def block_dims(n_tets_target: float, rng) -> tuple:
     """Integer a x b x c (>= 1) with aspect ratios in [0.5, 2] and 5abc ~ target."""
     r1, r2 = np.exp(rng.uniform(math.log(0.5), math.log(2.0), 2))
