@@ -820,6 +820,8 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
 // law is the particles' (section 4) at X_k = x + R p_k with velocity
 // V_k = v + omega x (R p_k); the world inertia is R I_b R^T; the step is
 //   v+ = v + dt (g + F/m),  omega+ = omega + dt I_w^-1 (tau - omega x I_w omega),
+// with I_w^-1 applied as R I_b^-1 R^T (equal for a unit quaternion; the
+// same function for any r, so the gradient in r is unambiguous),
 //   x+ = x + dt v+,  r+ = normalise(r + dt/2 (0, omega+) (x) r)
 // (velocities first, then positions with the new velocities, as App. B's
 // g(s-, s+, theta); the quaternion derivative is 1/2 omega (x) r).
@@ -867,7 +869,8 @@ void rigid_step_t(const orc_rigid* b, const T* s, const T* p, double dt, T* o) {
         vcross(d, fc, td);
         for (int i = 0; i < 3; ++i) { F[i] += fc[i]; tau[i] += td[i]; }
     }
-    // I_w = R I_b R^T;  alpha = I_w^-1 (tau - omega x I_w omega)
+    // I_w = R I_b R^T and I_w^-1 = R I_b^-1 R^T (a rotation R):
+    // alpha = R I_b^-1 R^T (tau - omega x R I_b R^T omega)
     T Iw[3][3];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
@@ -876,11 +879,13 @@ void rigid_step_t(const orc_rigid* b, const T* s, const T* p, double dt, T* o) {
                 for (int c = 0; c < 3; ++c) acc += R[i][a] * Ib[a][c] * R[j][c];
             Iw[i][j] = acc;
         }
-    T L[3], wL[3], h[3], alpha[3];
+    T L[3], wL[3], h[3], alpha[3], hb[3], ab[3];
     for (int i = 0; i < 3; ++i) L[i] = Iw[i][0] * w[0] + Iw[i][1] * w[1] + Iw[i][2] * w[2];
     vcross(w, L, wL);
     for (int i = 0; i < 3; ++i) h[i] = tau[i] - wL[i];
-    mat3_solve(Iw, h, alpha);
+    for (int i = 0; i < 3; ++i) hb[i] = R[0][i] * h[0] + R[1][i] * h[1] + R[2][i] * h[2];
+    mat3_solve(Ib, hb, ab);
+    for (int i = 0; i < 3; ++i) alpha[i] = R[i][0] * ab[0] + R[i][1] * ab[1] + R[i][2] * ab[2];
     T* xo = o; T* ro = o + 3; T* vo = o + 7; T* wo = o + 10;
     for (int i = 0; i < 3; ++i) {
         vo[i] = v[i] + dt * (sc->gravity[i] + F[i] / m);
