@@ -245,6 +245,58 @@ typedef struct gs_air {
     float wind[3];
 } gs_air;
 GS_API gs_status gs_mesh_set_air(gs_mesh* mesh, const gs_air* air, void* stream);
+/* ---- rigid bodies (App. A.1 "Rigid Bodies") ---------------------------
+ * State of a body, 13 floats: x (centre of mass), r = (w, x, y, z) unit
+ * quaternion (world from body), v, omega (world frame).  Newton-Euler with
+ * the compliant contact model (the particles' law, gs_contact) acting at
+ * the body's contact points, and semi-implicit Euler (App. B):
+ *   v+ = v + dt (g + F/m),  omega+ = omega + dt R I_b^-1 R^T (tau - omega x R I_b R^T omega),
+ *   x+ = x + dt v+,  r+ = normalise(r + dt/2 (0, omega+) (x) r).
+ * Design parameters per body: mass, body-frame inertia about the centre of
+ * mass (Ixx, Iyy, Izz, Ixy, Ixz, Iyz), contact (ke, kd, kf, mu).  Bodies do
+ * not interact; one launch runs a whole rollout of every body. */
+typedef struct gs_rigid_desc {
+    int n_bodies;
+    const int* point_begin; /* HOST [n_bodies + 1]: body b's points are [point_begin[b], point_begin[b+1]) */
+    const float* points;    /* HOST [n_points][3] body frame, about the centre of mass */
+    const float* mass;      /* HOST [n_bodies], > 0 */
+    const float* inertia;   /* HOST [n_bodies][6], positive definite */
+    const float* contact;   /* HOST [n_bodies][4] ke, kd, kf, mu (>= 0) */
+    gs_contact scene;       /* plane / sphere of the scene (its ke, kd, kf, mu_f unused) */
+    float gravity[3];
+} gs_rigid_desc;
+typedef struct gs_rigid gs_rigid;
+/* Caller-owned DEVICE outputs, each nullable. */
+typedef struct gs_rigid_grads {
+    float* d_state0;   /* [n_bodies][13] */
+    double* d_mass;    /* [n_bodies] */
+    double* d_inertia; /* [n_bodies][6] */
+    double* d_contact; /* [n_bodies][4] */
+} gs_rigid_grads;
+/* Copies everything.  GS_EINVAL for bad offsets, non-finite points,
+ * non-positive mass, an inertia that is not positive definite, negative
+ * contact parameters or a non-unit plane normal. */
+GS_API gs_status gs_rigid_create(gs_ctx* ctx, const gs_rigid_desc* desc, gs_rigid** out);
+GS_API void gs_rigid_destroy(gs_rigid* r);
+/* New per-body parameters (HOST arrays as in the description; nullable = unchanged). Synchronous. */
+GS_API gs_status gs_rigid_set_params(gs_rigid* r, const float* mass, const float* inertia, const float* contact,
+                                     void* stream);
+/* S steps from DEVICE state0 [n_bodies][13]; stores every state for the
+ * adjoint; the final state into DEVICE stateS (nullable).  A non-finite
+ * state sets the sticky flag gs_rigid_check reports. */
+GS_API gs_status gs_rigid_rollout(gs_rigid* r, float dt, int S, const float* state0, float* stateS, void* stream);
+/* Reverse of the last rollout (GS_ESTATE without one) for the seed
+ * dL/dstate(S) (DEVICE [n_bodies][13], nullable = 0).  Parameter
+ * gradients are FP64 sums over the steps. */
+GS_API gs_status gs_rigid_adjoint(gs_rigid* r, const float* dL_dstateS, gs_rigid_grads* grads, void* stream);
+/* World positions x + R p of every point at DEVICE state [n_bodies][13] into DEVICE points [n_points][3]. */
+GS_API gs_status gs_rigid_points(gs_rigid* r, const float* state, float* points, void* stream);
+/* dL/dstate [n_bodies][13] (DEVICE, written; velocity entries 0) from dL/dpoints [n_points][3]. */
+GS_API gs_status gs_rigid_points_backward(gs_rigid* r, const float* state, const float* dL_dpoints, float* dL_dstate,
+                                          void* stream);
+/* GS_OK, or GS_ENONFINITE if a rollout produced a non-finite state (reset clears). */
+GS_API gs_status gs_rigid_check(gs_rigid* r, int reset, void* stream);
+
 /* ---- differentiable soft rasteriser ------------------------------------
  * The rendering stage of Sec. 2 ("Differentiable rendering engine"): the
  * simulated surface becomes an image through SoftRas-style sigmoid edges and

@@ -165,3 +165,77 @@ class Render(torch.autograd.Function):
 def render(raster, x, colours):
     """Differentiable image [H, W, 4] (RGB, silhouette) of `raster`'s triangles."""
     return Render.apply(raster, x, colours)
+
+
+class RigidRollout(torch.autograd.Function):
+    """Rollout of a set of rigid bodies (App. A.1 "Rigid Bodies") as an
+    autograd operation: final states [B, 13] from initial states and the
+    per-body mass [B], inertia [B, 6] and contact parameters [B, 4]; backward
+    runs gs_rigid_adjoint.  A later rollout on the same body set makes this
+    one's backward recompute its states."""
+
+    @staticmethod
+    def _run(rigid, dt, steps, state0, mass, inertia, contact):
+        rigid.set_params(mass=mass.detach().double().cpu().numpy(), inertia=inertia.detach().double().cpu().numpy(),
+                         contact=contact.detach().double().cpu().numpy())
+        sS = torch.empty_like(state0)
+        rigid.rollout(dt, steps, state0, sS)
+        return sS
+
+    @staticmethod
+    def forward(ctx, rigid, dt, steps, state0, mass, inertia, contact):
+        s0 = state0.detach().to(torch.float32).contiguous()
+        sS = RigidRollout._run(rigid, dt, steps, s0, mass, inertia, contact)
+        ctx.rigid = rigid
+        ctx.token = _claim(rigid)
+        ctx.replay = (dt, steps, s0, mass.detach(), inertia.detach(), contact.detach())
+        ctx.dtypes = (state0.dtype, mass.dtype, inertia.dtype, contact.dtype)
+        return sS
+
+    @staticmethod
+    def backward(ctx, gS):
+        r = ctx.rigid
+        if getattr(r, "_rollout_token", None) != ctx.token:
+            dt, steps, s0, m, I, c = ctx.replay
+            RigidRollout._run(r, dt, steps, s0, m, I, c)
+            r._rollout_token = ctx.token
+        dev = gS.device
+        B = r.n_bodies
+        g = {"d_state0": torch.zeros(B, 13, dtype=torch.float32, device=dev),
+             "d_mass": torch.zeros(B, dtype=torch.float64, device=dev),
+             "d_inertia": torch.zeros(B, 6, dtype=torch.float64, device=dev),
+             "d_contact": torch.zeros(B, 4, dtype=torch.float64, device=dev)}
+        r.adjoint(g, seed=gS.detach().to(torch.float32).contiguous())
+        ts, tm, ti, tc = ctx.dtypes
+        return (None, None, None, g["d_state0"].to(ts), g["d_mass"].to(tm), g["d_inertia"].to(ti),
+                g["d_contact"].to(tc))
+
+
+def rigid_rollout(rigid, dt, steps, state0, mass, inertia, contact):
+    """Differentiable rollout of a body set; see RigidRollout."""
+    return RigidRollout.apply(rigid, dt, steps, state0, mass, inertia, contact)
+
+
+class RigidPoints(torch.autograd.Function):
+    """World positions [n_points, 3] of the bodies' points at states [B, 13]."""
+
+    @staticmethod
+    def forward(ctx, rigid, state):
+        s = state.detach().to(torch.float32).contiguous()
+        out = torch.empty(rigid.n_points, 3, dtype=torch.float32, device=s.device)
+        rigid.points(s, out)
+        ctx.rigid = rigid
+        ctx.save_for_backward(s)
+        return out
+
+    @staticmethod
+    def backward(ctx, gX):
+        (s,) = ctx.saved_tensors
+        ds = torch.empty_like(s)
+        ctx.rigid.points_backward(s, gX.detach().to(torch.float32).contiguous(), ds)
+        return None, ds
+
+
+def rigid_points(rigid, state):
+    return RigidPoints.apply(rigid, state)
+

@@ -60,6 +60,15 @@ class gs_raster_desc(C.Structure):
                 ("bg", C.c_float * 3)]
 
 
+class gs_rigid_desc(C.Structure):
+    _fields_ = [("n_bodies", C.c_int), ("point_begin", C.POINTER(C.c_int)), ("points", _fp), ("mass", _fp),
+                ("inertia", _fp), ("contact", _fp), ("scene", gs_contact), ("gravity", C.c_float * 3)]
+
+
+class gs_rigid_grads(C.Structure):
+    _fields_ = [("d_state0", _vp), ("d_mass", _vp), ("d_inertia", _vp), ("d_contact", _vp)]
+
+
 class gs_air(C.Structure):
     _fields_ = [("k_drag", C.c_float), ("k_lift", C.c_float), ("wind", C.c_float * 3)]
 
@@ -145,6 +154,14 @@ _PROTOS = {
     "gs_result_free": (None, [C.POINTER(gs_result)]),
     "gs_selftest_bounded_wait": (C.c_int, [C.c_int, C.POINTER(C.c_int), _vp]),
     "gs_raster_create": (C.c_int, [_vp, C.POINTER(gs_raster_desc), C.POINTER(_vp)]),
+    "gs_rigid_create": (C.c_int, [_vp, C.POINTER(gs_rigid_desc), C.POINTER(_vp)]),
+    "gs_rigid_destroy": (None, [_vp]),
+    "gs_rigid_set_params": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "gs_rigid_rollout": (C.c_int, [_vp, C.c_float, C.c_int, _vp, _vp, _vp]),
+    "gs_rigid_adjoint": (C.c_int, [_vp, _vp, C.POINTER(gs_rigid_grads), _vp]),
+    "gs_rigid_points": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "gs_rigid_points_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "gs_rigid_check": (C.c_int, [_vp, C.c_int, _vp]),
     "gs_raster_destroy": (None, [_vp]),
     "gs_raster_set_camera": (C.c_int, [_vp, C.POINTER(gs_camera)]),
     "gs_raster_forward": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -435,6 +452,85 @@ class Batch:
         try:
             self.close()
         except Exception:  # noqa: BLE001
+            pass
+
+
+def contact_struct(con) -> "gs_contact":
+    """gs_contact from an ``inputs.Contact``."""
+    c = gs_contact()
+    c.ke, c.kd, c.kf, c.mu_f = float(con.ke), float(con.kd), float(con.kf), float(con.mu_f)
+    c.plane_on = int(con.plane_on)
+    c.plane_n = (C.c_float * 3)(*[float(v) for v in con.plane_n])
+    c.plane_h = float(con.plane_h)
+    c.sphere_on = int(con.sphere_on)
+    c.sphere_c = (C.c_float * 3)(*[float(v) for v in con.sphere_c])
+    c.sphere_r = float(con.sphere_r)
+    return c
+
+
+class Rigid:
+    """A gs_rigid: a set of independent rigid bodies (``inputs.RigidBody``
+    list; they share the scene and gravity of the first)."""
+
+    def __init__(self, ctx: Context, bodies):
+        self.ctx = ctx
+        self.bodies = list(bodies)
+        nb = len(self.bodies)
+        pb = np.zeros(nb + 1, dtype=np.int32)
+        for b, body in enumerate(self.bodies):
+            pb[b + 1] = pb[b] + len(body.points)
+        self._pb = pb
+        self._pts = np.ascontiguousarray(np.vstack([b.points for b in self.bodies]), dtype=np.float32)
+        self._m = np.array([b.mass for b in self.bodies], dtype=np.float32)
+        self._I = np.ascontiguousarray([b.inertia for b in self.bodies], dtype=np.float32)
+        self._c = np.ascontiguousarray([b.contact for b in self.bodies], dtype=np.float32)
+        d = gs_rigid_desc()
+        d.n_bodies = nb
+        d.point_begin = pb.ctypes.data_as(C.POINTER(C.c_int))
+        d.points = self._pts.ctypes.data_as(_fp)
+        d.mass = self._m.ctypes.data_as(_fp)
+        d.inertia = self._I.ctypes.data_as(_fp)
+        d.contact = self._c.ctypes.data_as(_fp)
+        d.scene = contact_struct(self.bodies[0].scene)
+        d.gravity = (C.c_float * 3)(*[float(g) for g in self.bodies[0].gravity])
+        self.h = _vp()
+        check(load().gs_rigid_create(ctx.h, C.byref(d), C.byref(self.h)))
+        self.n_bodies, self.n_points = nb, int(pb[-1])
+
+    def state0(self):
+        return np.ascontiguousarray(np.stack([b.state0 for b in self.bodies]), dtype=np.float32)
+
+    def set_params(self, mass=None, inertia=None, contact=None, stream=None):
+        def host(a, shape):
+            return None if a is None else np.ascontiguousarray(np.asarray(a, dtype=np.float32).reshape(shape))
+        m, I, c = host(mass, (-1,)), host(inertia, (-1, 6)), host(contact, (-1, 4))
+        check(load().gs_rigid_set_params(self.h, _ptr(m), _ptr(I), _ptr(c), _stream(stream)))
+
+    def rollout(self, dt, steps, state0, stateS=None, stream=None):
+        check(load().gs_rigid_rollout(self.h, float(dt), int(steps), _ptr(state0), _ptr(stateS), _stream(stream)))
+
+    def adjoint(self, grads: dict, seed=None, stream=None):
+        g = gs_rigid_grads(**{k: _ptr(v) for k, v in grads.items()})
+        check(load().gs_rigid_adjoint(self.h, _ptr(seed), C.byref(g), _stream(stream)))
+
+    def points(self, state, out, stream=None):
+        check(load().gs_rigid_points(self.h, _ptr(state), _ptr(out), _stream(stream)))
+
+    def points_backward(self, state, dpoints, dstate, stream=None):
+        check(load().gs_rigid_points_backward(self.h, _ptr(state), _ptr(dpoints), _ptr(dstate), _stream(stream)))
+
+    def check_finite(self, reset=False, stream=None) -> int:
+        return load().gs_rigid_check(self.h, int(reset), _stream(stream))
+
+    def close(self):
+        if self.h:
+            load().gs_rigid_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
             pass
 
 

@@ -450,9 +450,12 @@ def box_body(size=(0.2, 0.2, 0.2), density=125.0, n: int = 2, contact=(1.0e4, 10
 
 def rigid_batch(n_bodies: int = 1024, seed: int = 0, n: int = 5, steps: int = 300) -> List[RigidBody]:
     """Seeded boxes in the ranges of the paper's rigid experiments (App. E:
-    densities 2-12 kg/m^3 of boxes up to ~2 m, friction 0.2-1.0, random
-    poses and velocities; contact stiffness chosen per body so the resting
-    penetration is ~1 mm at dt 1e-3), n x n x n surface lattice points."""
+    densities 2-12 kg/m^3 of boxes up to ~2 m, friction coefficient 0.2-1.0,
+    random poses and velocities).  The paper's contact stiffnesses (1-500)
+    are in unstated units; here k_e makes four corners rest 1 mm deep,
+    k_d damps at 0.3 of critical, and k_f is 1-500 x m/100 N s/m so that
+    explicit Euler at dt 1e-3 stays stable with a whole face (n^2 points) in
+    contact.  n x n x n surface lattice points."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n_bodies):
@@ -461,7 +464,7 @@ def rigid_batch(n_bodies: int = 1024, seed: int = 0, n: int = 5, steps: int = 30
         m = dens * size[0] * size[1] * size[2]
         ke = m * 9.81 / 4 / 1e-3
         kd = 2.0 * math.sqrt(ke * m / 4) * 0.3
-        kf = rng.uniform(1.0, 500.0) * m
+        kf = rng.uniform(1.0, 500.0) * m / 100.0
         mu = rng.uniform(0.2, 1.0)
         ax = rng.normal(size=3)
         ang = rng.uniform(0, math.pi)
