@@ -60,7 +60,7 @@ def parse():
                     help="block: library defaults instead of the autotuner's patch shape and K")
     ap.add_argument("--cpu-steps", type=int, default=4,
                     help="oracle steps in the CPU sample (about 3 s each on one core for block64)")
-    ap.add_argument("--workload", default="block", choices=["block", "bar", "cloth", "batch", "serve", "control", "cloth_air", "render"],
+    ap.add_argument("--workload", default="block", choices=["block", "bar", "cloth", "batch", "serve", "control", "cloth_air", "render", "rigid"],
                     help="block: the 1.3M-tet solid (default line); the others measure the remaining workloads")
     ap.add_argument("--meshes", type=int, default=512, help="batch: number of meshes")
     ap.add_argument("--rates", default="10,20,50,100,200,500", help="serve: arrival rates (req/s)")
@@ -859,8 +859,50 @@ def _pair_count(u, v, z, cam, spec):
     return int(n[ok].sum())
 
 
+def workload_rigid(args):
+    """Rigid bodies (App. A.1): 16,384 seeded boxes (98 surface contact
+    points each, the ranges of the paper's rigid experiments) dropped on the
+    ground, 300 steps, rollout + adjoint in one launch each; and the paper's
+    mass loss landscape (a unit-mass cube after a known impulse, 6 rendered
+    frames at 96^2, 10 guessed masses)."""
+    import torch
+    from paper_2104_02646_gb300 import autograd as A
+    from paper_2104_02646_gb300 import gradsim as gs
+    from paper_2104_02646_gb300 import inputs as I
+    gs.load()
+    dev = torch.device("cuda", 0)
+    ctx = gs.Context(0)
+    S, nb = 300, 16384
+    bodies = I.rigid_batch(nb, seed=0, n=5, steps=S)
+    rig = gs.Rigid(ctx, bodies)
+    s0 = torch.tensor(rig.state0(), device=dev)
+    sS = torch.empty_like(s0)
+    g = {"d_state0": torch.zeros(nb, 13, device=dev), "d_mass": torch.zeros(nb, dtype=torch.float64, device=dev),
+         "d_inertia": torch.zeros(nb, 6, dtype=torch.float64, device=dev),
+         "d_contact": torch.zeros(nb, 4, dtype=torch.float64, device=dev)}
+    seed = torch.ones(nb, 13, device=dev)
+
+    def run():
+        rig.rollout(1e-3, S, s0, sS)
+        rig.adjoint(g, seed=seed)
+
+    for _ in range(args.warmup):
+        run()
+    t = min(_events_ms(run) for _ in range(args.steps))
+    t_f = min(_events_ms(lambda: rig.rollout(1e-3, S, s0, sS)) for _ in range(args.steps))
+    line = {"metric": "rigid fwd+adjoint body-steps/s", "workload": "rigid16384", "value": nb * S / (t / 1e3),
+            "unit": "body-steps/s", "ms": t, "ms_forward": t_f,
+            "contact_point_steps_per_s": rig.n_points * S / (t / 1e3), "dtype": "f32", "data": "synthetic",
+            "finite": rig.check_finite() == gs.GS_OK,
+            "config": {"bodies": nb, "points_per_body": rig.n_points // nb, "steps": S, "dt": 1e-3,
+                       "launches": "1 rollout + 1 adjoint"}}
+    print(json.dumps(line), flush=True)
+    rig.close()
+
+
 WORKLOADS = {"bar": workload_bar, "cloth": workload_cloth, "batch": workload_batch, "serve": workload_serve,
-             "control": workload_control, "cloth_air": workload_cloth_air, "render": workload_render}
+             "control": workload_control, "cloth_air": workload_cloth_air, "render": workload_render,
+             "rigid": workload_rigid}
 
 if __name__ == "__main__":
     main()

@@ -477,6 +477,20 @@ def rigid_batch(n_bodies: int = 1024, seed: int = 0, n: int = 5, steps: int = 30
     return out
 
 
+def hanging_beam(mu: float = 1000.0, steps: int = 300, cells=(8, 2, 2), h: float = 0.025,
+                 density: float = 100.0, dt: float = 1.0e-3) -> Problem:
+    """The beam of the paper's deformable loss landscape (Sec. 3: a beam
+    hanging under gravity, Lame parameters mu = lambda = 1000): an 8 x 2 x 2
+    cell tet beam of 0.025 m cells, pinned at its x = 0 face, mu = lambda =
+    `mu`, density 100 kg/m^3, no ground."""
+    X, tets = hex_block(*cells, h=h, origin=(0.0, 0.5, 0.0))
+    E = tets.shape[0]
+    pin = (X[:, 0] < 1e-9).astype(np.uint8)
+    return Problem(name="hanging_beam", kind=TET, X=X, elems=tets, mu=np.full(E, float(mu)),
+                   lam=np.full(E, float(mu)), rho=np.full(E, density), pinned=pin,
+                   contact=Contact(plane_on=False), dt=dt, steps=steps)
+
+
 def block_dims(n_tets_target: float, rng) -> tuple:
     """Integer a x b x c (>= 1) with aspect ratios in [0.5, 2] and 5abc ~ target."""
     r1, r2 = np.exp(rng.uniform(math.log(0.5), math.log(2.0), 2))
