@@ -11,8 +11,8 @@
 // rollout in one launch: lanes take the contact points, a fixed xor tree
 // sums force and torque, and every lane integrates the (identical) body
 // state.  The rollout stores every state; the adjoint runs the steps in
-// reverse in one launch, recomputing each step's contacts, with the
-// parameter gradients summed in FP64.  Deterministic; no atomics.
+// reverse in one launch, recomputing each step's contacts in one pass,
+// with the parameter gradients summed in FP64.  Deterministic; no atomics.
 
 #include <cuda_runtime.h>
 
@@ -330,6 +330,10 @@ struct RigidGradOut {
     double* d_contact; // [nb][4]
 };
 
+// One pass over the points per reverse step: the stored next state holds
+// omega+ and r+, so dL/dF and dL/dtau are known before the contacts are
+// evaluated; F and tau (the same sums, in the same order, as the forward's)
+// come out of the same pass and finish the terms that need them.
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     k_rigid_adjoint(const int* __restrict__ pbeg, const float* __restrict__ params, const float* __restrict__ pts,
                     Scene sc, int nb, const float* __restrict__ traj, float dt, int S, const float* __restrict__ seed,
@@ -338,33 +342,44 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     const int lane = threadIdx.x & 31;
     if (b >= nb) return;
     const Body B = load_body(pbeg, params, b);
+    float Ib[9], Binv[9];
+    sym_full(B.I, Ib);
+    inv3(Ib, Binv);
     float lam[13];
     for (int i = 0; i < 13; ++i) lam[i] = seed ? seed[13 * (size_t)b + i] : 0.f;
     double gm = 0.0, gI[6] = {0, 0, 0, 0, 0, 0}, gc[4] = {0, 0, 0, 0};
     for (int n = S - 1; n >= 0; --n) {
         float s[13], o[13];
         load_state(traj + ((size_t)n * nb + b) * kStateStride, s);
-        StepVals V;
-        step_forward(sc, B, pts, s, dt, lane, V, o);
+        load_state(traj + ((size_t)(n + 1) * nb + b) * kStateStride, o);
         const float* r = s + 3;
         const float* w = s + 10;
-        // r+ = q / |q|
+        const float* wo = o + 10;
+        float R[9];
+        quat_rot(r, R);
+        // q = r + dt/2 (0, wo) (x) r, r+ = q / |q|
+        float q[4];
+        {
+            float ax[3];
+            cross(wo, r + 1, ax);
+            q[0] = r[0] - 0.5f * dt * dot(wo, r + 1);
+            for (int i = 0; i < 3; ++i) q[1 + i] = r[1 + i] + 0.5f * dt * (r[0] * wo[i] + ax[i]);
+        }
+        const float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
         float qb[4];
         {
             float rr = 0.f;
             for (int i = 0; i < 4; ++i) rr += lam[3 + i] * o[3 + i];
-            for (int i = 0; i < 4; ++i) qb[i] = (lam[3 + i] - rr * o[3 + i]) / V.qn;
+            for (int i = 0; i < 4; ++i) qb[i] = (lam[3 + i] - rr * o[3 + i]) / qn;
         }
         float rb[4], wob[3], xb[3], vb[3], wb[3], Rb[9];
         for (int i = 0; i < 9; ++i) Rb[i] = 0.f;
-        // q = r + dt/2 (0, wo) (x) r
         {
             const float h = 0.5f * dt;
-            float t[3];
-            cross(V.wo, qb + 1, t);
-            rb[0] = qb[0] + h * dot(V.wo, qb + 1);
-            for (int i = 0; i < 3; ++i) rb[1 + i] = qb[1 + i] - h * V.wo[i] * qb[0] - h * t[i];
-            float u[3];
+            float t[3], u[3];
+            cross(wo, qb + 1, t);
+            rb[0] = qb[0] + h * dot(wo, qb + 1);
+            for (int i = 0; i < 3; ++i) rb[1 + i] = qb[1 + i] - h * wo[i] * qb[0] - h * t[i];
             cross(r + 1, qb + 1, u);
             for (int i = 0; i < 3; ++i) wob[i] = lam[10 + i] - h * r[1 + i] * qb[0] + h * (r[0] * qb[1 + i] + u[i]);
         }
@@ -378,82 +393,97 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
             wb[i] = wob[i];
             alb[i] = dt * wob[i];
         }
-        gm += -(double)dt * (double)dot(V.F, vob) / ((double)B.m * (double)B.m);
-        // alpha = R bb, bb = Binv a, a = R^T h
-        float IbB[9];  // dL/d(I_b) as a full matrix
+        // alpha = R Binv R^T h: dL/dh = R Binv R^T dL/dalpha = dL/dtau
+        float bbb[3], ab[3], hb[3];
+        matTvec(R, alb, bbb);
+        matvec(Binv, bbb, ab);
+        matvec(R, ab, hb);
+        // L = R Ib R^T w (independent of the contacts); h = tau - w x L
+        float e[3], c[3], L[3];
+        matTvec(R, w, e);
+        matvec(Ib, e, c);
+        matvec(R, c, L);
+        float IbB[9];
         {
-            float bbb[3], ab[3], hb[3];
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) Rb[3 * i + j] += alb[i] * V.bb[j];
-            matTvec(V.R, alb, bbb);
-            matvec(V.Binv, bbb, ab);  // Binv symmetric
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) IbB[3 * i + j] = -ab[i] * V.bb[j];
-            matvec(V.R, ab, hb);
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) Rb[3 * i + j] += V.h[i] * ab[j];
-            // h = tau - w x L
-            float Lb[3], t[3];
-            cross(w, hb, Lb);      // dL/dL = w x hb
-            cross(V.L, hb, t);     // w gets -(L x hb)
+            float Lb[3], t[3], cb[3], eb[3], t2[3];
+            cross(w, hb, Lb);
+            cross(L, hb, t);
             for (int i = 0; i < 3; ++i) wb[i] -= t[i];
-            // L = R c, c = Ib e, e = R^T w
-            float cb[3], eb[3];
             for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) Rb[3 * i + j] += Lb[i] * V.c[j];
-            matTvec(V.R, Lb, cb);
+                for (int j = 0; j < 3; ++j) Rb[3 * i + j] += Lb[i] * c[j];
+            matTvec(R, Lb, cb);
             for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) IbB[3 * i + j] += cb[i] * V.e[j];
-            matvec(V.Ib, cb, eb);  // Ib symmetric
+                for (int j = 0; j < 3; ++j) IbB[3 * i + j] = cb[i] * e[j];
+            matvec(Ib, cb, eb);
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j) Rb[3 * i + j] += w[i] * eb[j];
-            float t2[3];
-            matvec(V.R, eb, t2);
+            matvec(R, eb, t2);
             for (int i = 0; i < 3; ++i) wb[i] += t2[i];
-            // per point: F = sum fc, tau = sum d x fc
-            float taub[3] = {hb[0], hb[1], hb[2]};
-            float acc[22];  // x(3) v(3) w(3) R(9) contact(4), this lane's points
-            for (int i = 0; i < 22; ++i) acc[i] = 0.f;
-            for (int k = B.p0 + lane; k < B.p1; k += 32) {
-                const float p[3] = {pts[3 * (size_t)k], pts[3 * (size_t)k + 1], pts[3 * (size_t)k + 2]};
-                float d[3], wd[3], X[3], Vv[3], fc[3];
-                matvec(V.R, p, d);
-                cross(w, d, wd);
-                for (int i = 0; i < 3; ++i) {
-                    X[i] = s[i] + d[i];
-                    Vv[i] = s[7 + i] + wd[i];
-                }
-                contact_force(sc, B, X, Vv, fc);
-                float fcb[3], db[3], t3[3];
-                cross(taub, d, t3);
-                for (int i = 0; i < 3; ++i) fcb[i] = Fb[i] + t3[i];
-                cross(fc, taub, db);
-                float Xb[3] = {0.f, 0.f, 0.f}, Vb[3] = {0.f, 0.f, 0.f};
-                contact_adj(sc, B, X, Vv, fcb, Xb, Vb, acc + 18);
-                // X = x + d ; V = v + w x d
-                float t4[3], t5[3];
-                cross(d, Vb, t4);   // w gets d x Vb
-                cross(Vb, w, t5);   // d gets Vb x w
-                for (int i = 0; i < 3; ++i) {
-                    acc[i] += Xb[i];
-                    acc[3 + i] += Vb[i];
-                    acc[6 + i] += t4[i];
-                    db[i] += Xb[i] + t5[i];
-                }
-                // d = R p
-                for (int i = 0; i < 3; ++i)
-                    for (int j = 0; j < 3; ++j) acc[9 + 3 * i + j] += db[i] * p[j];
-            }
-            for (int i = 0; i < 22; ++i) acc[i] = warp_sum(acc[i]);
-            for (int i = 0; i < 3; ++i) {
-                xb[i] += acc[i];
-                vb[i] += acc[3 + i];
-                wb[i] += acc[6 + i];
-            }
-            for (int i = 0; i < 9; ++i) Rb[i] += acc[9 + i];
-            for (int i = 0; i < 4; ++i) gc[i] += (double)acc[18 + i];
         }
-        // I_b is built from (Ixx, Iyy, Izz, Ixy, Ixz, Iyz)
+        // the points: F, tau and the adjoint sums in one pass
+        float f6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float acc[22];  // x(3) v(3) w(3) R(9) contact(4)
+        for (int i = 0; i < 22; ++i) acc[i] = 0.f;
+        for (int k = B.p0 + lane; k < B.p1; k += 32) {
+            const float p[3] = {pts[3 * (size_t)k], pts[3 * (size_t)k + 1], pts[3 * (size_t)k + 2]};
+            float d[3], wd[3], X[3], Vv[3], fc[3], td[3];
+            matvec(R, p, d);
+            cross(w, d, wd);
+            for (int i = 0; i < 3; ++i) {
+                X[i] = s[i] + d[i];
+                Vv[i] = s[7 + i] + wd[i];
+            }
+            contact_force(sc, B, X, Vv, fc);
+            cross(d, fc, td);
+            for (int i = 0; i < 3; ++i) {
+                f6[i] += fc[i];
+                f6[3 + i] += td[i];
+            }
+            float fcb[3], db[3], t3[3];
+            cross(hb, d, t3);
+            for (int i = 0; i < 3; ++i) fcb[i] = Fb[i] + t3[i];
+            cross(fc, hb, db);
+            float Xb[3] = {0.f, 0.f, 0.f}, Vb[3] = {0.f, 0.f, 0.f};
+            contact_adj(sc, B, X, Vv, fcb, Xb, Vb, acc + 18);
+            float t4[3], t5[3];
+            cross(d, Vb, t4);
+            cross(Vb, w, t5);
+            for (int i = 0; i < 3; ++i) {
+                acc[i] += Xb[i];
+                acc[3 + i] += Vb[i];
+                acc[6 + i] += t4[i];
+                db[i] += Xb[i] + t5[i];
+            }
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) acc[9 + 3 * i + j] += db[i] * p[j];
+        }
+        float F[3], tau[3];
+        for (int i = 0; i < 3; ++i) {
+            F[i] = warp_sum(f6[i]);
+            tau[i] = warp_sum(f6[3 + i]);
+        }
+        for (int i = 0; i < 22; ++i) acc[i] = warp_sum(acc[i]);
+        // the terms that need F and tau
+        {
+            float wL[3], h[3], a[3], bb[3];
+            cross(w, L, wL);
+            for (int i = 0; i < 3; ++i) h[i] = tau[i] - wL[i];
+            matTvec(R, h, a);
+            matvec(Binv, a, bb);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    Rb[3 * i + j] += alb[i] * bb[j] + h[i] * ab[j];
+                    IbB[3 * i + j] += -ab[i] * bb[j];
+                }
+            gm += -(double)dt * (double)dot(F, vob) / ((double)B.m * (double)B.m);
+        }
+        for (int i = 0; i < 3; ++i) {
+            xb[i] += acc[i];
+            vb[i] += acc[3 + i];
+            wb[i] += acc[6 + i];
+        }
+        for (int i = 0; i < 9; ++i) Rb[i] += acc[9 + i];
+        for (int i = 0; i < 4; ++i) gc[i] += (double)acc[18 + i];
         gI[0] += IbB[0]; gI[1] += IbB[4]; gI[2] += IbB[8];
         gI[3] += (double)IbB[1] + IbB[3];
         gI[4] += (double)IbB[2] + IbB[6];
