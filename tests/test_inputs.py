@@ -1,0 +1,71 @@
+"""Host-side input generators: counts, structure and ranges of the seeded
+workloads (no physics; CPU only)."""
+import collections
+import math
+
+import numpy as np
+
+from paper_2104_02646_gb300 import inputs as I
+
+
+def test_surface_faces_form_a_closed_oriented_surface():
+    for dims in ((1, 1, 1), (3, 2, 4)):
+        X, tets = I.hex_block(*dims, h=0.1)
+        F = I.surface_faces(tets)
+        a, b, c = dims
+        assert len(F) == 4 * (a * b + b * c + c * a)
+        # every directed edge appears once and its reverse once: closed and consistently oriented
+        directed = collections.Counter()
+        for f in F:
+            for i in range(3):
+                directed[(f[i], f[(i + 1) % 3])] += 1
+        assert all(v == 1 for v in directed.values())
+        assert all(directed[(q, p)] == 1 for (p, q) in directed)
+        # enclosed volume by the divergence theorem equals the block's
+        vol = sum(np.dot(X[f[0]], np.cross(X[f[1]], X[f[2]])) for f in F) / 6.0
+        assert abs(vol - a * b * c * 1e-3) < 1e-12
+
+
+def test_box_points_and_inertia():
+    pts, faces = I.box_points((0.4, 0.2, 0.6), n=5)
+    assert len(pts) == 5 ** 3 - 3 ** 3
+    half = np.array([0.2, 0.1, 0.3])
+    assert np.allclose(np.abs(pts).max(axis=0), half)
+    assert np.all(np.isclose(np.abs(pts) / half, 1.0).any(axis=1))  # on the surface
+    assert faces.max() == 7 and len(faces) == 12
+    b = I.box_body(size=(0.4, 0.2, 0.6), density=10.0)
+    assert abs(b.mass - 10.0 * 0.048) < 1e-12
+    assert abs(np.linalg.norm(b.state0[3:7]) - 1.0) < 1e-15
+
+
+def test_rigid_batch_ranges():
+    bodies = I.rigid_batch(64, seed=5, n=3)
+    for body in bodies:
+        size = 2 * np.abs(body.points).max(axis=0)
+        dens = body.mass / np.prod(size)
+        assert 2.0 <= dens <= 12.0
+        assert 0.2 <= body.contact[3] <= 1.0
+        assert abs(np.linalg.norm(body.state0[3:7]) - 1.0) < 1e-12
+        assert np.all(np.abs(body.state0[[0, 2]]) <= 6.5)
+    assert len({round(b.mass, 9) for b in bodies}) == 64  # seeded, distinct
+
+
+def test_cloth_throw_and_hanging_beam():
+    p = I.cloth_throw(n=9, steps=10, seed=3)
+    assert p.n_elems == 2 * 8 * 8 and p.air is not None
+    assert p.n_hinges == 3 * 8 * 8 - 2 * 8  # interior edges of an 8 x 8 grid split by one diagonal
+    assert np.all(np.isfinite(p.v0)) and p.v0[:, 1].mean() > 0  # thrown upwards
+    q = I.cloth_throw(n=9, steps=10, seed=3)
+    assert np.array_equal(p.X, q.X) and np.array_equal(p.v0, q.v0)
+    beam = I.hanging_beam(1000.0)
+    assert beam.pinned.sum() == 3 * 3 and beam.n_elems == 5 * 8 * 2 * 2
+    assert np.all(beam.X[beam.pinned.astype(bool), 0] == 0.0)
+
+
+def test_look_at_camera():
+    cam = I.look_at((1.0, 2.0, -3.0), (0.0, 0.5, 0.0), width=80, height=60, fov_deg=45.0)
+    assert np.allclose(cam.R @ cam.R.T, np.eye(3), atol=1e-12)
+    assert abs(np.linalg.det(cam.R) - 1.0) < 1e-12
+    eye = -cam.R.T @ cam.t
+    assert np.allclose(eye, (1.0, 2.0, -3.0))
+    assert abs(cam.fx - 40.0 / math.tan(math.radians(22.5))) < 1e-9
