@@ -59,6 +59,17 @@ __host__ __device__ __forceinline__ int act_slice_n(int begin, int n) { return (
 
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch between the step kernels: a kernel waits
+// for the previous one in its stream to complete and its memory to be
+// visible before it reads anything (pdl_enter), and once a CTA has finished
+// its work it lets the next kernel be scheduled (pdl_done; the next kernel
+// launches when every CTA has done so or exited, and still waits for this
+// one to complete).  Without the launch attribute both are no-ops.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_done() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // TMA bulk copies global -> shared completing on an mbarrier
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -810,6 +821,7 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
         mbar_init_fence();
     }
     __syncthreads();
+    pdl_enter();
     if (n_patches <= 0) return;
     int* const status = rts[patches[blockIdx.x < n_patches ? blockIdx.x : 0].mesh].status;
     if (warp == (nt >> 5)) {
@@ -861,7 +873,10 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
         unsigned char* const b = buf0 + s * stage_bytes;
         if (!mbar_wait_bounded(&full[s], (it / kStages) & 1u, status)) return;
         const PatchDesc p = *(const PatchDesc*)b;
-        if (p.n_e < 0) return;
+        if (p.n_e < 0) {
+            pdl_done();
+            return;
+        }
         const MeshRT& m = *(const MeshRT*)(b + kHdrRt);
         Stage S = stage_at(p, KIND, b + kHdr, ADJ);
         bind_act(S, p, m, tick);
@@ -942,6 +957,7 @@ __device__ __forceinline__ void partial_sums2(const float4* __restrict__ P, int 
 
 __global__ void __launch_bounds__(kBndThreads, 8)
     k_fwd_boundary(const NodeBlock* __restrict__ blocks, int n_blocks, const MeshRT* __restrict__ rts, int tick) {
+    pdl_enter();
     for (int bi = blockIdx.x; bi < n_blocks; bi += gridDim.x) {
         const NodeBlock nb = blocks[bi];
         const MeshRT& m = rts[nb.mesh];
@@ -971,10 +987,12 @@ __global__ void __launch_bounds__(kBndThreads, 8)
         if (h0) node_forward(m, tick, m.n_int + b0, x0, v0, xyz(f0));
         if (h1) node_forward(m, tick, m.n_int + b1, x1, v1, xyz(f1));
     }
+    pdl_done();
 }
 
 __global__ void __launch_bounds__(kBndThreads, 6)
     k_adj_boundary(const NodeBlock* __restrict__ blocks, int n_blocks, const MeshRT* __restrict__ rts, int tick) {
+    pdl_enter();
     for (int bi = blockIdx.x; bi < n_blocks; bi += gridDim.x) {
         const NodeBlock nb = blocks[bi];
         const MeshRT& m = rts[nb.mesh];
@@ -1013,6 +1031,7 @@ __global__ void __launch_bounds__(kBndThreads, 6)
         if (h0) node_adjoint(m, g0, x0, v0, xb0, vb0, xyz(a0), a0.w, w0, z);
         if (h1) node_adjoint(m, g1, x1, v1, xb1, vb1, xyz(a1), a1.w, w1, z);
     }
+    pdl_done();
 }
 
 // Cloth with air, after k_adj_boundary: each boundary node's dL/dv from the
@@ -1020,6 +1039,7 @@ __global__ void __launch_bounds__(kBndThreads, 6)
 // last to v_bar as node_adjoint does for interior nodes.
 __global__ void __launch_bounds__(kBndThreads)
     k_adj_boundary_air(const NodeBlock* __restrict__ blocks, int n_blocks, const MeshRT* __restrict__ rts) {
+    pdl_enter();
     for (int bi = blockIdx.x; bi < n_blocks; bi += gridDim.x) {
         const NodeBlock nb = blocks[bi];
         const MeshRT& m = rts[nb.mesh];
@@ -1031,6 +1051,7 @@ __global__ void __launch_bounds__(kBndThreads)
             m.vb[g] = f4(xyz(m.vb[g]) + c, 0.0f);
         }
     }
+    pdl_done();
 }
 
 // ===========================================================================
@@ -1468,28 +1489,49 @@ const char* kernel_name(int kind) {
         if (prof) prof->end(kind, s);   \
     } while (0)
 
+// step kernels are launched with programmatic stream serialisation (see pdl_enter)
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 void launch_forward_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
     if (L.n_tet_patches)
-        GS_TIMED(KT_TET_FWD, (k_tet_fwd<<<L.grid[0], L.threads + 32, 128 + kStages * (size_t)L.stage[0], s>>>(
-                                 L.tet_patches, L.n_tet_patches, L.rt, tick, L.stage[0])));
+        GS_TIMED(KT_TET_FWD, launch_pdl(k_tet_fwd, L.grid[0], L.threads + 32, 128 + kStages * (size_t)L.stage[0], s,
+                                        L.tet_patches, L.n_tet_patches, (const MeshRT*)L.rt, tick, L.stage[0]));
     if (L.n_cloth_patches)
-        GS_TIMED(KT_CLOTH_FWD, (k_cloth_fwd<<<L.grid[1], L.threads + 32, 128 + kStages * (size_t)L.stage[1], s>>>(
-                                   L.cloth_patches, L.n_cloth_patches, L.rt, tick, L.stage[1])));
+        GS_TIMED(KT_CLOTH_FWD, launch_pdl(k_cloth_fwd, L.grid[1], L.threads + 32, 128 + kStages * (size_t)L.stage[1],
+                                          s, L.cloth_patches, L.n_cloth_patches, (const MeshRT*)L.rt, tick,
+                                          L.stage[1]));
     if (L.n_bnd_blocks)
-        GS_TIMED(KT_FWD_BND, (k_fwd_boundary<<<L.bgrid[0], kBndThreads, 0, s>>>(L.bnd_blocks, L.n_bnd_blocks, L.rt, tick)));
+        GS_TIMED(KT_FWD_BND, launch_pdl(k_fwd_boundary, L.bgrid[0], kBndThreads, 0, s, L.bnd_blocks,
+                                        L.n_bnd_blocks, (const MeshRT*)L.rt, tick));
 }
 
 void launch_adjoint_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
     if (L.n_tet_patches)
-        GS_TIMED(KT_TET_ADJ, (k_tet_adj<<<L.grid[2], L.threads + 32, 128 + kStages * (size_t)L.stage[2], s>>>(
-                                 L.tet_patches, L.n_tet_patches, L.rt, tick, L.stage[2])));
+        GS_TIMED(KT_TET_ADJ, launch_pdl(k_tet_adj, L.grid[2], L.threads + 32, 128 + kStages * (size_t)L.stage[2], s,
+                                        L.tet_patches, L.n_tet_patches, (const MeshRT*)L.rt, tick, L.stage[2]));
     if (L.n_cloth_patches)
-        GS_TIMED(KT_CLOTH_ADJ, (k_cloth_adj<<<L.grid[3], L.threads + 32, 128 + kStages * (size_t)L.stage[3], s>>>(
-                                   L.cloth_patches, L.n_cloth_patches, L.rt, tick, L.stage[3])));
+        GS_TIMED(KT_CLOTH_ADJ, launch_pdl(k_cloth_adj, L.grid[3], L.threads + 32, 128 + kStages * (size_t)L.stage[3],
+                                          s, L.cloth_patches, L.n_cloth_patches, (const MeshRT*)L.rt, tick,
+                                          L.stage[3]));
     if (L.n_bnd_blocks)
-        GS_TIMED(KT_ADJ_BND, (k_adj_boundary<<<L.bgrid[1], kBndThreads, 0, s>>>(L.bnd_blocks, L.n_bnd_blocks, L.rt, tick)));
+        GS_TIMED(KT_ADJ_BND, launch_pdl(k_adj_boundary, L.bgrid[1], kBndThreads, 0, s, L.bnd_blocks,
+                                        L.n_bnd_blocks, (const MeshRT*)L.rt, tick));
     if (L.air && L.n_bnd_blocks)
-        GS_TIMED(KT_ADJ_BND, (k_adj_boundary_air<<<L.bgrid[1], kBndThreads, 0, s>>>(L.bnd_blocks, L.n_bnd_blocks, L.rt)));
+        GS_TIMED(KT_ADJ_BND, launch_pdl(k_adj_boundary_air, L.bgrid[1], kBndThreads, 0, s, L.bnd_blocks,
+                                        L.n_bnd_blocks, (const MeshRT*)L.rt));
 }
 
 void launch_copy_state(const Launch& L, cudaStream_t s) {
