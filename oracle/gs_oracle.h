@@ -6,7 +6,7 @@
  * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, obviously-correct
  * restatement of the paper's equations in double precision, used by the test
  * suite, by the package's smoke check and by the benchmark's CPU-baseline leg
- * to judge the CUDA library.  Nothing in the product path may link, load or
+ * to check the CUDA library.  Nothing in the product path may link, load or
  * call it, and it shares no code with the CUDA library.
  *
  * What it computes (paper section / equation in brackets):
