@@ -26,6 +26,9 @@ namespace {
 using gs::Buf;
 
 constexpr int kWarpsPerBlock = 8;
+// the adjoint holds ~150 registers per thread: blocks of 2 warps let six
+// blocks (12 warps) share an SM where one 8-warp block would leave 8
+constexpr int kAdjWarps = 2;
 constexpr int kStateStride = 16;  // floats per stored body state (13 used)
 
 struct Scene {
@@ -334,11 +337,11 @@ struct RigidGradOut {
 // omega+ and r+, so dL/dF and dL/dtau are known before the contacts are
 // evaluated; F and tau (the same sums, in the same order, as the forward's)
 // come out of the same pass and finish the terms that need them.
-__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+__global__ void __launch_bounds__(32 * kAdjWarps, 6)
     k_rigid_adjoint(const int* __restrict__ pbeg, const float* __restrict__ params, const float* __restrict__ pts,
                     Scene sc, int nb, const float* __restrict__ traj, float dt, int S, const float* __restrict__ seed,
                     RigidGradOut out) {
-    const int b = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int b = blockIdx.x * kAdjWarps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= nb) return;
     const Body B = load_body(pbeg, params, b);
@@ -697,8 +700,8 @@ extern "C" gs_status gs_rigid_adjoint(gs_rigid* r, const float* dL_dstateS, gs_r
     if (r->S < 0) return gs::set_error(GS_ESTATE, "gs_rigid_adjoint needs a gs_rigid_rollout first");
     cudaStream_t s = (cudaStream_t)stream;
     RigidGradOut o{g->d_state0, g->d_mass, g->d_inertia, g->d_contact};
-    const int grid = (r->nb + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    k_rigid_adjoint<<<grid, 32 * kWarpsPerBlock, 0, s>>>((const int*)r->pbeg.p, (const float*)r->params.p,
+    const int grid = (r->nb + kAdjWarps - 1) / kAdjWarps;
+    k_rigid_adjoint<<<grid, 32 * kAdjWarps, 0, s>>>((const int*)r->pbeg.p, (const float*)r->params.p,
                                                          (const float*)r->pts.p, r->sc, r->nb,
                                                          (const float*)r->traj.p, r->dt, r->S, dL_dstateS, o);
     GS_CUDA(cudaGetLastError());
