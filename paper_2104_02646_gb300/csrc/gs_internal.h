@@ -158,12 +158,13 @@ struct Launch {
     int stage[4] = {0, 0, 0, 0};
     int bgrid[2] = {0, 0};  // boundary kernels (fwd, adj): CTAs striding over bnd_blocks
     int air = 0;            // some cloth mesh of the set has air on: the adjoint step adds k_adj_boundary_air
+    int extras = -1;        // stages hold actuation slices / boundary v (a mesh has a sequence or air); -1: unset
 };
 
 // --------------------------------------------------------------------------
 // kernels (gs_kernels.cu)
 // --------------------------------------------------------------------------
-size_t patch_smem_bytes(int kind, int n_e, int n_h, int n_loc, int n_int, int n_slots, bool adjoint);
+size_t patch_smem_bytes(int kind, int n_e, int n_h, int n_loc, int n_int, int n_slots, bool adjoint, bool extras);
 int patch_grid(int which, int threads, int stage_bytes, int n_patches, int num_sms);
 int boundary_grid(int adjoint, int n_blocks, int num_sms);
 gs_status selftest_bounded_wait(int iterations, int* status_host, cudaStream_t s);

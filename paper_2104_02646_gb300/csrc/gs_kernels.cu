@@ -150,8 +150,11 @@ struct Layout {
     int rec, rp, sl, pos, xs, vh, vs, xb, vb, xbB, vbB, gml, wb, act, hact, vB, total;
 };
 
+// `extras`: the stage also holds the step's actuation slices and, for
+// cloth, the boundary velocities the air needs (a launch set reserves them
+// only when one of its meshes has an actuation sequence or air on)
 __host__ __device__ __forceinline__ Layout patch_layout(int kind, int n_e, int n_h, int n_loc, int n_int,
-                                                        int n_slots, bool adjoint) {
+                                                        int n_slots, bool adjoint, bool extras) {
     const int n_rec = n_e + n_h;
     const int n_bnd = n_loc - n_int;
     Layout L;
@@ -173,11 +176,11 @@ __host__ __device__ __forceinline__ Layout patch_layout(int kind, int n_e, int n
     // the step's row slices of a time-varying actuation (elements, hinges);
     // up to 3 entries of slack on each side for the aligned slice ends
     L.act = L.wb + (adjoint ? r16(8 * n_int) : 0);
-    L.hact = L.act + r16(4 * (n_e + 6));
+    L.hact = L.act + (extras ? r16(4 * (n_e + 6)) : 0);
     // cloth: v of the boundary nodes (the air on the triangles needs every
     // corner's velocity)
-    L.vB = L.hact + (n_h ? r16(4 * (n_h + 6)) : 0);
-    L.total = L.vB + (kind == GS_CLOTH ? 16 * (n_loc - n_int) : 0);
+    L.vB = L.hact + (extras && n_h ? r16(4 * (n_h + 6)) : 0);
+    L.total = L.vB + (extras && kind == GS_CLOTH ? 16 * (n_loc - n_int) : 0);
     return L;
 }
 
@@ -323,12 +326,14 @@ struct Stage {
     const float* act;   // this step's actuation of the patch's elements [n_e], or null
     const float* hact;  // this step's actuation of the patch's hinges [n_h], or null
     float4* vB;         // cloth with air: boundary v
+    bool extras;        // the actuation slices and boundary v regions exist
 };
 
-__device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned char* buf, bool adjoint) {
+__device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned char* buf, bool adjoint,
+                                          bool extras) {
     const int n_loc = p.n_int + p.n_bnd;
     const int n_rec = p.n_e + p.n_h;
-    const Layout L = patch_layout(kind, p.n_e, p.n_h, n_loc, p.n_int, p.n_slots, adjoint);
+    const Layout L = patch_layout(kind, p.n_e, p.n_h, n_loc, p.n_int, p.n_slots, adjoint, extras);
     Stage S;
     S.n_rec = n_rec;
     S.n_e = p.n_e;
@@ -349,14 +354,17 @@ __device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned
     S.act = (const float*)(buf + L.act) + (p.e_begin & 3);
     S.hact = (const float*)(buf + L.hact) + (p.h_begin & 3);
     S.vB = (float4*)(buf + L.vB);
+    S.extras = extras;
     return S;
 }
 
 // staged actuation of the current step, if the producer copied one
 __device__ __forceinline__ void bind_act(Stage& S, const PatchDesc& p, const MeshRT& m, int tick) {
-    if (act_row(m, m.act_seq, tick) < 0 || p.n_e == 0) S.act = nullptr;
-    if (act_row(m, m.hact_seq, tick) < 0 || p.n_h == 0) S.hact = nullptr;
+    if (!S.extras || act_row(m, m.act_seq, tick) < 0 || p.n_e == 0) S.act = nullptr;
+    if (!S.extras || act_row(m, m.hact_seq, tick) < 0 || p.n_h == 0) S.hact = nullptr;
 }
+// the air acts on this stage's triangles (cloth with air on, region present)
+__device__ __forceinline__ bool stage_air(const Stage& S, const MeshRT& m) { return S.extras && m.air_on; }
 __device__ __forceinline__ float act_of(const float* a, int i) { return a ? a[i] : 0.f; }
 
 // velocity of local node l (cloth with air: interior staged in vs, boundary in vB)
@@ -381,8 +389,8 @@ __device__ __forceinline__ int in_buffer(const MeshRT& m, int tick, bool adjoint
 // interior node data into `buf`, completing on `bar`.
 __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_global, const MeshRT& m, int tick,
                                            unsigned char* buf, MeshRT* hdr_rt, bool copy_rt, uint64_t* bar,
-                                           bool adjoint) {
-    const Stage S = stage_at(p, m.kind, buf, adjoint);
+                                           bool adjoint, bool extras) {
+    const Stage S = stage_at(p, m.kind, buf, adjoint, extras);
     const int n_loc = p.n_int + p.n_bnd;
     const int n_rec = S.n_rec;
     const int n_slots = p.n_slots;
@@ -394,8 +402,8 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
     const uint32_t b_g = adjoint ? 16u * p.n_e : 0u;
     const uint32_t b_pos = (uint32_t)r16(4 * p.n_bnd);
     // this step's actuation rows, aligned slices around the patch's entries
-    const int ra = p.n_e ? act_row(m, m.act_seq, tick) : -1;
-    const int rh = p.n_h ? act_row(m, m.hact_seq, tick) : -1;
+    const int ra = extras && p.n_e ? act_row(m, m.act_seq, tick) : -1;
+    const int rh = extras && p.n_h ? act_row(m, m.hact_seq, tick) : -1;
     const uint32_t b_act = ra >= 0 ? 4u * act_slice_n(p.e_begin, p.n_e) : 0u;
     const uint32_t b_hact = rh >= 0 ? 4u * act_slice_n(p.h_begin, p.n_h) : 0u;
     const uint32_t tx = (copy_rt ? (uint32_t)sizeof(MeshRT) : 0u) + 64u * n_rec + b_rp + b_sl + b_pos +
@@ -440,9 +448,9 @@ __device__ __forceinline__ void prefetch_ids(const PatchDesc& p, const MeshRT& m
 }
 
 __device__ __forceinline__ void produce_gather(const PatchDesc& p, const MeshRT& m, const float4* X, const float4* V,
-                                               const int* g, unsigned char* buf, bool adjoint, int lane) {
-    const Stage S = stage_at(p, m.kind, buf, adjoint);
-    const bool gv = m.kind == GS_CLOTH && m.air_on;  // boundary v for the air
+                                               const int* g, unsigned char* buf, bool adjoint, bool extras, int lane) {
+    const Stage S = stage_at(p, m.kind, buf, adjoint, extras);
+    const bool gv = m.kind == GS_CLOTH && stage_air(S, m);  // boundary v for the air
 #pragma unroll
     for (int j = 0; j < kPrefetchIds; ++j) {
         const int k = lane + 32 * j;
@@ -533,7 +541,7 @@ __device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Mes
                       make_float3(c.x, c.y, c.z), make_float3(c.w, w.z, w.w), s);
             float3 f0, f1, f2;
             tri_forces(s, a, b, f0, f1, f2);
-            if (m.air_on) {
+            if (stage_air(S, m)) {
                 const float3 vr = air_vr(m, S, p, id.x & 0xffff, id.x >> 16, id.y & 0xffff);
                 const float3 Fa = air_force(b.x * cross3(s.F0, s.F1), vr, m.k_drag, m.k_lift) * (1.0f / 3.0f);
                 f0 += Fa;
@@ -614,7 +622,7 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             float gmu, glam, gact;
             const float3 y0 = (dt * x0.w) * v0, y1 = (dt * x1.w) * v1, y2 = (dt * x2.w) * v2;
             tri_adjoint(s, a, bt, y0, y1, y2, xb0, xb1, xb2, gmu, glam, gact);
-            if (m.air_on) {
+            if (stage_air(S, m)) {
                 // F on each corner F/3: dL/dF = (y0 + y1 + y2)/3; N = A (F0 x F1)
                 const float3 vr = air_vr(m, S, p, i0, i1, i2);
                 const float3 N = b.x * cross3(s.F0, s.F1);
@@ -743,7 +751,7 @@ __device__ __forceinline__ float3 row_sum_air_v(const Stage& S, int k, int k1) {
 template <int KIND>
 __device__ __forceinline__ void adjoint_nodes(const PatchDesc& p, const MeshRT& m, const Stage& S, int nt) {
     const int n_loc = p.n_int + p.n_bnd;
-    const bool air = KIND == GS_CLOTH && m.air_on;
+    const bool air = KIND == GS_CLOTH && stage_air(S, m);
     for (int l = threadIdx.x; l < n_loc; l += nt) {
         const float4 acc = row_sum4(S, S.rp[l], S.rp[l + 1]);
         const float3 va = air ? row_sum_air_v(S, S.rp[l], S.rp[l + 1]) : make_float3(0.f, 0.f, 0.f);
@@ -804,7 +812,8 @@ __device__ __forceinline__ int next_live(const PatchDesc* __restrict__ patches, 
 
 template <int KIND, bool ADJ>
 __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ patches, int n_patches,
-                                               const MeshRT* __restrict__ rts, int tick, int stage_bytes) {
+                                               const MeshRT* __restrict__ rts, int tick, int stage_bytes,
+                                               int extras) {
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* full = (uint64_t*)sm;
     uint64_t* empty = full + kStages;
@@ -854,9 +863,9 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
                 // the stage keeps its mesh record from the last patch it held
                 const bool copy_rt = ((const PatchDesc*)b)->mesh != p.mesh;
                 *(PatchDesc*)b = p;
-                issue_bulk(p, &rts[p.mesh], m, tick, b + kHdr, (MeshRT*)(b + kHdrRt), copy_rt, &full[s], ADJ);
+                issue_bulk(p, &rts[p.mesh], m, tick, b + kHdr, (MeshRT*)(b + kHdrRt), copy_rt, &full[s], ADJ, extras != 0);
             }
-            produce_gather(p, m, X, V, g, b + kHdr, ADJ, lane);
+            produce_gather(p, m, X, V, g, b + kHdr, ADJ, extras != 0, lane);
             cp_async_mbar_arrive(&full[s]);
             pi = next_live(patches, n_patches, rts, pi + gridDim.x, mask);
             if (pi < n_patches) {
@@ -878,7 +887,7 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
             return;
         }
         const MeshRT& m = *(const MeshRT*)(b + kHdrRt);
-        Stage S = stage_at(p, KIND, b + kHdr, ADJ);
+        Stage S = stage_at(p, KIND, b + kHdr, ADJ, extras != 0);
         bind_act(S, p, m, tick);
         if (ADJ) {
             for (int l = threadIdx.x; l < p.n_int; l += nt) S.vh[l] = f4(xyz(S.vb[l]) + m.dt * xyz(S.xb[l]), 0.f);
@@ -910,20 +919,20 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
 // patch kernels (persistent, pipelined)
 // ===========================================================================
 __global__ void k_tet_fwd(const PatchDesc* __restrict__ patches, int n_patches, const MeshRT* __restrict__ rts,
-                          int tick, int stage_bytes) {
-    patch_pipeline<GS_TET, false>(patches, n_patches, rts, tick, stage_bytes);
+                          int tick, int stage_bytes, int extras) {
+    patch_pipeline<GS_TET, false>(patches, n_patches, rts, tick, stage_bytes, extras);
 }
 __global__ void k_cloth_fwd(const PatchDesc* __restrict__ patches, int n_patches, const MeshRT* __restrict__ rts,
-                            int tick, int stage_bytes) {
-    patch_pipeline<GS_CLOTH, false>(patches, n_patches, rts, tick, stage_bytes);
+                            int tick, int stage_bytes, int extras) {
+    patch_pipeline<GS_CLOTH, false>(patches, n_patches, rts, tick, stage_bytes, extras);
 }
 __global__ void k_tet_adj(const PatchDesc* __restrict__ patches, int n_patches, const MeshRT* __restrict__ rts,
-                          int tick, int stage_bytes) {
-    patch_pipeline<GS_TET, true>(patches, n_patches, rts, tick, stage_bytes);
+                          int tick, int stage_bytes, int extras) {
+    patch_pipeline<GS_TET, true>(patches, n_patches, rts, tick, stage_bytes, extras);
 }
 __global__ void k_cloth_adj(const PatchDesc* __restrict__ patches, int n_patches, const MeshRT* __restrict__ rts,
-                            int tick, int stage_bytes) {
-    patch_pipeline<GS_CLOTH, true>(patches, n_patches, rts, tick, stage_bytes);
+                            int tick, int stage_bytes, int extras) {
+    patch_pipeline<GS_CLOTH, true>(patches, n_patches, rts, tick, stage_bytes, extras);
 }
 
 // Boundary nodes: sum the node's partials (contiguous, in patch order), then
@@ -1431,8 +1440,8 @@ __global__ void k_elem_grads(const PatchDesc* __restrict__ patches, const MeshRT
 // ===========================================================================
 // launchers
 // ===========================================================================
-size_t patch_smem_bytes(int kind, int n_e, int n_h, int n_loc, int n_int, int n_slots, bool adjoint) {
-    return (size_t)((kHdr + patch_layout(kind, n_e, n_h, n_loc, n_int, n_slots, adjoint).total + 127) & ~127);
+size_t patch_smem_bytes(int kind, int n_e, int n_h, int n_loc, int n_int, int n_slots, bool adjoint, bool extras) {
+    return (size_t)((kHdr + patch_layout(kind, n_e, n_h, n_loc, n_int, n_slots, adjoint, extras).total + 127) & ~127);
 }
 
 // persistent grid: resident CTAs per SM x SMs, at most one CTA per patch
@@ -1508,11 +1517,11 @@ static void launch_pdl(void (*k)(KArgs...), int grid, int block, size_t smem, cu
 void launch_forward_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
     if (L.n_tet_patches)
         GS_TIMED(KT_TET_FWD, launch_pdl(k_tet_fwd, L.grid[0], L.threads + 32, 128 + kStages * (size_t)L.stage[0], s,
-                                        L.tet_patches, L.n_tet_patches, (const MeshRT*)L.rt, tick, L.stage[0]));
+                                        L.tet_patches, L.n_tet_patches, (const MeshRT*)L.rt, tick, L.stage[0], L.extras));
     if (L.n_cloth_patches)
         GS_TIMED(KT_CLOTH_FWD, launch_pdl(k_cloth_fwd, L.grid[1], L.threads + 32, 128 + kStages * (size_t)L.stage[1],
                                           s, L.cloth_patches, L.n_cloth_patches, (const MeshRT*)L.rt, tick,
-                                          L.stage[1]));
+                                          L.stage[1], L.extras));
     if (L.n_bnd_blocks)
         GS_TIMED(KT_FWD_BND, launch_pdl(k_fwd_boundary, L.bgrid[0], kBndThreads, 0, s, L.bnd_blocks,
                                         L.n_bnd_blocks, (const MeshRT*)L.rt, tick));
@@ -1521,11 +1530,11 @@ void launch_forward_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) 
 void launch_adjoint_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
     if (L.n_tet_patches)
         GS_TIMED(KT_TET_ADJ, launch_pdl(k_tet_adj, L.grid[2], L.threads + 32, 128 + kStages * (size_t)L.stage[2], s,
-                                        L.tet_patches, L.n_tet_patches, (const MeshRT*)L.rt, tick, L.stage[2]));
+                                        L.tet_patches, L.n_tet_patches, (const MeshRT*)L.rt, tick, L.stage[2], L.extras));
     if (L.n_cloth_patches)
         GS_TIMED(KT_CLOTH_ADJ, launch_pdl(k_cloth_adj, L.grid[3], L.threads + 32, 128 + kStages * (size_t)L.stage[3],
                                           s, L.cloth_patches, L.n_cloth_patches, (const MeshRT*)L.rt, tick,
-                                          L.stage[3]));
+                                          L.stage[3], L.extras));
     if (L.n_bnd_blocks)
         GS_TIMED(KT_ADJ_BND, launch_pdl(k_adj_boundary, L.bgrid[1], kBndThreads, 0, s, L.bnd_blocks,
                                         L.n_bnd_blocks, (const MeshRT*)L.rt, tick));

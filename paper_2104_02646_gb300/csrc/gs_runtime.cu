@@ -109,7 +109,7 @@ struct Topology {
     std::vector<int> bnd_rowptr, part_pos;
     std::vector<uint4> topo;  // per patch: row pointers, slots, partial positions (16 B aligned pieces)
     int n_int = 0, n_bnd = 0, max_loc = 0, max_slots = 0, max_rec = 0;
-    size_t smem_fwd = 0, smem_adj = 0;
+    size_t smem_fwd[2] = {0, 0}, smem_adj[2] = {0, 0};  // [without, with] the extra stage regions
 };
 
 static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
@@ -327,8 +327,12 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
         T.max_loc = std::max(T.max_loc, n_loc);
         T.max_slots = std::max(T.max_slots, n_slots);
         T.max_rec = std::max(T.max_rec, n_rec);
-        T.smem_fwd = std::max(T.smem_fwd, patch_smem_bytes(d.kind, q.n_e, q.n_h, n_loc, q.n_int, n_slots, false));
-        T.smem_adj = std::max(T.smem_adj, patch_smem_bytes(d.kind, q.n_e, q.n_h, n_loc, q.n_int, n_slots, true));
+        for (int x = 0; x < 2; ++x) {
+            T.smem_fwd[x] =
+                std::max(T.smem_fwd[x], patch_smem_bytes(d.kind, q.n_e, q.n_h, n_loc, q.n_int, n_slots, false, x != 0));
+            T.smem_adj[x] =
+                std::max(T.smem_adj[x], patch_smem_bytes(d.kind, q.n_e, q.n_h, n_loc, q.n_int, n_slots, true, x != 0));
+        }
         for (int g : bl) {
             loc[g] = -1;
             pdeg[g] = 0;
@@ -569,12 +573,14 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     m->max_loc = T.max_loc;
     m->max_slots = T.max_slots;
     m->max_rec = T.max_rec;
-    m->smem_fwd = T.smem_fwd;
-    m->smem_adj = T.smem_adj;
+    for (int x = 0; x < 2; ++x) {
+        m->smem_fwd[x] = T.smem_fwd[x];
+        m->smem_adj[x] = T.smem_adj[x];
+    }
     m->patches = T.patches;
     m->bnd_blocks = make_blocks(0, T.n_bnd, kNodeBlock, 0);
     m->node_blocks = make_blocks(0, N, 256, 0);
-    const size_t need = std::max(128 + kStages * T.smem_adj, sizeof(double) * (3 * (size_t)T.max_loc + 4 * (size_t)T.max_rec + 1));
+    const size_t need = std::max(128 + kStages * T.smem_adj[1], sizeof(double) * (3 * (size_t)T.max_loc + 4 * (size_t)T.max_rec + 1));
     if (need > ctx->smem_optin)
         return set_error(GS_EINVAL, "patch needs " + std::to_string(need) + " B of shared memory; lower patch_elems");
     // element records in internal order, 4 planes (geometry filled by the set-up kernel)
@@ -863,7 +869,7 @@ gs_status LaunchSet::build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStrea
     meshes = ms;
     std::vector<PatchDesc> tp, cp;
     std::vector<NodeBlock> bb, nb;
-    size_t sf_t = 0, sa_t = 0, sf_c = 0, sa_c = 0;
+    size_t sf_t[2] = {0, 0}, sa_t[2] = {0, 0}, sf_c[2] = {0, 0}, sa_c[2] = {0, 0};
     threads = 32;
     node_block_begin.clear();
     for (int i = 0; i < (int)ms.size(); ++i) {
@@ -882,12 +888,14 @@ gs_status LaunchSet::build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStrea
             b.mesh = i;
             nb.push_back(b);
         }
-        if (m->info.kind == GS_TET) {
-            sf_t = std::max(sf_t, m->smem_fwd);
-            sa_t = std::max(sa_t, m->smem_adj);
-        } else {
-            sf_c = std::max(sf_c, m->smem_fwd);
-            sa_c = std::max(sa_c, m->smem_adj);
+        for (int x = 0; x < 2; ++x) {
+            if (m->info.kind == GS_TET) {
+                sf_t[x] = std::max(sf_t[x], m->smem_fwd[x]);
+                sa_t[x] = std::max(sa_t[x], m->smem_adj[x]);
+            } else {
+                sf_c[x] = std::max(sf_c[x], m->smem_fwd[x]);
+                sa_c[x] = std::max(sa_c[x], m->smem_adj[x]);
+            }
         }
         threads = std::max(threads, m->threads);
     }
@@ -909,14 +917,13 @@ gs_status LaunchSet::build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStrea
     launch.n_node_blocks = (int)nb.size();
     launch.rt = (MeshRT*)d_rt.p;
     launch.threads = threads;
-    launch.stage[0] = (int)sf_t;
-    launch.stage[1] = (int)sf_c;
-    launch.stage[2] = (int)sa_t;
-    launch.stage[3] = (int)sa_c;
-    launch.grid[0] = patch_grid(0, threads, launch.stage[0], (int)tp.size(), c->num_sms);
-    launch.grid[1] = patch_grid(1, threads, launch.stage[1], (int)cp.size(), c->num_sms);
-    launch.grid[2] = patch_grid(2, threads, launch.stage[2], (int)tp.size(), c->num_sms);
-    launch.grid[3] = patch_grid(3, threads, launch.stage[3], (int)cp.size(), c->num_sms);
+    for (int x = 0; x < 2; ++x) {
+        stage_var[x][0] = (int)sf_t[x];
+        stage_var[x][1] = (int)sf_c[x];
+        stage_var[x][2] = (int)sa_t[x];
+        stage_var[x][3] = (int)sa_c[x];
+    }
+    launch.extras = -1;  // stages and grids set by sync_rt
     launch.bgrid[0] = boundary_grid(0, (int)bb.size(), c->num_sms);
     launch.bgrid[1] = boundary_grid(1, (int)bb.size(), c->num_sms);
     return sync_rt(s);
@@ -924,9 +931,21 @@ gs_status LaunchSet::build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStrea
 
 gs_status LaunchSet::sync_rt(cudaStream_t s) {
     launch.air = 0;
+    int extras = 0;
     for (size_t i = 0; i < meshes.size(); ++i) {
         host_rt[i] = meshes[i]->rt;
-        if (host_rt[i].kind == GS_CLOTH && host_rt[i].air_on) launch.air = 1;
+        const MeshRT& r = host_rt[i];
+        if (r.kind == GS_CLOTH && r.air_on) launch.air = 1;
+        if (r.act_seq || r.hact_seq || (r.kind == GS_CLOTH && r.air_on)) extras = 1;
+    }
+    if (extras != launch.extras) {
+        // stages with / without the actuation slices and boundary v; the grids follow their size
+        launch.extras = extras;
+        const int np[4] = {launch.n_tet_patches, launch.n_cloth_patches, launch.n_tet_patches, launch.n_cloth_patches};
+        for (int k = 0; k < 4; ++k) {
+            launch.stage[k] = stage_var[extras][k];
+            launch.grid[k] = patch_grid(k, launch.threads, launch.stage[k], np[k], ctx->num_sms);
+        }
     }
     GS_CUDA(cudaMemcpyAsync(d_rt.p, host_rt.data(), host_rt.size() * sizeof(MeshRT), cudaMemcpyHostToDevice, s));
     return GS_OK;
@@ -948,7 +967,8 @@ gs_status LaunchSet::run(int phase, int steps, cudaStream_t s) {
         GS_CUDA(cudaGetLastError());
         return GS_OK;
     }
-    const std::pair<int, int> key{phase + 2 * launch.air, steps};  // the air adds a kernel to adjoint steps
+    // the air adds a kernel to adjoint steps; the extra stage regions change stages and grids
+    const std::pair<int, int> key{phase + 2 * launch.air + 4 * launch.extras, steps};
     auto it = graphs.find(key);
     if (it == graphs.end()) {
         cudaStream_t cs = ctx->capture_stream;

@@ -85,6 +85,7 @@ struct LaunchSet {
     std::vector<MeshRT> host_rt;
     std::vector<int> node_block_begin;
     Launch launch;
+    int stage_var[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // stage bytes per patch kernel, [extras]
     int threads = 256;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
 
@@ -107,7 +108,7 @@ struct gs_mesh {
     gs_ctx* ctx = nullptr;
     gs_mesh_info info{};
     int n_pad = 0, threads = 256, max_loc = 0, max_slots = 0, max_rec = 0, n_bufs = 0;
-    size_t smem_fwd = 0, smem_adj = 0;
+    size_t smem_fwd[2] = {0, 0}, smem_adj[2] = {0, 0};  // stage bytes [without, with] the extra regions
     std::vector<gs::PatchDesc> patches;
     std::vector<gs::NodeBlock> bnd_blocks, node_blocks;
     gs::Buf rec, hrec, Xs, Xp, v0, bnd_ids, loc_rowptr, loc_slots, bnd_rowptr, part_pos, topo, partials,
