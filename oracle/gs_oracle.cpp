@@ -15,9 +15,14 @@
 
 #include "gs_oracle.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -454,6 +459,19 @@ void contact_t(const orc_model* m, const T* x, const T* v, T ke, T kd, T kf, T m
 // ---------------------------------------------------------------------------
 // Total force on every node at state (x, v): elements, hinges, then contact
 // (each element adds its corner forces to its nodes in element order).
+//
+// Threads (OpenMP, when the oracle is built with it) only ever split loops
+// whose iterations are independent: each element's corner forces go to its
+// own rows of a scratch array, and the node sums then run on one thread in
+// element order.  The arithmetic and its order are those of the plain
+// serial loop, so every result is bitwise the same for any thread count.
+template <class T>
+std::vector<T>& corner_scratch(size_t n) {
+    thread_local std::vector<T> buf;
+    if (buf.size() < n) buf.resize(n);
+    return buf;
+}
+
 template <class T>
 void total_force(const orc_model* m, const Rest& r, const T* x, const T* v,
                  const T* tmu, const T* tlam, const T* tact,
@@ -461,45 +479,65 @@ void total_force(const orc_model* m, const Rest& r, const T* x, const T* v,
                  const T* kb, const T* hact, const T* cp, T* f) {
     const size_t N = (size_t)m->n_nodes;
     for (size_t i = 0; i < 3 * N; ++i) f[i] = T(0.0);
-    for (int e = 0; e < m->n_tets; ++e) {
-        T xe[12], fe[12];
-        for (int c = 0; c < 4; ++c)
-            for (int k = 0; k < 3; ++k) xe[3 * c + k] = x[3 * (size_t)m->tets[4 * e + c] + k];
-        tet_forces_t(xe, &r.tet_Dminv[9 * (size_t)e], r.tet_V[e], tmu[e], tlam[e], tact[e], fe);
-        for (int c = 0; c < 4; ++c)
-            for (int k = 0; k < 3; ++k) f[3 * (size_t)m->tets[4 * e + c] + k] += fe[3 * c + k];
+    {
+        std::vector<T>& fe = corner_scratch<T>(12 * (size_t)m->n_tets);
+#pragma omp parallel for schedule(static)
+        for (int e = 0; e < m->n_tets; ++e) {
+            T xe[12];
+            for (int c = 0; c < 4; ++c)
+                for (int k = 0; k < 3; ++k) xe[3 * c + k] = x[3 * (size_t)m->tets[4 * e + c] + k];
+            tet_forces_t(xe, &r.tet_Dminv[9 * (size_t)e], r.tet_V[e], tmu[e], tlam[e], tact[e], &fe[12 * (size_t)e]);
+        }
+        for (int e = 0; e < m->n_tets; ++e)
+            for (int c = 0; c < 4; ++c)
+                for (int k = 0; k < 3; ++k) f[3 * (size_t)m->tets[4 * e + c] + k] += fe[12 * (size_t)e + 3 * c + k];
     }
-    for (int t = 0; t < m->n_tris; ++t) {
-        T xe[9], fe[9];
-        for (int c = 0; c < 3; ++c)
-            for (int k = 0; k < 3; ++k) xe[3 * c + k] = x[3 * (size_t)m->tris[3 * t + c] + k];
-        tri_forces_t(xe, &r.tri_Dminv[4 * (size_t)t], r.tri_A[t], rmu[t], rlam[t], ract[t], fe);
-        for (int c = 0; c < 3; ++c)
-            for (int k = 0; k < 3; ++k) f[3 * (size_t)m->tris[3 * t + c] + k] += fe[3 * c + k];
+    {
+        std::vector<T>& fe = corner_scratch<T>(9 * (size_t)m->n_tris);
+#pragma omp parallel for schedule(static)
+        for (int t = 0; t < m->n_tris; ++t) {
+            T xe[9];
+            for (int c = 0; c < 3; ++c)
+                for (int k = 0; k < 3; ++k) xe[3 * c + k] = x[3 * (size_t)m->tris[3 * t + c] + k];
+            tri_forces_t(xe, &r.tri_Dminv[4 * (size_t)t], r.tri_A[t], rmu[t], rlam[t], ract[t], &fe[9 * (size_t)t]);
+        }
+        for (int t = 0; t < m->n_tris; ++t)
+            for (int c = 0; c < 3; ++c)
+                for (int k = 0; k < 3; ++k) f[3 * (size_t)m->tris[3 * t + c] + k] += fe[9 * (size_t)t + 3 * c + k];
     }
     if (m->air_on) {
+        std::vector<T>& fe = corner_scratch<T>(9 * (size_t)m->n_tris);
+#pragma omp parallel for schedule(static)
         for (int t = 0; t < m->n_tris; ++t) {
-            T xe[9], ve[9], fe[9];
+            T xe[9], ve[9];
             for (int c = 0; c < 3; ++c)
                 for (int k = 0; k < 3; ++k) {
                     xe[3 * c + k] = x[3 * (size_t)m->tris[3 * t + c] + k];
                     ve[3 * c + k] = v[3 * (size_t)m->tris[3 * t + c] + k];
                 }
-            air_forces_t(xe, ve, m->k_drag, m->k_lift, m->wind, fe);
-            for (int c = 0; c < 3; ++c)
-                for (int k = 0; k < 3; ++k) f[3 * (size_t)m->tris[3 * t + c] + k] += fe[3 * c + k];
+            air_forces_t(xe, ve, m->k_drag, m->k_lift, m->wind, &fe[9 * (size_t)t]);
         }
+        for (int t = 0; t < m->n_tris; ++t)
+            for (int c = 0; c < 3; ++c)
+                for (int k = 0; k < 3; ++k) f[3 * (size_t)m->tris[3 * t + c] + k] += fe[9 * (size_t)t + 3 * c + k];
     }
-    for (int h = 0; h < m->n_hinges; ++h) {
-        T xe[12], fe[12];
-        for (int c = 0; c < 4; ++c)
-            for (int k = 0; k < 3; ++k) xe[3 * c + k] = x[3 * (size_t)m->hinges[4 * h + c] + k];
-        hinge_forces_t(xe, kb[h], hact[h], fe);
-        for (int c = 0; c < 4; ++c)
-            for (int k = 0; k < 3; ++k) f[3 * (size_t)m->hinges[4 * h + c] + k] += fe[3 * c + k];
+    {
+        std::vector<T>& fe = corner_scratch<T>(12 * (size_t)m->n_hinges);
+#pragma omp parallel for schedule(static)
+        for (int h = 0; h < m->n_hinges; ++h) {
+            T xe[12];
+            for (int c = 0; c < 4; ++c)
+                for (int k = 0; k < 3; ++k) xe[3 * c + k] = x[3 * (size_t)m->hinges[4 * h + c] + k];
+            hinge_forces_t(xe, kb[h], hact[h], &fe[12 * (size_t)h]);
+        }
+        for (int h = 0; h < m->n_hinges; ++h)
+            for (int c = 0; c < 4; ++c)
+                for (int k = 0; k < 3; ++k) f[3 * (size_t)m->hinges[4 * h + c] + k] += fe[12 * (size_t)h + 3 * c + k];
     }
     if (m->plane_on || m->sphere_on) {
-        for (size_t i = 0; i < N; ++i) {
+        // one node per iteration, adding to that node's own rows only
+#pragma omp parallel for schedule(static)
+        for (long long i = 0; i < (long long)N; ++i) {
             T fc[3];
             contact_t(m, x + 3 * i, v + 3 * i, cp[0], cp[1], cp[2], cp[3], fc);
             for (int k = 0; k < 3; ++k) f[3 * i + k] += fc[k];
@@ -661,6 +699,10 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
     double cp_b[4] = {0, 0, 0, 0};
     std::vector<double> w_b(N, 0.0);
     std::vector<double> cq(3 * N), cu(3 * N), y(3 * N), lq_new(3 * N), lu_new(3 * N);
+    // per-element (per-node) scratch of the parallel VJP loops
+    const size_t n_rows = std::max({(size_t)12 * m->n_tets, (size_t)9 * m->n_tris, (size_t)12 * m->n_hinges,
+                                    m->air_on ? (size_t)18 * m->n_tris : (size_t)0});
+    std::vector<double> xb_e(n_rows), cpb_n(4 * N);
 
     std::vector<double> ta, ra, ha;
     for (int n = S - 1; n >= 0; --n) {
@@ -680,8 +722,13 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
             for (int k = 0; k < 3; ++k) y[3 * i + k] = -dt * w[i] * cu[3 * i + k];
         for (size_t i = 0; i < 3 * N; ++i) { lq_new[i] = -cq[i]; lu_new[i] = -cu[i]; }
 
+        // element VJPs in parallel, each into its own rows of xb_e; the node
+        // sums follow on one thread in element order (bitwise the serial loop)
+#pragma omp parallel for schedule(static)
         for (int e = 0; e < m->n_tets; ++e) {
-            double xe[12], ye[12], xb[12] = {0}, pb[3] = {0, 0, 0};
+            double xe[12], ye[12], pb[3] = {0, 0, 0};
+            double* xb = &xb_e[12 * (size_t)e];
+            for (int k = 0; k < 12; ++k) xb[k] = 0.0;
             const int* t = &m->tets[4 * e];
             for (int c = 0; c < 4; ++c)
                 for (int k = 0; k < 3; ++k) { xe[3 * c + k] = xn[3 * (size_t)t[c] + k]; ye[3 * c + k] = y[3 * (size_t)t[c] + k]; }
@@ -691,13 +738,17 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
             element_vjp<12, 3>(xe, pe, ye, xb, pb, [&](auto* xd, auto* pd, auto* fd) {
                 tet_forces_t(xd, Dmi, Ve, pd[0], pd[1], pd[2], fd);
             });
-            for (int c = 0; c < 4; ++c)
-                for (int k = 0; k < 3; ++k) lq_new[3 * (size_t)t[c] + k] += xb[3 * c + k];
             tmu_b[e] += pb[0]; tlam_b[e] += pb[1]; tact_b[e] += pb[2];
             if (tseq_b) tseq_b[(size_t)n * m->n_tets + e] = pb[2];
         }
+        for (int e = 0; e < m->n_tets; ++e)
+            for (int c = 0; c < 4; ++c)
+                for (int k = 0; k < 3; ++k) lq_new[3 * (size_t)m->tets[4 * e + c] + k] += xb_e[12 * (size_t)e + 3 * c + k];
+#pragma omp parallel for schedule(static)
         for (int e = 0; e < m->n_tris; ++e) {
-            double xe[9], ye[9], xb[9] = {0}, pb[3] = {0, 0, 0};
+            double xe[9], ye[9], pb[3] = {0, 0, 0};
+            double* xb = &xb_e[9 * (size_t)e];
+            for (int k = 0; k < 9; ++k) xb[k] = 0.0;
             const int* t = &m->tris[3 * e];
             for (int c = 0; c < 3; ++c)
                 for (int k = 0; k < 3; ++k) { xe[3 * c + k] = xn[3 * (size_t)t[c] + k]; ye[3 * c + k] = y[3 * (size_t)t[c] + k]; }
@@ -707,13 +758,17 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
             element_vjp<9, 3>(xe, pe, ye, xb, pb, [&](auto* xd, auto* pd, auto* fd) {
                 tri_forces_t(xd, Dmi, Ae, pd[0], pd[1], pd[2], fd);
             });
-            for (int c = 0; c < 3; ++c)
-                for (int k = 0; k < 3; ++k) lq_new[3 * (size_t)t[c] + k] += xb[3 * c + k];
             rmu_b[e] += pb[0]; rlam_b[e] += pb[1]; ract_b[e] += pb[2];
             if (rseq_b) rseq_b[(size_t)n * m->n_tris + e] = pb[2];
         }
+        for (int e = 0; e < m->n_tris; ++e)
+            for (int c = 0; c < 3; ++c)
+                for (int k = 0; k < 3; ++k) lq_new[3 * (size_t)m->tris[3 * e + c] + k] += xb_e[9 * (size_t)e + 3 * c + k];
+#pragma omp parallel for schedule(static)
         for (int h = 0; h < m->n_hinges; ++h) {
-            double xe[12], ye[12], xb[12] = {0}, pb[2] = {0, 0};
+            double xe[12], ye[12], pb[2] = {0, 0};
+            double* xb = &xb_e[12 * (size_t)h];
+            for (int k = 0; k < 12; ++k) xb[k] = 0.0;
             const int* t = &m->hinges[4 * h];
             for (int c = 0; c < 4; ++c)
                 for (int k = 0; k < 3; ++k) { xe[3 * c + k] = xn[3 * (size_t)t[c] + k]; ye[3 * c + k] = y[3 * (size_t)t[c] + k]; }
@@ -721,16 +776,20 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
             element_vjp<12, 2>(xe, pe, ye, xb, pb, [&](auto* xd, auto* pd, auto* fd) {
                 hinge_forces_t(xd, pd[0], pd[1], fd);
             });
-            for (int c = 0; c < 4; ++c)
-                for (int k = 0; k < 3; ++k) lq_new[3 * (size_t)t[c] + k] += xb[3 * c + k];
             kb_b[h] += pb[0]; hact_b[h] += pb[1];
             if (hseq_b) hseq_b[(size_t)n * m->n_hinges + h] = pb[1];
         }
+        for (int h = 0; h < m->n_hinges; ++h)
+            for (int c = 0; c < 4; ++c)
+                for (int k = 0; k < 3; ++k) lq_new[3 * (size_t)m->hinges[4 * h + c] + k] += xb_e[12 * (size_t)h + 3 * c + k];
         if (m->air_on) {
             // air force of a triangle as a function of its corners' (x, v):
             // 18 inputs, 9 force outputs (y padded with zeros)
+#pragma omp parallel for schedule(static)
             for (int e = 0; e < m->n_tris; ++e) {
-                double xv[18], ye[18] = {0}, xb[18] = {0}, pb[1] = {0};
+                double xv[18], ye[18] = {0}, pb[1] = {0};
+                double* xb = &xb_e[18 * (size_t)e];
+                for (int k = 0; k < 18; ++k) xb[k] = 0.0;
                 const int* t = &m->tris[3 * e];
                 for (int c = 0; c < 3; ++c)
                     for (int k = 0; k < 3; ++k) {
@@ -742,16 +801,22 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
                     (void)pd;
                     air_forces_t(xd, xd + 9, m->k_drag, m->k_lift, m->wind, fd);
                 });
+            }
+            for (int e = 0; e < m->n_tris; ++e)
                 for (int c = 0; c < 3; ++c)
                     for (int k = 0; k < 3; ++k) {
-                        lq_new[3 * (size_t)t[c] + k] += xb[3 * c + k];
-                        lu_new[3 * (size_t)t[c] + k] += xb[9 + 3 * c + k];
+                        lq_new[3 * (size_t)m->tris[3 * e + c] + k] += xb_e[18 * (size_t)e + 3 * c + k];
+                        lu_new[3 * (size_t)m->tris[3 * e + c] + k] += xb_e[18 * (size_t)e + 9 + 3 * c + k];
                     }
-            }
         }
         if (m->plane_on || m->sphere_on) {
-            for (size_t i = 0; i < N; ++i) {
-                double xv[6], yi[6] = {0}, xb[6] = {0, 0, 0, 0, 0, 0}, pb[4] = {0, 0, 0, 0};
+            // one node per iteration (its own rows of lq_new, lu_new and of
+            // the contact-parameter scratch); the parameter sums follow in node order
+#pragma omp parallel for schedule(static)
+            for (long long i = 0; i < (long long)N; ++i) {
+                double xv[6], yi[6] = {0}, xb[6] = {0, 0, 0, 0, 0, 0};
+                double* pb = &cpb_n[4 * (size_t)i];
+                for (int k = 0; k < 4; ++k) pb[k] = 0.0;
                 for (int k = 0; k < 3; ++k) { xv[k] = xn[3 * i + k]; xv[3 + k] = vn[3 * i + k]; yi[k] = y[3 * i + k]; }
                 const double pe[4] = {m->ke, m->kd, m->kf, m->mu_f};
                 // contact force as a function of the 6-vector (x, v): only its
@@ -760,8 +825,9 @@ int loss_grad(const orc_model* m, const double* x0, const double* v0, double dt,
                     contact_t(m, xd, xd + 3, pd[0], pd[1], pd[2], pd[3], fd);
                 });
                 for (int k = 0; k < 3; ++k) { lq_new[3 * i + k] += xb[k]; lu_new[3 * i + k] += xb[3 + k]; }
-                for (int k = 0; k < 4; ++k) cp_b[k] += pb[k];
             }
+            for (size_t i = 0; i < N; ++i)
+                for (int k = 0; k < 4; ++k) cp_b[k] += cpb_n[4 * i + k];
         }
         // dl/dw_i: the step uses w_i f_i(s-) (gravity does not depend on w)
         {
@@ -1113,6 +1179,25 @@ int orc_loss_dir(const orc_model* m, const double* x0, const double* v0, double 
     if (loss) *loss = L.v;
     if (dloss) *dloss = L.d[0];
     return 0;
+}
+
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    static const int all = omp_get_max_threads();
+    omp_set_num_threads(n > 0 ? n : all);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 }  // extern "C"

@@ -196,6 +196,13 @@ int orc_loss_grad(const orc_model* m, const double* x0, const double* v0, double
 int orc_loss_dir(const orc_model* m, const double* x0, const double* v0, double dt, int S,
                  const double* target, const orc_dirs* d, double* loss, double* dloss);
 
+/* Threads for the independent per-element and per-node loops (OpenMP; the
+ * node sums stay serial in element order, so results are bitwise the same
+ * for any count).  n <= 0 restores the default (all cores).  Returns the
+ * count now in effect; 1 when the oracle was built without OpenMP. */
+int orc_set_threads(int n);
+int orc_max_threads(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,8 +90,21 @@ def lib():
                                     _dp, _dp, C.POINTER(_Grads)]
         L.orc_loss_dir.argtypes = [C.POINTER(_Model), _dp, _dp, C.c_double, C.c_int, _dp,
                                    C.POINTER(_Dirs), _dp, _dp]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = C.c_int
+        L.orc_max_threads.restype = C.c_int
         _lib = L
     return _lib
+
+
+def set_threads(n):
+    """Threads of the oracle's independent element / node loops (n <= 0: all
+    cores); results are bitwise the same for any count.  Returns the count."""
+    return int(lib().orc_set_threads(int(n)))
+
+
+def max_threads():
+    return int(lib().orc_max_threads())
 
 
 def _d(a):
