@@ -29,6 +29,8 @@ class Rollout(torch.autograd.Function):
     @staticmethod
     def _run(mesh, dt, steps, K, mu, lam, rho, x0, v0):
         f32 = dict(dtype=torch.float32, device=x0.device)
+        # no time-varying actuation: clear one an earlier actuated rollout left
+        mesh.set_act_seq(None, None)
         mesh.set_params(mu=mu, lam=lam, rho=rho)
         mesh.set_state(x=x0, v=v0)
         mesh.rollout(dt, steps, K)
@@ -58,6 +60,9 @@ class Rollout(torch.autograd.Function):
             # rendered frames) replaced the stored states: recompute them
             dt, steps, K, args = ctx.replay
             Rollout._run(mesh, dt, steps, K, *args)
+        else:
+            # the adjoint re-evaluates the element forces: no actuation sequence
+            mesh.set_act_seq(None, None)
         mesh._rollout_token = None  # the adjoint consumes the stored rollout
         dev = gx.device if gx is not None else gv.device
         E, N = mesh.info.n_elems, mesh.n_nodes
@@ -87,20 +92,29 @@ class ActuatedRollout(torch.autograd.Function):
     dL/dx0, dL/dv0."""
 
     @staticmethod
-    def forward(ctx, mesh, dt, steps, K, act_seq, hinge_act_seq, x0, v0):
-        dev = x0.device
-        f32 = dict(dtype=torch.float32, device=dev)
-        a = None if act_seq is None else act_seq.detach().to(**f32).contiguous()
-        h = None if hinge_act_seq is None else hinge_act_seq.detach().to(**f32).contiguous()
+    def _run(mesh, dt, steps, K, a, h, x0, v0):
+        f32 = dict(dtype=torch.float32, device=x0.device)
         mesh.set_act_seq(a, h)
-        mesh.set_state(x=x0.detach().to(**f32).contiguous(), v=v0.detach().to(**f32).contiguous())
+        mesh.set_state(x=x0, v=v0)
         mesh.rollout(dt, steps, K)
         N = mesh.n_nodes
         xS = torch.empty(N, 3, **f32)
         vS = torch.empty(N, 3, **f32)
         mesh.get_state(xS, vS)
-        _claim(mesh)
+        return xS, vS
+
+    @staticmethod
+    def forward(ctx, mesh, dt, steps, K, act_seq, hinge_act_seq, x0, v0):
+        dev = x0.device
+        f32 = dict(dtype=torch.float32, device=dev)
+        a = None if act_seq is None else act_seq.detach().to(**f32).contiguous()
+        h = None if hinge_act_seq is None else hinge_act_seq.detach().to(**f32).contiguous()
+        xf = x0.detach().to(**f32).contiguous()
+        vf = v0.detach().to(**f32).contiguous()
+        xS, vS = ActuatedRollout._run(mesh, dt, steps, K, a, h, xf, vf)
         ctx.mesh = mesh
+        ctx.token = _claim(mesh)
+        ctx.replay = (dt, steps, K, a, h, xf, vf)
         ctx.steps = steps
         ctx.has = (act_seq is not None, hinge_act_seq is not None)
         ctx.dtypes = (x0.dtype, v0.dtype)
@@ -109,6 +123,15 @@ class ActuatedRollout(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gx, gv):
         mesh = ctx.mesh
+        dt, steps, K, a, h, xf, vf = ctx.replay
+        if getattr(mesh, "_rollout_token", None) != ctx.token:
+            # a later rollout on this mesh replaced the stored states (and
+            # perhaps the actuation): recompute this one's
+            ActuatedRollout._run(mesh, dt, steps, K, a, h, xf, vf)
+        else:
+            # the adjoint re-evaluates the element forces under this rollout's actuation
+            mesh.set_act_seq(a, h)
+        mesh._rollout_token = None  # the adjoint consumes the stored rollout
         dev = gx.device if gx is not None else gv.device
         S, E, B, N = ctx.steps, mesh.info.n_elems, mesh.info.n_hinges, mesh.n_nodes
         f32 = dict(dtype=torch.float32, device=dev)
