@@ -5,8 +5,10 @@ Two choices, made per mesh shape:
 * the patch decomposition: elements per patch and consumer threads per CTA
   (so elements per thread), picked by timing a short rollout + adjoint of the
   actual mesh for each candidate through the library;
-* the checkpoint interval K of the rollout (Sec. 3.3 of the paper
-  checkpoints a rollout every K steps and recomputes in between).  A
+* the checkpoint interval K of the rollout.  The paper's adjoint of an
+  explicit method keeps every step's state (App. B); storing a checkpoint
+  every K steps and recomputing in between is this library's way of fitting
+  long rollouts of large meshes in memory, at the price of recomputation.  A
   segment of n steps costs n - 1 recomputed forward steps, so the recompute
   work falls as K shrinks, while the stored states, 1 + ceil(S/K) checkpoints
   and K + 1 segment buffers (S + 2 states when K = 1, which stores every
