@@ -1,16 +1,29 @@
-"""Parity at the full sizes of the benchmark configurations, in the launch
-shape the benchmark times (256-element patches, 128 consumer threads).  The
-oracle computes whole short rollouts of the full meshes (a few steps of the
-1.3M-tet block, ten steps of the 256^2 cloth, sampled members of the
-512-mesh batch), and the CUDA path is compared with it element by element.
+"""Parity at the full sizes AND the full horizons of the benchmark
+configurations, in the launch shape the benchmark times (256-element
+patches, 128 consumer threads): the 1.3M-tet block through all 200 steps
+(every state kept, K = 1, and the checkpoint / recompute path with K = 14:
+fourteen segments and a ragged 4-step tail), the 256^2 cloth through all 500
+steps, and sampled members of the 512-mesh batch through all 300 steps.  The
+oracle (FP64, threaded over elements; bitwise the same as one thread) runs
+the same rollouts and adjoints.
+
+What is compared (FP32 GPU vs FP64 oracle, bars from the workload
+statement): the displacement x(S) - x(0) by rel-L2 and node by node, the
+velocity v(S) by rel-L2 (node by node reported: with contact a node can
+switch contact one step apart in FP32 and FP64), with the contact bar 1e-3
+(`check_state`); the loss; every gradient array by rel-L2, cosine and entry
+by entry (`check_grads`).  Comparing the
+displacement rather than absolute positions keeps the check able to fail: a
+path that did not move the mesh at all has displacement error 1.
 """
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2104_02646_gb300 import inputs as I
 
-from gpu_util import (CLOTH_KEYS, POS_CONTACT, TET_KEYS, check_grads, make_target, rel_pos, run_gpu,
-                      run_oracle)
+from gpu_util import (CLOTH_KEYS, POS_CONTACT, TET_KEYS, check_grads, check_grads_conditioned, check_state,
+                      fp32_inputs, make_target, run_gpu, run_oracle)
 
 pytestmark = pytest.mark.gpu
 
@@ -20,47 +33,68 @@ def ctx(gs):
     return gs.Context(0)
 
 
-@pytest.mark.parametrize("K", [1, 0])
-def test_block64_full_size(gs, ctx, K):
+@pytest.fixture(scope="module")
+def block64_ref():
     # 1,310,720 tets on the ground (contact from step 0), heterogeneous
-    # materials, random velocities: 2 steps, every state kept (K = 1) and the
-    # checkpoint-and-recompute path (library K)
-    S = 2
+    # materials, random velocities; the oracle's rollout + adjoint over the
+    # benchmark's 200 steps, shared by the K = 1 and K = 14 runs
+    S = 200
+    O.set_threads(0)
     p = I.block(n=64, steps=S)
     assert p.n_elems == 1310720 and p.n_nodes == 274625
     tgt = make_target(p, S)
-    ref = run_oracle(p, S, tgt)
+    return p, tgt, run_oracle(p, S, tgt)
+
+
+@pytest.mark.parametrize("K", [1, 14])
+def test_block64_full_horizon(gs, ctx, block64_ref, K):
+    p, tgt, ref = block64_ref
+    S = p.steps
     out = run_gpu(gs, ctx, p, S, tgt, K=K, patch_elems=256, block_threads=128)
-    assert rel_pos(out["x"], ref["x"]) <= POS_CONTACT
+    check_state(out["x"], out["v"], ref["x"], ref["v"], p.x0, POS_CONTACT, vel_entry=False)
     assert abs(out["loss"] - ref["loss"]) <= 1e-3 * abs(ref["loss"])
     check_grads(out, ref, TET_KEYS)
 
 
-def test_cloth_256_full_size(gs, ctx):
-    # the stable variant of the 256^2 cloth (130,050 triangles, 194,565 hinges),
-    # placed 1 cm below the top of the sphere so that contact, membrane and
-    # bending respond from step 0 (a flat cloth in free fall has no material
-    # sensitivity): 10 steps
-    S = 10
-    p = I.cloth("3s", n=256, steps=S, height=0.29)
+@pytest.mark.parametrize("S", [330, 500])
+def test_cloth_256_full_horizon(gs, ctx, S):
+    # the stable variant of the 256^2 cloth (130,050 triangles, 194,565
+    # hinges) over the 500 steps of the workload: it falls 5 mm onto the
+    # sphere (near step 320) and drapes over it for the rest.  At 330 steps
+    # (ten steps into contact; before it the flat sheet is unstrained and its
+    # material gradients vanish) every bar holds as stated.  Over the draping phase the
+    # gradients become ill-conditioned at FP32 precision (C20): the FP64
+    # oracle itself, run on its inputs rounded to FP32, moves them by up to
+    # ~8e-3 at step 500, concentrated on the triangles in contact; there the
+    # gradients are held to 10x that sensitivity (check_grads_conditioned)
+    # while the state keeps the contact bar
+    O.set_threads(0)
+    p = I.cloth("3s", n=256, steps=S)
     assert (p.n_nodes, p.n_elems, p.n_hinges) == (65536, 130050, 194565)
     tgt = make_target(p, S)
     ref = run_oracle(p, S, tgt)
     out = run_gpu(gs, ctx, p, S, tgt, K=1, patch_elems=256, block_threads=128)
-    assert rel_pos(out["x"], ref["x"]) <= POS_CONTACT
-    check_grads(out, ref, CLOTH_KEYS)
+    check_state(out["x"], out["v"], ref["x"], ref["v"], p.x0, POS_CONTACT, vel_entry=False)
+    assert abs(out["loss"] - ref["loss"]) <= 1e-3 * abs(ref["loss"])
+    if S <= 330:
+        check_grads(out, ref, CLOTH_KEYS)
+    else:
+        q, tgt32 = fp32_inputs(p, tgt)
+        ref32 = run_oracle(q, S, tgt32)
+        check_grads_conditioned(out, ref, ref32, CLOTH_KEYS)
 
 
-def test_batch_512_sampled_members(gs, ctx):
+def test_batch_512_sampled_members_full_horizon(gs, ctx):
     # all 512 meshes of the batch workload advance together in one launch per
-    # step; sampled members (smallest, median, largest) are compared with the
-    # oracle run alone
+    # step for the workload's 300 steps; sampled members (smallest, median,
+    # largest) are compared with the oracle run alone
     import torch
-    S = 6
+    S = 300
+    O.set_threads(0)
     probs = I.batch(n_meshes=512, steps=S)
-    # a seeded N(0, 0.1 m/s) initial velocity field on every member, so that the
-    # short rollout strains the solids (6 steps of free fall alone would leave
-    # the material gradients at exactly zero)
+    # a seeded N(0, 0.1 m/s) initial velocity field on every member, so that
+    # the rollout strains the solids (300 steps of free fall from >= 5 cm
+    # alone would leave the material gradients at exactly zero)
     rng = np.random.default_rng(11)
     for p in probs:
         p.v0 = rng.normal(0.0, 0.1, p.X.shape)
@@ -88,8 +122,11 @@ def test_batch_512_sampled_members(gs, ctx):
     for i in picks:
         ref = run_oracle(probs[i], S, targets[i])
         x = torch.empty(probs[i].n_nodes, 3, device=dev)
-        meshes[i].get_state(x)
-        assert rel_pos(x.cpu().numpy().astype(np.float64), ref["x"]) <= POS_CONTACT
+        v = torch.empty(probs[i].n_nodes, 3, device=dev)
+        meshes[i].get_state(x, v)
+        check_state(x.cpu().numpy().astype(np.float64), v.cpu().numpy().astype(np.float64), ref["x"], ref["v"],
+                    probs[i].x0, POS_CONTACT)
+        assert abs(loss[i].item() - ref["loss"]) <= 1e-3 * abs(ref["loss"])
         out = {k: t.cpu().numpy().astype(np.float64) for k, t in grads[i].items()}
         check_grads(out, ref, TET_KEYS)
     batch.close()

@@ -14,7 +14,8 @@ from oracle import oracle as O
 from oracle import render_oracle as RO
 from paper_2104_02646_gb300 import inputs as I
 
-from gpu_util import CLOTH_KEYS, GRAD_COS, GRAD_REL, POS_CONTACT, TET_KEYS, check_grads, cosine, make_target, rel, rel_pos
+from gpu_util import (CLOTH_KEYS, GRAD_COS, GRAD_REL, POS_CONTACT, TET_KEYS, check_grads, cosine, make_target,
+                      quat_tangent, rel, rel_pos)
 
 pytestmark = pytest.mark.gpu
 
@@ -146,7 +147,9 @@ def test_rigid16384_sampled_bodies(gs, ctx):
         ref_s = ro.rollout(bodies[b].state0, 1e-3, S)
         np.testing.assert_allclose(sS[b, :3], ref_s[:3], atol=1e-3 * (1 + np.abs(ref_s[:3]).max()))
         _, ref = ro.loss_grad(bodies[b].state0, 1e-3, S, None, seed[b])
-        for a, r in ((out["d_state0"][b], ref["state0"]), (out["d_contact"][b], ref["contact"]),
+        q0 = bodies[b].state0[3:7]
+        for a, r in ((quat_tangent(out["d_state0"][b], q0), quat_tangent(ref["state0"], q0)),
+                     (out["d_contact"][b], ref["contact"]),
                      (out["d_inertia"][b], ref["inertia"])):
             if np.linalg.norm(r) == 0:
                 continue
