@@ -66,6 +66,7 @@ enum {
     GS_ECANCELLED = -7,  /* query cancelled                                   */
     GS_ENOTFOUND = -8,   /* unknown ticket                                    */
     GS_EUNSUPPORTED = -9,
+    GS_EINDEX = -10,     /* checked build: a table index was out of range     */
     GS_PENDING = 1,      /* query not finished yet                            */
     GS_WUNSTABLE = 2     /* dt above the explicit stability estimate (ran)    */
 };
@@ -175,6 +176,13 @@ typedef struct gs_grads {
 
 /* ---- library ------------------------------------------------------------ */
 GS_API int gs_version(void);
+/* Build options of the loaded library (no paper counterpart): the bit
+ * GS_BUILD_CHECKED is set in the checked build (libgradsim_check.so), whose
+ * step kernels test every mesh-table index on the device before using it;
+ * an out-of-range index sets the mesh's status and gs_mesh_check then
+ * returns GS_EINDEX (no trap: the kernel skips the access). */
+#define GS_BUILD_CHECKED 1
+GS_API int gs_build_flags(void);
 /* Message of the last failed call on this thread ("" if none). */
 GS_API const char* gs_last_error(void);
 
@@ -191,8 +199,11 @@ GS_API gs_status gs_set_graphs(gs_ctx* ctx, int enable);
 
 /* Per-launch timing of the step kernels with CUDA events on the launching
  * stream (measurement support; the paper has no counterpart).  While on,
- * steps run as one launch per kernel (no graphs) with an event pair around
- * each patch and boundary kernel.  gs_profile_read synchronises the pending
+ * every patch and boundary kernel has an event pair around it: with CUDA
+ * graphs on (gs_set_graphs), each run of steps is captured as a graph of
+ * its own with the events as external event nodes (which ends the
+ * programmatic overlap of neighbouring kernels); with graphs off, steps run
+ * as one launch per kernel.  gs_profile_read synchronises the pending
  * events and returns, per kernel, the launch count and summed milliseconds,
  * then clears them; n_out receives the number of kernels with launches. */
 typedef struct gs_kernel_time {
@@ -411,9 +422,12 @@ GS_API gs_status gs_batch_adjoint(gs_batch* batch, const gs_grads* grads, void* 
  * GPU loading the library holds until exit.  n_nodes above
  * GS_NOALLOC_MAX_NODES is rejected with GS_EINVAL before any work.  The first
  * call on a device looks up the array's device address (once per device);
- * make that first call before any stream capture.  All calls share the
- * array: calls whose work overlaps on the GPU race and must be serialised
- * by the caller.  Enqueued on `stream`. */
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process: after cudaDeviceReset (which destroys the device's
+ * primary context and with it the array) this entry point must not be
+ * called again on that device.  All calls share the array: calls whose work
+ * overlaps on the GPU race and must be serialised by the caller.  Enqueued
+ * on `stream`. */
 #define GS_NOALLOC_MAX_NODES 4194304
 GS_API gs_status gs_loss_noalloc(const float* x, const float* target, int n_nodes, double* loss_out,
                                  float* dL_dx, void* stream);

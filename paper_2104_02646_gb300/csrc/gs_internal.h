@@ -78,6 +78,7 @@ struct alignas(16) MeshRT {  // 16 B aligned: the patch kernels bulk-copy it int
     // static mesh data
     int kind, n_nodes, n_int, n_bnd;
     int n_elems, n_hinges, active, pe;  // pe: elements per patch
+    int n_part, pad_[3];                // boundary partials (bnd_rowptr[n_bnd])
     float4* rec;             // element records, patch-contiguous (rec_at), 4 float4 planes per patch
     float4* hrec;            // [4][B] hinge records
     const int* bnd_ids;      // per-patch boundary lists (internal node ids)

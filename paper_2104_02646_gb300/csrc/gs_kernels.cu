@@ -70,6 +70,52 @@ __device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;
 __device__ __forceinline__ void pdl_done() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
+// Index checks of the checked build (compiled with -DGS_CHECK): every index
+// that the step kernels read from the mesh tables and then use to address
+// shared or global memory (local node ids of a record, CSR row pointers and
+// slots, partial positions, boundary node ids, interior node ranges, the
+// stage layout) is tested against its range first.  A violation sets bit 2
+// (value 4) of the mesh's status word and the access is skipped or sent to a
+// harmless slot, so the kernel never leaves its buffers; the run's results
+// are then invalid and gs_mesh_check reports GS_EINDEX.  Without GS_CHECK
+// every test compiles away.
+// ---------------------------------------------------------------------------
+#ifdef GS_CHECK
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+constexpr int kStatusIndex = 4;
+
+__device__ __forceinline__ bool idx_ok(bool ok, int* status) {
+    if (kChecked && !ok) {
+        atomicOr(status, kStatusIndex);
+        return false;
+    }
+    return true;
+}
+// the four (three) 16-bit local node ids of a record are below n_loc
+__device__ __forceinline__ bool ids_in(uint2 id, int n_loc, int n_ids) {
+    return (int)(id.x & 0xffff) < n_loc && (int)(id.x >> 16) < n_loc && (int)(id.y & 0xffff) < n_loc &&
+           (n_ids < 4 || (int)(id.y >> 16) < n_loc);
+}
+// four CSR slots (float4 indices into the staged planes, 4 n_rec = the zero
+// slot): out-of-range slots are sent to the zero slot
+__device__ __forceinline__ uint2 checked_slots(uint2 q, int n_rec, int* status) {
+    if (!kChecked) return q;
+    const uint32_t lim = 4u * (uint32_t)n_rec;
+    uint32_t a = q.x & 0xffff, b = q.x >> 16, c = q.y & 0xffff, d = q.y >> 16;
+    if (a > lim || b > lim || c > lim || d > lim) {
+        atomicOr(status, kStatusIndex);
+        a = a > lim ? lim : a;
+        b = b > lim ? lim : b;
+        c = c > lim ? lim : c;
+        d = d > lim ? lim : d;
+    }
+    return make_uint2(a | (b << 16), c | (d << 16));
+}
+
+// ---------------------------------------------------------------------------
 // TMA bulk copies global -> shared completing on an mbarrier
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -454,7 +500,7 @@ __device__ __forceinline__ void produce_gather(const PatchDesc& p, const MeshRT&
 #pragma unroll
     for (int j = 0; j < kPrefetchIds; ++j) {
         const int k = lane + 32 * j;
-        if (k < p.n_bnd) {
+        if (k < p.n_bnd && idx_ok(g[j] >= m.n_int && g[j] < m.n_nodes, m.status)) {
             cp16(S.xs + p.n_int + k, X + g[j]);
             if (gv) cp16(S.vB + k, V + g[j]);
             if (adjoint) {
@@ -474,7 +520,7 @@ __device__ __forceinline__ void produce_gather(const PatchDesc& p, const MeshRT&
 #pragma unroll
         for (int j = 0; j < kPrefetchIds; ++j) {
             const int k = k0 + lane + 32 * j;
-            if (k < p.n_bnd) {
+            if (k < p.n_bnd && idx_ok(h[j] >= m.n_int && h[j] < m.n_nodes, m.status)) {
                 cp16(S.xs + p.n_int + k, X + h[j]);
                 if (gv) cp16(S.vB + k, V + h[j]);
                 if (adjoint) {
@@ -510,9 +556,11 @@ __device__ __forceinline__ void tet_elements_fwd(const PatchDesc& p, const MeshR
                                                  int nt) {
     const int nr = S.n_rec;
     zero_pad_slot(S);
+    const int n_loc = p.n_int + p.n_bnd;
     for (int le = threadIdx.x; le < p.n_e; le += nt) {
         const float4 a = S.rec[le], b = S.rec[nr + le], c = S.rec[2 * nr + le], w = S.rec[3 * nr + le];
         const uint2 id = rec_ids(w);
+        if (!idx_ok(ids_in(id, n_loc, 4), m.status)) continue;
         TetState s;
         tet_state(xyz(S.xs[id.x & 0xffff]), xyz(S.xs[id.x >> 16]), xyz(S.xs[id.y & 0xffff]), xyz(S.xs[id.y >> 16]), a,
                   b, c, w.z + act_of(S.act, le), s);
@@ -529,11 +577,13 @@ __device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Mes
                                                    int nt) {
     const int nr = S.n_rec;
     zero_pad_slot(S);
+    const int n_loc = p.n_int + p.n_bnd;
     for (int lr = threadIdx.x; lr < nr; lr += nt) {
         const RecAt q = rec_slot(S, lr);
         const float4 a = S.rec[q.base], c = S.rec[q.base + 2 * q.stride], w = S.rec[q.base + 3 * q.stride];
         float4 b = S.rec[q.base + q.stride];
         const uint2 id = rec_ids(w);
+        if (!idx_ok(ids_in(id, n_loc, lr < p.n_e ? 3 : 4), m.status)) continue;
         if (lr < p.n_e) {
             TriState s;
             b.w += act_of(S.act, lr);  // actuation (b.w)
@@ -572,9 +622,11 @@ __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshR
     const float dt = m.dt;
     const int nr = S.n_rec;
     zero_pad_slot(S);
+    const int n_loc = p.n_int + p.n_bnd;
     for (int le = threadIdx.x; le < p.n_e; le += nt) {
         const float4 a = S.rec[le], b = S.rec[nr + le], c = S.rec[2 * nr + le], w = S.rec[3 * nr + le];
         const uint2 id = rec_ids(w);
+        if (!idx_ok(ids_in(id, n_loc, 4), m.status)) continue;
         const int i0 = id.x & 0xffff, i1 = id.x >> 16, i2 = id.y & 0xffff, i3 = id.y >> 16;
         const float4 x0 = S.xs[i0], x1 = S.xs[i1], x2 = S.xs[i2], x3 = S.xs[i3];
         const float3 v0 = xyz(S.vh[i0]), v1 = xyz(S.vh[i1]), v2 = xyz(S.vh[i2]), v3 = xyz(S.vh[i3]);
@@ -603,11 +655,13 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
     const float dt = m.dt;
     const int nr = S.n_rec;
     zero_pad_slot(S);
+    const int n_loc = p.n_int + p.n_bnd;
     for (int lr = threadIdx.x; lr < nr; lr += nt) {
         const RecAt q = rec_slot(S, lr);
         const float4 a = S.rec[q.base], b = S.rec[q.base + q.stride], c = S.rec[q.base + 2 * q.stride],
                      w = S.rec[q.base + 3 * q.stride];
         const uint2 id = rec_ids(w);
+        if (!idx_ok(ids_in(id, n_loc, lr < p.n_e ? 3 : 4), m.status)) continue;
         if (lr < p.n_e) {
             const int i0 = id.x & 0xffff, i1 = id.x >> 16, i2 = id.y & 0xffff;
             const float4 x0 = S.xs[i0], x1 = S.xs[i1], x2 = S.xs[i2];
@@ -693,10 +747,10 @@ __device__ __forceinline__ void add3(float3& acc, float4 q) {
 #define GS_ROW_SUM(T, ADD, ZERO)                                                                            \
     T acc = ZERO;                                                                                           \
     if (k >= k1) return acc;                                                                                \
-    uint2 q = *reinterpret_cast<const uint2*>(S.sl + k);                                                    \
+    uint2 q = checked_slots(*reinterpret_cast<const uint2*>(S.sl + k), S.n_rec, status);                   \
     float4 c0 = S.rec[q.x & 0xffff], c1 = S.rec[q.x >> 16], c2 = S.rec[q.y & 0xffff], c3 = S.rec[q.y >> 16]; \
     for (k += 4; k < k1; k += 4) {                                                                          \
-        q = *reinterpret_cast<const uint2*>(S.sl + k);                                                      \
+        q = checked_slots(*reinterpret_cast<const uint2*>(S.sl + k), S.n_rec, status);                     \
         const float4 n0 = S.rec[q.x & 0xffff], n1 = S.rec[q.x >> 16], n2 = S.rec[q.y & 0xffff],              \
                      n3 = S.rec[q.y >> 16];                                                                 \
         ADD(acc, c0);                                                                                       \
@@ -714,21 +768,32 @@ __device__ __forceinline__ void add3(float3& acc, float4 q) {
     ADD(acc, c3);                                                                                           \
     return acc;
 
-__device__ __forceinline__ float4 row_sum4(const Stage& S, int k, int k1) {
+__device__ __forceinline__ float4 row_sum4(const Stage& S, int k, int k1, int* status) {
     GS_ROW_SUM(float4, add4, make_float4(0.f, 0.f, 0.f, 0.f))
 }
-__device__ __forceinline__ float3 row_sum3(const Stage& S, int k, int k1) {
+__device__ __forceinline__ float3 row_sum3(const Stage& S, int k, int k1, int* status) {
     GS_ROW_SUM(float3, add3, make_float3(0.f, 0.f, 0.f))
+}
+// a local CSR row [k, k1): 4-aligned (padded rows) and inside the patch's slots
+__device__ __forceinline__ bool row_ok(int k, int k1, int n_slots, int* status) {
+    return idx_ok(k <= k1 && k1 <= n_slots && (k & 3) == 0 && (k1 & 3) == 0, status);
 }
 #undef GS_ROW_SUM
 
 // node phases: fixed-order corner sums, then interior update or partial
 __device__ __forceinline__ void forward_nodes(const PatchDesc& p, const MeshRT& m, int tick, const Stage& S, int nt) {
     const int n_loc = p.n_int + p.n_bnd;
+    if (!idx_ok(p.int_begin >= 0 && p.int_begin + p.n_int <= m.n_int, m.status)) return;
     for (int l = threadIdx.x; l < n_loc; l += nt) {
-        const float3 f = row_sum3(S, S.rp[l], S.rp[l + 1]);
-        if (l < p.n_int) node_forward(m, tick, p.int_begin + l, S.xs[l], S.vs[l], f);
-        else m.partials[S.pos[l - p.n_int]] = f4(f, 0.f);
+        const int k = S.rp[l], k1 = S.rp[l + 1];
+        if (!row_ok(k, k1, p.n_slots, m.status)) continue;
+        const float3 f = row_sum3(S, k, k1, m.status);
+        if (l < p.n_int) {
+            node_forward(m, tick, p.int_begin + l, S.xs[l], S.vs[l], f);
+        } else {
+            const int pp = S.pos[l - p.n_int];
+            if (idx_ok(pp >= 0 && pp < m.n_part, m.status)) m.partials[pp] = f4(f, 0.f);
+        }
     }
 }
 
@@ -752,14 +817,19 @@ template <int KIND>
 __device__ __forceinline__ void adjoint_nodes(const PatchDesc& p, const MeshRT& m, const Stage& S, int nt) {
     const int n_loc = p.n_int + p.n_bnd;
     const bool air = KIND == GS_CLOTH && stage_air(S, m);
+    if (!idx_ok(p.int_begin >= 0 && p.int_begin + p.n_int <= m.n_int, m.status)) return;
     for (int l = threadIdx.x; l < n_loc; l += nt) {
-        const float4 acc = row_sum4(S, S.rp[l], S.rp[l + 1]);
-        const float3 va = air ? row_sum_air_v(S, S.rp[l], S.rp[l + 1]) : make_float3(0.f, 0.f, 0.f);
+        const int k = S.rp[l], k1 = S.rp[l + 1];
+        if (!row_ok(k, k1, p.n_slots, m.status)) continue;
+        const float4 acc = row_sum4(S, k, k1, m.status);
+        const float3 va = air ? row_sum_air_v(S, k, k1) : make_float3(0.f, 0.f, 0.f);
         if (l < p.n_int) {
             node_adjoint(m, p.int_begin + l, S.xs[l], S.vs[l], S.xb[l], S.vb[l], xyz(acc), acc.w, S.wb[l], va);
         } else {
-            m.partials[S.pos[l - p.n_int]] = acc;
-            if (air) m.partials_v[S.pos[l - p.n_int]] = f4(va, 0.f);
+            const int pp = S.pos[l - p.n_int];
+            if (!idx_ok(pp >= 0 && pp < m.n_part, m.status)) continue;
+            m.partials[pp] = acc;
+            if (air) m.partials_v[pp] = f4(va, 0.f);
         }
     }
 }
@@ -859,6 +929,16 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
                 return;
             }
             const MeshRT& m = rts[p.mesh];
+            if (kChecked) {
+                // the patch's stage fits the stage the launch reserved and its
+                // local ids fit 16 bits; otherwise it is replaced by an empty patch
+                const Layout Lc = patch_layout(m.kind, p.n_e, p.n_h, p.n_int + p.n_bnd, p.n_int, p.n_slots, ADJ,
+                                               extras != 0);
+                if (!idx_ok(kHdr + Lc.total <= stage_bytes && p.n_int + p.n_bnd < 65536 && 4 * (p.n_e + p.n_h) < 65535,
+                            m.status)) {
+                    p.n_e = p.n_h = p.n_int = p.n_bnd = p.n_slots = 0;
+                }
+            }
             if (lane == 0) {
                 // the stage keeps its mesh record from the last patch it held
                 const bool copy_rt = ((const PatchDesc*)b)->mesh != p.mesh;
@@ -975,10 +1055,14 @@ __global__ void __launch_bounds__(kBndThreads, 8)
         const float4* X = bufx(m, ib);
         const float4* V = bufv(m, ib);
         const int i0 = threadIdx.x, i1 = threadIdx.x + kBndThreads;
-        const bool h0 = i0 < nb.count, h1 = i1 < nb.count;
+        bool h0 = i0 < nb.count, h1 = i1 < nb.count;
         const int b0 = nb.begin + i0, b1 = nb.begin + i1;
         int k0 = 0, e0 = 0, k1 = 0, e1 = 0;
         float4 x0, v0, x1, v1;
+        if (kChecked) {
+            h0 = h0 && idx_ok(b0 >= 0 && b0 < m.n_bnd, m.status);
+            h1 = h1 && idx_ok(b1 >= 0 && b1 < m.n_bnd, m.status);
+        }
         if (h0) {
             k0 = m.bnd_rowptr[b0];
             e0 = m.bnd_rowptr[b0 + 1];
@@ -990,6 +1074,10 @@ __global__ void __launch_bounds__(kBndThreads, 8)
             e1 = m.bnd_rowptr[b1 + 1];
             x1 = X[m.n_int + b1];
             v1 = V[m.n_int + b1];
+        }
+        if (kChecked) {
+            if (!idx_ok(!h0 || (b0 < m.n_bnd && 0 <= k0 && k0 <= e0 && e0 <= m.n_part), m.status)) h0 = false, k0 = e0 = 0;
+            if (!idx_ok(!h1 || (b1 < m.n_bnd && 0 <= k1 && k1 <= e1 && e1 <= m.n_part), m.status)) h1 = false, k1 = e1 = 0;
         }
         float4 f0, f1;
         partial_sums2(m.partials, k0, e0 - k0, k1, e1 - k1, f0, f1);
@@ -1010,9 +1098,13 @@ __global__ void __launch_bounds__(kBndThreads, 6)
         const float4* X = bufx(m, sb);
         const float4* V = bufv(m, sb);
         const int i0 = threadIdx.x, i1 = threadIdx.x + kBndThreads;
-        const bool h0 = i0 < nb.count, h1 = i1 < nb.count;
+        bool h0 = i0 < nb.count, h1 = i1 < nb.count;
         const int b0 = nb.begin + i0, b1 = nb.begin + i1;
         const int g0 = m.n_int + b0, g1 = m.n_int + b1;
+        if (kChecked) {
+            h0 = h0 && idx_ok(b0 >= 0 && b0 < m.n_bnd, m.status);
+            h1 = h1 && idx_ok(b1 >= 0 && b1 < m.n_bnd, m.status);
+        }
         int k0 = 0, e0 = 0, k1 = 0, e1 = 0;
         float4 x0, v0, xb0, vb0, x1, v1, xb1, vb1;
         double w0 = 0.0, w1 = 0.0;
@@ -1033,6 +1125,10 @@ __global__ void __launch_bounds__(kBndThreads, 6)
             xb1 = m.xb[g1];
             vb1 = m.vb[g1];
             w1 = m.wbar[g1];
+        }
+        if (kChecked) {
+            if (!idx_ok(!h0 || (b0 < m.n_bnd && 0 <= k0 && k0 <= e0 && e0 <= m.n_part), m.status)) h0 = false, k0 = e0 = 0;
+            if (!idx_ok(!h1 || (b1 < m.n_bnd && 0 <= k1 && k1 <= e1 && e1 <= m.n_part), m.status)) h1 = false, k1 = e1 = 0;
         }
         float4 a0, a1;
         partial_sums2(m.partials, k0, e0 - k0, k1, e1 - k1, a0, a1);
@@ -1640,3 +1736,5 @@ void launch_finalize_grads(const Launch& L, double* mbar, const gs_grads& g, siz
 }
 
 }  // namespace gs
+
+extern "C" GS_API int gs_build_flags(void) { return gs::kChecked ? GS_BUILD_CHECKED : 0; }

@@ -1,6 +1,7 @@
 // Host runtime of the gradsim C ABI: context, mesh construction, launch sets,
 // checkpointed rollout and adjoint, batching.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -22,6 +23,15 @@ namespace gs {
 // errors
 // ---------------------------------------------------------------------------
 static thread_local std::string g_last_error;
+
+// NVTX range for profilers (forward phase, adjoint phase, each segment);
+// costs nothing when no profiler is attached
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 gs_status set_error(gs_status s, const std::string& msg) {
     g_last_error = msg;
@@ -680,6 +690,7 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     r.topo = (const uint4*)m->topo.p;
     r.pe = pe;
     r.bnd_rowptr = (const int*)m->bnd_rowptr.p;
+    r.n_part = T.bnd_rowptr.empty() ? 0 : T.bnd_rowptr[T.n_bnd];
     r.part_pos = (const int*)m->part_pos.p;
     r.partials = (float4*)m->partials.p;
     r.node_perm = (const int*)m->node_perm.p;
@@ -849,6 +860,7 @@ extern "C" gs_status gs_mesh_check(gs_mesh* m, int reset, void* stream) {
     GS_CUDA(cudaMemcpyAsync(&st, m->status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     GS_CUDA(cudaStreamSynchronize(s));
     if (reset) GS_CUDA(cudaMemsetAsync(m->status.p, 0, sizeof(int), s));
+    if (st & 4) return set_error(GS_EINDEX, "an index check of the checked build failed; results are invalid");
     if (st & 2) return set_error(GS_ETIMEOUT, "a bounded wait in a step kernel ran out; results are invalid");
     if (st & 1) return set_error(GS_ENONFINITE, "non-finite state");
     return GS_OK;
@@ -959,7 +971,31 @@ LaunchSet::~LaunchSet() {
 // `steps` forward (phase 0) or adjoint (phase 1) steps, ticks 0..steps-1
 gs_status LaunchSet::run(int phase, int steps, cudaStream_t s) {
     if (steps <= 0) return GS_OK;
-    if (!ctx->graphs || ctx->prof) {
+    if (ctx->graphs && ctx->prof) {
+        // timed launches in the graph path: a graph captured for this call
+        // with an event node before and after every kernel (the event nodes
+        // end the programmatic overlap between neighbouring kernels)
+        cudaStream_t cs = ctx->capture_stream;
+        GS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        ctx->prof->capture = true;
+        for (int t = 0; t < steps; ++t) {
+            if (phase == 0) launch_forward_step(launch, t, cs, ctx->prof);
+            else launch_adjoint_step(launch, t, cs, ctx->prof);
+        }
+        ctx->prof->capture = false;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+        cudaGraphExec_t ge = nullptr;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+        e = cudaGraphLaunch(ge, s);
+        cudaGraphExecDestroy(ge);  // freed once the launch completes
+        if (e != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
+        return GS_OK;
+    }
+    if (!ctx->graphs) {
         for (int t = 0; t < steps; ++t) {
             if (phase == 0) launch_forward_step(launch, t, s, ctx->prof);
             else launch_adjoint_step(launch, t, s, ctx->prof);
@@ -999,6 +1035,7 @@ static int choose_K(int S, int K) {
 // forward rollout over a launch set (App. B, checkpoint every K steps)
 gs_status LaunchSet::rollout(const std::vector<float>& dts, int S, int K, const std::vector<const float*>& targets,
                              double* loss_dev, cudaStream_t s) {
+    NvtxRange range("gs forward rollout");
     if (S < 0) return set_error(GS_EINVAL, "n_steps must be >= 0");
     K = choose_K(S, K);
     // K = 1 keeps every state (state n in buffer 1 + n): the adjoint then
@@ -1052,6 +1089,7 @@ gs_status LaunchSet::rollout(const std::vector<float>& dts, int S, int K, const 
         launch_copy_state(launch, s);
     } else {
         for (int c = 0; c < n_ck; ++c) {
+            NvtxRange seg("gs forward segment");
             const int steps = std::min(K, S - c * K);
             for (gs_mesh* m : meshes) {
                 m->rt.in_a = m->rt.in_b = m->rt.out_a = m->rt.out_b = 0;
@@ -1089,6 +1127,7 @@ gs_status LaunchSet::rollout(const std::vector<float>& dts, int S, int K, const 
 // reverse steps read the stored states directly.
 gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std::vector<const float*>& seed_v,
                              const std::vector<gs_grads>& grads, int keep, cudaStream_t s) {
+    NvtxRange range("gs adjoint");
     for (gs_mesh* m : meshes)
         if (!m->ro.valid) return set_error(GS_ESTATE, "gs_adjoint needs a preceding gs_rollout");
     const int S = meshes[0]->ro.S, K = meshes[0]->ro.K, n_ck = meshes[0]->ro.n_ck;
@@ -1139,6 +1178,7 @@ gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std:
         GS_TRY(run(1, S, s));
     }
     for (int sg = K == 1 ? -1 : n_ck - 1; sg >= 0; --sg) {
+        NvtxRange seg("gs adjoint segment (recompute + reverse)");
         const int steps = std::min(K, S - sg * K);
         for (gs_mesh* m : meshes) {
             MeshRT& r = m->rt;
@@ -1257,11 +1297,13 @@ cudaEvent_t EventProf::get() {
 }
 void EventProf::begin(int, cudaStream_t s) {
     open = get();
-    cudaEventRecord(open, s);
+    if (capture) cudaEventRecordWithFlags(open, s, cudaEventRecordExternal);
+    else cudaEventRecord(open, s);
 }
 void EventProf::end(int kind, cudaStream_t s) {
     cudaEvent_t b = get();
-    cudaEventRecord(b, s);
+    if (capture) cudaEventRecordWithFlags(b, s, cudaEventRecordExternal);
+    else cudaEventRecord(b, s);
     pending.push_back(Pending{kind, open, b});
     open = nullptr;
 }

@@ -11,7 +11,8 @@
 #include "gs_internal.h"
 
 namespace gs {
-// per-launch CUDA-event timing of the step kernels (gs_profile)
+// per-launch CUDA-event timing of the step kernels (gs_profile); with CUDA
+// graphs on, the events are external event nodes of the captured graphs
 struct EventProf : Prof {
     struct Pending {
         int kind;
@@ -20,6 +21,7 @@ struct EventProf : Prof {
     std::vector<cudaEvent_t> pool;
     std::vector<Pending> pending;
     cudaEvent_t open = nullptr;
+    bool capture = false;  // recording into a stream capture: external event nodes
     double total_ms[KT_COUNT] = {0};
     unsigned long long launches[KT_COUNT] = {0};
     cudaEvent_t get();

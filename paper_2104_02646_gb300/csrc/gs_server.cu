@@ -297,7 +297,7 @@ void gs_server::collect() {
         if (r.status == GS_OK && q->h_stage) {
             int st = 0;
             cudaMemcpy(&st, m->status.p, sizeof(int), cudaMemcpyDeviceToHost);
-            r.status = (st & 2) ? GS_ETIMEOUT : (st & 1) ? GS_ENONFINITE : GS_OK;
+            r.status = (st & 4) ? GS_EINDEX : (st & 2) ? GS_ETIMEOUT : (st & 1) ? GS_ENONFINITE : GS_OK;
             const double* d = q->h_stage;
             r.n_elems = (int)E;
             r.n_hinges = (int)B;

@@ -17,6 +17,8 @@ from . import _build
 
 GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ESTATE, GS_ENONFINITE = 0, -1, -2, -3, -4, -5
 GS_ETIMEOUT, GS_ECANCELLED, GS_ENOTFOUND, GS_EUNSUPPORTED = -6, -7, -8, -9
+GS_EINDEX = -10
+GS_BUILD_CHECKED = 1
 GS_PENDING, GS_WUNSTABLE = 1, 2
 GS_NOALLOC_MAX_NODES = 4194304
 GS_TET, GS_CLOTH = 0, 1
@@ -119,6 +121,7 @@ class gs_kernel_time(C.Structure):
 # every entry point of include/gradsim.h with its C signature
 _PROTOS = {
     "gs_version": (C.c_int, []),
+    "gs_build_flags": (C.c_int, []),
     "gs_last_error": (C.c_char_p, []),
     "gs_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_size_t, C.POINTER(gs_allocator)]),
     "gs_destroy": (None, [_vp]),
@@ -172,15 +175,19 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if os.environ.get("GRADSIM_CHECKED") == "1" else _build.LIB
 
 
 def load(build: bool = False):
-    """Load libgradsim.so (building it first when ``build`` is set)."""
+    """Load libgradsim.so (building it first when ``build`` is set); with the
+    environment variable GRADSIM_CHECKED=1, the index-checked build
+    libgradsim_check.so instead."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build() if build else _build.LIB
+    if build:
+        _build.build()
+    path = library_path()
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library {path} is not built; run __graft_entry__.build() first")
     L = C.CDLL(path)
