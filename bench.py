@@ -59,12 +59,15 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="block: library defaults instead of the autotuner's patch shape and K")
     ap.add_argument("--cpu-steps", type=int, default=4,
-                    help="oracle steps in the CPU sample (about 3 s each on one core for block64)")
-    ap.add_argument("--workload", default="block", choices=["block", "bar", "cloth", "batch", "serve", "control", "cloth_air", "render", "rigid"],
+                    help="oracle steps in the one-thread CPU sample (the all-core sample runs 4x as many)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="block: skip the batched and served comparisons added to the default line")
+    ap.add_argument("--extra-queries", type=int, default=300, help="block: queries per rate of the served comparison")
+    ap.add_argument("--workload", default="block", choices=["block", "bar", "cloth", "batch", "serve", "control", "cloth_air", "render", "rigid", "recompute"],
                     help="block: the 1.3M-tet solid (default line); the others measure the remaining workloads")
     ap.add_argument("--meshes", type=int, default=512, help="batch: number of meshes")
     ap.add_argument("--rates", default="10,20,50,100,200,500", help="serve: arrival rates (req/s)")
-    ap.add_argument("--queries", type=int, default=200, help="serve: queries per rate")
+    ap.add_argument("--queries", type=int, default=2000, help="serve: queries per rate")
     return ap.parse_args()
 
 
@@ -150,33 +153,48 @@ def ncu_traffic(kernel, n_elems):
     return float(k["dram_bytes_per_elem"]) * n_elems
 
 
-def cpu_sample(problem, steps):
+def cpu_sample(problem, steps, threads=0):
     """The FP64 oracle as it stands on a bounded sample: `steps` forward steps
-    of the same mesh plus their adjoint.  Returns (elem-steps/s, seconds)."""
+    of the same mesh plus their adjoint, on `threads` host threads (0: every
+    core; the results do not depend on it).  Returns (elem-steps/s, seconds,
+    threads used)."""
     from oracle import oracle as O
+    used = O.set_threads(threads)
     m = O.Model(problem)
     xS, _ = m.rollout(problem.x0, problem.v0, problem.dt, steps)
     target = xS + 1e-3
     t0 = time.perf_counter()
     m.loss_grad(problem.x0, problem.v0, problem.dt, steps, target)
     t = time.perf_counter() - t0
-    return problem.n_elems * steps / t, t
+    O.set_threads(0)
+    return problem.n_elems * steps / t, t, used
+
+
+def cpu_baseline(problem, steps_one, steps_all, label):
+    """The oracle on every host core (the reported value) and on one thread."""
+    v1, t1, _ = cpu_sample(problem, steps_one, 1)
+    va, ta, cores = cpu_sample(problem, steps_all, 0)
+    return {"value": va, "unit": "element-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{label}: {steps_all} forward steps + their adjoint on {cores} threads ({ta:.1f} s); "
+                      f"{steps_one} steps on 1 thread ({t1:.1f} s)",
+            "single_thread": {"value": v1, "cores": 1}}
 
 
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return
+    from oracle import oracle as O
     from paper_2104_02646_gb300 import inputs as I
     p = I.block(n=args.cells, steps=args.rollout)
     times = []
     for i in range(args.warmup + args.steps):
-        _, t = cpu_sample(p, args.cpu_steps)
+        _, t, cores = cpu_sample(p, args.cpu_steps, 0)
         if i >= args.warmup:
             times.append(t)
     value = p.n_elems * args.cpu_steps * len(times) / sum(times)
     sample = (f"block{args.cells} ({p.n_elems} tets): {args.cpu_steps} forward step(s) + their adjoint per "
-              f"benchmark step, FP64 oracle, 1 thread")
+              f"benchmark step, FP64 oracle, {cores} threads")
     line = {
         "impl": "reference", "metric": "fwd+adjoint element-steps/s", "value": value,
         "unit": "element-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -184,7 +202,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"block{args.cells}: {args.cells}^3 hex cells x 5 tets, "
                                f"{args.rollout}-step rollout at dt 5e-5 (sampled on the CPU)"},
-        "cpu_baseline": {"value": value, "unit": "element-steps/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "element-steps/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "element-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -333,6 +351,9 @@ def main():
     peak, peak_kind = measured_peaks()
     achieved = abytes / avg_s / 1e9
     traffic = ncu_traffic(dom, E)
+    # the whole timed step against the roofline of its algorithmic bytes
+    step_bytes = S * (alg_bytes(True, E, N) + alg_bytes(False, E, N))
+    step_achieved = step_bytes / (total_ms / args.steps / 1e3) / 1e9
 
     # ---- end to end through the C ABI with pinned host buffers ---------------
     e2e = None
@@ -367,10 +388,15 @@ def main():
     # ---- CPU baseline: the oracle on a bounded sample -------------------------
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v_cpu, t_cpu = cpu_sample(p, args.cpu_steps)
-        cpu = {"value": v_cpu, "unit": "element-steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"block{args.cells} ({E} tets): {args.cpu_steps} forward step(s) + adjoint, "
-                         f"FP64 oracle, 1 thread, {t_cpu:.1f} s"}
+        cpu = cpu_baseline(p, args.cpu_steps, 4 * args.cpu_steps, f"block{args.cells} ({E} tets), FP64 oracle")
+
+    # ---- batched and served forms against the plain loop (untimed extras) ----
+    extras = None
+    if rank == 0 and ws == 1 and not args.no_extras:
+        mesh.close()
+        torch.cuda.empty_cache()
+        extras = {"batch": measure_batch(args, 512, reps=2),
+                  "serve": [measure_serve(args, rate, args.extra_queries) for rate in (50.0, 500.0)]}
 
     if rank == 0:
         line = {
@@ -389,13 +415,22 @@ def main():
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "alg_bytes_per_launch": abytes, "avg_launch_ms": avg_s * 1e3,
-                         "kernel_share": {k: v[1] / sum(x[1] for x in kt.values()) for k, v in kt.items()}},
+                         "launches_per_step": launches,
+                         "timing": "CUDA events around each kernel inside the captured graphs of one extra step",
+                         "profiled_kernels_ms_per_step": sum(x[1] for x in kt.values()),
+                         "kernel_share": {k: v[1] / sum(x[1] for x in kt.values()) for k, v in kt.items()},
+                         "step": {"alg_bytes": step_bytes, "achieved": step_achieved,
+                                  "frac": step_achieved / peak,
+                                  "element_steps_per_s_at_peak": E * S / (step_bytes / (peak * 1e9))}},
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches_per_step(S, args.K, mesh.info.n_boundary_nodes > 0) * args.steps,
             "cpu_baseline": cpu,
             "wall_s": t_wall,
         }
+        if extras is not None:
+            line["batched_vs_plain"] = extras["batch"]
+            line["served_vs_plain"] = extras["serve"]
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -433,8 +468,10 @@ def _grads(problem, dev):
     return g
 
 
-def _single_mesh_line(args, name, problem, extra_cfg):
-    """Forward rollout + adjoint of one mesh: element-steps/s and steps/s."""
+def _single_mesh_line(args, name, problem, extra_cfg, cpu_steps=None):
+    """Forward rollout + adjoint of one mesh: element-steps/s and steps/s;
+    with cpu_steps = (one-thread steps, all-core steps), the oracle's rate on
+    that sample of the same mesh beside it."""
     import torch
     from paper_2104_02646_gb300 import gradsim as gs
     gs.load()
@@ -479,13 +516,16 @@ def _single_mesh_line(args, name, problem, extra_cfg):
                            block_threads=mesh.info.block_threads, K=mesh_K(K, S),
                            autotune=None if tuned is None else {
                                f'{t["patch_elems"]}/{t["block_threads"]}': t["ms"] for t in tuned["timings"]})}
+    if cpu_steps is not None and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(problem, cpu_steps[0], cpu_steps[1], f"{name} ({E} elements), FP64 oracle")
     print(json.dumps(line), flush=True)
 
 
 def workload_bar(args):
     from paper_2104_02646_gb300 import inputs as I
     for v in ("a", "b"):
-        _single_mesh_line(args, f"bar1{v}", I.bar(v, steps=1000), {"cells": "4x4x4", "drop": "0.2 m" if v == "a" else "0.02 m"})
+        _single_mesh_line(args, f"bar1{v}", I.bar(v, steps=1000), {"cells": "4x4x4", "drop": "0.2 m" if v == "a" else "0.02 m"},
+                          cpu_steps=(1000, 1000))
 
 
 def workload_cloth(args):
@@ -493,18 +533,20 @@ def workload_cloth(args):
     # the stated materials diverge under explicit Euler at dt 1e-4 (reported
     # by `finite`); the stable variant has the same mesh and work
     for v in ("3s", "3"):
-        _single_mesh_line(args, f"cloth{v}", I.cloth(v, n=256, steps=500), {"grid": "256x256", "variant": v})
+        _single_mesh_line(args, f"cloth{v}", I.cloth(v, n=256, steps=500), {"grid": "256x256", "variant": v},
+                          cpu_steps=(10, 40) if v == "3s" else None)
 
 
-def workload_batch(args):
-    """512 heterogeneous meshes: one launch per kernel per step (graphs) vs the
-    plain loop (one mesh per launch, one step per launch, no graphs)."""
+def measure_batch(args, n_meshes, reps):
+    """Config 4: n heterogeneous meshes, fwd+adj in one launch per kernel per
+    step (graphs) against the plain loop (one mesh per launch, one step per
+    launch, no graphs) on the same GPU.  Returns a dict."""
     import torch
     from paper_2104_02646_gb300 import gradsim as gs
     from paper_2104_02646_gb300 import inputs as I
     gs.load()
     dev = torch.device("cuda", 0)
-    probs = I.batch(args.meshes, steps=300)
+    probs = I.batch(n_meshes, steps=300)
     ctx = gs.Context(0)
     t0 = time.perf_counter()
     meshes = [gs.Mesh(ctx, p, patch_elems=args.patch, block_threads=args.threads) for p in probs]
@@ -536,83 +578,145 @@ def workload_batch(args):
             m.adjoint(g)
 
     batched()
-    t_b = min(_events_ms(batched) for _ in range(max(1, args.steps)))
+    t_b = min(_events_ms(batched) for _ in range(max(1, reps)))
     ctx.set_graphs(False)
     plain()
     t_p = _events_ms(plain)
     ctx.set_graphs(True)
-    line = {"metric": "fwd+adjoint element-steps/s", "workload": f"batch{len(probs)}",
-            "value": E * S / (t_b / 1e3), "unit": "element-steps/s",
-            "plain_loop_value": E * S / (t_p / 1e3), "speedup_vs_plain": t_p / t_b,
-            "ms_batched": t_b, "ms_plain": t_p, "dtype": "f32", "data": "synthetic",
-            "config": {"meshes": len(probs), "tets": E, "nodes": sum(p.n_nodes for p in probs), "steps": S,
-                       "dt": 1e-4, "K": mesh_K(K, S), "mesh_create_s": t_create}}
+    out = {"metric": "fwd+adjoint element-steps/s", "workload": f"batch{len(probs)}",
+           "value": E * S / (t_b / 1e3), "unit": "element-steps/s",
+           "plain_loop_value": E * S / (t_p / 1e3), "speedup_vs_plain": t_p / t_b,
+           "ms_batched": t_b, "ms_plain": t_p,
+           "config": {"meshes": len(probs), "tets": E, "nodes": sum(p.n_nodes for p in probs), "steps": S,
+                      "dt": 1e-4, "K": mesh_K(K, S), "mesh_create_s": t_create,
+                      "plain_loop": "same kernels, one mesh per launch, one step per launch, no graphs"}}
+    batch.close()
+    for m in meshes:
+        m.close()
+    del ctx
+    torch.cuda.empty_cache()
+    return out
+
+
+def workload_batch(args):
+    """512 heterogeneous meshes: one launch per kernel per step (graphs) vs the
+    plain loop (one mesh per launch, one step per launch, no graphs)."""
+    line = measure_batch(args, args.meshes, args.steps)
+    line.update({"dtype": "f32", "data": "synthetic"})
     print(json.dumps(line), flush=True)
 
 
-def workload_serve(args):
-    """Poisson gradient queries through the continuous-batching server vs the
-    plain loop (each query alone, in arrival order, one launch per kernel)."""
-    import numpy as np
+def measure_serve(args, rate, n_queries):
+    """Config 5 at one arrival rate: Poisson gradient queries through the
+    continuous-batching server vs the plain loop (each query alone, in
+    arrival order, one launch per kernel).  Returns a dict."""
     import torch
     from paper_2104_02646_gb300 import gradsim as gs
     from paper_2104_02646_gb300 import inputs as I
     gs.load()
     dev = torch.device("cuda", 0)
+    qs = I.query_stream(rate, n_queries, seed=int(rate))
+    work = sum(q.problem.n_elems * q.problem.steps for q in qs)
+    ctx = gs.Context(0)
+    server = gs.Server(ctx, budget=120 << 30)
+    t0 = time.perf_counter()
+    tickets = []
+    for q in qs:
+        delay = t0 + q.t_arrival - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(server.submit(q.problem, q.problem.X + q.target_offset))
+    res = [server.poll(t, timeout_ms=600000) for t in tickets]
+    t_all = time.perf_counter() - t0
+    ok = [r for st, r in res if st == gs.GS_OK]
+    lat = sorted(r["t_done"] - r["t_submit"] for r in ok)
+    stats = server.stats()
+    server.close()
+    # plain loop: FIFO, one query at a time (no batching, no graphs)
+    ctx2 = gs.Context(0)
+    ctx2.set_graphs(False)
+    clock = 0.0
+    plain_lat = []
+    busy = 0.0
+    for q in qs:
+        p = q.problem
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        # service time includes building the mesh, as the server's latency does
+        m = gs.Mesh(ctx2, p)
+        t = torch.tensor(p.X + q.target_offset, dtype=torch.float32, device=dev)
+        l = torch.zeros(1, dtype=torch.float64, device=dev)
+        g = _grads(p, dev)
+        m.rollout(p.dt, p.steps, 0, t, l)
+        m.adjoint(g)
+        torch.cuda.synchronize()
+        dur = time.perf_counter() - w0
+        busy += dur
+        clock = max(clock, q.t_arrival) + dur
+        plain_lat.append(clock - q.t_arrival)
+        m.close()
+    plain_lat.sort()
+    pct = lambda v, f: v[min(len(v) - 1, int(round(f * (len(v) - 1))))] if v else None
+    return {"metric": "p50/p99 query latency and aggregate element-steps/s", "workload": "serve",
+            "rate_req_s": rate, "queries": len(qs), "completed": len(ok),
+            "p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99), "elem_steps_per_s": stats["elem_steps_per_s"],
+            "wall_s": t_all, "plain_p50_s": pct(plain_lat, 0.5), "plain_p99_s": pct(plain_lat, 0.99),
+            "plain_elem_steps_per_s": work / busy,
+            "server_time_s": {k: round(stats[k], 4) for k in
+                              ("busy_s", "build_s", "start_s", "rebuild_s", "rt_sync_s", "gpu_wait_s")},
+            "server_counts": {k: int(stats[k]) for k in ("ticks", "rebuilds", "rt_syncs")},
+            "config": {"budget_GB": 120, "tets": "log-uniform 1e3..2e5", "cloth": "32^2..192^2",
+                       "horizon": "100..1000", "dt": 1e-4, "service_time": "mesh build + rollout + adjoint"}}
+
+
+def workload_serve(args):
+    """Poisson gradient queries through the continuous-batching server vs the
+    plain loop (each query alone, in arrival order, one launch per kernel)."""
     for rate in [float(r) for r in args.rates.split(",")]:
-        qs = I.query_stream(rate, args.queries, seed=int(rate))
-        work = sum(q.problem.n_elems * q.problem.steps for q in qs)
-        ctx = gs.Context(0)
-        server = gs.Server(ctx, budget=120 << 30)
-        t0 = time.perf_counter()
-        tickets = []
-        for q in qs:
-            delay = t0 + q.t_arrival - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            tickets.append(server.submit(q.problem, q.problem.X + q.target_offset))
-        res = [server.poll(t, timeout_ms=600000) for t in tickets]
-        t_all = time.perf_counter() - t0
-        ok = [r for st, r in res if st == gs.GS_OK]
-        lat = sorted(r["t_done"] - r["t_submit"] for r in ok)
-        stats = server.stats()
-        server.close()
-        # plain loop: FIFO, one query at a time (no batching, no graphs)
-        ctx2 = gs.Context(0)
-        ctx2.set_graphs(False)
-        clock = 0.0
-        plain_lat = []
-        busy = 0.0
-        for q in qs:
-            p = q.problem
-            torch.cuda.synchronize()
-            w0 = time.perf_counter()
-            # service time includes building the mesh, as the server's latency does
-            m = gs.Mesh(ctx2, p)
-            t = torch.tensor(p.X + q.target_offset, dtype=torch.float32, device=dev)
-            l = torch.zeros(1, dtype=torch.float64, device=dev)
-            g = _grads(p, dev)
-            m.rollout(p.dt, p.steps, 0, t, l)
-            m.adjoint(g)
-            torch.cuda.synchronize()
-            dur = time.perf_counter() - w0
-            busy += dur
-            clock = max(clock, q.t_arrival) + dur
-            plain_lat.append(clock - q.t_arrival)
-            m.close()
-        plain_lat.sort()
-        pct = lambda v, f: v[min(len(v) - 1, int(round(f * (len(v) - 1))))] if v else None
-        line = {"metric": "p50/p99 query latency and aggregate element-steps/s", "workload": "serve",
-                "rate_req_s": rate, "queries": len(qs), "completed": len(ok),
-                "p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99), "elem_steps_per_s": stats["elem_steps_per_s"],
-                "wall_s": t_all, "plain_p50_s": pct(plain_lat, 0.5), "plain_p99_s": pct(plain_lat, 0.99),
-                "plain_elem_steps_per_s": work / busy, "data": "synthetic",
-                "server_time_s": {k: round(stats[k], 4) for k in
-                                  ("busy_s", "build_s", "start_s", "rebuild_s", "rt_sync_s", "gpu_wait_s")},
-                "server_counts": {k: int(stats[k]) for k in ("ticks", "rebuilds", "rt_syncs")},
-                "config": {"budget_GB": 120, "tets": "log-uniform 1e3..2e5", "cloth": "32^2..192^2",
-                           "horizon": "100..1000", "dt": 1e-4, "service_time": "mesh build + rollout + adjoint"}}
+        line = measure_serve(args, rate, args.queries)
+        line["data"] = "synthetic"
         print(json.dumps(line), flush=True)
+
+
+def workload_recompute(args):
+    """The checkpoint / recompute path at size: the 1.3M-tet block over a
+    1,000-step rollout + adjoint with every state kept (K = 1) against a
+    checkpoint every K = ceil(sqrt(S)) steps, the memory-minimal choice
+    (one recomputed forward step per reverse step, less one per segment)."""
+    import math as _m
+    import torch
+    from paper_2104_02646_gb300 import gradsim as gs
+    from paper_2104_02646_gb300 import inputs as I
+    gs.load()
+    dev = torch.device("cuda", 0)
+    S = 1000
+    p = I.block(n=args.cells, steps=S)
+    ctx = gs.Context(0)
+    mesh = gs.Mesh(ctx, p, patch_elems=args.patch, block_threads=args.threads)
+    target = torch.tensor(p.X + 1e-3, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = _grads(p, dev)
+    res = {}
+    for K in (1, int(_m.ceil(_m.sqrt(S)))):
+        def both():
+            mesh.reset()
+            mesh.rollout(p.dt, S, K, target, loss)
+            mesh.adjoint(g)
+        for _ in range(max(1, args.warmup)):
+            both()
+        res[K] = min(_events_ms(both) for _ in range(max(1, args.steps)))
+    K1, Kc = sorted(res)
+    state_mb = 32 * p.n_nodes / 1e6
+    n_ck = -(-S // Kc)
+    line = {"metric": "fwd+adjoint element-steps/s", "workload": f"recompute_block{args.cells}",
+            "value": p.n_elems * S / (res[Kc] / 1e3), "unit": "element-steps/s",
+            "K1_value": p.n_elems * S / (res[K1] / 1e3), "ms_K1": res[K1], f"ms_K{Kc}": res[Kc],
+            "recompute_cost": res[Kc] / res[K1] - 1.0,
+            "stored_states_MB": {"K1": (S + 2) * state_mb, f"K{Kc}": (1 + n_ck + Kc + 1) * state_mb},
+            "dtype": "f32", "data": "synthetic",
+            "config": {"tets": p.n_elems, "nodes": p.n_nodes, "steps": S, "dt": p.dt, "K": [K1, Kc]}}
+    print(json.dumps(line), flush=True)
+    mesh.close()
 
 
 def workload_control(args):
@@ -902,7 +1006,7 @@ def workload_rigid(args):
 
 WORKLOADS = {"bar": workload_bar, "cloth": workload_cloth, "batch": workload_batch, "serve": workload_serve,
              "control": workload_control, "cloth_air": workload_cloth_air, "render": workload_render,
-             "rigid": workload_rigid}
+             "rigid": workload_rigid, "recompute": workload_recompute}
 
 if __name__ == "__main__":
     main()
