@@ -33,7 +33,10 @@ static __device__ __align__(256) double g_noalloc_partials[kMaxBlocks];
 
 // Per-device address of the scratch array.  In host code the array's name is
 // only a host-side stand-in, so the device address is looked up once per
-// device (with that device current) and passed to the kernels.
+// device (with that device current) and passed to the kernels.  The cached
+// address belongs to the device's primary context: a cudaDeviceReset by the
+// host application destroys it, and the entry point is not to be used on
+// that device afterwards.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {nullptr};
