@@ -190,10 +190,10 @@ __host__ __device__ __forceinline__ int r16(int bytes) { return (bytes + 15) & ~
 // Shared-memory layout of one pipeline stage (byte offsets, 16 B aligned):
 // the 4 record planes and one zero float4 (the target of padded CSR slots),
 // the local CSR, the partial positions of the boundary nodes, local node
-// state.  The adjoint also holds v_hat for all local nodes, the interior
-// adjoint state and the boundary nodes' raw adjoint state.
+// state.  The adjoint also holds the adjoint state x_bar, v_bar of every
+// local node (interior ones bulk-copied, boundary ones gathered behind them).
 struct Layout {
-    int rec, rp, sl, pos, xs, vh, vs, xb, vb, xbB, vbB, gml, wb, act, hact, vB, total;
+    int rec, rp, sl, pos, xs, vs, xb, xbB, vb, vbB, gml, wb, act, hact, vB, total;
 };
 
 // `extras`: the stage also holds the step's actuation slices and, for
@@ -209,12 +209,13 @@ __host__ __device__ __forceinline__ Layout patch_layout(int kind, int n_e, int n
     L.sl = L.rp + r16(2 * (n_loc + 1));
     L.pos = L.sl + r16(2 * n_slots);
     L.xs = L.pos + r16(4 * n_bnd);
-    L.vh = L.xs + 16 * n_loc;
-    L.vs = L.vh + (adjoint ? 16 * n_loc : 0);
+    L.vs = L.xs + 16 * n_loc;
+    // adjoint: x_bar of the interior nodes then of the boundary nodes (one
+    // array over the local nodes), then v_bar likewise
     L.xb = L.vs + 16 * n_int;
-    L.vb = L.xb + (adjoint ? 16 * n_int : 0);
-    L.xbB = L.vb + (adjoint ? 16 * n_int : 0);
-    L.vbB = L.xbB + (adjoint ? 16 * n_bnd : 0);
+    L.xbB = L.xb + (adjoint ? 16 * n_int : 0);
+    L.vb = L.xbB + (adjoint ? 16 * n_bnd : 0);
+    L.vbB = L.vb + (adjoint ? 16 * n_int : 0);
     // adjoint: the patch's FP64 dL/dmu, dL/dlambda accumulators (records 0..n_rec)
     L.gml = L.vbB + (adjoint ? 16 * n_bnd : 0);
     // adjoint: dL/dw of the interior nodes
@@ -361,12 +362,11 @@ struct Stage {
     uint16_t* sl;
     int* pos;     // partial positions of the boundary local nodes
     float4* xs;   // local node state (u, w)
-    float4* vh;   // adjoint: v_hat of local nodes
     float4* vs;   // interior v
-    float4* xb;   // adjoint: interior x_bar
-    float4* vb;   // adjoint: interior v_bar
-    float4* xbB;  // adjoint: boundary x_bar (raw)
-    float4* vbB;  // adjoint: boundary v_bar (raw)
+    float4* xb;   // adjoint: x_bar of the local nodes (interior, then boundary = xbB)
+    float4* vb;   // adjoint: v_bar of the local nodes (interior, then boundary = vbB)
+    float4* xbB;  // adjoint: boundary x_bar (gathered)
+    float4* vbB;  // adjoint: boundary v_bar (gathered)
     double2* gml;  // adjoint: staged (dL/dmu, dL/dlambda) of the patch's elements
     double* wb;   // adjoint: dL/dw of the interior nodes
     const float* act;   // this step's actuation of the patch's elements [n_e], or null
@@ -389,7 +389,6 @@ __device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned
     S.sl = (uint16_t*)(buf + L.sl);
     S.pos = (int*)(buf + L.pos);
     S.xs = (float4*)(buf + L.xs);
-    S.vh = (float4*)(buf + L.vh);
     S.vs = (float4*)(buf + L.vs);
     S.xb = (float4*)(buf + L.xb);
     S.vb = (float4*)(buf + L.vb);
@@ -616,6 +615,9 @@ __device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Mes
     }
 }
 
+// v_hat = v_bar + dt x_bar (dL/dv+, App. B) of local node l, formed where it is used
+__device__ __forceinline__ float3 vhat(const Stage& S, float dt, int l) { return xyz(S.vb[l]) + dt * xyz(S.xb[l]); }
+
 // corner result (dL/du_corner, f_corner . v_hat_node) in place
 __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshRT& m, int tick, const Stage& S,
                                                  int nt) {
@@ -629,7 +631,7 @@ __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshR
         if (!idx_ok(ids_in(id, n_loc, 4), m.status)) continue;
         const int i0 = id.x & 0xffff, i1 = id.x >> 16, i2 = id.y & 0xffff, i3 = id.y >> 16;
         const float4 x0 = S.xs[i0], x1 = S.xs[i1], x2 = S.xs[i2], x3 = S.xs[i3];
-        const float3 v0 = xyz(S.vh[i0]), v1 = xyz(S.vh[i1]), v2 = xyz(S.vh[i2]), v3 = xyz(S.vh[i3]);
+        const float3 v0 = vhat(S, dt, i0), v1 = vhat(S, dt, i1), v2 = vhat(S, dt, i2), v3 = vhat(S, dt, i3);
         TetState s;
         tet_state(xyz(x0), xyz(x1), xyz(x2), xyz(x3), a, b, c, w.z + act_of(S.act, le), s);
         float3 f0, f1, f2, f3;
@@ -665,7 +667,7 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
         if (lr < p.n_e) {
             const int i0 = id.x & 0xffff, i1 = id.x >> 16, i2 = id.y & 0xffff;
             const float4 x0 = S.xs[i0], x1 = S.xs[i1], x2 = S.xs[i2];
-            const float3 v0 = xyz(S.vh[i0]), v1 = xyz(S.vh[i1]), v2 = xyz(S.vh[i2]);
+            const float3 v0 = vhat(S, dt, i0), v1 = vhat(S, dt, i1), v2 = vhat(S, dt, i2);
             TriState s;
             float4 bt = b;
             bt.w += act_of(S.act, lr);  // actuation (b.w)
@@ -705,7 +707,7 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
         } else {
             const int i1 = id.x & 0xffff, i2 = id.x >> 16, i3 = id.y & 0xffff, i4 = id.y >> 16;
             const float4 x1 = S.xs[i1], x2 = S.xs[i2], x3 = S.xs[i3], x4 = S.xs[i4];
-            const float3 v1 = xyz(S.vh[i1]), v2 = xyz(S.vh[i2]), v3 = xyz(S.vh[i3]), v4 = xyz(S.vh[i4]);
+            const float3 v1 = vhat(S, dt, i1), v2 = vhat(S, dt, i2), v3 = vhat(S, dt, i3), v4 = vhat(S, dt, i4);
             HingeState s;
             hinge_state(xyz(x1), xyz(x2), xyz(x3), xyz(x4), xyz(a), xyz(b), xyz(c),
                         b.w + act_of(S.hact, lr - p.n_e), s);
@@ -969,12 +971,6 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
         const MeshRT& m = *(const MeshRT*)(b + kHdrRt);
         Stage S = stage_at(p, KIND, b + kHdr, ADJ, extras != 0);
         bind_act(S, p, m, tick);
-        if (ADJ) {
-            for (int l = threadIdx.x; l < p.n_int; l += nt) S.vh[l] = f4(xyz(S.vb[l]) + m.dt * xyz(S.xb[l]), 0.f);
-            for (int k = threadIdx.x; k < p.n_bnd; k += nt)
-                S.vh[p.n_int + k] = f4(xyz(S.vbB[k]) + m.dt * xyz(S.xbB[k]), 0.f);
-            consumer_sync(nt);
-        }
         if (KIND == GS_TET) {
             if (ADJ) tet_elements_adj(p, m, tick, S, nt);
             else tet_elements_fwd(p, m, tick, S, nt);
