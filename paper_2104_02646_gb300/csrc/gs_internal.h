@@ -141,6 +141,14 @@ struct alignas(16) MeshRT {  // 16 B aligned: the patch kernels bulk-copy it int
     float4* partials_v;
 };
 
+// Dynamic shared memory of a patch kernel: the mbarriers, kStages stages, and
+// the producer warp's own copy of the current mesh record
+constexpr size_t kPipeHead = 128;
+constexpr size_t kProdRt = (sizeof(MeshRT) + 127) / 128 * 128;
+__host__ __device__ __forceinline__ size_t patch_dyn_smem(int stage_bytes) {
+    return kPipeHead + kStages * (size_t)stage_bytes + kProdRt;
+}
+
 // Everything one kernel launch over a launch set needs.
 struct Launch {
     const PatchDesc* tet_patches = nullptr;

@@ -193,7 +193,7 @@ __host__ __device__ __forceinline__ int r16(int bytes) { return (bytes + 15) & ~
 // state.  The adjoint also holds the adjoint state x_bar, v_bar of every
 // local node (interior ones bulk-copied, boundary ones gathered behind them).
 struct Layout {
-    int rec, rp, sl, pos, xs, vs, xb, xbB, vb, vbB, gml, wb, act, hact, vB, total;
+    int rec, rp, sl, pos, xs, vs, xb, xbB, vb, vbB, wb, act, hact, vB, total;
 };
 
 // `extras`: the stage also holds the step's actuation slices and, for
@@ -216,10 +216,8 @@ __host__ __device__ __forceinline__ Layout patch_layout(int kind, int n_e, int n
     L.xbB = L.xb + (adjoint ? 16 * n_int : 0);
     L.vb = L.xbB + (adjoint ? 16 * n_bnd : 0);
     L.vbB = L.vb + (adjoint ? 16 * n_int : 0);
-    // adjoint: the patch's FP64 dL/dmu, dL/dlambda accumulators (records 0..n_rec)
-    L.gml = L.vbB + (adjoint ? 16 * n_bnd : 0);
     // adjoint: dL/dw of the interior nodes
-    L.wb = L.gml + (adjoint ? 16 * n_rec : 0);
+    L.wb = L.vbB + (adjoint ? 16 * n_bnd : 0);
     // the step's row slices of a time-varying actuation (elements, hinges);
     // up to 3 entries of slack on each side for the aligned slice ends
     L.act = L.wb + (adjoint ? r16(8 * n_int) : 0);
@@ -367,7 +365,6 @@ struct Stage {
     float4* vb;   // adjoint: v_bar of the local nodes (interior, then boundary = vbB)
     float4* xbB;  // adjoint: boundary x_bar (gathered)
     float4* vbB;  // adjoint: boundary v_bar (gathered)
-    double2* gml;  // adjoint: staged (dL/dmu, dL/dlambda) of the patch's elements
     double* wb;   // adjoint: dL/dw of the interior nodes
     const float* act;   // this step's actuation of the patch's elements [n_e], or null
     const float* hact;  // this step's actuation of the patch's hinges [n_h], or null
@@ -394,7 +391,6 @@ __device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned
     S.vb = (float4*)(buf + L.vb);
     S.xbB = (float4*)(buf + L.xbB);
     S.vbB = (float4*)(buf + L.vbB);
-    S.gml = (double2*)(buf + L.gml);
     S.wb = (double*)(buf + L.wb);
     S.act = (const float*)(buf + L.act) + (p.e_begin & 3);
     S.hact = (const float*)(buf + L.hact) + (p.h_begin & 3);
@@ -443,8 +439,6 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
     const float4* X = bufx(m, ib);
     const float4* V = bufv(m, ib);
     const uint32_t b_rp = r16(2 * (n_loc + 1)), b_sl = r16(2 * n_slots), b_int = 16 * p.n_int;
-    // (dL/dmu, dL/dlambda) of the tet / triangle records, 16 B each
-    const uint32_t b_g = adjoint ? 16u * p.n_e : 0u;
     const uint32_t b_pos = (uint32_t)r16(4 * p.n_bnd);
     // this step's actuation rows, aligned slices around the patch's entries
     const int ra = extras && p.n_e ? act_row(m, m.act_seq, tick) : -1;
@@ -452,7 +446,7 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
     const uint32_t b_act = ra >= 0 ? 4u * act_slice_n(p.e_begin, p.n_e) : 0u;
     const uint32_t b_hact = rh >= 0 ? 4u * act_slice_n(p.h_begin, p.n_h) : 0u;
     const uint32_t tx = (copy_rt ? (uint32_t)sizeof(MeshRT) : 0u) + 64u * n_rec + b_rp + b_sl + b_pos +
-                        (p.n_int ? (adjoint ? 4u : 2u) * b_int : 0u) + b_g + b_act + b_hact;
+                        (p.n_int ? (adjoint ? 4u : 2u) * b_int : 0u) + b_act + b_hact;
     fence_proxy_async();
     mbar_expect_tx(bar, tx);
     if (copy_rt) bulk_g2s(hdr_rt, rt_global, (uint32_t)sizeof(MeshRT), bar);
@@ -467,9 +461,6 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
             bulk_g2s(S.xb, m.xb + p.int_begin, b_int, bar);
             bulk_g2s(S.vb, m.vb + p.int_begin, b_int, bar);
         }
-    }
-    if (b_g) {
-        bulk_g2s(S.gml, m.g_ml + p.e_begin, b_g, bar);
     }
     if (b_act)
         bulk_g2s((void*)(S.act - (p.e_begin & 3)), m.act_seq + (size_t)ra * m.act_ld + act_slice_lo(p.e_begin), b_act, bar);
@@ -616,6 +607,15 @@ __device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Mes
 }
 
 // v_hat = v_bar + dt x_bar (dL/dv+, App. B) of local node l, formed where it is used
+// adds one step's (dL/dmu, dL/dlambda) of an element to its FP64 accumulator
+// as fire-and-forget reductions in L2: one thread owns an element per launch
+// and the launches are ordered, so each entry receives its terms one per step
+// in step order, each rounded once, as a load / add / store would
+__device__ __forceinline__ void accumulate_ml(double2* g, float gmu, float glam) {
+    atomicAdd(&g->x, (double)gmu);
+    atomicAdd(&g->y, (double)glam);
+}
+
 __device__ __forceinline__ float3 vhat(const Stage& S, float dt, int l) { return xyz(S.vb[l]) + dt * xyz(S.xb[l]); }
 
 // corner result (dL/du_corner, f_corner . v_hat_node) in place
@@ -645,8 +645,7 @@ __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshR
         put(S, le, 2, f4(xb2, dot3(f2, v2)));
         put(S, le, 3, f4(xb3, dot3(f3, v3)));
         const int e = p.e_begin + le;
-        const double2 g0 = S.gml[le];
-        m.g_ml[e] = make_double2(g0.x + (double)gmu, g0.y + (double)glam);
+        accumulate_ml(m.g_ml + e, gmu, glam);
         if (m.g_act) m.g_act[e] += (double)gact;
         act_grad_step(m, m.d_act_seq, m.act_ld, tick, e, gact);
     }
@@ -700,8 +699,7 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             put(S, q, 1, f4(xb1, dot3(f1, v1)));
             put(S, q, 2, f4(xb2, dot3(f2, v2)));
             const int t = p.e_begin + lr;
-            const double2 g0 = S.gml[lr];
-            m.g_ml[t] = make_double2(g0.x + (double)gmu, g0.y + (double)glam);
+            accumulate_ml(m.g_ml + t, gmu, glam);
             if (m.g_act) m.g_act[t] += (double)gact;
             act_grad_step(m, m.d_act_seq, m.act_ld, tick, t, gact);
         } else {
@@ -874,12 +872,25 @@ constexpr int kHdr = kHdrRt + (int)((sizeof(MeshRT) + 63) / 64 * 64);
 
 __device__ __forceinline__ void consumer_sync(int nt) { asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory"); }
 
-// first live patch at or after `pi` in steps of gridDim.x
+// first live patch at or after `pi` in steps of gridDim.x; `cached` is the
+// record of mesh `cached_mesh` in shared memory (or null)
 __device__ __forceinline__ int next_live(const PatchDesc* __restrict__ patches, int n_patches,
-                                         const MeshRT* __restrict__ rts, int pi, int mask) {
-    for (; pi < n_patches; pi += gridDim.x)
-        if (rts[patches[pi].mesh].active & mask) break;
+                                         const MeshRT* __restrict__ rts, int pi, int mask,
+                                         const MeshRT* cached = nullptr, int cached_mesh = -1) {
+    for (; pi < n_patches; pi += gridDim.x) {
+        const int pm = patches[pi].mesh;
+        if ((pm == cached_mesh && cached ? cached->active : rts[pm].active) & mask) break;
+    }
     return pi;
+}
+
+// the producer warp's copy of a mesh record in shared memory: every field it
+// reads per patch comes from there instead of a chain of global loads
+__device__ __forceinline__ void load_producer_rt(MeshRT* dst, const MeshRT* src, int lane) {
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(dst);
+    for (int k = lane; k < (int)(sizeof(MeshRT) / sizeof(int)); k += 32) d[k] = s[k];
+    __syncwarp();
 }
 
 template <int KIND, bool ADJ>
@@ -889,7 +900,8 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* full = (uint64_t*)sm;
     uint64_t* empty = full + kStages;
-    unsigned char* const buf0 = sm + 128;
+    unsigned char* const buf0 = sm + kPipeHead;
+    MeshRT* const prt = reinterpret_cast<MeshRT*>(buf0 + kStages * stage_bytes);  // the producer's mesh record
     const int mask = ADJ ? ACT_ADJ : ACT_FWD;
     const int nt = (int)blockDim.x - 32;  // consumer threads
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -909,15 +921,18 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
         // ---- producer warp: the next patch's descriptor, boundary ids and
         // state pointer are loaded while waiting for its stage ----
         int pi = next_live(patches, n_patches, rts, blockIdx.x, mask);
+        int rt_mesh = -1;  // the mesh whose record *prt holds
         PatchDesc p;
         int g[kPrefetchIds];
         const float4* X = nullptr;
         const float4* V = nullptr;
         if (pi < n_patches) {
             p = patches[pi];
-            prefetch_ids(p, rts[p.mesh], lane, g);
-            X = bufx(rts[p.mesh], in_buffer(rts[p.mesh], tick, ADJ));
-            V = bufv(rts[p.mesh], in_buffer(rts[p.mesh], tick, ADJ));
+            load_producer_rt(prt, &rts[p.mesh], lane);
+            rt_mesh = p.mesh;
+            prefetch_ids(p, *prt, lane, g);
+            X = bufx(*prt, in_buffer(*prt, tick, ADJ));
+            V = bufv(*prt, in_buffer(*prt, tick, ADJ));
         }
         for (int it = 0;; ++it) {
             const int s = it % kStages;
@@ -930,7 +945,7 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
                 if (lane == 0) mbar_arrive(&full[s]);
                 return;
             }
-            const MeshRT& m = rts[p.mesh];
+            const MeshRT& m = *prt;  // the record of p.mesh
             if (kChecked) {
                 // the patch's stage fits the stage the launch reserved and its
                 // local ids fit 16 bits; otherwise it is replaced by an empty patch
@@ -949,12 +964,16 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
             }
             produce_gather(p, m, X, V, g, b + kHdr, ADJ, extras != 0, lane);
             cp_async_mbar_arrive(&full[s]);
-            pi = next_live(patches, n_patches, rts, pi + gridDim.x, mask);
+            pi = next_live(patches, n_patches, rts, pi + gridDim.x, mask, prt, rt_mesh);
             if (pi < n_patches) {
                 p = patches[pi];
-                prefetch_ids(p, rts[p.mesh], lane, g);
-                X = bufx(rts[p.mesh], in_buffer(rts[p.mesh], tick, ADJ));
-                V = bufv(rts[p.mesh], in_buffer(rts[p.mesh], tick, ADJ));
+                if (p.mesh != rt_mesh) {
+                    load_producer_rt(prt, &rts[p.mesh], lane);
+                    rt_mesh = p.mesh;
+                }
+                prefetch_ids(p, *prt, lane, g);
+                X = bufx(*prt, in_buffer(*prt, tick, ADJ));
+                V = bufv(*prt, in_buffer(*prt, tick, ADJ));
             }
         }
     }
@@ -1544,7 +1563,7 @@ int patch_grid(int which, int threads, int stage_bytes, int n_patches, int num_s
                   : which == 2 ? (const void*)k_tet_adj
                                : (const void*)k_cloth_adj;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads + 32, 128 + kStages * (size_t)stage_bytes) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads + 32, patch_dyn_smem(stage_bytes)) !=
         cudaSuccess) {
         cudaGetLastError();
         nb = 1;
@@ -1608,10 +1627,10 @@ static void launch_pdl(void (*k)(KArgs...), int grid, int block, size_t smem, cu
 
 void launch_forward_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
     if (L.n_tet_patches)
-        GS_TIMED(KT_TET_FWD, launch_pdl(k_tet_fwd, L.grid[0], L.threads + 32, 128 + kStages * (size_t)L.stage[0], s,
+        GS_TIMED(KT_TET_FWD, launch_pdl(k_tet_fwd, L.grid[0], L.threads + 32, patch_dyn_smem(L.stage[0]), s,
                                         L.tet_patches, L.n_tet_patches, (const MeshRT*)L.rt, tick, L.stage[0], L.extras));
     if (L.n_cloth_patches)
-        GS_TIMED(KT_CLOTH_FWD, launch_pdl(k_cloth_fwd, L.grid[1], L.threads + 32, 128 + kStages * (size_t)L.stage[1],
+        GS_TIMED(KT_CLOTH_FWD, launch_pdl(k_cloth_fwd, L.grid[1], L.threads + 32, patch_dyn_smem(L.stage[1]),
                                           s, L.cloth_patches, L.n_cloth_patches, (const MeshRT*)L.rt, tick,
                                           L.stage[1], L.extras));
     if (L.n_bnd_blocks)
@@ -1621,10 +1640,10 @@ void launch_forward_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) 
 
 void launch_adjoint_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
     if (L.n_tet_patches)
-        GS_TIMED(KT_TET_ADJ, launch_pdl(k_tet_adj, L.grid[2], L.threads + 32, 128 + kStages * (size_t)L.stage[2], s,
+        GS_TIMED(KT_TET_ADJ, launch_pdl(k_tet_adj, L.grid[2], L.threads + 32, patch_dyn_smem(L.stage[2]), s,
                                         L.tet_patches, L.n_tet_patches, (const MeshRT*)L.rt, tick, L.stage[2], L.extras));
     if (L.n_cloth_patches)
-        GS_TIMED(KT_CLOTH_ADJ, launch_pdl(k_cloth_adj, L.grid[3], L.threads + 32, 128 + kStages * (size_t)L.stage[3],
+        GS_TIMED(KT_CLOTH_ADJ, launch_pdl(k_cloth_adj, L.grid[3], L.threads + 32, patch_dyn_smem(L.stage[3]),
                                           s, L.cloth_patches, L.n_cloth_patches, (const MeshRT*)L.rt, tick,
                                           L.stage[3], L.extras));
     if (L.n_bnd_blocks)

@@ -590,7 +590,7 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     m->patches = T.patches;
     m->bnd_blocks = make_blocks(0, T.n_bnd, kNodeBlock, 0);
     m->node_blocks = make_blocks(0, N, 256, 0);
-    const size_t need = std::max(128 + kStages * T.smem_adj[1], sizeof(double) * (3 * (size_t)T.max_loc + 4 * (size_t)T.max_rec + 1));
+    const size_t need = std::max(patch_dyn_smem((int)T.smem_adj[1]), sizeof(double) * (3 * (size_t)T.max_loc + 4 * (size_t)T.max_rec + 1));
     if (need > ctx->smem_optin)
         return set_error(GS_EINVAL, "patch needs " + std::to_string(need) + " B of shared memory; lower patch_elems");
     // element records in internal order, 4 planes (geometry filled by the set-up kernel)
