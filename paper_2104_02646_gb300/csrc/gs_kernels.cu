@@ -233,14 +233,9 @@ __host__ __device__ __forceinline__ Layout patch_layout(int kind, int n_e, int n
 __device__ __forceinline__ void cp16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp4(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr(dst)), "l"(src) : "memory");
-}
 __device__ __forceinline__ void cp8(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 // order earlier generic-proxy accesses of shared memory before async-proxy writes
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -834,22 +829,6 @@ __device__ __forceinline__ void adjoint_nodes(const PatchDesc& p, const MeshRT& 
     }
 }
 
-// boundary nodes: the node's partials (contiguous, in patch order), loads
-// grouped by four
-__device__ __forceinline__ float4 partial_sum(const MeshRT& m, int b) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    int k = m.bnd_rowptr[b];
-    const int k1 = m.bnd_rowptr[b + 1];
-    for (; k + 4 <= k1; k += 4) {
-        const float4 q0 = m.partials[k], q1 = m.partials[k + 1], q2 = m.partials[k + 2], q3 = m.partials[k + 3];
-        add4(acc, q0);
-        add4(acc, q1);
-        add4(acc, q2);
-        add4(acc, q3);
-    }
-    for (; k < k1; ++k) add4(acc, m.partials[k]);
-    return acc;
-}
 
 // ---------------------------------------------------------------------------
 // The pipeline: a persistent CTA walks the live patches blockIdx.x,
@@ -871,6 +850,39 @@ constexpr int kHdrRt = 64;
 constexpr int kHdr = kHdrRt + (int)((sizeof(MeshRT) + 63) / 64 * 64);
 
 __device__ __forceinline__ void consumer_sync(int nt) { asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory"); }
+
+// hint: bring [p, p + bytes) into L2 (16 B aligned, a multiple of 16 B)
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Run by the producer warp once its CTA has no patch left.  The next launch of
+// the same kernel gives this CTA the same patches, and its first two start
+// cold (nothing else overlaps the stage fill at the start of a launch), so
+// their records, topology block and boundary ids are brought into L2 now,
+// with this CTA's slice of the boundary row pointers that the boundary kernel
+// between the two launches reads.  Hints only: the data are constant over a
+// rollout and nothing depends on the prefetch.
+__device__ __forceinline__ void prefetch_next_launch(const PatchDesc* __restrict__ patches, int n_patches,
+                                                     const MeshRT* __restrict__ rts, const MeshRT* prt, int rt_mesh,
+                                                     int lane) {
+    if (lane < 2) {
+        const int q = blockIdx.x + lane * gridDim.x;
+        if (q < n_patches) {
+            const PatchDesc pq = patches[q];
+            const MeshRT& mq = pq.mesh == rt_mesh ? *prt : rts[pq.mesh];
+            const uint32_t bt = r16(2 * (pq.n_int + pq.n_bnd + 1)) + r16(2 * pq.n_slots) + r16(4 * pq.n_bnd);
+            if (pq.n_e) l2_prefetch(mq.rec + 4 * (size_t)pq.e_begin, 64u * pq.n_e);
+            l2_prefetch(mq.topo + pq.topo, bt);
+            if (pq.n_bnd >= 4) l2_prefetch(mq.bnd_ids + pq.bnd_begin, (4u * pq.n_bnd) & ~15u);
+        }
+    } else if (lane == 2 && rt_mesh >= 0 && prt->n_bnd > 0) {
+        const int per = ((prt->n_bnd + 1 + (int)gridDim.x - 1) / (int)gridDim.x + 3) & ~3;
+        const int lo = blockIdx.x * per;
+        const int hi = min(lo + per, (prt->n_bnd + 1) & ~3);
+        if (hi - lo >= 4) l2_prefetch(prt->bnd_rowptr + lo, 4u * (uint32_t)(hi - lo));
+    }
+}
 
 // first live patch at or after `pi` in steps of gridDim.x; `cached` is the
 // record of mesh `cached_mesh` in shared memory (or null)
@@ -943,6 +955,7 @@ __device__ __forceinline__ void patch_pipeline(const PatchDesc* __restrict__ pat
                 __syncwarp();
                 mbar_arrive(&full[s]);
                 if (lane == 0) mbar_arrive(&full[s]);
+                prefetch_next_launch(patches, n_patches, rts, prt, rt_mesh, lane);
                 return;
             }
             const MeshRT& m = *prt;  // the record of p.mesh
