@@ -1046,7 +1046,11 @@ __global__ void k_cloth_adj(const PatchDesc* __restrict__ patches, int n_patches
 // Boundary nodes: sum the node's partials (contiguous, in patch order), then
 // finish the node.  A CTA of 128 threads takes a 256-node block, two nodes
 // per thread, with every independent load of both nodes issued before the
-// dependent ones; CTAs stride over the blocks (grid sized to one wave).
+// dependent ones; CTAs stride over the blocks (grid sized to one wave).  The
+// row pointers and the node's state (written by the boundary kernel of the
+// previous step, which completed before the patch kernel in between could
+// signal its dependents) are loaded before waiting on that patch kernel, so
+// a CTA that starts during its tail has them in flight already.
 constexpr int kBndThreads = kNodeBlock / 2;
 
 // fixed-order sums of the partials [k0, k0 + n0) and [k1, k1 + n1), four
@@ -1074,7 +1078,6 @@ __device__ __forceinline__ void partial_sums2(const float4* __restrict__ P, int 
 
 __global__ void __launch_bounds__(kBndThreads, 8)
     k_fwd_boundary(const NodeBlock* __restrict__ blocks, int n_blocks, const MeshRT* __restrict__ rts, int tick) {
-    pdl_enter();
     for (int bi = blockIdx.x; bi < n_blocks; bi += gridDim.x) {
         const NodeBlock nb = blocks[bi];
         const MeshRT& m = rts[nb.mesh];
@@ -1107,6 +1110,8 @@ __global__ void __launch_bounds__(kBndThreads, 8)
             if (!idx_ok(!h0 || (b0 < m.n_bnd && 0 <= k0 && k0 <= e0 && e0 <= m.n_part), m.status)) h0 = false, k0 = e0 = 0;
             if (!idx_ok(!h1 || (b1 < m.n_bnd && 0 <= k1 && k1 <= e1 && e1 <= m.n_part), m.status)) h1 = false, k1 = e1 = 0;
         }
+        // only the partials come from the patch kernel this launch follows
+        pdl_enter();
         float4 f0, f1;
         partial_sums2(m.partials, k0, e0 - k0, k1, e1 - k1, f0, f1);
         if (h0) node_forward(m, tick, m.n_int + b0, x0, v0, xyz(f0));
@@ -1117,7 +1122,6 @@ __global__ void __launch_bounds__(kBndThreads, 8)
 
 __global__ void __launch_bounds__(kBndThreads, 6)
     k_adj_boundary(const NodeBlock* __restrict__ blocks, int n_blocks, const MeshRT* __restrict__ rts, int tick) {
-    pdl_enter();
     for (int bi = blockIdx.x; bi < n_blocks; bi += gridDim.x) {
         const NodeBlock nb = blocks[bi];
         const MeshRT& m = rts[nb.mesh];
@@ -1158,6 +1162,8 @@ __global__ void __launch_bounds__(kBndThreads, 6)
             if (!idx_ok(!h0 || (b0 < m.n_bnd && 0 <= k0 && k0 <= e0 && e0 <= m.n_part), m.status)) h0 = false, k0 = e0 = 0;
             if (!idx_ok(!h1 || (b1 < m.n_bnd && 0 <= k1 && k1 <= e1 && e1 <= m.n_part), m.status)) h1 = false, k1 = e1 = 0;
         }
+        // only the partials come from the patch kernel this launch follows
+        pdl_enter();
         float4 a0, a1;
         partial_sums2(m.partials, k0, e0 - k0, k1, e1 - k1, a0, a1);
         const float3 z = make_float3(0.f, 0.f, 0.f);
