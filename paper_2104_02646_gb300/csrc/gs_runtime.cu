@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <numeric>
 #include <string>
@@ -121,6 +122,80 @@ struct Topology {
     int n_int = 0, n_bnd = 0, max_loc = 0, max_slots = 0, max_rec = 0;
     size_t smem_fwd[2] = {0, 0}, smem_adj[2] = {0, 0};  // [without, with] the extra stage regions
 };
+
+
+// Order the entries of each local CSR row (the node's corner slots) so that
+// the rows the node phase reads together hit distinct shared-memory banks.
+// The node phase gives local node l to consumer thread l (mod the thread
+// count); a quarter-warp (8 consecutive nodes) issues each 16-byte corner
+// load together, and those 8 loads are conflict-free when the slots lie in 8
+// different 16-byte bank groups (slot mod 8).  Column by column, a bipartite
+// matching of the quarter's rows to bank groups picks each row's next entry;
+// the padding reads of exhausted rows (the zero slot, one address, shared by
+// broadcast) keep their group.  The order of a node's terms is fixed by the
+// mesh and the patching alone, so sums stay bitwise reproducible.
+static void order_rows_for_banks(uint16_t* slots, const int* rc, const int* fill, int n_loc, uint16_t zero_slot) {
+    constexpr int kQ = 8, kG = 8;
+    std::vector<uint16_t> bucket[kQ][kG];
+    std::vector<uint16_t> out[kQ];
+    for (int q0 = 0; q0 < n_loc; q0 += kQ) {
+        const int nq = std::min(kQ, n_loc - q0);
+        int len[kQ] = {0}, padded[kQ] = {0}, maxlen = 0;
+        for (int i = 0; i < nq; ++i) {
+            const int l = q0 + i;
+            len[i] = fill[l] - rc[l];
+            padded[i] = rc[l + 1] - rc[l];
+            maxlen = std::max(maxlen, padded[i]);
+            for (int g = 0; g < kG; ++g) bucket[i][g].clear();
+            for (int k = rc[l]; k < fill[l]; ++k) bucket[i][slots[k] % kG].push_back(slots[k]);
+            out[i].clear();
+        }
+        for (int col = 0; col < maxlen; ++col) {
+            bool taken[kG] = {false};
+            for (int i = 0; i < nq; ++i)
+                if (col >= len[i] && col < padded[i]) taken[zero_slot % kG] = true;
+            // Kuhn's augmenting paths over the rows that still have entries
+            int match_g[kG];  // group -> row
+            for (int g = 0; g < kG; ++g) match_g[g] = taken[g] ? -2 : -1;
+            int row_g[kQ];
+            for (int i = 0; i < kQ; ++i) row_g[i] = -1;
+            for (int i = 0; i < nq; ++i) {
+                if ((int)out[i].size() >= len[i]) continue;
+                bool seen[kG] = {false};
+                // iterative DFS is overkill for 8 x 8; a recursive lambda keeps it short
+                std::function<bool(int)> augment = [&](int r) -> bool {
+                    for (int g = 0; g < kG; ++g) {
+                        if (bucket[r][g].empty() || seen[g] || match_g[g] == -2) continue;
+                        seen[g] = true;
+                        if (match_g[g] == -1 || augment(match_g[g])) {
+                            match_g[g] = r;
+                            row_g[r] = g;
+                            return true;
+                        }
+                    }
+                    return false;
+                };
+                augment(i);
+            }
+            for (int i = 0; i < nq; ++i) {
+                if ((int)out[i].size() >= len[i]) continue;
+                int g = row_g[i];
+                if (g < 0) {  // no free group: the largest bucket
+                    g = 0;
+                    for (int h = 1; h < kG; ++h)
+                        if (bucket[i][h].size() > bucket[i][g].size()) g = h;
+                }
+                out[i].push_back(bucket[i][g].back());
+                bucket[i][g].pop_back();
+            }
+        }
+        for (int i = 0; i < nq; ++i) {
+            const int l = q0 + i;
+            for (int k = 0; k < len[i]; ++k) slots[rc[l] + k] = out[i][k];
+            for (int k = len[i]; k < padded[i]; ++k) slots[rc[l] + k] = zero_slot;
+        }
+    }
+}
 
 static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
     const int N = d.n_nodes, E = d.n_elems, B = d.kind == GS_CLOTH ? d.n_hinges : 0;
@@ -333,6 +408,7 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
             return r < q.n_e ? c * q.n_e + r : 4 * q.n_e + c * q.n_h + (r - q.n_e);
         };
         for (auto& cn : code_node) slots[fill[cn.second]++] = (uint16_t)slot_of(cn.first);
+        order_rows_for_banks(slots.data(), rc.data(), fill.data(), n_loc, (uint16_t)(4 * n_rec));
         T.loc_slots.insert(T.loc_slots.end(), slots.begin(), slots.end());
         T.max_loc = std::max(T.max_loc, n_loc);
         T.max_slots = std::max(T.max_slots, n_slots);
