@@ -190,7 +190,7 @@ __host__ __device__ __forceinline__ int r16(int bytes) { return (bytes + 15) & ~
 // Shared-memory layout of one pipeline stage (byte offsets, 16 B aligned):
 // the 4 record planes and one zero float4 (the target of padded CSR slots),
 // the local CSR, the partial positions of the boundary nodes, local node
-// state.  The adjoint also holds the adjoint state x_bar, v_bar of every
+// state.  The adjoint also holds the adjoint state x_bar, v_hat of every
 // local node (interior ones bulk-copied, boundary ones gathered behind them).
 struct Layout {
     int rec, rp, sl, pos, xs, vs, xb, xbB, vb, vbB, wb, act, hact, vB, total;
@@ -211,7 +211,7 @@ __host__ __device__ __forceinline__ Layout patch_layout(int kind, int n_e, int n
     L.xs = L.pos + r16(4 * n_bnd);
     L.vs = L.xs + 16 * n_loc;
     // adjoint: x_bar of the interior nodes then of the boundary nodes (one
-    // array over the local nodes), then v_bar likewise
+    // array over the local nodes), then v_hat likewise
     L.xb = L.vs + 16 * n_int;
     L.xbB = L.xb + (adjoint ? 16 * n_int : 0);
     L.vb = L.xbB + (adjoint ? 16 * n_bnd : 0);
@@ -328,22 +328,28 @@ __device__ __forceinline__ void node_forward(const MeshRT& m, int tick, int gid,
         atomicOr(m.status, 1);
 }
 
+// The adjoint state kept per node between reverse steps is x_bar = dL/du(n)
+// and v_hat = dL/dv(n) + dt x_bar: the total dL/dv+ that the reverse of step
+// n - 1 needs (x+ = x + dt v+), which is all the element phase reads of a
+// node's velocity adjoint.  dL/dv(n) itself is v_hat - dt x_bar.
+__device__ __forceinline__ float3 vhat_of(const MeshRT& m, float3 xb, float3 vb) { return vb + m.dt * xb; }
+
 // reverse of node_forward for one node.  Inputs: state (u, v) at step n, the
-// adjoint (xb, vb) of step n+1, the gathered element terms xsum = sum of
+// adjoint (xb, vh) of step n+1, the gathered element terms xsum = sum of
 // corner dL/du and ssum = sum of corner f . v_hat, and dL/dw so far.  Writes
-// the adjoint of step n and the accumulated dL/dw (FP64).
-__device__ __forceinline__ void node_adjoint(const MeshRT& m, int gid, float4 x4, float4 v4, float4 xb4, float4 vb4,
+// the adjoint (x_bar, v_hat) of step n and the accumulated dL/dw (FP64).
+__device__ __forceinline__ void node_adjoint(const MeshRT& m, int gid, float4 x4, float4 v4, float4 xb4, float4 vh4,
                                              float3 xsum, float ssum, double wb_old, float3 vsum) {
     const float w = x4.w;
     const float3 xbn = xyz(xb4);
-    const float3 vh = xyz(vb4) + m.dt * xbn;    // dL/dv+ (total)
+    const float3 vh = xyz(vh4);                 // dL/dv+ (total)
     const float3 fb = (m.dt * w) * vh;          // dL/df
     float3 xb = xbn + xsum;
     float3 vb = vh;
     const float3 fc = contact_adjoint(m, gid, xyz(x4), xyz(v4), v4.w, fb, xb, vb);
     vb += vsum;  // the elements' velocity-dependent forces (air), added last
     m.xb[gid] = f4(xb, 0.0f);
-    m.vb[gid] = f4(vb, 0.0f);
+    m.vb[gid] = f4(vhat_of(m, xb, vb), 0.0f);
     m.wbar[gid] = wb_old + (double)(m.dt * (ssum + dot3(fc, vh)));
 }
 
@@ -357,9 +363,9 @@ struct Stage {
     float4* xs;   // local node state (u, w)
     float4* vs;   // interior v
     float4* xb;   // adjoint: x_bar of the local nodes (interior, then boundary = xbB)
-    float4* vb;   // adjoint: v_bar of the local nodes (interior, then boundary = vbB)
+    float4* vb;   // adjoint: v_hat of the local nodes (interior, then boundary = vbB)
     float4* xbB;  // adjoint: boundary x_bar (gathered)
-    float4* vbB;  // adjoint: boundary v_bar (gathered)
+    float4* vbB;  // adjoint: boundary v_hat (gathered)
     double* wb;   // adjoint: dL/dw of the interior nodes
     const float* act;   // this step's actuation of the patch's elements [n_e], or null
     const float* hact;  // this step's actuation of the patch's hinges [n_h], or null
@@ -601,7 +607,6 @@ __device__ __forceinline__ void cloth_elements_fwd(const PatchDesc& p, const Mes
     }
 }
 
-// v_hat = v_bar + dt x_bar (dL/dv+, App. B) of local node l, formed where it is used
 // adds one step's (dL/dmu, dL/dlambda) of an element to its FP64 accumulator
 // as fire-and-forget reductions in L2: one thread owns an element per launch
 // and the launches are ordered, so each entry receives its terms one per step
@@ -611,7 +616,9 @@ __device__ __forceinline__ void accumulate_ml(double2* g, float gmu, float glam)
     atomicAdd(&g->y, (double)glam);
 }
 
-__device__ __forceinline__ float3 vhat(const Stage& S, float dt, int l) { return xyz(S.vb[l]) + dt * xyz(S.xb[l]); }
+// v_hat = v_bar + dt x_bar (dL/dv+, App. B) of local node l: the stage holds
+// the adjoint state as (x_bar, v_hat)
+__device__ __forceinline__ float3 vhat(const Stage& S, int l) { return xyz(S.vb[l]); }
 
 // corner result (dL/du_corner, f_corner . v_hat_node) in place
 __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshRT& m, int tick, const Stage& S,
@@ -626,7 +633,7 @@ __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshR
         if (!idx_ok(ids_in(id, n_loc, 4), m.status)) continue;
         const int i0 = id.x & 0xffff, i1 = id.x >> 16, i2 = id.y & 0xffff, i3 = id.y >> 16;
         const float4 x0 = S.xs[i0], x1 = S.xs[i1], x2 = S.xs[i2], x3 = S.xs[i3];
-        const float3 v0 = vhat(S, dt, i0), v1 = vhat(S, dt, i1), v2 = vhat(S, dt, i2), v3 = vhat(S, dt, i3);
+        const float3 v0 = vhat(S, i0), v1 = vhat(S, i1), v2 = vhat(S, i2), v3 = vhat(S, i3);
         TetState s;
         tet_state(xyz(x0), xyz(x1), xyz(x2), xyz(x3), a, b, c, w.z + act_of(S.act, le), s);
         float3 f0, f1, f2, f3;
@@ -661,7 +668,7 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
         if (lr < p.n_e) {
             const int i0 = id.x & 0xffff, i1 = id.x >> 16, i2 = id.y & 0xffff;
             const float4 x0 = S.xs[i0], x1 = S.xs[i1], x2 = S.xs[i2];
-            const float3 v0 = vhat(S, dt, i0), v1 = vhat(S, dt, i1), v2 = vhat(S, dt, i2);
+            const float3 v0 = vhat(S, i0), v1 = vhat(S, i1), v2 = vhat(S, i2);
             TriState s;
             float4 bt = b;
             bt.w += act_of(S.act, lr);  // actuation (b.w)
@@ -700,7 +707,7 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
         } else {
             const int i1 = id.x & 0xffff, i2 = id.x >> 16, i3 = id.y & 0xffff, i4 = id.y >> 16;
             const float4 x1 = S.xs[i1], x2 = S.xs[i2], x3 = S.xs[i3], x4 = S.xs[i4];
-            const float3 v1 = vhat(S, dt, i1), v2 = vhat(S, dt, i2), v3 = vhat(S, dt, i3), v4 = vhat(S, dt, i4);
+            const float3 v1 = vhat(S, i1), v2 = vhat(S, i2), v3 = vhat(S, i3), v4 = vhat(S, i4);
             HingeState s;
             hinge_state(xyz(x1), xyz(x2), xyz(x3), xyz(x4), xyz(a), xyz(b), xyz(c),
                         b.w + act_of(S.hact, lr - p.n_e), s);
@@ -1175,7 +1182,8 @@ __global__ void __launch_bounds__(kBndThreads, 6)
 
 // Cloth with air, after k_adj_boundary: each boundary node's dL/dv from the
 // triangles' air forces (partials at the node's partial positions), added
-// last to v_bar as node_adjoint does for interior nodes.
+// last to v_bar (so to v_hat = v_bar + dt x_bar) as node_adjoint does for
+// interior nodes.
 __global__ void __launch_bounds__(kBndThreads)
     k_adj_boundary_air(const NodeBlock* __restrict__ blocks, int n_blocks, const MeshRT* __restrict__ rts) {
     pdl_enter();
@@ -1232,7 +1240,7 @@ __global__ void k_seed_loss(const NodeBlock* __restrict__ blocks, const MeshRT* 
         if (m.seed_v) vb = make_float3(m.seed_v[3 * u], m.seed_v[3 * u + 1], m.seed_v[3 * u + 2]);
         if (write_seeds) {
             m.xb[g] = f4(xb, 0.f);
-            m.vb[g] = f4(vb, 0.f);
+            m.vb[g] = f4(vhat_of(m, xb, vb), 0.f);  // the adjoint state holds v_hat
         }
     }
     red[threadIdx.x] = acc;
@@ -1524,7 +1532,8 @@ __global__ void k_node_grads(const MeshRT* __restrict__ rts, double* mbar, float
             d_x0[3 * u] = q.x; d_x0[3 * u + 1] = q.y; d_x0[3 * u + 2] = q.z;
         }
         if (d_v0) {
-            const float4 q = m.vb[i];
+            // dL/dv(0) = v_hat - dt x_bar
+            const float3 q = xyz(m.vb[i]) - m.dt * xyz(m.xb[i]);
             d_v0[3 * u] = q.x; d_v0[3 * u + 1] = q.y; d_v0[3 * u + 2] = q.z;
         }
     }
