@@ -8,10 +8,10 @@
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
-#include <functional>
 #include <memory>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -124,76 +124,112 @@ struct Topology {
 };
 
 
+// augmenting path for row r over the groups in avail[r] not yet seen (Kuhn)
+static bool bank_augment(int r, const unsigned* avail, int* match_g, int* row_g, unsigned& seen) {
+    unsigned m = avail[r] & ~seen;
+    while (m) {
+        const int g = __builtin_ctz(m);
+        m &= m - 1;
+        seen |= 1u << g;
+        if (match_g[g] < 0 || bank_augment(match_g[g], avail, match_g, row_g, seen)) {
+            match_g[g] = r;
+            row_g[r] = g;
+            return true;
+        }
+    }
+    return false;
+}
+
 // Order the entries of each local CSR row (the node's corner slots) so that
 // the rows the node phase reads together hit distinct shared-memory banks.
 // The node phase gives local node l to consumer thread l (mod the thread
 // count); a quarter-warp (8 consecutive nodes) issues each 16-byte corner
 // load together, and those 8 loads are conflict-free when the slots lie in 8
-// different 16-byte bank groups (slot mod 8).  Column by column, a bipartite
-// matching of the quarter's rows to bank groups picks each row's next entry;
-// the padding reads of exhausted rows (the zero slot, one address, shared by
-// broadcast) keep their group.  The order of a node's terms is fixed by the
-// mesh and the patching alone, so sums stay bitwise reproducible.
+// different 16-byte bank groups (slot mod 8).  Column by column, the quarter's
+// rows are matched to bank groups: greedily (each row the first free group at
+// or after its rotation), then by augmenting paths (Kuhn) for the rows left
+// over.  The padding reads of exhausted rows (the zero slot, one address,
+// shared by broadcast) keep their group.  The order of a node's terms is
+// fixed by the mesh and the patching alone, so sums stay bitwise
+// reproducible.  `fill[l]` is the end of row l's entries.
 static void order_rows_for_banks(uint16_t* slots, const int* rc, const int* fill, int n_loc, uint16_t zero_slot) {
     constexpr int kQ = 8, kG = 8;
-    std::vector<uint16_t> bucket[kQ][kG];
-    std::vector<uint16_t> out[kQ];
+    const unsigned zbit = 1u << (zero_slot % kG);
+    std::vector<uint16_t> ent;  // a quarter's entries, row by row, grouped by bank group
     for (int q0 = 0; q0 < n_loc; q0 += kQ) {
         const int nq = std::min(kQ, n_loc - q0);
         int len[kQ] = {0}, padded[kQ] = {0}, maxlen = 0;
+        int next[kQ][kG], left[kQ][kG];
+        unsigned avail[kQ] = {0};  // groups with entries left, per row
+        size_t total = 0;
+        for (int i = 0; i < nq; ++i) total += (size_t)(fill[q0 + i] - rc[q0 + i]);
+        ent.resize(total);
+        int at = 0;
         for (int i = 0; i < nq; ++i) {
             const int l = q0 + i;
             len[i] = fill[l] - rc[l];
             padded[i] = rc[l + 1] - rc[l];
             maxlen = std::max(maxlen, padded[i]);
-            for (int g = 0; g < kG; ++g) bucket[i][g].clear();
-            for (int k = rc[l]; k < fill[l]; ++k) bucket[i][slots[k] % kG].push_back(slots[k]);
-            out[i].clear();
+            for (int g = 0; g < kG; ++g) left[i][g] = 0;
+            for (int k = rc[l]; k < fill[l]; ++k) left[i][slots[k] % kG]++;
+            int put[kG];
+            for (int g = 0; g < kG; ++g) {
+                next[i][g] = put[g] = at;
+                at += left[i][g];
+                if (left[i][g]) avail[i] |= 1u << g;
+            }
+            for (int k = rc[l]; k < fill[l]; ++k) ent[put[slots[k] % kG]++] = slots[k];
         }
         for (int col = 0; col < maxlen; ++col) {
-            bool taken[kG] = {false};
+            unsigned taken = 0;
             for (int i = 0; i < nq; ++i)
-                if (col >= len[i] && col < padded[i]) taken[zero_slot % kG] = true;
-            // Kuhn's augmenting paths over the rows that still have entries
-            int match_g[kG];  // group -> row
-            for (int g = 0; g < kG; ++g) match_g[g] = taken[g] ? -2 : -1;
-            int row_g[kQ];
-            for (int i = 0; i < kQ; ++i) row_g[i] = -1;
+                if (col >= len[i] && col < padded[i]) taken = zbit;
+            int match_g[kG], row_g[kQ];
+            for (int g = 0; g < kG; ++g) match_g[g] = -1;
+            // greedy first (each row its free group with the most entries left),
+            // then augmenting paths for the rows left without one
+            unsigned used = taken;
             for (int i = 0; i < nq; ++i) {
-                if ((int)out[i].size() >= len[i]) continue;
-                bool seen[kG] = {false};
-                // iterative DFS is overkill for 8 x 8; a recursive lambda keeps it short
-                std::function<bool(int)> augment = [&](int r) -> bool {
-                    for (int g = 0; g < kG; ++g) {
-                        if (bucket[r][g].empty() || seen[g] || match_g[g] == -2) continue;
-                        seen[g] = true;
-                        if (match_g[g] == -1 || augment(match_g[g])) {
-                            match_g[g] = r;
-                            row_g[r] = g;
-                            return true;
-                        }
-                    }
-                    return false;
-                };
-                augment(i);
+                row_g[i] = -1;
+                const unsigned f = avail[i] & ~used & 0xffu;
+                if (!f) continue;
+                // the first free group at or after (i + col) mod 8
+                const int w = (i + col) % kG;
+                const unsigned rot = ((f >> w) | (f << (kG - w))) & 0xffu;
+                const int g = (w + __builtin_ctz(rot)) % kG;
+                used |= 1u << g;
+                match_g[g] = i;
+                row_g[i] = g;
             }
-            for (int i = 0; i < nq; ++i) {
-                if ((int)out[i].size() >= len[i]) continue;
-                int g = row_g[i];
-                if (g < 0) {  // no free group: the largest bucket
-                    g = 0;
-                    for (int h = 1; h < kG; ++h)
-                        if (bucket[i][h].size() > bucket[i][g].size()) g = h;
+            // an augmenting path ends at a group that is free and that some row
+            // can take; without one, the rows left over keep a conflict
+            unsigned want = 0;
+            for (int i = 0; i < nq; ++i) want |= avail[i];
+            for (int i = 0; i < nq && (want & ~used & 0xffu); ++i) {
+                if (!avail[i] || row_g[i] >= 0) continue;
+                unsigned seen = taken;
+                if (bank_augment(i, avail, match_g, row_g, seen)) {
+                    used = taken;
+                    for (int g = 0; g < kG; ++g)
+                        if (match_g[g] >= 0) used |= 1u << g;
                 }
-                out[i].push_back(bucket[i][g].back());
-                bucket[i][g].pop_back();
+            }
+            for (int i = 0; i < nq; ++i) {
+                if (!avail[i]) continue;
+                int g = row_g[i];
+                if (g < 0) {  // no free group: the one with the most entries left
+                    g = __builtin_ctz(avail[i]);
+                    for (unsigned m = avail[i]; m; m &= m - 1) {
+                        const int h = __builtin_ctz(m);
+                        if (left[i][h] > left[i][g]) g = h;
+                    }
+                }
+                slots[rc[q0 + i] + col] = ent[next[i][g]++];
+                if (--left[i][g] == 0) avail[i] &= ~(1u << g);
             }
         }
-        for (int i = 0; i < nq; ++i) {
-            const int l = q0 + i;
-            for (int k = 0; k < len[i]; ++k) slots[rc[l] + k] = out[i][k];
-            for (int k = len[i]; k < padded[i]; ++k) slots[rc[l] + k] = zero_slot;
-        }
+        for (int i = 0; i < nq; ++i)
+            for (int k = len[i]; k < padded[i]; ++k) slots[rc[q0 + i] + k] = zero_slot;
     }
 }
 
@@ -363,10 +399,11 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
             return set_error(GS_EINVAL, "patch too large for 16-bit local indices; lower patch_elems");
         auto lid = [&](int u) { return (uint32_t)loc[T.node_inv[u]]; };
         // local ids, and the CSR over corner codes (record << 2 | corner) in
-        // ascending code order (= ascending element order, hinges last); the
-        // stored slot is the corner's float4 index in the staged record planes,
-        // corner * n_rec + record, and rows are padded to a multiple of 4 with
-        // index 4 * n_rec (a zero float4 after the planes)
+        // ascending code order (= ascending element order, hinges last; step 7
+        // reorders each row against bank conflicts); the stored slot is the
+        // corner's float4 index in the staged record planes, corner * n_rec +
+        // record, and rows are padded to a multiple of 4 with index 4 * n_rec
+        // (a zero float4 after the planes)
         std::vector<int> rc(n_loc + 1, 0);
         std::vector<std::pair<int, int>> code_node;  // (code, local node)
         code_node.reserve(nc * q.n_e + 4 * q.n_h);
@@ -408,7 +445,6 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
             return r < q.n_e ? c * q.n_e + r : 4 * q.n_e + c * q.n_h + (r - q.n_e);
         };
         for (auto& cn : code_node) slots[fill[cn.second]++] = (uint16_t)slot_of(cn.first);
-        order_rows_for_banks(slots.data(), rc.data(), fill.data(), n_loc, (uint16_t)(4 * n_rec));
         T.loc_slots.insert(T.loc_slots.end(), slots.begin(), slots.end());
         T.max_loc = std::max(T.max_loc, n_loc);
         T.max_slots = std::max(T.max_slots, n_slots);
@@ -441,7 +477,38 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
     for (size_t i = 0; i < entry_node.size(); ++i)
         if (entry_node[i] >= 0) T.part_pos[i] = T.bnd_rowptr[entry_node[i]] + entry_j[i];
     for (int k = 0; k < 4; ++k) T.bnd_ids.push_back(0);
-    // 7. per patch topology blocks for the one-copy staging
+    // 7. each patch's CSR rows ordered against bank conflicts (patches in
+    // parallel: they are independent), then the topology blocks
+    {
+        auto order_patches = [&](int p0, int p1) {
+            std::vector<int> fill;
+            for (int p = p0; p < p1; ++p) {
+                const PatchDesc& q = T.patches[p];
+                const int n_loc = q.n_int + q.n_bnd;
+                const uint16_t zero = (uint16_t)(4 * (q.n_e + q.n_h));
+                const uint16_t* rp = &T.loc_rowptr[q.lr_begin];
+                uint16_t* sl = &T.loc_slots[q.slot_begin];
+                std::vector<int> rc(rp, rp + n_loc + 1);
+                fill.resize(n_loc);
+                for (int l = 0; l < n_loc; ++l) {
+                    int k = rc[l];
+                    while (k < rc[l + 1] && sl[k] != zero) ++k;
+                    fill[l] = k;
+                }
+                order_rows_for_banks(sl, rc.data(), fill.data(), n_loc, zero);
+            }
+        };
+        const int n_thr = std::max(1, std::min({(int)std::thread::hardware_concurrency(), 16, P / 256}));
+        if (n_thr == 1) {
+            order_patches(0, P);
+        } else {
+            std::vector<std::thread> pool;
+            for (int t = 0; t < n_thr; ++t) pool.emplace_back(order_patches, (int)((long long)P * t / n_thr),
+                                                              (int)((long long)P * (t + 1) / n_thr));
+            for (auto& th : pool) th.join();
+        }
+    }
+    // per patch topology blocks for the one-copy staging
     auto append = [&](const void* src, size_t bytes) {
         const size_t n16 = (bytes + 15) / 16, at = T.topo.size();
         T.topo.resize(at + n16, make_uint4(0, 0, 0, 0));
