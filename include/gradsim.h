@@ -31,8 +31,10 @@
  *     copies it, synchronising the stream for device->host results).
  *   - FP32 state and element math; FP64 for the loss and for the gradient
  *     sums over elements and time steps.  Results are deterministic: node
- *     forces are gathered in a fixed order (no floating-point atomics), so
- *     the same inputs give bitwise the same outputs, alone or in a batch.
+ *     forces are gathered in a fixed order (no floating-point atomics), and
+ *     the per-element FP64 gradient sums over time take one term per element
+ *     per launch, in launch order, so the same inputs give bitwise the same
+ *     outputs, alone or in a batch.
  *   - One gs_ctx per GPU; a context and everything made from it must be used
  *     from one host thread at a time (the server runs its own thread).
  */
