@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--K", type=int, default=0, help="checkpoint interval (0 = library choice)")
     ap.add_argument("--patch", type=int, default=0, help="elements per patch (0 = tuned/default)")
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--threads-adj", type=int, default=0, help="adjoint consumer threads (0 = --threads)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
@@ -129,6 +130,12 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def _shape_key(t):
+    """'patch/threads' or 'patch/threads/adjoint threads' of an autotune timing."""
+    k = f'{t["patch_elems"]}/{t["block_threads"]}'
+    return k + (f'/{t["block_threads_adj"]}' if t.get("block_threads_adj") else "")
 
 
 def kernel_source_hash():
@@ -280,9 +287,10 @@ def main():
         tuned = autotune.tune(ctx, p, steps=10, horizon=S, use_cache=False)
         if args.patch == 0 and args.threads == 0:
             args.patch, args.threads = tuned["patch_elems"], tuned["block_threads"]
+            args.threads_adj = tuned["block_threads_adj"]
         if args.K == 0:
             args.K = tuned["K"]
-    mesh = gs.Mesh(ctx, p, patch_elems=args.patch, block_threads=args.threads)
+    mesh = gs.Mesh(ctx, p, patch_elems=args.patch, block_threads=args.threads, block_threads_adj=args.threads_adj)
     dev = torch.device("cuda", local)
     x0 = torch.tensor(p.x0, dtype=torch.float32, device=dev)
     v0 = torch.tensor(p.v0, dtype=torch.float32, device=dev)
@@ -408,10 +416,10 @@ def main():
                                    f"{S}-step rollout at dt {p.dt} + adjoint, K={mesh_K(args.K, S)}",
                        "parallelism": f"replicas x{ws}", "l2": "flushed between timed iterations (512 MiB write)",
                        "patch_elems": mesh.info.patch_elems, "block_threads": mesh.info.block_threads,
+                       "block_threads_adj": mesh.info.block_threads_adj,
                        "autotune": None if tuned is None else {
                            "K": tuned["K"], "budget": "half the free device memory",
-                           "candidates_ms": {f'{t["patch_elems"]}/{t["block_threads"]}': t["ms"]
-                                             for t in tuned["timings"]}}},
+                           "candidates_ms": {_shape_key(t): t["ms"] for t in tuned["timings"]}}},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "alg_bytes_per_launch": abytes, "avg_launch_ms": avg_s * 1e3,
@@ -478,14 +486,14 @@ def _single_mesh_line(args, name, problem, extra_cfg, cpu_steps=None):
     dev = torch.device("cuda", 0)
     ctx = gs.Context(0)
     S = problem.steps
-    pe, bt, K = args.patch, args.threads, args.K
+    pe, bt, bta, K = args.patch, args.threads, args.threads_adj, args.K
     tuned = None
     if not args.no_autotune and pe == 0 and bt == 0:
         from paper_2104_02646_gb300 import autotune
         tuned = autotune.tune(ctx, problem, steps=min(S, 20), horizon=S, use_cache=False)
-        pe, bt = tuned["patch_elems"], tuned["block_threads"]
+        pe, bt, bta = tuned["patch_elems"], tuned["block_threads"], tuned["block_threads_adj"]
         K = tuned["K"] if K == 0 else K
-    mesh = gs.Mesh(ctx, problem, patch_elems=pe, block_threads=bt)
+    mesh = gs.Mesh(ctx, problem, patch_elems=pe, block_threads=bt, block_threads_adj=bta)
     target = torch.tensor(problem.X + 1e-3, dtype=torch.float32, device=dev)
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
     g = _grads(problem, dev)
@@ -513,9 +521,9 @@ def _single_mesh_line(args, name, problem, extra_cfg, cpu_steps=None):
             "finite": mesh.check_finite() == 0, "dtype": "f32", "data": "synthetic",
             "config": dict(extra_cfg, elems=E, nodes=problem.n_nodes, hinges=problem.n_hinges, steps=S,
                            dt=problem.dt, patch_elems=mesh.info.patch_elems,
-                           block_threads=mesh.info.block_threads, K=mesh_K(K, S),
-                           autotune=None if tuned is None else {
-                               f'{t["patch_elems"]}/{t["block_threads"]}': t["ms"] for t in tuned["timings"]})}
+                           block_threads=mesh.info.block_threads, block_threads_adj=mesh.info.block_threads_adj,
+                           K=mesh_K(K, S),
+                           autotune=None if tuned is None else {_shape_key(t): t["ms"] for t in tuned["timings"]})}
     if cpu_steps is not None and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(problem, cpu_steps[0], cpu_steps[1], f"{name} ({E} elements), FP64 oracle")
     print(json.dumps(line), flush=True)
@@ -549,7 +557,8 @@ def measure_batch(args, n_meshes, reps):
     probs = I.batch(n_meshes, steps=300)
     ctx = gs.Context(0)
     t0 = time.perf_counter()
-    meshes = [gs.Mesh(ctx, p, patch_elems=args.patch, block_threads=args.threads) for p in probs]
+    meshes = [gs.Mesh(ctx, p, patch_elems=args.patch, block_threads=args.threads,
+                      block_threads_adj=args.threads_adj) for p in probs]
     t_create = time.perf_counter() - t0
     batch = gs.Batch(ctx, meshes)
     S = 300
@@ -692,7 +701,7 @@ def workload_recompute(args):
     S = 1000
     p = I.block(n=args.cells, steps=S)
     ctx = gs.Context(0)
-    mesh = gs.Mesh(ctx, p, patch_elems=args.patch, block_threads=args.threads)
+    mesh = gs.Mesh(ctx, p, patch_elems=args.patch, block_threads=args.threads, block_threads_adj=args.threads_adj)
     target = torch.tensor(p.X + 1e-3, dtype=torch.float32, device=dev)
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
     g = _grads(p, dev)

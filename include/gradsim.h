@@ -120,9 +120,11 @@ typedef struct gs_contact {
  *   act, hinge_act: per-element / per-hinge actuation, nullable (0).
  *   pinned: nullable; 1 marks a kinematic node (inverse mass 0, no gravity).
  *   patch_elems, block_threads: work decomposition (0 = defaults, or the
- *   tuned values); they change performance only, never results of a given
- *   decomposition (results may differ in the last bits between different
- *   decompositions because the FP32 force sums are grouped differently). */
+ *   tuned values); block_threads_adj: consumer threads of the adjoint patch
+ *   kernels (0 = block_threads).  They change performance only, never
+ *   results of a given decomposition (results may differ in the last bits
+ *   between different patch sizes because the FP32 force sums are grouped
+ *   differently; the thread counts do not change any sum). */
 typedef struct gs_mesh_desc {
     int kind;
     int n_nodes;
@@ -143,6 +145,7 @@ typedef struct gs_mesh_desc {
     float gravity[3];
     int patch_elems;
     int block_threads;
+    int block_threads_adj;
 } gs_mesh_desc;
 
 typedef struct gs_mesh_info {
@@ -150,6 +153,7 @@ typedef struct gs_mesh_info {
     int n_patches;          /* element patches (one CTA each)                 */
     int n_boundary_nodes;   /* nodes shared between patches                   */
     int patch_elems, block_threads;
+    int block_threads_adj;  /* consumer threads of the adjoint patch kernels  */
     double dt_stable;       /* explicit stability estimate (seconds)          */
     size_t device_bytes;    /* bytes the mesh holds on the device             */
 } gs_mesh_info;

@@ -28,7 +28,9 @@ import time
 STATE_BYTES = 32  # one stored state per node: (u, w) and (v, plane offset) as float4
 
 # (elements per patch, consumer threads per CTA)
-DEFAULT_CANDIDATES = ((256, 128), (128, 128), (256, 256), (384, 128), (512, 256), (128, 64), (64, 64))
+# (patch elements, forward consumer threads[, adjoint consumer threads])
+DEFAULT_CANDIDATES = ((256, 128), (320, 160, 128), (128, 128), (256, 256), (384, 128), (512, 256), (128, 64),
+                      (64, 64))
 
 
 def state_buffers(S: int, K: int) -> int:
@@ -95,12 +97,13 @@ def store_cache(entries: dict, path: str | None = None) -> None:
     os.replace(tmp, p)
 
 
-def _time_candidate(ctx, problem, patch_elems, block_threads, steps, K, reps):
+def _time_candidate(ctx, problem, patch_elems, block_threads, steps, K, reps, block_threads_adj=0):
     import torch
     from . import gradsim as gs
     dev = torch.device("cuda", ctx.device)
     try:
-        m = gs.Mesh(ctx, problem, patch_elems=patch_elems, block_threads=block_threads)
+        m = gs.Mesh(ctx, problem, patch_elems=patch_elems, block_threads=block_threads,
+                    block_threads_adj=block_threads_adj)
     except gs.GradsimError:
         return None  # e.g. the patch does not fit in shared memory
     try:
@@ -130,11 +133,13 @@ def _time_candidate(ctx, problem, patch_elems, block_threads, steps, K, reps):
 
 def tune(ctx, problem, steps: int | None = None, horizon: int | None = None, candidates=DEFAULT_CANDIDATES,
          budget_bytes: int | None = None, reps: int = 2, cache: str | None = None, use_cache: bool = True) -> dict:
-    """Pick (patch_elems, block_threads) by timing `steps` rollout + adjoint
-    steps of `problem` per candidate, and K for a rollout of `horizon` steps
-    (default problem.steps) under `budget_bytes` (default: half the free
-    device memory).  Returns {"patch_elems", "block_threads",
-    "elems_per_thread", "K", "ms", "timings"}."""
+    """Pick (patch_elems, block_threads, block_threads_adj) by timing
+    `steps` rollout + adjoint steps of `problem` per candidate (a candidate
+    without a third entry runs the adjoint with block_threads), and K for a
+    rollout of `horizon` steps (default problem.steps) under `budget_bytes`
+    (default: half the free device memory).  Returns {"patch_elems",
+    "block_threads", "block_threads_adj", "elems_per_thread", "K", "ms",
+    "timings"}."""
     import torch
     horizon = int(problem.steps if horizon is None else horizon)
     steps = int(min(horizon, 20) if steps is None else steps)
@@ -146,19 +151,23 @@ def tune(ctx, problem, steps: int | None = None, horizon: int | None = None, can
     hit = entries.get(key)
     if hit and all(k in hit for k in ("patch_elems", "block_threads", "ms")):
         out = dict(hit)
+        out.setdefault("block_threads_adj", 0)
         out["K"] = K
         out["cached"] = True
         return out
     timings = []
     t0 = time.perf_counter()
-    for pe, bt in candidates:
-        ms = _time_candidate(ctx, problem, pe, bt, steps, min(K, max(steps, 1)), reps)
-        timings.append({"patch_elems": pe, "block_threads": bt, "ms": ms})
+    for cand in candidates:
+        pe, bt = cand[0], cand[1]
+        bta = cand[2] if len(cand) > 2 else 0
+        ms = _time_candidate(ctx, problem, pe, bt, steps, min(K, max(steps, 1)), reps, bta)
+        timings.append({"patch_elems": pe, "block_threads": bt, "block_threads_adj": bta, "ms": ms})
     ok = [t for t in timings if t["ms"] is not None]
     if not ok:
         raise RuntimeError("autotune: no candidate launch shape could be built for this mesh")
     best = min(ok, key=lambda t: t["ms"])
     out = {"patch_elems": best["patch_elems"], "block_threads": best["block_threads"],
+           "block_threads_adj": best["block_threads_adj"],
            "elems_per_thread": best["patch_elems"] / best["block_threads"], "ms": best["ms"],
            "steps_timed": steps, "timings": timings, "tune_s": time.perf_counter() - t0}
     if use_cache:

@@ -160,7 +160,8 @@ struct Launch {
     const NodeBlock* node_blocks = nullptr;
     int n_node_blocks = 0;
     MeshRT* rt = nullptr;
-    int threads = 256;
+    int threads = 256;      // consumer threads of the forward patch kernels
+    int threads_adj = 256;  // consumer threads of the adjoint patch kernels
     // patch kernels (tet fwd, cloth fwd, tet adj, cloth adj): persistent grid
     // size and bytes of one of the two shared-memory pipeline stages
     int grid[4] = {0, 0, 0, 0};

@@ -1671,10 +1671,10 @@ void launch_forward_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) 
 
 void launch_adjoint_step(const Launch& L, int tick, cudaStream_t s, Prof* prof) {
     if (L.n_tet_patches)
-        GS_TIMED(KT_TET_ADJ, launch_pdl(k_tet_adj, L.grid[2], L.threads + 32, patch_dyn_smem(L.stage[2]), s,
+        GS_TIMED(KT_TET_ADJ, launch_pdl(k_tet_adj, L.grid[2], L.threads_adj + 32, patch_dyn_smem(L.stage[2]), s,
                                         L.tet_patches, L.n_tet_patches, (const MeshRT*)L.rt, tick, L.stage[2], L.extras));
     if (L.n_cloth_patches)
-        GS_TIMED(KT_CLOTH_ADJ, launch_pdl(k_cloth_adj, L.grid[3], L.threads + 32, patch_dyn_smem(L.stage[3]),
+        GS_TIMED(KT_CLOTH_ADJ, launch_pdl(k_cloth_adj, L.grid[3], L.threads_adj + 32, patch_dyn_smem(L.stage[3]),
                                           s, L.cloth_patches, L.n_cloth_patches, (const MeshRT*)L.rt, tick,
                                           L.stage[3], L.extras));
     if (L.n_bnd_blocks)

@@ -704,6 +704,9 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     const int nc = d.kind == GS_TET ? 4 : 3;
     int threads = d.block_threads > 0 ? d.block_threads : 128;
     if (threads % 32 || threads > 1024) return set_error(GS_EINVAL, "block_threads must be a multiple of 32, <= 1024");
+    const int threads_adj = d.block_threads_adj > 0 ? d.block_threads_adj : threads;
+    if (threads_adj % 32 || threads_adj > 1024)
+        return set_error(GS_EINVAL, "block_threads_adj must be a multiple of 32, <= 1024");
     int pe = d.patch_elems > 0 ? d.patch_elems : (d.kind == GS_TET ? 256 : 256);
     pe = (pe + 1) & ~1;  // even, so every patch's FP64 accumulators start 16 B aligned
     if (pe > 16383) return set_error(GS_EINVAL, "patch_elems must be <= 16383");
@@ -720,9 +723,11 @@ gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s,
     m->info.n_boundary_nodes = T.n_bnd;
     m->info.patch_elems = pe;
     m->info.block_threads = threads;
+    m->info.block_threads_adj = threads_adj;
     m->info.dt_stable = stability_estimate(d);
     m->n_pad = (N + 31) & ~31;
     m->threads = threads;
+    m->threads_adj = threads_adj;
     m->max_loc = T.max_loc;
     m->max_slots = T.max_slots;
     m->max_rec = T.max_rec;
@@ -1026,6 +1031,7 @@ gs_status LaunchSet::build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStrea
     std::vector<NodeBlock> bb, nb;
     size_t sf_t[2] = {0, 0}, sa_t[2] = {0, 0}, sf_c[2] = {0, 0}, sa_c[2] = {0, 0};
     threads = 32;
+    threads_adj = 32;
     node_block_begin.clear();
     for (int i = 0; i < (int)ms.size(); ++i) {
         gs_mesh* m = ms[i];
@@ -1053,6 +1059,7 @@ gs_status LaunchSet::build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStrea
             }
         }
         threads = std::max(threads, m->threads);
+        threads_adj = std::max(threads_adj, m->threads_adj);
     }
     node_block_begin.push_back((int)nb.size());
     GS_TRY(upload(c, d_tet, tp, s));
@@ -1072,6 +1079,7 @@ gs_status LaunchSet::build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStrea
     launch.n_node_blocks = (int)nb.size();
     launch.rt = (MeshRT*)d_rt.p;
     launch.threads = threads;
+    launch.threads_adj = threads_adj;
     for (int x = 0; x < 2; ++x) {
         stage_var[x][0] = (int)sf_t[x];
         stage_var[x][1] = (int)sf_c[x];
@@ -1099,7 +1107,8 @@ gs_status LaunchSet::sync_rt(cudaStream_t s) {
         const int np[4] = {launch.n_tet_patches, launch.n_cloth_patches, launch.n_tet_patches, launch.n_cloth_patches};
         for (int k = 0; k < 4; ++k) {
             launch.stage[k] = stage_var[extras][k];
-            launch.grid[k] = patch_grid(k, launch.threads, launch.stage[k], np[k], ctx->num_sms);
+            const int thr = k < 2 ? launch.threads : launch.threads_adj;  // forward, adjoint kernels
+            launch.grid[k] = patch_grid(k, thr, launch.stage[k], np[k], ctx->num_sms);
         }
     }
     GS_CUDA(cudaMemcpyAsync(d_rt.p, host_rt.data(), host_rt.size() * sizeof(MeshRT), cudaMemcpyHostToDevice, s));

@@ -88,7 +88,7 @@ struct LaunchSet {
     std::vector<int> node_block_begin;
     Launch launch;
     int stage_var[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // stage bytes per patch kernel, [extras]
-    int threads = 256;
+    int threads = 256, threads_adj = 256;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
 
     gs_status build(gs_ctx* c, const std::vector<gs_mesh*>& ms, cudaStream_t s);
@@ -109,7 +109,7 @@ void launch_gather_elems(const MeshRT* rt_dev, const float* src_caller_order, fl
 struct gs_mesh {
     gs_ctx* ctx = nullptr;
     gs_mesh_info info{};
-    int n_pad = 0, threads = 256, max_loc = 0, max_slots = 0, max_rec = 0, n_bufs = 0;
+    int n_pad = 0, threads = 256, threads_adj = 256, max_loc = 0, max_slots = 0, max_rec = 0, n_bufs = 0;
     size_t smem_fwd[2] = {0, 0}, smem_adj[2] = {0, 0};  // stage bytes [without, with] the extra regions
     std::vector<gs::PatchDesc> patches;
     std::vector<gs::NodeBlock> bnd_blocks, node_blocks;

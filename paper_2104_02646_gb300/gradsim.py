@@ -41,13 +41,14 @@ class gs_mesh_desc(C.Structure):
                 ("n_hinges", C.c_int), ("hinges", _ip), ("X", _dp), ("v0", _dp), ("mu", _dp),
                 ("lambda_", _dp), ("density", _dp), ("kb", _dp), ("act", _dp), ("hinge_act", _dp),
                 ("pinned", C.POINTER(C.c_uint8)), ("contact", gs_contact), ("gravity", C.c_float * 3),
-                ("patch_elems", C.c_int), ("block_threads", C.c_int)]
+                ("patch_elems", C.c_int), ("block_threads", C.c_int), ("block_threads_adj", C.c_int)]
 
 
 class gs_mesh_info(C.Structure):
     _fields_ = [("kind", C.c_int), ("n_nodes", C.c_int), ("n_elems", C.c_int), ("n_hinges", C.c_int),
                 ("n_patches", C.c_int), ("n_boundary_nodes", C.c_int), ("patch_elems", C.c_int),
-                ("block_threads", C.c_int), ("dt_stable", C.c_double), ("device_bytes", C.c_size_t)]
+                ("block_threads", C.c_int), ("block_threads_adj", C.c_int), ("dt_stable", C.c_double),
+                ("device_bytes", C.c_size_t)]
 
 
 class gs_camera(C.Structure):
@@ -254,7 +255,7 @@ def _contact(c) -> gs_contact:
     return out
 
 
-def mesh_desc(problem, patch_elems: int = 0, block_threads: int = 0):
+def mesh_desc(problem, patch_elems: int = 0, block_threads: int = 0, block_threads_adj: int = 0):
     """gs_mesh_desc for an ``inputs.Problem``; returns (desc, keep-alive list)."""
     keep = []
 
@@ -292,6 +293,7 @@ def mesh_desc(problem, patch_elems: int = 0, block_threads: int = 0):
     d.gravity = (C.c_float * 3)(*problem.gravity)
     d.patch_elems = int(patch_elems)
     d.block_threads = int(block_threads)
+    d.block_threads_adj = int(block_threads_adj)
     return d, keep
 
 
@@ -341,10 +343,11 @@ class Context:
 class Mesh:
     """A gs_mesh built from an ``inputs.Problem`` (host arrays are copied)."""
 
-    def __init__(self, ctx: Context, problem, patch_elems: int = 0, block_threads: int = 0):
+    def __init__(self, ctx: Context, problem, patch_elems: int = 0, block_threads: int = 0,
+                 block_threads_adj: int = 0):
         self.ctx = ctx
         self.problem = problem
-        d, keep = mesh_desc(problem, patch_elems, block_threads)
+        d, keep = mesh_desc(problem, patch_elems, block_threads, block_threads_adj)
         self.h = _vp()
         check(load().gs_mesh_create(ctx.h, C.byref(d), C.byref(self.h)))
         self.info = gs_mesh_info()

@@ -181,9 +181,11 @@ def make_target(problem, steps, seed=0, scale=1.1):
     return xS + I.position_noise(problem.n_nodes, seed=seed)
 
 
-def run_gpu(gs, ctx, problem, steps, target=None, K=0, patch_elems=0, block_threads=0, grads=True):
+def run_gpu(gs, ctx, problem, steps, target=None, K=0, patch_elems=0, block_threads=0, grads=True,
+            block_threads_adj=0):
     import torch
-    m = gs.Mesh(ctx, problem, patch_elems=patch_elems, block_threads=block_threads)
+    m = gs.Mesh(ctx, problem, patch_elems=patch_elems, block_threads=block_threads,
+                block_threads_adj=block_threads_adj)
     N = problem.n_nodes
     dev = "cuda"
     tgt = None if target is None else torch.tensor(target, dtype=torch.float32, device=dev)

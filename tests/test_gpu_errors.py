@@ -58,6 +58,14 @@ def _mutations():
     return [out_of_range, negative_index, repeated_node, inverted, nan_position, zero_mu, bad_plane]
 
 
+@pytest.mark.parametrize("shape", [dict(block_threads=100), dict(block_threads=2048),
+                                   dict(block_threads_adj=48), dict(block_threads_adj=1056)])
+def test_bad_thread_counts_are_rejected(gs, ctx, shape):
+    with pytest.raises(gs.GradsimError) as ei:
+        gs.Mesh(ctx, I.block(n=3, steps=1), **shape)
+    assert ei.value.status == gs.GS_EINVAL
+
+
 @pytest.mark.parametrize("mutate", _mutations(), ids=lambda f: f.__name__)
 def test_malformed_mesh_is_rejected(gs, ctx, mutate):
     p = _copy(I.block(n=3, steps=1))

@@ -156,6 +156,23 @@ def test_checkpoint_interval_does_not_change_results(gs, ctx):
         np.testing.assert_array_equal(a[k], d[k])
 
 
+def test_thread_counts_do_not_change_results(gs, ctx):
+    # the forward and adjoint consumer thread counts change only which thread
+    # takes an element or a node: every sum keeps its order, so the results
+    # are bitwise the same (tets and cloth, ragged patches)
+    for p, pe in ((I.block(n=6, steps=40, seed=7), 320), (I.cloth("3s", n=16, steps=40, grid_scaled=True, height=0.29), 100)):
+        tgt = make_target(p, 40)
+        a = run_gpu(gs, ctx, p, 40, tgt, patch_elems=pe, block_threads=160)
+        b = run_gpu(gs, ctx, p, 40, tgt, patch_elems=pe, block_threads=160, block_threads_adj=128)
+        c = run_gpu(gs, ctx, p, 40, tgt, patch_elems=pe, block_threads=64, block_threads_adj=96)
+        assert b["mesh"].info.block_threads_adj == 128 and c["mesh"].info.block_threads_adj == 96
+        assert a["mesh"].info.block_threads_adj == 160  # 0 means the forward count
+        keys = ("x", "v", "d_mu", "d_lambda", "d_density", "d_v0", "d_x0")
+        for k in keys:
+            np.testing.assert_array_equal(a[k], b[k])
+            np.testing.assert_array_equal(a[k], c[k])
+
+
 def test_deterministic_and_graphs_match_plain_loop(gs, ctx):
     p = I.block(n=6, steps=40, seed=6)
     tgt = make_target(p, 40)
