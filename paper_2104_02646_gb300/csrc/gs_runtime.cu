@@ -11,6 +11,7 @@
 #include <memory>
 #include <numeric>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -499,14 +500,21 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
             }
         };
         const int n_thr = std::max(1, std::min({(int)std::thread::hardware_concurrency(), 16, P / 256}));
-        if (n_thr == 1) {
-            order_patches(0, P);
-        } else {
-            std::vector<std::thread> pool;
-            for (int t = 0; t < n_thr; ++t) pool.emplace_back(order_patches, (int)((long long)P * t / n_thr),
-                                                              (int)((long long)P * (t + 1) / n_thr));
-            for (auto& th : pool) th.join();
+        // patches [0, done) are handed to threads; if a thread cannot be
+        // started, this thread orders the rest itself
+        int done = 0;
+        std::vector<std::thread> pool;
+        for (int t = 1; t < n_thr; ++t) {
+            const int p0 = (int)((long long)P * (t - 1) / n_thr), p1 = (int)((long long)P * t / n_thr);
+            try {
+                pool.emplace_back(order_patches, p0, p1);
+            } catch (const std::system_error&) {
+                break;
+            }
+            done = p1;
         }
+        order_patches(done, P);
+        for (auto& th : pool) th.join();
     }
     // per patch topology blocks for the one-copy staging
     auto append = [&](const void* src, size_t bytes) {
