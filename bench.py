@@ -359,6 +359,13 @@ def main():
     peak, peak_kind = measured_peaks()
     achieved = abytes / avg_s / 1e9
     traffic = ncu_traffic(dom, E)
+    # the same kernel's share of the profiled step applied to the timed step:
+    # the event nodes of the profiled step end the programmatic overlap
+    # between neighbouring kernels, so the per-launch times above add up to
+    # more than the timed step; scaled by their shares they add up to it
+    prof_ms = sum(x[1] for x in kt.values())
+    avg_s_timed = (kms / prof_ms) * (total_ms / args.steps) / launches / 1e3
+    achieved_timed = abytes / avg_s_timed / 1e9
     # the whole timed step against the roofline of its algorithmic bytes
     step_bytes = S * (alg_bytes(True, E, N) + alg_bytes(False, E, N))
     step_achieved = step_bytes / (total_ms / args.steps / 1e3) / 1e9
@@ -425,7 +432,12 @@ def main():
                          "alg_bytes_per_launch": abytes, "avg_launch_ms": avg_s * 1e3,
                          "launches_per_step": launches,
                          "timing": "CUDA events around each kernel inside the captured graphs of one extra step",
-                         "profiled_kernels_ms_per_step": sum(x[1] for x in kt.values()),
+                         "profiled_kernels_ms_per_step": prof_ms,
+                         "in_timed_step": {"avg_launch_ms": avg_s_timed * 1e3, "achieved": achieved_timed,
+                                           "frac": achieved_timed / peak,
+                                           "how": "the kernel's share of the profiled step x the timed step "
+                                                  "/ launches (the per-kernel events remove the overlap of "
+                                                  "neighbouring kernels that the timed step has)"},
                          "kernel_share": {k: v[1] / sum(x[1] for x in kt.values()) for k, v in kt.items()},
                          "step": {"alg_bytes": step_bytes, "achieved": step_achieved,
                                   "frac": step_achieved / peak,
