@@ -245,7 +245,7 @@ def launches_per_step(S, K, have_bnd):
     if K == 1:
         n += per_step * S           # reverse steps over the stored states
     else:
-        n += n_ck + per_step * (S - n_ck) + per_step * S  # per segment: copy, n-1 recomputed, n reverse
+        n += n_ck + per_step * S + per_step * S  # per segment: copy, n recomputed, n reverse
     n += 2                          # node and element gradient kernels
     return n
 
@@ -727,7 +727,7 @@ def workload_recompute(args):
             both()
         res[K] = min(_events_ms(both) for _ in range(max(1, args.steps)))
     K1, Kc = sorted(res)
-    state_mb = 32 * p.n_nodes / 1e6
+    state_mb = 48 * p.n_nodes / 1e6
     n_ck = -(-S // Kc)
     line = {"metric": "fwd+adjoint element-steps/s", "workload": f"recompute_block{args.cells}",
             "value": p.n_elems * S / (res[Kc] / 1e3), "unit": "element-steps/s",

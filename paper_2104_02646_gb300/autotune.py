@@ -25,7 +25,7 @@ import math
 import os
 import time
 
-STATE_BYTES = 32  # one stored state per node: (u, w) and (v, plane offset) as float4
+STATE_BYTES = 48  # one stored state per node: (u, w), (v, plane offset) and the element force as float4
 
 # (elements per patch, consumer threads per CTA)
 # (patch elements, forward consumer threads[, adjoint consumer threads])

@@ -99,6 +99,11 @@ struct alignas(16) MeshRT {  // 16 B aligned: the patch kernels bulk-copy it int
     // displacement u = x - X (and the inverse mass in .w)
     float4* st_x;            // (ux, uy, uz, w)
     float4* st_v;            // (vx, vy, vz, 0)
+    // buffer b of st_f: the elements' force on each node in the state of
+    // buffer b, written by the forward step that starts from it (the
+    // adjoint's dL/dw term needs it, and recomputing it cost the adjoint's
+    // element phase a force evaluation per element)
+    float4* st_f;            // (fx, fy, fz, 0)
     long long buf_stride;
     int in_a, in_b, out_a, out_b;   // forward: in = in_a + in_b * tick, out likewise
     int ck_tick, ck_buf;            // tick at which the output is also written to ck_buf

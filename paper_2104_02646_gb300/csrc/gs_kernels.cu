@@ -193,7 +193,7 @@ __host__ __device__ __forceinline__ int r16(int bytes) { return (bytes + 15) & ~
 // state.  The adjoint also holds the adjoint state x_bar, v_hat of every
 // local node (interior ones bulk-copied, boundary ones gathered behind them).
 struct Layout {
-    int rec, rp, sl, pos, xs, vs, xb, xbB, vb, vbB, wb, act, hact, vB, total;
+    int rec, rp, sl, pos, xs, vs, xb, xbB, vb, vbB, fs, wb, act, hact, vB, total;
 };
 
 // `extras`: the stage also holds the step's actuation slices and, for
@@ -216,8 +216,10 @@ __host__ __device__ __forceinline__ Layout patch_layout(int kind, int n_e, int n
     L.xbB = L.xb + (adjoint ? 16 * n_int : 0);
     L.vb = L.xbB + (adjoint ? 16 * n_bnd : 0);
     L.vbB = L.vb + (adjoint ? 16 * n_int : 0);
+    // adjoint: the element force of the interior nodes at the step's state
+    L.fs = L.vbB + (adjoint ? 16 * n_bnd : 0);
     // adjoint: dL/dw of the interior nodes
-    L.wb = L.vbB + (adjoint ? 16 * n_bnd : 0);
+    L.wb = L.fs + (adjoint ? 16 * n_int : 0);
     // the step's row slices of a time-varying actuation (elements, hinges);
     // up to 3 entries of slack on each side for the aligned slice ends
     L.act = L.wb + (adjoint ? r16(8 * n_int) : 0);
@@ -316,6 +318,7 @@ __device__ __forceinline__ void node_forward(const MeshRT& m, int tick, int gid,
         v.z = v.z + m.dt * (w * f.z + m.gz);
     }
     const float3 xn = x + m.dt * v;
+    m.st_f[(size_t)(m.in_a + m.in_b * tick) * (size_t)m.buf_stride + gid] = f4(fel, 0.f);
     const int ob = m.out_a + m.out_b * tick;
     const float4 xo = f4(xn, w), vo = f4(v, v4.w);
     bufx(m, ob)[gid] = xo;
@@ -336,10 +339,12 @@ __device__ __forceinline__ float3 vhat_of(const MeshRT& m, float3 xb, float3 vb)
 
 // reverse of node_forward for one node.  Inputs: state (u, v) at step n, the
 // adjoint (xb, vh) of step n+1, the gathered element terms xsum = sum of
-// corner dL/du and ssum = sum of corner f . v_hat, and dL/dw so far.  Writes
-// the adjoint (x_bar, v_hat) of step n and the accumulated dL/dw (FP64).
+// corner dL/du, the elements' force fel on the node at step n (stored by the
+// forward; the sum over the node's corners of f . v_hat is fel . v_hat), and
+// dL/dw so far.  Writes the adjoint (x_bar, v_hat) of step n and the
+// accumulated dL/dw (FP64).
 __device__ __forceinline__ void node_adjoint(const MeshRT& m, int gid, float4 x4, float4 v4, float4 xb4, float4 vh4,
-                                             float3 xsum, float ssum, double wb_old, float3 vsum) {
+                                             float3 xsum, float3 fel, double wb_old, float3 vsum) {
     const float w = x4.w;
     const float3 xbn = xyz(xb4);
     const float3 vh = xyz(vh4);                 // dL/dv+ (total)
@@ -350,7 +355,7 @@ __device__ __forceinline__ void node_adjoint(const MeshRT& m, int gid, float4 x4
     vb += vsum;  // the elements' velocity-dependent forces (air), added last
     m.xb[gid] = f4(xb, 0.0f);
     m.vb[gid] = f4(vhat_of(m, xb, vb), 0.0f);
-    m.wbar[gid] = wb_old + (double)(m.dt * (ssum + dot3(fc, vh)));
+    m.wbar[gid] = wb_old + (double)(m.dt * (dot3(fel, vh) + dot3(fc, vh)));
 }
 
 // A staged patch in shared memory.
@@ -366,6 +371,7 @@ struct Stage {
     float4* vb;   // adjoint: v_hat of the local nodes (interior, then boundary = vbB)
     float4* xbB;  // adjoint: boundary x_bar (gathered)
     float4* vbB;  // adjoint: boundary v_hat (gathered)
+    float4* fs;   // adjoint: element force of the interior nodes at the step's state
     double* wb;   // adjoint: dL/dw of the interior nodes
     const float* act;   // this step's actuation of the patch's elements [n_e], or null
     const float* hact;  // this step's actuation of the patch's hinges [n_h], or null
@@ -392,6 +398,7 @@ __device__ __forceinline__ Stage stage_at(const PatchDesc& p, int kind, unsigned
     S.vb = (float4*)(buf + L.vb);
     S.xbB = (float4*)(buf + L.xbB);
     S.vbB = (float4*)(buf + L.vbB);
+    S.fs = (float4*)(buf + L.fs);
     S.wb = (double*)(buf + L.wb);
     S.act = (const float*)(buf + L.act) + (p.e_begin & 3);
     S.hact = (const float*)(buf + L.hact) + (p.h_begin & 3);
@@ -447,7 +454,7 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
     const uint32_t b_act = ra >= 0 ? 4u * act_slice_n(p.e_begin, p.n_e) : 0u;
     const uint32_t b_hact = rh >= 0 ? 4u * act_slice_n(p.h_begin, p.n_h) : 0u;
     const uint32_t tx = (copy_rt ? (uint32_t)sizeof(MeshRT) : 0u) + 64u * n_rec + b_rp + b_sl + b_pos +
-                        (p.n_int ? (adjoint ? 4u : 2u) * b_int : 0u) + b_act + b_hact;
+                        (p.n_int ? (adjoint ? 5u : 2u) * b_int : 0u) + b_act + b_hact;
     fence_proxy_async();
     mbar_expect_tx(bar, tx);
     if (copy_rt) bulk_g2s(hdr_rt, rt_global, (uint32_t)sizeof(MeshRT), bar);
@@ -461,6 +468,7 @@ __device__ __forceinline__ void issue_bulk(const PatchDesc& p, const MeshRT* rt_
         if (adjoint) {
             bulk_g2s(S.xb, m.xb + p.int_begin, b_int, bar);
             bulk_g2s(S.vb, m.vb + p.int_begin, b_int, bar);
+            bulk_g2s(S.fs, m.st_f + (size_t)ib * (size_t)m.buf_stride + p.int_begin, b_int, bar);
         }
     }
     if (b_act)
@@ -620,7 +628,8 @@ __device__ __forceinline__ void accumulate_ml(double2* g, float gmu, float glam)
 // the adjoint state as (x_bar, v_hat)
 __device__ __forceinline__ float3 vhat(const Stage& S, int l) { return xyz(S.vb[l]); }
 
-// corner result (dL/du_corner, f_corner . v_hat_node) in place
+// corner result dL/du_corner in place (the fourth lane is unused: the
+// dL/dw term takes the stored element force of the node)
 __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshRT& m, int tick, const Stage& S,
                                                  int nt) {
     const float dt = m.dt;
@@ -636,16 +645,14 @@ __device__ __forceinline__ void tet_elements_adj(const PatchDesc& p, const MeshR
         const float3 v0 = vhat(S, i0), v1 = vhat(S, i1), v2 = vhat(S, i2), v3 = vhat(S, i3);
         TetState s;
         tet_state(xyz(x0), xyz(x1), xyz(x2), xyz(x3), a, b, c, w.z + act_of(S.act, le), s);
-        float3 f0, f1, f2, f3;
-        tet_forces(s, a, b, c, f0, f1, f2, f3);
         float3 xb0, xb1, xb2, xb3;
         float gmu, glam, gact;
         tet_adjoint(s, a, b, c, (dt * x0.w) * v0, (dt * x1.w) * v1, (dt * x2.w) * v2, (dt * x3.w) * v3, xb0, xb1,
                     xb2, xb3, gmu, glam, gact);
-        put(S, le, 0, f4(xb0, dot3(f0, v0)));
-        put(S, le, 1, f4(xb1, dot3(f1, v1)));
-        put(S, le, 2, f4(xb2, dot3(f2, v2)));
-        put(S, le, 3, f4(xb3, dot3(f3, v3)));
+        put(S, le, 0, f4(xb0, 0.f));
+        put(S, le, 1, f4(xb1, 0.f));
+        put(S, le, 2, f4(xb2, 0.f));
+        put(S, le, 3, f4(xb3, 0.f));
         const int e = p.e_begin + le;
         accumulate_ml(m.g_ml + e, gmu, glam);
         if (m.g_act) m.g_act[e] += (double)gact;
@@ -673,8 +680,6 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             float4 bt = b;
             bt.w += act_of(S.act, lr);  // actuation (b.w)
             tri_state(xyz(x0), xyz(x1), xyz(x2), a, bt, make_float3(c.x, c.y, c.z), make_float3(c.w, w.z, w.w), s);
-            float3 f0, f1, f2;
-            tri_forces(s, a, b, f0, f1, f2);
             float3 xb0, xb1, xb2;
             float gmu, glam, gact;
             const float3 y0 = (dt * x0.w) * v0, y1 = (dt * x1.w) * v1, y2 = (dt * x2.w) * v2;
@@ -683,10 +688,6 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
                 // F on each corner F/3: dL/dF = (y0 + y1 + y2)/3; N = A (F0 x F1)
                 const float3 vr = air_vr(m, S, p, i0, i1, i2);
                 const float3 N = b.x * cross3(s.F0, s.F1);
-                const float3 Fa = air_force(N, vr, m.k_drag, m.k_lift) * (1.0f / 3.0f);
-                f0 += Fa;
-                f1 += Fa;
-                f2 += Fa;
                 float3 Nb = make_float3(0.f, 0.f, 0.f), vrb = make_float3(0.f, 0.f, 0.f);
                 air_adjoint(N, vr, m.k_drag, m.k_lift, (y0 + y1 + y2) * (1.0f / 3.0f), Nb, vrb);
                 const float3 F0b = b.x * cross3(s.F1, Nb), F1b = b.x * cross3(Nb, s.F0);
@@ -697,9 +698,9 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
                 // the same dL/dv for each corner, summed per node by the node phase
                 put(S, q, 3, f4(vrb * (1.0f / 3.0f), 0.f));
             }
-            put(S, q, 0, f4(xb0, dot3(f0, v0)));
-            put(S, q, 1, f4(xb1, dot3(f1, v1)));
-            put(S, q, 2, f4(xb2, dot3(f2, v2)));
+            put(S, q, 0, f4(xb0, 0.f));
+            put(S, q, 1, f4(xb1, 0.f));
+            put(S, q, 2, f4(xb2, 0.f));
             const int t = p.e_begin + lr;
             accumulate_ml(m.g_ml + t, gmu, glam);
             if (m.g_act) m.g_act[t] += (double)gact;
@@ -711,16 +712,14 @@ __device__ __forceinline__ void cloth_elements_adj(const PatchDesc& p, const Mes
             HingeState s;
             hinge_state(xyz(x1), xyz(x2), xyz(x3), xyz(x4), xyz(a), xyz(b), xyz(c),
                         b.w + act_of(S.hact, lr - p.n_e), s);
-            float3 f1, f2, f3, f4_;
-            hinge_forces(s, a.w, f1, f2, f3, f4_);
             float3 xb1, xb2, xb3, xb4;
             float gkb, gact;
             hinge_adjoint(s, a.w, (dt * x1.w) * v1, (dt * x2.w) * v2, (dt * x3.w) * v3, (dt * x4.w) * v4, xb1, xb2,
                           xb3, xb4, gkb, gact);
-            put(S, q, 0, f4(xb1, dot3(f1, v1)));
-            put(S, q, 1, f4(xb2, dot3(f2, v2)));
-            put(S, q, 2, f4(xb3, dot3(f3, v3)));
-            put(S, q, 3, f4(xb4, dot3(f4_, v4)));
+            put(S, q, 0, f4(xb1, 0.f));
+            put(S, q, 1, f4(xb2, 0.f));
+            put(S, q, 2, f4(xb3, 0.f));
+            put(S, q, 3, f4(xb4, 0.f));
             const int h = p.h_begin + (lr - p.n_e);
             m.g_kb[h] += (double)gkb;
             if (m.g_hact) m.g_hact[h] += (double)gact;
@@ -826,7 +825,7 @@ __device__ __forceinline__ void adjoint_nodes(const PatchDesc& p, const MeshRT& 
         const float4 acc = row_sum4(S, k, k1, m.status);
         const float3 va = air ? row_sum_air_v(S, k, k1) : make_float3(0.f, 0.f, 0.f);
         if (l < p.n_int) {
-            node_adjoint(m, p.int_begin + l, S.xs[l], S.vs[l], S.xb[l], S.vb[l], xyz(acc), acc.w, S.wb[l], va);
+            node_adjoint(m, p.int_begin + l, S.xs[l], S.vs[l], S.xb[l], S.vb[l], xyz(acc), xyz(S.fs[l]), S.wb[l], va);
         } else {
             const int pp = S.pos[l - p.n_int];
             if (!idx_ok(pp >= 0 && pp < m.n_part, m.status)) continue;
@@ -1139,6 +1138,7 @@ __global__ void __launch_bounds__(kBndThreads, 6)
         const int sb = m.adj_a + m.adj_b * tick;
         const float4* X = bufx(m, sb);
         const float4* V = bufv(m, sb);
+        const float4* F = m.st_f + (size_t)sb * (size_t)m.buf_stride;
         const int i0 = threadIdx.x, i1 = threadIdx.x + kBndThreads;
         bool h0 = i0 < nb.count, h1 = i1 < nb.count;
         const int b0 = nb.begin + i0, b1 = nb.begin + i1;
@@ -1148,7 +1148,7 @@ __global__ void __launch_bounds__(kBndThreads, 6)
             h1 = h1 && idx_ok(b1 >= 0 && b1 < m.n_bnd, m.status);
         }
         int k0 = 0, e0 = 0, k1 = 0, e1 = 0;
-        float4 x0, v0, xb0, vb0, x1, v1, xb1, vb1;
+        float4 x0, v0, xb0, vb0, f0, x1, v1, xb1, vb1, f1;
         double w0 = 0.0, w1 = 0.0;
         if (h0) {
             k0 = m.bnd_rowptr[b0];
@@ -1157,6 +1157,7 @@ __global__ void __launch_bounds__(kBndThreads, 6)
             v0 = V[g0];
             xb0 = m.xb[g0];
             vb0 = m.vb[g0];
+            f0 = F[g0];
             w0 = m.wbar[g0];
         }
         if (h1) {
@@ -1166,6 +1167,7 @@ __global__ void __launch_bounds__(kBndThreads, 6)
             v1 = V[g1];
             xb1 = m.xb[g1];
             vb1 = m.vb[g1];
+            f1 = F[g1];
             w1 = m.wbar[g1];
         }
         if (kChecked) {
@@ -1177,8 +1179,8 @@ __global__ void __launch_bounds__(kBndThreads, 6)
         float4 a0, a1;
         partial_sums2(m.partials, k0, e0 - k0, k1, e1 - k1, a0, a1);
         const float3 z = make_float3(0.f, 0.f, 0.f);
-        if (h0) node_adjoint(m, g0, x0, v0, xb0, vb0, xyz(a0), a0.w, w0, z);
-        if (h1) node_adjoint(m, g1, x1, v1, xb1, vb1, xyz(a1), a1.w, w1, z);
+        if (h0) node_adjoint(m, g0, x0, v0, xb0, vb0, xyz(a0), xyz(f0), w0, z);
+        if (h1) node_adjoint(m, g1, x1, v1, xb1, vb1, xyz(a1), xyz(f1), w1, z);
     }
     pdl_done();
 }

@@ -643,6 +643,7 @@ gs_status gs_mesh::refresh_rt() {
     MeshRT& r = rt;
     r.st_x = (float4*)st.p;
     r.st_v = st.p ? (float4*)st.p + (size_t)n_bufs * n_pad : nullptr;
+    r.st_f = st.p ? (float4*)st.p + 2 * (size_t)n_bufs * n_pad : nullptr;
     r.buf_stride = n_pad;
     r.xb = (float4*)xb.p;
     r.vb = (float4*)vb.p;
@@ -658,7 +659,7 @@ gs_status gs_mesh::refresh_rt() {
 gs_status gs_mesh::ensure_buffers(int n, cudaStream_t s) {
     if (n <= n_bufs && st.p) return GS_OK;
     Buf nb;
-    GS_TRY(nb.alloc(ctx, (size_t)2 * n * n_pad * sizeof(float4), s));
+    GS_TRY(nb.alloc(ctx, (size_t)3 * n * n_pad * sizeof(float4), s));  // x, v, element forces
     if (st.p) {
         GS_CUDA(cudaMemcpyAsync(nb.p, st.p, (size_t)n_pad * sizeof(float4), cudaMemcpyDeviceToDevice, s));
         GS_CUDA(cudaMemcpyAsync((float4*)nb.p + (size_t)n * n_pad, (float4*)st.p + (size_t)n_bufs * n_pad,
@@ -1356,7 +1357,10 @@ gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std:
         }
         GS_TRY(sync_rt(s));
         launch_copy_state(launch, s);
-        GS_TRY(run(0, steps - 1, s));
+        // all the segment's steps: the reverse steps read the states 0..n-1
+        // and the element forces at each, which the forward step from that
+        // state writes (the state after the last step is not read)
+        GS_TRY(run(0, steps, s));
         for (gs_mesh* m : meshes) {
             m->rt.st_a = sg * K + steps - 1;  // reverse: tick t is step sg K + steps - 1 - t
             m->rt.st_b = -1;

@@ -88,7 +88,7 @@ size_t estimate_bytes(const gs_mesh_desc& d, int S, int K) {
     const size_t N = d.n_nodes, E = d.n_elems, B = d.kind == GS_CLOTH ? d.n_hinges : 0;
     const int n_ck = std::max(1, (S + K - 1) / K);
     const size_t bufs = 2 + n_ck + K;
-    return E * 200 + B * 80 + N * (32 * bufs + 160) + ((size_t)1 << 20);
+    return E * 200 + B * 80 + N * (48 * bufs + 160) + ((size_t)1 << 20);
 }
 
 }  // namespace
@@ -163,9 +163,11 @@ gs_status gs_server::enter_phase(Query* q) {
         r.ck_tick = (q->chunk + 1 < q->n_ck) ? q->t0 + q->steps - 1 : -1;
         r.ck_buf = 2 + q->chunk;
     } else if (q->phase == P_REC) {
-        // a segment of n steps needs its states 0..n-1: n - 1 forward steps
+        // a segment of n steps needs its states 0..n-1 and the element forces
+        // at each of them, which the forward step from that state writes: n
+        // forward steps
         q->seg_steps = std::min(q->K, q->S - q->chunk * q->K);
-        q->steps = q->seg_steps - 1;
+        q->steps = q->seg_steps;
         r.active = ACT_FWD;
         r.cp_src = 1 + q->chunk;
         r.cp_dst = seg0;
