@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 # Algorithmic bytes per element-step (reads + writes the method must do):
 # forward: element stream 64 B (4 node ids, Dm^-1, V, mu, lambda) + node
 # traffic 52 B per node (x, v, w read; x, v written) x N/E; adjoint: 64 B +
-# 88 B per node (x, v read; x_bar, v_bar read + written; FP64 w_bar r/w) x N/E.
+# 88 B per node (x, v read; x_bar, v_hat read + written; FP64 w_bar r/w) x N/E.
 FWD_NODE_B, ADJ_NODE_B, ELEM_B = 52.0, 88.0, 64.0
 
 

@@ -382,8 +382,9 @@ GS_API gs_status gs_mesh_check(gs_mesh* mesh, int reset, void* stream);
 GS_API gs_status gs_step(gs_mesh* mesh, float dt, int n_steps, void* stream);
 
 /* Differentiable rollout: n_steps steps from the current state, keeping a
- * checkpoint of (x, v) every K steps (K = 0: chosen by the library under the
- * context budget, about sqrt(n_steps)).  With target (N x 3, caller order,
+ * checkpoint of (x, v) every K steps (K = 0: ceil(sqrt(n_steps)); K = 1
+ * keeps every state and the element force at each, 48 B per node and step,
+ * and the adjoint then recomputes nothing).  With target (N x 3, caller order,
  * nullable) the FP64 loss L = sum_i |x_i(S) - x*_i|^2 is written to *loss_out
  * (DEVICE or HOST per mem_space; nullable).  The current state advances to
  * step S.  Enables one later gs_adjoint. */

@@ -1283,9 +1283,10 @@ gs_status LaunchSet::rollout(const std::vector<float>& dts, int S, int K, const 
 
 // discrete adjoint over the whole rollout: per segment (last first) restore
 // the checkpoint, recompute and store the segment's states, then run the
-// reverse steps (App. B).  A segment of n steps needs its states 0..n-1, so
-// n - 1 forward steps are recomputed; with every state kept (K = 1) the
-// reverse steps read the stored states directly.
+// reverse steps (App. B).  A segment of n steps needs its states 0..n-1 and
+// the element force at each, which the forward step from that state stores,
+// so all n forward steps are recomputed; with every state kept (K = 1) the
+// reverse steps read the stored states and forces directly.
 gs_status LaunchSet::adjoint(const std::vector<const float*>& seed_x, const std::vector<const float*>& seed_v,
                              const std::vector<gs_grads>& grads, int keep, cudaStream_t s) {
     NvtxRange range("gs adjoint");
