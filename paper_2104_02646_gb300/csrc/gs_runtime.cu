@@ -4,11 +4,13 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
 #include <memory>
+#include <new>
 #include <numeric>
 #include <string>
 #include <system_error>
@@ -481,7 +483,10 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
     // 7. each patch's CSR rows ordered against bank conflicts (patches in
     // parallel: they are independent), then the topology blocks
     {
-        auto order_patches = [&](int p0, int p1) {
+        // a worker that fails (host memory) records it; the pass then fails as
+        // a whole once every thread has been joined
+        std::atomic<bool> failed{false};
+        auto order_range = [&](int p0, int p1) {
             std::vector<int> fill;
             for (int p = p0; p < p1; ++p) {
                 const PatchDesc& q = T.patches[p];
@@ -499,22 +504,31 @@ static gs_status build_topology(const gs_mesh_desc& d, int pe, Topology& T) {
                 order_rows_for_banks(sl, rc.data(), fill.data(), n_loc, zero);
             }
         };
+        auto order_patches = [&](int p0, int p1) {
+            try {
+                order_range(p0, p1);
+            } catch (...) {
+                failed = true;
+            }
+        };
         const int n_thr = std::max(1, std::min({(int)std::thread::hardware_concurrency(), 16, P / 256}));
         // patches [0, done) are handed to threads; if a thread cannot be
         // started, this thread orders the rest itself
         int done = 0;
         std::vector<std::thread> pool;
+        pool.reserve(n_thr);
         for (int t = 1; t < n_thr; ++t) {
             const int p0 = (int)((long long)P * (t - 1) / n_thr), p1 = (int)((long long)P * t / n_thr);
             try {
                 pool.emplace_back(order_patches, p0, p1);
-            } catch (const std::system_error&) {
+            } catch (...) {  // std::system_error: no thread could be started
                 break;
             }
             done = p1;
         }
         order_patches(done, P);
         for (auto& th : pool) th.join();
+        if (failed) throw std::bad_alloc();
     }
     // per patch topology blocks for the one-copy staging
     auto append = [&](const void* src, size_t bytes) {
@@ -704,9 +718,22 @@ extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_me
     return gs::mesh_create(ctx, desc, 0, out);
 }
 
+static gs_status mesh_create_impl(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s, gs_mesh** out);
+
 // Builds a mesh with all its uploads and set-up kernels on stream s and waits
-// for them; the mesh is ready for use on any stream when this returns.
+// for them; the mesh is ready for use on any stream when this returns.  The
+// host-side build (ordering, patches, topology) allocates host memory: a
+// failed allocation returns GS_ENOMEM (what was allocated is released) and
+// never reaches the C caller, or a server's builder thread, as an exception.
 gs_status gs::mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s, gs_mesh** out) {
+    try {
+        return mesh_create_impl(ctx, desc, s, out);
+    } catch (const std::bad_alloc&) {
+        return set_error(GS_ENOMEM, "host allocation failed while building the mesh");
+    }
+}
+
+static gs_status mesh_create_impl(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s, gs_mesh** out) {
     GS_CUDA(cudaSetDevice(ctx->device));
     const gs_mesh_desc& d = *desc;
     GS_TRY(validate(d));
