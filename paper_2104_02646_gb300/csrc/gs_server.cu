@@ -26,6 +26,7 @@
 #include <map>
 #include <string>
 #include <memory>
+#include <new>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -615,8 +616,7 @@ extern "C" void gs_server_destroy(gs_server* s) {
     delete s;
 }
 
-extern "C" gs_status gs_query_submit(gs_server* s, const gs_query* q, uint64_t* ticket) {
-    clear_error();
+static gs_status query_submit(gs_server* s, const gs_query* q, uint64_t* ticket) {
     if (!s || !q || !ticket) return set_error(GS_EINVAL, "null argument");
     const gs_mesh_desc& d = q->mesh;
     if (d.n_nodes <= 0 || d.n_elems <= 0 || !d.elems || !d.X || !d.mu || !d.lambda || !d.density || !q->target)
@@ -666,6 +666,17 @@ extern "C" gs_status gs_query_submit(gs_server* s, const gs_query* q, uint64_t* 
     s->pending.push_back(Q.release());
     s->cv.notify_all();
     return GS_OK;
+}
+
+// the query is deep-copied on the host: a failed allocation returns
+// GS_ENOMEM rather than reaching the C caller as an exception
+extern "C" gs_status gs_query_submit(gs_server* s, const gs_query* q, uint64_t* ticket) {
+    clear_error();
+    try {
+        return query_submit(s, q, ticket);
+    } catch (const std::bad_alloc&) {
+        return set_error(GS_ENOMEM, "host allocation failed while copying the query");
+    }
 }
 
 extern "C" gs_status gs_query_poll(gs_server* s, uint64_t ticket, gs_result* out, int timeout_ms) {
