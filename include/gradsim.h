@@ -69,6 +69,7 @@ enum {
     GS_ENOTFOUND = -8,   /* unknown ticket                                    */
     GS_EUNSUPPORTED = -9,
     GS_EINDEX = -10,     /* checked build: a table index was out of range     */
+    GS_EINTERNAL = -11,  /* unexpected host-side failure (message has the text) */
     GS_PENDING = 1,      /* query not finished yet                            */
     GS_WUNSTABLE = 2     /* dt above the explicit stability estimate (ran)    */
 };

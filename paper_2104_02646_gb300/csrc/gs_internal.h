@@ -19,7 +19,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <exception>
 #include <map>
+#include <new>
 #include <string>
 #include <utility>
 #include <vector>
@@ -218,6 +220,20 @@ void launch_finalize_grads(const Launch& L, double* mbar, const gs_grads& g, siz
 gs_status set_error(gs_status s, const std::string& msg);
 gs_status cuda_error(cudaError_t e, const char* what);
 void clear_error();
+
+// Closes the function-try-block of every extern "C" entry point that returns
+// a status, so that no C++ exception crosses the C ABI: a failed host
+// allocation becomes GS_ENOMEM, anything else GS_EINTERNAL with its text.
+#define GS_ABI_CATCH                                                                       \
+    catch (const std::bad_alloc&) {                                                        \
+        return ::gs::set_error(GS_ENOMEM, "host allocation failed");                       \
+    }                                                                                      \
+    catch (const std::exception& _x) {                                                     \
+        return ::gs::set_error(GS_EINTERNAL, std::string("host exception: ") + _x.what()); \
+    }                                                                                      \
+    catch (...) {                                                                          \
+        return ::gs::set_error(GS_EINTERNAL, "unknown host exception");                    \
+    }
 
 #define GS_CUDA(call)                                              \
     do {                                                           \

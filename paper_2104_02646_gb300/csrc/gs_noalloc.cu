@@ -93,7 +93,7 @@ __global__ void k_noalloc_finalize(const double* __restrict__ partials, int nblo
 using namespace gs;
 
 extern "C" gs_status gs_loss_noalloc(const float* x, const float* target, int n_nodes, double* loss_out,
-                                     float* dL_dx, void* stream) {
+                                     float* dL_dx, void* stream) try {
     clear_error();
     if (!x || !target || !loss_out) return set_error(GS_EINVAL, "gs_loss_noalloc: x, target and loss_out are required");
     if (n_nodes < 0) return set_error(GS_EINVAL, "gs_loss_noalloc: n_nodes must be >= 0");
@@ -109,4 +109,4 @@ extern "C" gs_status gs_loss_noalloc(const float* x, const float* target, int n_
     k_noalloc_finalize<<<1, 32, 0, s>>>(scratch, nblocks, loss_out);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
-}
+} GS_ABI_CATCH

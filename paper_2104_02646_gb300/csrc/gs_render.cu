@@ -572,7 +572,7 @@ static void set_camera(gs_raster* r, const gs_camera& c) {
     r->cam.H = c.height;
 }
 
-extern "C" gs_status gs_raster_create(gs_ctx* ctx, const gs_raster_desc* d, gs_raster** out) {
+extern "C" gs_status gs_raster_create(gs_ctx* ctx, const gs_raster_desc* d, gs_raster** out) try {
     gs::clear_error();
     if (!ctx || !d || !out) return gs::set_error(GS_EINVAL, "null argument");
     *out = nullptr;
@@ -651,7 +651,7 @@ extern "C" gs_status gs_raster_create(gs_ctx* ctx, const gs_raster_desc* d, gs_r
     }
     *out = r;
     return GS_OK;
-}
+} GS_ABI_CATCH
 
 extern "C" void gs_raster_destroy(gs_raster* r) {
     if (!r) return;
@@ -659,7 +659,7 @@ extern "C" void gs_raster_destroy(gs_raster* r) {
     delete r;
 }
 
-extern "C" gs_status gs_raster_set_camera(gs_raster* r, const gs_camera* c) {
+extern "C" gs_status gs_raster_set_camera(gs_raster* r, const gs_camera* c) try {
     gs::clear_error();
     if (!r || !c) return gs::set_error(GS_EINVAL, "null argument");
     if (c->width != r->cam.W || c->height != r->cam.H)
@@ -668,9 +668,9 @@ extern "C" gs_status gs_raster_set_camera(gs_raster* r, const gs_camera* c) {
     set_camera(r, *c);
     r->have_forward = false;
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_raster_forward(gs_raster* r, const float* x, const float* colours, float* image, void* stream) {
+extern "C" gs_status gs_raster_forward(gs_raster* r, const float* x, const float* colours, float* image, void* stream) try {
     gs::clear_error();
     if (!r || !x || !colours || !image) return gs::set_error(GS_EINVAL, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
@@ -696,10 +696,10 @@ extern "C" gs_status gs_raster_forward(gs_raster* r, const float* x, const float
     GS_CUDA(cudaGetLastError());
     r->have_forward = true;
     return GS_OK;
-}
+} GS_ABI_CATCH
 
 extern "C" gs_status gs_raster_backward(gs_raster* r, const float* dL_dimage, float* dL_dx, float* dL_dcolours,
-                                        void* stream) {
+                                        void* stream) try {
     gs::clear_error();
     if (!r || !dL_dimage) return gs::set_error(GS_EINVAL, "null argument");
     if (!r->have_forward) return gs::set_error(GS_ESTATE, "gs_raster_backward needs a gs_raster_forward first");
@@ -716,4 +716,4 @@ extern "C" gs_status gs_raster_backward(gs_raster* r, const float* dL_dimage, fl
                                                        r->N, dL_dx, dL_dcolours);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
-}
+} GS_ABI_CATCH

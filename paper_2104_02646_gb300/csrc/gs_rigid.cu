@@ -584,7 +584,7 @@ static gs_status check_params(int nb, const float* mass, const float* inertia, c
     return GS_OK;
 }
 
-extern "C" gs_status gs_rigid_create(gs_ctx* ctx, const gs_rigid_desc* d, gs_rigid** out) {
+extern "C" gs_status gs_rigid_create(gs_ctx* ctx, const gs_rigid_desc* d, gs_rigid** out) try {
     gs::clear_error();
     if (!ctx || !d || !out) return gs::set_error(GS_EINVAL, "null argument");
     *out = nullptr;
@@ -648,7 +648,7 @@ extern "C" gs_status gs_rigid_create(gs_ctx* ctx, const gs_rigid_desc* d, gs_rig
     }
     *out = r;
     return GS_OK;
-}
+} GS_ABI_CATCH
 
 extern "C" void gs_rigid_destroy(gs_rigid* r) {
     if (!r) return;
@@ -657,7 +657,7 @@ extern "C" void gs_rigid_destroy(gs_rigid* r) {
 }
 
 extern "C" gs_status gs_rigid_set_params(gs_rigid* r, const float* mass, const float* inertia, const float* contact,
-                                         void* stream) {
+                                         void* stream) try {
     gs::clear_error();
     if (!r) return gs::set_error(GS_EINVAL, "null body set");
     GS_TRY(check_params(r->nb, mass, inertia, contact));
@@ -675,9 +675,9 @@ extern "C" gs_status gs_rigid_set_params(gs_rigid* r, const float* mass, const f
     GS_CUDA(cudaMemcpyAsync(r->params.p, params.data(), 4 * params.size(), cudaMemcpyHostToDevice, s));
     GS_CUDA(cudaStreamSynchronize(s));
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_rigid_rollout(gs_rigid* r, float dt, int S, const float* state0, float* stateS, void* stream) {
+extern "C" gs_status gs_rigid_rollout(gs_rigid* r, float dt, int S, const float* state0, float* stateS, void* stream) try {
     gs::clear_error();
     if (!r || !state0) return gs::set_error(GS_EINVAL, "null argument");
     if (S < 0 || !(dt > 0.f) || !std::isfinite(dt)) return gs::set_error(GS_EINVAL, "need S >= 0 and dt > 0");
@@ -692,9 +692,9 @@ extern "C" gs_status gs_rigid_rollout(gs_rigid* r, float dt, int S, const float*
     r->S = S;
     r->dt = dt;
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_rigid_adjoint(gs_rigid* r, const float* dL_dstateS, gs_rigid_grads* g, void* stream) {
+extern "C" gs_status gs_rigid_adjoint(gs_rigid* r, const float* dL_dstateS, gs_rigid_grads* g, void* stream) try {
     gs::clear_error();
     if (!r || !g) return gs::set_error(GS_EINVAL, "null argument");
     if (r->S < 0) return gs::set_error(GS_ESTATE, "gs_rigid_adjoint needs a gs_rigid_rollout first");
@@ -706,9 +706,9 @@ extern "C" gs_status gs_rigid_adjoint(gs_rigid* r, const float* dL_dstateS, gs_r
                                                          (const float*)r->traj.p, r->dt, r->S, dL_dstateS, o);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_rigid_points(gs_rigid* r, const float* state, float* points, void* stream) {
+extern "C" gs_status gs_rigid_points(gs_rigid* r, const float* state, float* points, void* stream) try {
     gs::clear_error();
     if (!r || !state || !points) return gs::set_error(GS_EINVAL, "null argument");
     if (r->np > 0)
@@ -716,10 +716,10 @@ extern "C" gs_status gs_rigid_points(gs_rigid* r, const float* state, float* poi
             (const int*)r->owner.p, (const float*)r->pts.p, r->np, state, points);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
-}
+} GS_ABI_CATCH
 
 extern "C" gs_status gs_rigid_points_backward(gs_rigid* r, const float* state, const float* dL_dpoints,
-                                              float* dL_dstate, void* stream) {
+                                              float* dL_dstate, void* stream) try {
     gs::clear_error();
     if (!r || !state || !dL_dpoints || !dL_dstate) return gs::set_error(GS_EINVAL, "null argument");
     const int grid = (r->nb + kWarpsPerBlock - 1) / kWarpsPerBlock;
@@ -727,9 +727,9 @@ extern "C" gs_status gs_rigid_points_backward(gs_rigid* r, const float* state, c
         (const int*)r->pbeg.p, (const float*)r->pts.p, r->nb, state, dL_dpoints, dL_dstate);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_rigid_check(gs_rigid* r, int reset, void* stream) {
+extern "C" gs_status gs_rigid_check(gs_rigid* r, int reset, void* stream) try {
     gs::clear_error();
     if (!r) return gs::set_error(GS_EINVAL, "null body set");
     int st = 0;
@@ -738,4 +738,4 @@ extern "C" gs_status gs_rigid_check(gs_rigid* r, int reset, void* stream) {
     GS_CUDA(cudaStreamSynchronize(s));
     if (reset) GS_CUDA(cudaMemsetAsync(r->status.p, 0, sizeof(int), s));
     return (st & 1) ? GS_ENONFINITE : GS_OK;
-}
+} GS_ABI_CATCH

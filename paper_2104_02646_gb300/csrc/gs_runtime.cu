@@ -711,12 +711,12 @@ gs_mesh::~gs_mesh() {
     cudaStreamSynchronize(s);
 }
 
-extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_mesh** out) {
+extern "C" gs_status gs_mesh_create(gs_ctx* ctx, const gs_mesh_desc* desc, gs_mesh** out) try {
     clear_error();
     if (!ctx || !desc || !out) return set_error(GS_EINVAL, "null argument");
     *out = nullptr;
     return gs::mesh_create(ctx, desc, 0, out);
-}
+} GS_ABI_CATCH
 
 static gs_status mesh_create_impl(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStream_t s, gs_mesh** out);
 
@@ -937,11 +937,11 @@ gs_status gs_mesh::run_setup(int geometry, cudaStream_t s) {
 
 extern "C" void gs_mesh_destroy(gs_mesh* m) { delete m; }
 
-extern "C" gs_status gs_mesh_info_get(const gs_mesh* m, gs_mesh_info* out) {
+extern "C" gs_status gs_mesh_info_get(const gs_mesh* m, gs_mesh_info* out) try {
     if (!m || !out) return set_error(GS_EINVAL, "null argument");
     *out = m->info;
     return GS_OK;
-}
+} GS_ABI_CATCH
 
 // copy a caller buffer to a device scratch when it lives on the host
 static gs_status stage_in(gs_ctx* ctx, Buf& tmp, const float* src, size_t n, int mem, cudaStream_t s,
@@ -961,7 +961,7 @@ static gs_status stage_in(gs_ctx* ctx, Buf& tmp, const float* src, size_t n, int
 }
 
 extern "C" gs_status gs_mesh_set_params(gs_mesh* m, const float* mu, const float* lambda, const float* density,
-                                        const float* act, const float* kb, int mem, void* stream) {
+                                        const float* act, const float* kb, int mem, void* stream) try {
     clear_error();
     if (!m) return set_error(GS_EINVAL, "null mesh");
     cudaStream_t s = (cudaStream_t)stream;
@@ -984,9 +984,9 @@ extern "C" gs_status gs_mesh_set_params(gs_mesh* m, const float* mu, const float
     GS_CUDA(cudaGetLastError());
     for (Buf* b : {&t1, &t2, &t3, &t4, &t5}) b->release(s);
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_mesh_set_state(gs_mesh* m, const float* x, const float* v, int mem, void* stream) {
+extern "C" gs_status gs_mesh_set_state(gs_mesh* m, const float* x, const float* v, int mem, void* stream) try {
     clear_error();
     if (!m) return set_error(GS_EINVAL, "null mesh");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1002,9 +1002,9 @@ extern "C" gs_status gs_mesh_set_state(gs_mesh* m, const float* x, const float* 
     t2.release(s);
     m->ro.valid = false;
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_mesh_reset(gs_mesh* m, void* stream) {
+extern "C" gs_status gs_mesh_reset(gs_mesh* m, void* stream) try {
     clear_error();
     if (!m) return set_error(GS_EINVAL, "null mesh");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1013,9 +1013,9 @@ extern "C" gs_status gs_mesh_reset(gs_mesh* m, void* stream) {
     GS_CUDA(cudaGetLastError());
     m->ro.valid = false;
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_mesh_get_state(gs_mesh* m, float* x, float* v, int mem, void* stream) {
+extern "C" gs_status gs_mesh_get_state(gs_mesh* m, float* x, float* v, int mem, void* stream) try {
     clear_error();
     if (!m) return set_error(GS_EINVAL, "null mesh");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1034,9 +1034,9 @@ extern "C" gs_status gs_mesh_get_state(gs_mesh* m, float* x, float* v, int mem, 
     GS_CUDA(cudaStreamSynchronize(s));
     t.release(s);
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_mesh_check(gs_mesh* m, int reset, void* stream) {
+extern "C" gs_status gs_mesh_check(gs_mesh* m, int reset, void* stream) try {
     clear_error();
     if (!m) return set_error(GS_EINVAL, "null mesh");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1048,14 +1048,14 @@ extern "C" gs_status gs_mesh_check(gs_mesh* m, int reset, void* stream) {
     if (st & 2) return set_error(GS_ETIMEOUT, "a bounded wait in a step kernel ran out; results are invalid");
     if (st & 1) return set_error(GS_ENONFINITE, "non-finite state");
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_selftest_bounded_wait(int iterations, int* status_out, void* stream) {
+extern "C" gs_status gs_selftest_bounded_wait(int iterations, int* status_out, void* stream) try {
     clear_error();
     if (!status_out || iterations < 1 || iterations > 1000000)
         return set_error(GS_EINVAL, "gs_selftest_bounded_wait: iterations in 1..1e6 and status_out required");
     return selftest_bounded_wait(iterations, status_out, (cudaStream_t)stream);
-}
+} GS_ABI_CATCH
 
 // ---------------------------------------------------------------------------
 // launch sets
@@ -1451,7 +1451,7 @@ namespace gs {
 const char* g_last_error_cstr() { return g_last_error.c_str(); }
 }  // namespace gs
 
-extern "C" gs_status gs_create(gs_ctx** out, int device, size_t budget, const gs_allocator* alloc) {
+extern "C" gs_status gs_create(gs_ctx** out, int device, size_t budget, const gs_allocator* alloc) try {
     clear_error();
     if (!out) return set_error(GS_EINVAL, "null argument");
     *out = nullptr;
@@ -1475,7 +1475,7 @@ extern "C" gs_status gs_create(gs_ctx** out, int device, size_t budget, const gs
     GS_CUDA(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
     *out = c.release();
     return GS_OK;
-}
+} GS_ABI_CATCH
 
 cudaEvent_t EventProf::get() {
     if (pool.empty()) {
@@ -1517,7 +1517,7 @@ EventProf::~EventProf() {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
 }
 
-extern "C" gs_status gs_profile(gs_ctx* c, int enable) {
+extern "C" gs_status gs_profile(gs_ctx* c, int enable) try {
     clear_error();
     if (!c) return set_error(GS_EINVAL, "null context");
     if (enable && !c->prof) c->prof = new EventProf();
@@ -1526,9 +1526,9 @@ extern "C" gs_status gs_profile(gs_ctx* c, int enable) {
         c->prof = nullptr;
     }
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_profile_read(gs_ctx* c, gs_kernel_time* out, int max, int* n_out) {
+extern "C" gs_status gs_profile_read(gs_ctx* c, gs_kernel_time* out, int max, int* n_out) try {
     clear_error();
     if (!c || !c->prof) return set_error(GS_ESTATE, "profiling is off");
     c->prof->collect();
@@ -1547,7 +1547,7 @@ extern "C" gs_status gs_profile_read(gs_ctx* c, gs_kernel_time* out, int max, in
     }
     if (n_out) *n_out = n;
     return GS_OK;
-}
+} GS_ABI_CATCH
 
 extern "C" void gs_destroy(gs_ctx* c) {
     if (!c) return;
@@ -1558,14 +1558,14 @@ extern "C" void gs_destroy(gs_ctx* c) {
 
 extern "C" size_t gs_ctx_bytes(const gs_ctx* c) { return c ? c->used.load() : (size_t)0; }
 
-extern "C" gs_status gs_set_graphs(gs_ctx* c, int enable) {
+extern "C" gs_status gs_set_graphs(gs_ctx* c, int enable) try {
     if (!c) return set_error(GS_EINVAL, "null context");
     c->graphs = enable != 0;
     return GS_OK;
-}
+} GS_ABI_CATCH
 
 extern "C" gs_status gs_mesh_set_act_seq(gs_mesh* m, const float* act, const float* hact, int n_steps, int mem,
-                                         void* stream) {
+                                         void* stream) try {
     clear_error();
     if (!m) return set_error(GS_EINVAL, "null mesh");
     if (n_steps < 0) return set_error(GS_EINVAL, "n_steps must be >= 0");
@@ -1607,9 +1607,9 @@ extern "C" gs_status gs_mesh_set_act_seq(gs_mesh* m, const float* act, const flo
     tmp.release(s);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_mesh_set_air(gs_mesh* m, const gs_air* air, void* stream) {
+extern "C" gs_status gs_mesh_set_air(gs_mesh* m, const gs_air* air, void* stream) try {
     clear_error();
     if (!m) return set_error(GS_EINVAL, "null mesh");
     if (!air) {
@@ -1631,17 +1631,17 @@ extern "C" gs_status gs_mesh_set_air(gs_mesh* m, const gs_air* air, void* stream
     m->rt.wz = air->wind[2];
     m->rt.air_on = (air->k_drag > 0.f || air->k_lift > 0.f) ? 1 : 0;
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_step(gs_mesh* m, float dt, int n, void* stream) {
+extern "C" gs_status gs_step(gs_mesh* m, float dt, int n, void* stream) try {
     clear_error();
     if (!m) return set_error(GS_EINVAL, "null mesh");
     if (n < 0) return set_error(GS_EINVAL, "n_steps must be >= 0");
     return m->self->step(std::vector<float>{dt}, n, (cudaStream_t)stream);
-}
+} GS_ABI_CATCH
 
 extern "C" gs_status gs_rollout(gs_mesh* m, float dt, int S, int K, const float* target, double* loss_out, int mem,
-                                void* stream) {
+                                void* stream) try {
     clear_error();
     if (!m) return set_error(GS_EINVAL, "null mesh");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1667,10 +1667,10 @@ extern "C" gs_status gs_rollout(gs_mesh* m, float dt, int S, int K, const float*
     tt.release(s);
     tl.release(s);
     return st;
-}
+} GS_ABI_CATCH
 
 extern "C" gs_status gs_adjoint(gs_mesh* m, const float* dLdx, const float* dLdv, const gs_grads* grads, int mem,
-                                int keep, void* stream) {
+                                int keep, void* stream) try {
     clear_error();
     if (!m) return set_error(GS_EINVAL, "null mesh");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1731,7 +1731,7 @@ extern "C" gs_status gs_adjoint(gs_mesh* m, const float* dLdx, const float* dLdv
     t1.release(s);
     t2.release(s);
     return GS_OK;
-}
+} GS_ABI_CATCH
 
 // ---------------------------------------------------------------------------
 // batches
@@ -1742,7 +1742,7 @@ struct gs_batch {
     std::unique_ptr<LaunchSet> ls;
 };
 
-extern "C" gs_status gs_batch_create(gs_ctx* ctx, gs_mesh* const* meshes, int n, gs_batch** out) {
+extern "C" gs_status gs_batch_create(gs_ctx* ctx, gs_mesh* const* meshes, int n, gs_batch** out) try {
     clear_error();
     if (!ctx || !meshes || n <= 0 || !out) return set_error(GS_EINVAL, "bad batch arguments");
     *out = nullptr;
@@ -1756,27 +1756,27 @@ extern "C" gs_status gs_batch_create(gs_ctx* ctx, gs_mesh* const* meshes, int n,
     GS_CUDA(cudaStreamSynchronize(0));
     *out = b.release();
     return GS_OK;
-}
+} GS_ABI_CATCH
 
 extern "C" void gs_batch_destroy(gs_batch* b) { delete b; }
 
-extern "C" gs_status gs_batch_step(gs_batch* b, const float* dt, int n, void* stream) {
+extern "C" gs_status gs_batch_step(gs_batch* b, const float* dt, int n, void* stream) try {
     clear_error();
     if (!b || !dt) return set_error(GS_EINVAL, "null argument");
     return b->ls->step(std::vector<float>(dt, dt + b->meshes.size()), n, (cudaStream_t)stream);
-}
+} GS_ABI_CATCH
 
 extern "C" gs_status gs_batch_rollout(gs_batch* b, const float* dt, int S, int K, const float* const* targets,
-                                      double* loss_out, void* stream) {
+                                      double* loss_out, void* stream) try {
     clear_error();
     if (!b || !dt) return set_error(GS_EINVAL, "null argument");
     std::vector<const float*> t(b->meshes.size(), nullptr);
     if (targets)
         for (size_t i = 0; i < t.size(); ++i) t[i] = targets[i];
     return b->ls->rollout(std::vector<float>(dt, dt + b->meshes.size()), S, K, t, loss_out, (cudaStream_t)stream);
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_batch_adjoint(gs_batch* b, const gs_grads* grads, void* stream) {
+extern "C" gs_status gs_batch_adjoint(gs_batch* b, const gs_grads* grads, void* stream) try {
     clear_error();
     if (!b) return set_error(GS_EINVAL, "null argument");
     const size_t n = b->meshes.size();
@@ -1785,4 +1785,4 @@ extern "C" gs_status gs_batch_adjoint(gs_batch* b, const gs_grads* grads, void* 
     if (grads)
         for (size_t i = 0; i < n; ++i) g[i] = grads[i];
     return b->ls->adjoint(z, z, g, 0, (cudaStream_t)stream);
-}
+} GS_ABI_CATCH

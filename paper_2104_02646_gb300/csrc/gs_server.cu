@@ -572,7 +572,7 @@ void gs_server::run() {
     free_events.clear();
 }
 
-extern "C" gs_status gs_server_create(gs_ctx* ctx, const gs_server_opts* opts, gs_server** out) {
+extern "C" gs_status gs_server_create(gs_ctx* ctx, const gs_server_opts* opts, gs_server** out) try {
     clear_error();
     if (!ctx || !out) return set_error(GS_EINVAL, "null argument");
     *out = nullptr;
@@ -583,11 +583,27 @@ extern "C" gs_status gs_server_create(gs_ctx* ctx, const gs_server_opts* opts, g
     GS_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     gs_server* raw = s.get();
     const int nb = s->opts.build_threads > 0 ? std::min(s->opts.build_threads, 64) : 4;
-    for (int i = 0; i < nb; ++i) s->builders.emplace_back([raw] { raw->build_loop(); });
-    s->worker = std::thread([raw] { raw->run(); });
+    try {
+        s->builders.reserve(nb);
+        for (int i = 0; i < nb; ++i) s->builders.emplace_back([raw] { raw->build_loop(); });
+        s->worker = std::thread([raw] { raw->run(); });
+    } catch (...) {  // a thread could not be started: stop and join the ones that were
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stop = true;
+        }
+        s->cv.notify_all();
+        s->cv_build.notify_all();
+        for (std::thread& t : s->builders)
+            if (t.joinable()) t.join();
+        if (s->worker.joinable()) s->worker.join();
+        cudaStreamDestroy(s->stream);
+        s->stream = nullptr;
+        return set_error(GS_ENOMEM, "could not start the server's threads");
+    }
     *out = s.release();
     return GS_OK;
-}
+} GS_ABI_CATCH
 
 extern "C" void gs_server_destroy(gs_server* s) {
     if (!s) return;
@@ -668,18 +684,13 @@ static gs_status query_submit(gs_server* s, const gs_query* q, uint64_t* ticket)
     return GS_OK;
 }
 
-// the query is deep-copied on the host: a failed allocation returns
-// GS_ENOMEM rather than reaching the C caller as an exception
-extern "C" gs_status gs_query_submit(gs_server* s, const gs_query* q, uint64_t* ticket) {
+// the query is deep-copied on the host (a failed allocation: GS_ENOMEM)
+extern "C" gs_status gs_query_submit(gs_server* s, const gs_query* q, uint64_t* ticket) try {
     clear_error();
-    try {
-        return query_submit(s, q, ticket);
-    } catch (const std::bad_alloc&) {
-        return set_error(GS_ENOMEM, "host allocation failed while copying the query");
-    }
-}
+    return query_submit(s, q, ticket);
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_query_poll(gs_server* s, uint64_t ticket, gs_result* out, int timeout_ms) {
+extern "C" gs_status gs_query_poll(gs_server* s, uint64_t ticket, gs_result* out, int timeout_ms) try {
     clear_error();
     if (!s) return set_error(GS_EINVAL, "null server");
     std::unique_lock<std::mutex> lk(s->mu);
@@ -700,9 +711,9 @@ extern "C" gs_status gs_query_poll(gs_server* s, uint64_t ticket, gs_result* out
     if (st == GS_ENONFINITE) return set_error(GS_ENONFINITE, "query produced a non-finite state");
     if (st < 0) return set_error(st, "query failed");
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_query_cancel(gs_server* s, uint64_t ticket) {
+extern "C" gs_status gs_query_cancel(gs_server* s, uint64_t ticket) try {
     clear_error();
     if (!s) return set_error(GS_EINVAL, "null server");
     std::lock_guard<std::mutex> lk(s->mu);
@@ -711,9 +722,9 @@ extern "C" gs_status gs_query_cancel(gs_server* s, uint64_t ticket) {
     it->second->cancelled = true;
     s->cv.notify_all();
     return GS_OK;
-}
+} GS_ABI_CATCH
 
-extern "C" gs_status gs_server_stats_get(gs_server* s, gs_server_stats* out) {
+extern "C" gs_status gs_server_stats_get(gs_server* s, gs_server_stats* out) try {
     clear_error();
     if (!s || !out) return set_error(GS_EINVAL, "null argument");
     std::lock_guard<std::mutex> lk(s->mu);
@@ -743,7 +754,7 @@ extern "C" gs_status gs_server_stats_get(gs_server* s, gs_server_stats* out) {
     out->rebuilds = s->n_rebuilds;
     out->rt_syncs = s->n_syncs;
     return GS_OK;
-}
+} GS_ABI_CATCH
 
 extern "C" void gs_result_free(gs_result* r) {
     if (!r) return;

@@ -17,7 +17,7 @@ from . import _build
 
 GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ESTATE, GS_ENONFINITE = 0, -1, -2, -3, -4, -5
 GS_ETIMEOUT, GS_ECANCELLED, GS_ENOTFOUND, GS_EUNSUPPORTED = -6, -7, -8, -9
-GS_EINDEX = -10
+GS_EINDEX, GS_EINTERNAL = -10, -11
 GS_BUILD_CHECKED = 1
 GS_PENDING, GS_WUNSTABLE = 1, 2
 GS_NOALLOC_MAX_NODES = 4194304
