@@ -19,7 +19,8 @@
  * Conventions
  *   - Every call returns gs_status: 0 = GS_OK, < 0 error, > 0 warning.  On an
  *     error nothing was enqueued and gs_last_error() (thread-local) says why.
- *     No C++ exception crosses this boundary.
+ *     No C++ exception crosses this boundary: a failed host allocation
+ *     returns GS_ENOMEM, any other host-side exception GS_EINTERNAL.
  *   - Streams are passed as `void*` holding a cudaStream_t (0 = legacy
  *     default stream).  Work is enqueued asynchronously on that stream; device
  *     buffers handed in must stay valid until the stream reaches the work.
