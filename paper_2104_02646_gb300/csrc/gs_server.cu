@@ -103,6 +103,7 @@ struct gs_server {
     std::condition_variable cv;      // wakes the worker
     std::condition_variable cv_done; // wakes pollers
     bool stop = false;
+    bool failed = false;             // the worker stopped on a host-side exception
     uint64_t next_id = 1;
     std::deque<Query*> pending;
     std::deque<Query*> to_build;     // admitted, waiting for a builder thread
@@ -127,6 +128,7 @@ struct gs_server {
     uint64_t n_ticks = 0, n_rebuilds = 0, n_syncs = 0;
 
     void run();
+    void run_loop();
     void build_loop();
     void admit_locked();
     gs_status start_query(Query* q);
@@ -375,7 +377,21 @@ void gs_server::admit_locked() {
     }
 }
 
+// The worker.  Should it meet a host-side exception (a failed allocation
+// while staging results, say), it stops: queries not finished by then, and
+// later submissions, fail with GS_EINTERNAL (their memory is released by
+// gs_server_destroy), so no poller waits on a worker that is gone.
 void gs_server::run() {
+    try {
+        run_loop();
+    } catch (...) {
+        std::lock_guard<std::mutex> lk(mu);
+        failed = true;
+        cv_done.notify_all();
+    }
+}
+
+void gs_server::run_loop() {
     cudaSetDevice(ctx->device);
     while (true) {
         std::vector<Query*> fresh;
@@ -671,6 +687,7 @@ static gs_status query_submit(gs_server* s, const gs_query* q, uint64_t* ticket)
     Q->bytes = estimate_bytes(d, Q->S, Q->K);
     Q->t_submit = now_s();
     std::lock_guard<std::mutex> lk(s->mu);
+    if (s->failed) return set_error(GS_EINTERNAL, "the server's worker stopped on a host-side failure");
     s->submitted++;
     if (s->opts.hbm_budget_bytes && Q->bytes > s->opts.hbm_budget_bytes) {
         s->rejected++;
@@ -697,9 +714,12 @@ extern "C" gs_status gs_query_poll(gs_server* s, uint64_t ticket, gs_result* out
     auto it = s->all.find(ticket);
     if (it == s->all.end()) return set_error(GS_ENOTFOUND, "unknown ticket");
     Query* q = it->second;
-    if (!q->ready && timeout_ms > 0)
-        s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [q] { return q->ready; });
-    if (!q->ready) return timeout_ms > 0 ? GS_ETIMEOUT : GS_PENDING;
+    if (!q->ready && timeout_ms > 0 && !s->failed)
+        s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [s, q] { return q->ready || s->failed; });
+    if (!q->ready) {
+        if (s->failed) return set_error(GS_EINTERNAL, "the server's worker stopped on a host-side failure");
+        return timeout_ms > 0 ? GS_ETIMEOUT : GS_PENDING;
+    }
     const gs_status st = q->res.status;
     if (out) {
         *out = q->res;  // ownership of the host arrays passes to the caller
