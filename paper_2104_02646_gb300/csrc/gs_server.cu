@@ -225,7 +225,17 @@ void gs_server::build_loop() {
             building++;
         }
         const double t = now_s();
-        gs_status st = have_stream ? build_query(ctx, opts, q, bs) : set_error(GS_ECUDA, "builder stream");
+        gs_status st;
+        try {  // the query then fails with the status; the builder carries on
+            st = have_stream ? build_query(ctx, opts, q, bs) : set_error(GS_ECUDA, "builder stream");
+        } catch (const std::bad_alloc&) {
+            st = set_error(GS_ENOMEM, "host allocation failed while building the query");
+        } catch (const std::exception& x) {
+            st = set_error(GS_EINTERNAL, std::string("host exception while building the query: ") + x.what());
+        }
+        // a failed build may leave copies in flight on the builder's stream:
+        // they finish before the worker releases the query's buffers
+        if (st < 0 && have_stream) cudaStreamSynchronize(bs);
         const std::string err = st < 0 ? std::string(gs_last_error()) : std::string();
         {
             std::lock_guard<std::mutex> lk(mu);
