@@ -8,6 +8,7 @@ restatement of the paper's equations, App. A-C) for numpy inputs built by
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -61,9 +62,12 @@ _lib = None
 
 
 def lib():
+    """The compiled oracle.  GS_ORACLE_LIB, if set, names another build of
+    the same source to load instead (the tests' copies with a planted
+    mistake, which the pins must reject)."""
     global _lib
     if _lib is None:
-        L = C.CDLL(_build.build())
+        L = C.CDLL(os.environ.get("GS_ORACLE_LIB") or _build.build())
         L.orc_tet_rest.argtypes = [_dp, _dp, _dp]
         L.orc_tri_rest.argtypes = [_dp, _dp, _dp]
         L.orc_node_masses.argtypes = [C.POINTER(_Model), _dp]

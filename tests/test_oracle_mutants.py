@@ -1,0 +1,89 @@
+"""The oracle's pins reject an oracle with a planted mistake.
+
+Each case copies oracle/gs_oracle.cpp, plants one plausible mistake in the
+copy (a dropped term, a flipped sign, a transposed operand, a wrong index or
+factor), builds it, and runs the pins of tests/test_oracle_pins.py against that
+build (GS_ORACLE_LIB): at least one pin must fail.  An unchanged copy built the
+same way must pass them all, so a failure is the planted mistake's doing.  The
+committed oracle source is never modified.  CPU only."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "gs_oracle.cpp")
+HDR = os.path.join(ROOT, "oracle", "gs_oracle.h")
+
+# name: (text in the oracle, its replacement, occurrences replaced)
+MUTANTS = {
+    # App. A.1 stable neo-Hookean P: the mu F / (I_C + 1) term dropped from the tet force
+    "tet_P_term_dropped": ("const T a = mu * (1.0 - 1.0 / (Ic + 1.0));\n    const T b = lam * (J - alpha);\n    T P[3][3];",
+                           "const T a = mu;\n    const T b = lam * (J - alpha);\n    T P[3][3];", 1),
+    # H = -V P Dm^-T with Dm^-1 in place of its transpose
+    "tet_Dm_untransposed": ("P[r][0] * Dminv[3 * c] + P[r][1] * Dminv[3 * c + 1] + P[r][2] * Dminv[3 * c + 2]",
+                            "P[r][0] * Dminv[c] + P[r][1] * Dminv[3 + c] + P[r][2] * Dminv[6 + c]", 1),
+    # the rest-stable alpha = 1 + 3 mu / (4 lambda) with a wrong factor (energy and force alike)
+    "tet_alpha_factor": ("0.75 * mu / lam", "0.5 * mu / lam", 2),
+    # membrane dJ/df_0 = f_1 x n with the cross product's operands swapped (a sign)
+    "tri_dJ_sign": ("vcross(f1, n, dJ0);", "vcross(n, f1, dJ0);", 1),
+    # lumped mass: a quarter of each tet's mass per corner, here a third
+    "mass_lumping_factor": ("mass[m->tets[4 * e + c]] += tet_rho[e] * (r.tet_V[e] / 4.0);",
+                            "mass[m->tets[4 * e + c]] += tet_rho[e] * (r.tet_V[e] / 3.0);", 1),
+    # contact damping k_d dC/dt with dC/dt = -v.n: the sign flipped
+    "contact_damping_sign": ("const T fn = ke * C - kd * vn;", "const T fn = ke * C + kd * vn;", 1),
+    # stick friction -k_f v_s: the sign flipped
+    "friction_stick_sign": ("for (int k = 0; k < 3; ++k) f[k] -= kf * vs[k];",
+                            "for (int k = 0; k < 3; ++k) f[k] += kf * vs[k];", 1),
+    # Bridson bending sin(phi / 2 + alpha): the half angle lost
+    "bending_half_angle": ("fsin(0.5 * phi + act)", "fsin(phi + act)", 1),
+    # bending direction u_3 with a wrong edge end (index)
+    "bending_u3_index": ("f[6 + k] = s * (p14 * g1[k] + p24 * g2[k]);",
+                         "f[6 + k] = s * (p13 * g1[k] + p24 * g2[k]);", 1),
+    # semi-implicit Euler (App. B): x+ from the old velocity (explicit Euler)
+    "euler_old_velocity": (
+        "            v[3 * (size_t)i + k] = v[3 * (size_t)i + k] + dt * (w[i] * f[3 * (size_t)i + k] + (dyn ? m->gravity[k] : 0.0));\n"
+        "            x[3 * (size_t)i + k] = x[3 * (size_t)i + k] + dt * v[3 * (size_t)i + k];",
+        "            x[3 * (size_t)i + k] = x[3 * (size_t)i + k] + dt * v[3 * (size_t)i + k];\n"
+        "            v[3 * (size_t)i + k] = v[3 * (size_t)i + k] + dt * (w[i] * f[3 * (size_t)i + k] + (dyn ? m->gravity[k] : 0.0));",
+        1),
+    # gravity applied to kinematic (pinned) nodes too
+    "gravity_on_pinned": ("(dyn ? m->gravity[k] : 0.0)", "m->gravity[k]", 1),
+    # discrete adjoint (App. B): c_u = -dl/du+ - dt dl/dq+ without its dt term
+    "adjoint_dt_term_dropped": ("cu[i] = -lu[i] - dt * lq[i];", "cu[i] = -lu[i];", 1),
+}
+
+
+def _build(tmp_path, name, text=None, repl=None, count=0):
+    src = open(SRC).read()
+    if text is not None:
+        assert src.count(text) == count, (name, src.count(text))
+        src = src.replace(text, repl)
+    d = tmp_path / name
+    d.mkdir()
+    (d / "gs_oracle.cpp").write_text(src)
+    (d / "gs_oracle.h").write_text(open(HDR).read())
+    so = d / "liboracle.so"
+    subprocess.check_call(["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(so),
+                           str(d / "gs_oracle.cpp")])
+    return str(so)
+
+
+def _pins(lib_path):
+    env = dict(os.environ, GS_ORACLE_LIB=lib_path, OMP_NUM_THREADS="1")
+    cmd = [sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x", "-q",
+           "-p", "no:cacheprovider"]
+    return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+
+
+def test_unchanged_copy_passes_the_pins(tmp_path):
+    r = _pins(_build(tmp_path, "unchanged"))
+    assert r.returncode == 0, r.stdout[-3000:]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_fails_a_pin(tmp_path, name):
+    text, repl, count = MUTANTS[name]
+    r = _pins(_build(tmp_path, name, text, repl, count))
+    assert r.returncode == 1 and "failed" in r.stdout, (name, r.returncode, r.stdout[-3000:])
