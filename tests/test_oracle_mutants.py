@@ -2,10 +2,12 @@
 
 Each case copies oracle/gs_oracle.cpp, plants one plausible mistake in the
 copy (a dropped term, a flipped sign, a transposed operand, a wrong index or
-factor), builds it, and runs the pins of tests/test_oracle_pins.py against that
-build (GS_ORACLE_LIB): at least one pin must fail.  An unchanged copy built the
-same way must pass them all, so a failure is the planted mistake's doing.  The
-committed oracle source is never modified.  CPU only."""
+factor), builds it, and runs the pins of that part of the oracle (elements,
+contact, integration and adjoint: tests/test_oracle_pins.py; air, rigid bodies,
+actuation sequences: their own pin files) against that build (GS_ORACLE_LIB):
+at least one pin must fail.  An unchanged copy built the same way must pass all
+four pin files, so a failure is the planted mistake's doing.  The committed
+oracle source is never modified.  CPU only."""
 import os
 import subprocess
 import sys
@@ -53,6 +55,32 @@ MUTANTS = {
     # discrete adjoint (App. B): c_u = -dl/du+ - dt dl/dq+ without its dt term
     "adjoint_dt_term_dropped": ("cu[i] = -lu[i] - dt * lq[i];", "cu[i] = -lu[i];", 1),
 }
+# the same for the air model, the rigid-body step and the actuation sequence,
+# each against its own pins: name: (text, replacement, occurrences, pin file)
+MUTANTS_MORE = {
+    # flat-plate lift with its direction reversed
+    "air_lift_sign": ("F[k] = F[k] - c * (q * N[k] - s * vr[k]);", "F[k] = F[k] + c * (q * N[k] - s * vr[k]);", 1,
+                      "test_oracle_air.py"),
+    # the plate's velocity through the air: the wind added instead of subtracted
+    "air_wind_sign": ("vr[k] = (v[k] + v[3 + k] + v[6 + k]) / 3.0 - wind[k];",
+                      "vr[k] = (v[k] + v[3 + k] + v[6 + k]) / 3.0 + wind[k];", 1, "test_oracle_air.py"),
+    # a triangle's air force shared over its corners by halves instead of thirds
+    "air_corner_share": ("for (int k = 0; k < 3; ++k) f[3 * c + k] = F[k] / 3.0;",
+                         "for (int k = 0; k < 3; ++k) f[3 * c + k] = F[k] / 2.0;", 1, "test_oracle_air.py"),
+    # quaternion update r + dt/2 (0, omega) r with dt in place of dt/2
+    "rigid_quat_half_step": ("0.5 * dt *", "1.0 * dt *", 2, "test_oracle_rigid.py"),
+    # Newton-Euler: tau - omega x (I omega) with the gyroscopic term's sign flipped
+    "rigid_gyroscopic_sign": ("h[i] = tau[i] - wL[i];", "h[i] = tau[i] + wL[i];", 1, "test_oracle_rigid.py"),
+    # world inertia R I_b R^T taken as R^T I_b R
+    "rigid_inertia_transposed": ("acc += R[i][a] * Ib[a][c] * R[j][c];", "acc += R[a][i] * Ib[a][c] * R[c][j];", 1,
+                                 "test_oracle_rigid.py"),
+    # a contact point's moment d x f with the operands swapped (a sign)
+    "rigid_moment_sign": ("vcross(d, fc, td);", "vcross(fc, d, td);", 1, "test_oracle_rigid.py"),
+    # the row of the actuation sequence added at half weight
+    "act_seq_scale": ("ta[e] += tseq[(size_t)n * m->n_tets + e];", "ta[e] += 0.5 * tseq[(size_t)n * m->n_tets + e];",
+                      1, "test_oracle_actuation.py"),
+}
+PIN_FILES = ("test_oracle_pins.py", "test_oracle_air.py", "test_oracle_rigid.py", "test_oracle_actuation.py")
 
 
 def _build(tmp_path, name, text=None, repl=None, count=0):
@@ -70,15 +98,15 @@ def _build(tmp_path, name, text=None, repl=None, count=0):
     return str(so)
 
 
-def _pins(lib_path):
+def _pins(lib_path, files=("test_oracle_pins.py",)):
     env = dict(os.environ, GS_ORACLE_LIB=lib_path, OMP_NUM_THREADS="1")
-    cmd = [sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x", "-q",
+    cmd = [sys.executable, "-m", "pytest", *[os.path.join(ROOT, "tests", f) for f in files], "-x", "-q",
            "-p", "no:cacheprovider"]
     return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
 
 
 def test_unchanged_copy_passes_the_pins(tmp_path):
-    r = _pins(_build(tmp_path, "unchanged"))
+    r = _pins(_build(tmp_path, "unchanged"), PIN_FILES)
     assert r.returncode == 0, r.stdout[-3000:]
 
 
@@ -86,4 +114,11 @@ def test_unchanged_copy_passes_the_pins(tmp_path):
 def test_planted_mistake_fails_a_pin(tmp_path, name):
     text, repl, count = MUTANTS[name]
     r = _pins(_build(tmp_path, name, text, repl, count))
+    assert r.returncode == 1 and "failed" in r.stdout, (name, r.returncode, r.stdout[-3000:])
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_MORE))
+def test_planted_mistake_fails_its_own_pins(tmp_path, name):
+    text, repl, count, pins = MUTANTS_MORE[name]
+    r = _pins(_build(tmp_path, name, text, repl, count), (pins,))
     assert r.returncode == 1 and "failed" in r.stdout, (name, r.returncode, r.stdout[-3000:])
