@@ -11,6 +11,7 @@ oracle source is never modified.  CPU only."""
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -105,20 +106,95 @@ def _pins(lib_path, files=("test_oracle_pins.py",)):
     return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
 
 
-def test_unchanged_copy_passes_the_pins(tmp_path):
-    r = _pins(_build(tmp_path, "unchanged"), PIN_FILES)
-    assert r.returncode == 0, r.stdout[-3000:]
+
+
+# the renderer's oracle (plain PyTorch) against tests/test_oracle_render.py: a
+# mutated copy of oracle/render_oracle.py is registered as oracle.render_oracle
+# before the pins import it
+RENDER_SRC = os.path.join(ROOT, "oracle", "render_oracle.py")
+RENDER_MUTANTS = {
+    # coverage sigmoid(+-d^2 / sigma): inside and outside swapped
+    "render_coverage_sign": ("tv = torch.where(inside, d2, -d2) / spec.sigma",
+                             "tv = torch.where(inside, -d2, d2) / spec.sigma"),
+    # silhouette as the probabilistic union 1 - prod(1 - D): a clamped sum instead
+    "render_union_as_sum": ("A = 1.0 - torch.prod(q, dim=1)", "A = D.sum(dim=1).clamp(max=1.0)"),
+    # perspective-correct depth 1/z = sum w_k / z_k: z interpolated affinely instead
+    "render_affine_depth": ("iz = (wc / zs[None]).sum(-1)", "iz = 1.0 / (wc * zs[None]).sum(-1)"),
+    # barycentric weights with two corners' weights swapped (an index)
+    "render_barycentric_order": ("w = torch.stack([_cross2(pb, pc), _cross2(pc, pa), _cross2(pa, pb)], dim=-1)",
+                                 "w = torch.stack([_cross2(pc, pa), _cross2(pb, pc), _cross2(pa, pb)], dim=-1)"),
+    # world to camera with the rotation transposed
+    "render_rotation_transposed": ("xc = x @ R.T + t", "xc = x @ R + t"),
+    # normalised depth with nearer = smaller, so the farthest covering triangle wins
+    "render_depth_order": ("zh = (cam.z_far - zp) / (cam.z_far - cam.z_near)",
+                           "zh = (zp - cam.z_near) / (cam.z_far - cam.z_near)"),
+}
+
+_RENDER_BOOT = """
+import importlib.util, sys
+root, path, test = sys.argv[1:4]
+sys.path.insert(0, root)
+import oracle
+spec = importlib.util.spec_from_file_location("oracle.render_oracle", path)
+mod = importlib.util.module_from_spec(spec)
+sys.modules["oracle.render_oracle"] = mod
+spec.loader.exec_module(mod)
+oracle.render_oracle = mod
+import pytest
+sys.exit(pytest.main([test, "-x", "-q", "-p", "no:cacheprovider"]))
+"""
+
+
+def _render_pins(tmp_path, name, text=None, repl=None):
+    src = open(RENDER_SRC).read()
+    if text is not None:
+        assert src.count(text) == 1, name
+        src = src.replace(text, repl)
+    path = tmp_path / f"{name}.py"
+    path.write_text(src)
+    cmd = [sys.executable, "-c", _RENDER_BOOT, ROOT, str(path), os.path.join(ROOT, "tests", "test_oracle_render.py")]
+    return subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=900)
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """Every copy built and run against its pins, several at a time (each
+    run is its own process, one thread each)."""
+    base = tmp_path_factory.mktemp("mutants")
+    rbase = tmp_path_factory.mktemp("render_mutants")
+    jobs = {"unchanged": lambda: _pins(_build(base, "unchanged"), PIN_FILES),
+            "render:unchanged": lambda: _render_pins(rbase, "unchanged")}
+    for name, (text, repl, count) in MUTANTS.items():
+        jobs[name] = lambda n=name, t=text, r=repl, c=count: _pins(_build(base, n, t, r, c))
+    for name, (text, repl, count, pins) in MUTANTS_MORE.items():
+        jobs[name] = lambda n=name, t=text, r=repl, c=count, f=pins: _pins(_build(base, n, t, r, c), (f,))
+    for name, (text, repl) in RENDER_MUTANTS.items():
+        jobs["render:" + name] = lambda n=name, t=text, r=repl: _render_pins(rbase, n, t, r)
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        futures = {k: ex.submit(f) for k, f in jobs.items()}
+        return {k: f.result() for k, f in futures.items()}
+
+
+def _caught(r):
+    return r.returncode == 1 and "failed" in r.stdout
+
+
+def test_unchanged_copies_pass_the_pins(outcomes):
+    for k in ("unchanged", "render:unchanged"):
+        assert outcomes[k].returncode == 0, (k, outcomes[k].stdout[-3000:])
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_planted_mistake_fails_a_pin(tmp_path, name):
-    text, repl, count = MUTANTS[name]
-    r = _pins(_build(tmp_path, name, text, repl, count))
-    assert r.returncode == 1 and "failed" in r.stdout, (name, r.returncode, r.stdout[-3000:])
+def test_planted_mistake_fails_a_pin(outcomes, name):
+    assert _caught(outcomes[name]), (name, outcomes[name].returncode, outcomes[name].stdout[-3000:])
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS_MORE))
-def test_planted_mistake_fails_its_own_pins(tmp_path, name):
-    text, repl, count, pins = MUTANTS_MORE[name]
-    r = _pins(_build(tmp_path, name, text, repl, count), (pins,))
-    assert r.returncode == 1 and "failed" in r.stdout, (name, r.returncode, r.stdout[-3000:])
+def test_planted_mistake_fails_its_own_pins(outcomes, name):
+    assert _caught(outcomes[name]), (name, outcomes[name].returncode, outcomes[name].stdout[-3000:])
+
+
+@pytest.mark.parametrize("name", sorted(RENDER_MUTANTS))
+def test_planted_render_mistake_fails_a_pin(outcomes, name):
+    r = outcomes["render:" + name]
+    assert _caught(r), (name, r.returncode, r.stdout[-3000:])

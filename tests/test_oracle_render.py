@@ -9,7 +9,8 @@ on an integer triangle; area preservation of the soft edges; the value on an
 edge and at a known distance outside; the probabilistic union of coverages;
 the nearest triangle winning the depth softmax; exact reproduction of an
 affine colour field; perspective-correct depth against a ray-plane
-intersection; and the autograd gradients against central differences.
+intersection, both in the interpolated attributes and in the depth softmax's
+blend; and the autograd gradients against central differences.
 """
 import math
 
@@ -168,6 +169,45 @@ def test_depth_is_perspective_correct():
         d = cam.R.T @ dc
         depth = np.dot(n, X[0] - eye) / np.dot(n, d)  # camera depth of eye + s d is s (dc has unit z)
         assert abs(1.0 / img[j, i, 0] - depth) < 1e-6 * depth, (i, j, 1.0 / img[j, i, 0], depth)
+
+
+def test_depth_softmax_uses_perspective_correct_depth():
+    # a slanted triangle (red) over a fronto-parallel one (green) at a depth
+    # between its corners' depths; with sharp edges (coverage 1 - Q_MIN deep
+    # inside) each pixel's colour is the closed-form softmax over the two
+    # triangles' normalised depths, taken where the pixel's ray meets each
+    # plane.  Depth interpolated affinely in the screen would give a visibly
+    # different blend, which the last check shows.
+    cam = _cam(32, 32)
+    S = np.stack([_screen_to_world(cam, u, v, d) for (u, v, d) in [(2.0, 2.0, 1.0), (30.0, 3.0, 3.0), (16.0, 30.0, 2.0)]])
+    P, _, _ = _tri_scene(cam, [(-20.0, -20.0), (60.0, -20.0), (-20.0, 60.0)], 1.9)
+    red, green = np.tile([1.0, 0.0, 0.0], (3, 1)), np.tile([0.0, 1.0, 0.0], (3, 1))
+    spec = I.RenderSpec(sigma=1e-4, gamma=0.01, bg=(0.0, 0.0, 0.0))
+    img = R.render(np.vstack([S, P]), np.array([[0, 1, 2], [3, 4, 5]]), np.vstack([red, green]), cam, spec).numpy()
+    n = np.cross(S[1] - S[0], S[2] - S[0])
+    eye = -cam.R.T @ cam.t
+    uvS = np.array([(2.0, 2.0), (30.0, 3.0), (16.0, 30.0)])
+    zS = np.array([1.0, 3.0, 2.0])
+    D = 1.0 - R.Q_MIN
+    zh = lambda z: (cam.z_far - z) / (cam.z_far - cam.z_near)
+
+    def red_of(z_s):
+        a, b, e = np.exp(zh(z_s) / spec.gamma), np.exp(zh(1.9) / spec.gamma), np.exp(spec.eps / spec.gamma)
+        return D * a / (D * a + D * b + e)
+
+    for (i, j) in [(16, 12), (13, 9), (20, 13), (15, 18)]:
+        p = np.array([i + 0.5, j + 0.5])
+        # screen-space barycentrics of the pixel in the slanted triangle (inside, away from the edges)
+        T = np.array([[uvS[0, 0] - uvS[2, 0], uvS[1, 0] - uvS[2, 0]], [uvS[0, 1] - uvS[2, 1], uvS[1, 1] - uvS[2, 1]]])
+        l01 = np.linalg.solve(T, p - uvS[2])
+        w = np.array([l01[0], l01[1], 1.0 - l01.sum()])
+        assert (w > 0.05).all()
+        dc = np.array([(p[0] - cam.cx) / cam.fx, (p[1] - cam.cy) / cam.fy, 1.0])
+        z_ray = np.dot(n, S[0] - eye) / np.dot(n, cam.R.T @ dc)
+        assert abs(1.0 / np.dot(w, 1.0 / zS) - z_ray) < 1e-9 * z_ray  # the same depth, by screen barycentrics
+        np.testing.assert_allclose(img[j, i, 0], red_of(z_ray), rtol=0, atol=1e-9)
+        np.testing.assert_allclose(img[j, i, 1], 1.0 - red_of(z_ray) - (img[j, i, 2]), rtol=0, atol=1e-9)
+        assert abs(red_of(np.dot(w, zS)) - red_of(z_ray)) > 1e-2  # the affine depth's blend is far off
 
 
 def test_gradients_match_finite_differences():
