@@ -55,6 +55,29 @@ MUTANTS = {
     "gravity_on_pinned": ("(dyn ? m->gravity[k] : 0.0)", "m->gravity[k]", 1),
     # discrete adjoint (App. B): c_u = -dl/du+ - dt dl/dq+ without its dt term
     "adjoint_dt_term_dropped": ("cu[i] = -lu[i] - dt * lq[i];", "cu[i] = -lu[i];", 1),
+    # the sphere's contact normal pointing inwards
+    "sphere_normal_sign": ("T nn[3] = {d[0] / dist, d[1] / dist, d[2] / dist};",
+                           "T nn[3] = {-d[0] / dist, -d[1] / dist, -d[2] / dist};", 1),
+    # Coulomb slip friction mu |f_n| v_s / |v_s| without the normalisation
+    "slip_not_normalised": ("const T scale = muf * afn / vsl;", "const T scale = muf * afn;", 1),
+    # hinge actuation inside the half angle: sin((phi + a) / 2) for sin(phi / 2 + a)
+    "hinge_act_halved": ("fsin(0.5 * phi + act)", "fsin(0.5 * (phi + act))", 1),
+    # the membrane's rest-stable alpha = 1 + 2 mu / (3 lambda) with the tet's factor
+    "tri_alpha_factor": ("(2.0 / 3.0) * mu / lam", "0.75 * mu / lam", 2),
+    # cloth mass lumping: a third of each triangle's mass per corner, here a quarter
+    "cloth_mass_lumping": ("mass[m->tris[3 * t + c]] += tri_rho[t] * (r.tri_A[t] / 3.0);",
+                           "mass[m->tris[3 * t + c]] += tri_rho[t] * (r.tri_A[t] / 4.0);", 1),
+    # density gradient rho_bar_e = (V_e / 4) sum m_bar_i with a wrong share
+    "density_grad_factor": ("g->tet_rho[e] = s * (r.tet_V[e] / 4.0);", "g->tet_rho[e] = s * (r.tet_V[e] / 3.0);", 1),
+    # dL/dw_i += -dt c_u,i . f_i with its sign flipped
+    "adjoint_w_term_sign": ("w_b[i] += -dt * cu[3 * i + k] * f_n[3 * i + k];",
+                            "w_b[i] += dt * cu[3 * i + k] * f_n[3 * i + k];", 1),
+    # m_bar = -w^2 w_bar (d(1/m)/dm) with its sign flipped
+    "mass_grad_sign": ("m_b[i] = -w[i] * w[i] * w_b[i];", "m_b[i] = w[i] * w[i] * w_b[i];", 1),
+    # the loss seed dL/dx(S) = 2 (x - x*) without its factor 2
+    "loss_seed_factor": ("lq[i] = 2.0 * d;", "lq[i] = d;", 1),
+    # rest volume det(Dm) / 6 with a wrong factor
+    "tet_volume_factor": ("*V = det / 6.0;", "*V = det / 2.0;", 1),
 }
 # the same for the air model, the rigid-body step and the actuation sequence,
 # each against its own pins: name: (text, replacement, occurrences, pin file)
@@ -77,6 +100,12 @@ MUTANTS_MORE = {
                                  "test_oracle_rigid.py"),
     # a contact point's moment d x f with the operands swapped (a sign)
     "rigid_moment_sign": ("vcross(d, fc, td);", "vcross(fc, d, td);", 1, "test_oracle_rigid.py"),
+    # Newton: the contact force multiplied by the mass instead of divided
+    "rigid_force_times_mass": ("vo[i] = v[i] + dt * (sc->gravity[i] + F[i] / m);",
+                               "vo[i] = v[i] + dt * (sc->gravity[i] + F[i] * m);", 1, "test_oracle_rigid.py"),
+    # flat-plate lift without the area normalisation of N
+    "air_lift_area": ("const T c = k_lift * s / (fsqrt(A2) * fsqrt(q));", "const T c = k_lift * s / fsqrt(q);", 1,
+                      "test_oracle_air.py"),
     # the row of the actuation sequence added at half weight
     "act_seq_scale": ("ta[e] += tseq[(size_t)n * m->n_tets + e];", "ta[e] += 0.5 * tseq[(size_t)n * m->n_tets + e];",
                       1, "test_oracle_actuation.py"),

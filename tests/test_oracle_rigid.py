@@ -87,9 +87,11 @@ def test_torque_free_angular_momentum_converges():
 
 
 def test_resting_box_penetration():
-    # a 1 kg box settles flat on its 4 bottom corners: each carries m g / 4
+    # a 2.4 kg box settles flat on its 4 bottom corners: each carries m g / 4
+    # (a mass other than 1 kg, so that the closed form tells F / m from F m)
     ke = 2.0e4
-    b = I.box_body(size=(0.2, 0.2, 0.2), density=125.0, contact=(ke, 30.0, 100.0, 0.5), x0=(0.0, 0.1, 0.0))
+    b = I.box_body(size=(0.2, 0.2, 0.2), density=300.0, contact=(ke, 30.0, 100.0, 0.5), x0=(0.0, 0.1, 0.0))
+    assert abs(b.mass - 2.4) < 1e-12
     r = O.Rigid(b)
     sS = r.rollout(b.state0, 1e-3, 3000)
     C = b.mass * 9.81 / (4 * ke)
