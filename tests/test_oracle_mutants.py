@@ -78,6 +78,29 @@ MUTANTS = {
     "loss_seed_factor": ("lq[i] = 2.0 * d;", "lq[i] = d;", 1),
     # rest volume det(Dm) / 6 with a wrong factor
     "tet_volume_factor": ("*V = det / 6.0;", "*V = det / 2.0;", 1),
+    # node gather: a tet's corner forces added to the next corner's node
+    "tet_gather_corner": ("f[3 * (size_t)m->tets[4 * e + c] + k] += fe[12 * (size_t)e + 3 * c + k];",
+                          "f[3 * (size_t)m->tets[4 * e + (c + 1) % 4] + k] += fe[12 * (size_t)e + 3 * c + k];", 1),
+    # node gather: a hinge's corner forces added to the next corner's node
+    "hinge_gather_corner": ("f[3 * (size_t)m->hinges[4 * h + c] + k] += fe[12 * (size_t)h + 3 * c + k];",
+                            "f[3 * (size_t)m->hinges[4 * h + (c + 1) % 4] + k] += fe[12 * (size_t)h + 3 * c + k];", 1),
+    # adjoint: a tet's corner x_bar added to the next corner's node
+    "adjoint_tet_scatter_corner": (
+        "lq_new[3 * (size_t)m->tets[4 * e + c] + k] += xb_e[12 * (size_t)e + 3 * c + k];",
+        "lq_new[3 * (size_t)m->tets[4 * e + (c + 1) % 4] + k] += xb_e[12 * (size_t)e + 3 * c + k];", 1),
+    # sphere penetration r - |x - c| with its sign flipped
+    "sphere_depth_sign": ("const T C = m->sphere_r - dist;", "const T C = dist - m->sphere_r;", 1),
+    # the stick / slip test reversed
+    "stick_slip_threshold": ("if (val(kf) * vsl_val <= val(muf) * val(afn)) {",
+                             "if (val(kf) * vsl_val >= val(muf) * val(afn)) {", 1),
+    # membrane corner forces with half the rest area
+    "tri_force_area": ("const T h = -A * (P[r][0] * Dminv[2 * cc] + P[r][1] * Dminv[2 * cc + 1]);",
+                       "const T h = -0.5 * A * (P[r][0] * Dminv[2 * cc] + P[r][1] * Dminv[2 * cc + 1]);", 1),
+    # Bridson direction u_4 with one term's sign flipped
+    "bending_u4_sign": ("f[9 + k] = s * (-(p13 * g1[k]) - p23 * g2[k]);",
+                        "f[9 + k] = s * ((p13 * g1[k]) - p23 * g2[k]);", 1),
+    # density gradient summing one corner's m_bar four times
+    "density_grad_corner": ("s += m_b[m->tets[4 * e + c]];", "s += m_b[m->tets[4 * e]];", 1),
 }
 # the same for the air model, the rigid-body step and the actuation sequence,
 # each against its own pins: name: (text, replacement, occurrences, pin file)
