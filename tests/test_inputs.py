@@ -69,3 +69,40 @@ def test_look_at_camera():
     eye = -cam.R.T @ cam.t
     assert np.allclose(eye, (1.0, 2.0, -3.0))
     assert abs(cam.fx - 40.0 / math.tan(math.radians(22.5))) < 1e-9
+
+
+def _cyclic(t):
+    """The three rotations of a triangle (same orientation)."""
+    a, b, c = (int(v) for v in t)
+    return {(a, b, c), (b, c, a), (c, a, b)}
+
+
+def test_cloth_hinges_are_the_interior_edges():
+    # brute force over the triangles: every edge shared by two triangles is
+    # one hinge (x1, x2, x3, x4) whose edge x3-x4 is that edge and whose
+    # wing tips x1, x2 are the triangles' third vertices, with (x1, x3, x4)
+    # and (x2, x4, x3) oriented as the triangles are; edges on the border
+    # carry no hinge (grids of 2, 3 and 7 nodes a side; the 256^2 count is
+    # pinned with the workload counts).
+    for n in (2, 3, 7):
+        X, tris, hinges = I.cloth_grid(n)
+        edges = collections.defaultdict(list)
+        for t, tri in enumerate(tris):
+            for k in range(3):
+                edges[frozenset((int(tri[k]), int(tri[(k + 1) % 3])))].append(t)
+        interior = {e: ts for e, ts in edges.items() if len(ts) == 2}
+        assert all(len(ts) in (1, 2) for ts in edges.values())
+        assert len(hinges) == len(interior) == 3 * (n - 1) ** 2 - 2 * (n - 1)
+        oriented = set()
+        for tri in tris:
+            oriented |= _cyclic(tri)
+        seen = set()
+        for x1, x2, x3, x4 in (tuple(int(v) for v in h) for h in hinges):
+            e = frozenset((x3, x4))
+            assert e in interior and e not in seen
+            seen.add(e)
+            assert {frozenset(tris[t]) for t in interior[e]} == {frozenset((x1, x3, x4)), frozenset((x2, x3, x4))}
+            assert (x1, x3, x4) in oriented and (x2, x4, x3) in oriented
+        # sorted by (min, max) edge node id
+        keys = [(min(h[2], h[3]), max(h[2], h[3])) for h in hinges.tolist()]
+        assert keys == sorted(keys)
