@@ -106,3 +106,60 @@ def test_cloth_hinges_are_the_interior_edges():
         # sorted by (min, max) edge node id
         keys = [(min(h[2], h[3]), max(h[2], h[3])) for h in hinges.tolist()]
         assert keys == sorted(keys)
+
+
+def test_batch_follows_its_recipe():
+    # 512 hex blocks: element-count targets log-uniform in [1e3, 1e5], the
+    # second and third sides at ratios in [0.5, 2] to the first (before
+    # rounding to whole cells), drop heights in
+    # [0.05, 0.5] m, E log-uniform in [1e4, 1e6], nu in [0.2, 0.45], dt 1e-4
+    ps = I.batch(512)
+    assert len(ps) == 512
+    E = np.array([p.n_elems for p in ps])
+    assert E.sum() == 10_830_100  # the benchmark's batch (about 10.8 M tets)
+    assert np.all(E % 5 == 0) and E.min() >= 5
+    logE = np.log10(E)
+    assert logE.min() > 2.5 and logE.max() < 5.1
+    assert 3.7 < np.median(logE) < 4.3  # log-uniform on [3, 5]: median near 4
+    for p in ps[:64]:
+        ext = p.X.max(axis=0) - p.X.min(axis=0)
+        cells = np.rint(ext / 0.025).astype(int)
+        assert 5 * np.prod(cells) == p.n_elems
+        a = cells[0]
+        if a >= 3:  # b / a and c / a were drawn in [0.5, 2]; each side is rounded to whole cells
+            for r in cells[1:] / a:
+                assert (0.5 * (a - 0.5) - 0.5) / a - 1e-9 <= r <= (2.0 * (a + 0.5) + 0.5) / a + 1e-9, cells
+        assert 0.05 <= p.X[:, 1].min() <= 0.5
+        mu, lam = p.mu[0], p.lam[0]
+        nu = lam / (2.0 * (lam + mu))
+        Ey = 2.0 * mu * (1.0 + nu)
+        assert 0.2 - 1e-12 <= nu <= 0.45 + 1e-12 and 1e4 * (1 - 1e-9) <= Ey <= 1e6 * (1 + 1e-9)
+        assert p.dt == 1e-4 and p.steps == 300
+    q = I.batch(4)
+    assert all(np.array_equal(a.X, b.X) and np.array_equal(a.mu, b.mu) for a, b in zip(q, ps[:4]))
+
+
+def test_query_stream_follows_its_recipe():
+    # Poisson arrivals at the rate; half tet blocks (targets log-uniform in
+    # [1e3, 2e5]), half cloth grids (32^2 .. 192^2); horizons in [100, 1000];
+    # dt 1e-4; targets offset by N(0, 1 mm^2)
+    rate, n = 200.0, 400
+    qs = I.query_stream(rate, n, seed=1)
+    t = np.array([q.t_arrival for q in qs])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert np.all(gaps > 0) and abs(gaps.mean() * rate - 1.0) < 0.15
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.2  # exponential gaps: coefficient of variation 1
+    kinds = np.array([q.problem.kind for q in qs])
+    assert 0.4 < (kinds == I.CLOTH).mean() < 0.6
+    for q in qs:
+        p = q.problem
+        assert 100 <= p.steps <= 1000 and p.dt == 1e-4
+        if p.kind == I.CLOTH:
+            side = int(round(math.sqrt(p.n_nodes)))
+            assert side * side == p.n_nodes and 32 <= side <= 192
+            assert p.n_elems == 2 * (side - 1) ** 2
+        else:
+            assert p.n_elems % 5 == 0 and 1e3 / 3 < p.n_elems < 2e5 * 1.5
+        assert q.target_offset.shape == (p.n_nodes, 3)
+    off = np.concatenate([q.target_offset.ravel() for q in qs])
+    assert abs(off.std() - 1e-3) < 2e-5 and abs(off.mean()) < 2e-5
