@@ -163,3 +163,34 @@ def test_query_stream_follows_its_recipe():
         assert q.target_offset.shape == (p.n_nodes, 3)
     off = np.concatenate([q.target_offset.ravel() for q in qs])
     assert abs(off.std() - 1e-3) < 2e-5 and abs(off.mean()) < 2e-5
+
+
+def test_benchmark_workloads_follow_their_recipes():
+    # block64: 1.6 m cube of 0.025 m cells on the ground; per-element E
+    # log-uniform in [1e4, 1e6] and nu uniform in [0.2, 0.45]; v0 ~ N(0, 0.1^2)
+    # per component; density 1000; 200 steps at dt 5e-5
+    p = I.block(64)
+    assert p.n_elems == 1_310_720 and p.n_nodes == 274_625 and p.steps == 200 and p.dt == 5e-5
+    assert p.X[:, 1].min() == 0.0 and np.allclose(p.X.max(axis=0) - p.X.min(axis=0), 1.6)
+    nu = p.lam / (2.0 * (p.lam + p.mu))
+    Ey = 2.0 * p.mu * (1.0 + nu)
+    assert nu.min() >= 0.2 - 1e-12 and nu.max() <= 0.45 + 1e-12 and abs(nu.mean() - 0.325) < 1e-3
+    lE = np.log10(Ey)
+    assert lE.min() >= 4 - 1e-9 and lE.max() <= 6 + 1e-9 and abs(lE.mean() - 5.0) < 2e-3
+    assert abs(p.v0.std() - 0.1) < 1e-3 and abs(p.v0.mean()) < 1e-3
+    assert np.all(p.rho == 1000.0) and p.contact.plane_on and not p.contact.sphere_on
+    # bars 1a / 1b: 4^3 cells, E 1e5, nu 0.3, bottom face at 0.2 m / 0.02 m
+    for v, drop in (("a", 0.2), ("b", 0.02)):
+        b = I.bar(v)
+        assert b.n_elems == 320 and abs(b.X[:, 1].min() - drop) < 1e-15 and b.dt == 1e-4 and b.steps == 1000
+        mu, lam = I.lame(1e5, 0.3)
+        assert np.allclose(b.mu, mu) and np.allclose(b.lam, lam) and np.all(b.rho == 1000.0)
+        if b.v0 is not None:  # dropped from rest
+            assert np.all(b.v0 == 0.0)
+    # cloths 3 / 3s: 256^2 nodes over [0, 1]^2 at y = 0.305 above a 0.3 m sphere at (0.5, 0, 0.5)
+    for v, mu, lam, kb in (("3", 5e3, 1e4, 1e-2), ("3s", 10.0, 20.0, 1e-6)):
+        c = I.cloth(v)
+        assert c.n_nodes == 65_536 and c.n_elems == 130_050 and c.n_hinges == 194_565 and c.steps == 500
+        assert np.all(c.X[:, 1] == 0.305) and c.X[:, 0].min() == 0.0 and c.X[:, 0].max() == 1.0
+        assert np.all(c.mu == mu) and np.all(c.lam == lam) and np.all(c.kb == kb) and np.all(c.rho == 0.2)
+        assert c.contact.sphere_on and c.contact.sphere_r == 0.3 and tuple(c.contact.sphere_c) == (0.5, 0.0, 0.5)
