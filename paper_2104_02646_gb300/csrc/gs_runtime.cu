@@ -737,7 +737,6 @@ static gs_status mesh_create_impl(gs_ctx* ctx, const gs_mesh_desc* desc, cudaStr
     GS_CUDA(cudaSetDevice(ctx->device));
     const gs_mesh_desc& d = *desc;
     GS_TRY(validate(d));
-    const int nc = d.kind == GS_TET ? 4 : 3;
     int threads = d.block_threads > 0 ? d.block_threads : 128;
     if (threads % 32 || threads > 1024) return set_error(GS_EINVAL, "block_threads must be a multiple of 32, <= 1024");
     const int threads_adj = d.block_threads_adj > 0 ? d.block_threads_adj : threads;
@@ -967,7 +966,7 @@ extern "C" gs_status gs_mesh_set_params(gs_mesh* m, const float* mu, const float
     cudaStream_t s = (cudaStream_t)stream;
     const size_t E = m->info.n_elems, B = m->info.n_hinges;
     Buf t1, t2, t3, t4, t5;
-    const float *dmu, *dlam, *drho, *dact, *dkb;
+    const float *dmu = nullptr, *dlam = nullptr, *drho = nullptr, *dact = nullptr, *dkb = nullptr;
     GS_TRY(stage_in(m->ctx, t1, mu, E, mem, s, &dmu));
     GS_TRY(stage_in(m->ctx, t2, lambda, E, mem, s, &dlam));
     GS_TRY(stage_in(m->ctx, t3, density, E, mem, s, &drho));
@@ -992,7 +991,7 @@ extern "C" gs_status gs_mesh_set_state(gs_mesh* m, const float* x, const float* 
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = 3 * (size_t)m->info.n_nodes;
     Buf t1, t2;
-    const float *dx, *dv;
+    const float *dx = nullptr, *dv = nullptr;
     GS_TRY(stage_in(m->ctx, t1, x, n, mem, s, &dx));
     GS_TRY(stage_in(m->ctx, t2, v, n, mem, s, &dv));
     GS_TRY(m->self->sync_rt(s));
@@ -1646,7 +1645,7 @@ extern "C" gs_status gs_rollout(gs_mesh* m, float dt, int S, int K, const float*
     if (!m) return set_error(GS_EINVAL, "null mesh");
     cudaStream_t s = (cudaStream_t)stream;
     Buf tt;
-    const float* dtarget;
+    const float* dtarget = nullptr;
     GS_TRY(stage_in(m->ctx, tt, target, 3 * (size_t)m->info.n_nodes, mem, s, &dtarget));
     double* dloss = nullptr;
     Buf tl;
@@ -1676,7 +1675,7 @@ extern "C" gs_status gs_adjoint(gs_mesh* m, const float* dLdx, const float* dLdv
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n3 = 3 * (size_t)m->info.n_nodes;
     Buf t1, t2;
-    const float *sx, *sv;
+    const float *sx = nullptr, *sv = nullptr;
     GS_TRY(stage_in(m->ctx, t1, dLdx, n3, mem, s, &sx));
     GS_TRY(stage_in(m->ctx, t2, dLdv, n3, mem, s, &sv));
     gs_grads g{};

@@ -193,7 +193,7 @@ gs_status gs_server::enter_phase(Query* q) {
 
 // builder thread: the mesh, its state/checkpoint/adjoint buffers and the
 // target, all on the builder's stream, finished before the query is handed on
-static gs_status build_query(gs_ctx* ctx, const gs_server_opts& opts, Query* q, cudaStream_t bs) {
+static gs_status build_query(gs_ctx* ctx, Query* q, cudaStream_t bs) {
     gs_mesh* m = nullptr;
     GS_TRY(mesh_create(ctx, &q->desc, bs, &m));
     q->mesh = m;
@@ -227,7 +227,7 @@ void gs_server::build_loop() {
         const double t = now_s();
         gs_status st;
         try {  // the query then fails with the status; the builder carries on
-            st = have_stream ? build_query(ctx, opts, q, bs) : set_error(GS_ECUDA, "builder stream");
+            st = have_stream ? build_query(ctx, q, bs) : set_error(GS_ECUDA, "builder stream");
         } catch (const std::bad_alloc&) {
             st = set_error(GS_ENOMEM, "host allocation failed while building the query");
         } catch (const std::exception& x) {
