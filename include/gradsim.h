@@ -248,8 +248,8 @@ GS_API gs_status gs_mesh_set_params(gs_mesh* mesh, const float* mu, const float*
  * gs_grads.d_act_seq / d_hinge_act_seq. */
 GS_API gs_status gs_mesh_set_act_seq(gs_mesh* mesh, const float* act_seq, const float* hinge_act_seq, int n_steps,
                                      int mem_space, void* stream);
-/* Air on the cloth surface (App. A.1 "Deformable Thin-Shells": a lift/drag
- * model of the surrounding air; the paper prints no formula).  Flat-plate
+/* Air on the cloth surface (App. A.1 "Deformable Thin-Shells" adds lift and
+ * drag from the surrounding air but prints no formula).  Flat-plate
  * reading, per triangle with deformed vector area N (|N| = A), mean corner
  * velocity minus the wind v_r, s = N . v_r:
  *   drag F_D = -k_drag |s| v_r,
@@ -371,6 +371,9 @@ GS_API gs_status gs_mesh_set_state(gs_mesh* mesh, const float* x, const float* v
 /* Back to the description's initial state: x = X exactly (the state is
  * held as the displacement from X), v = v0.  Enqueued on `stream`. */
 GS_API gs_status gs_mesh_reset(gs_mesh* mesh, void* stream);
+/* Current state (x, v) [n_nodes][3] in caller order into caller buffers
+ * (nullable = not read).  DEVICE: enqueued on `stream`; HOST: copied through a
+ * device scratch, and the call synchronises `stream`. */
 GS_API gs_status gs_mesh_get_state(gs_mesh* mesh, float* x, float* v, int mem_space, void* stream);
 /* Sticky per-mesh status from the device since the last reset: GS_OK,
  * GS_ETIMEOUT (a bounded wait inside a step kernel ran out: the kernel gave
@@ -408,6 +411,8 @@ GS_API gs_status gs_adjoint(gs_mesh* mesh, const float* dL_dxT, const float* dL_
  * own state.  Results per mesh are bitwise those of the mesh run alone. */
 GS_API gs_status gs_batch_create(gs_ctx* ctx, gs_mesh* const* meshes, int n, gs_batch** out);
 GS_API void gs_batch_destroy(gs_batch* batch);
+/* Every mesh advances n_steps steps of its own dt[i] (host array [n]), one
+ * launch per kernel per step (App. B); GS_WUNSTABLE as gs_step. */
 GS_API gs_status gs_batch_step(gs_batch* batch, const float* dt, int n_steps, void* stream);
 /* dt[n]; targets[n] (nullable entries) device pointers; loss_out device [n]. */
 GS_API gs_status gs_batch_rollout(gs_batch* batch, const float* dt, int n_steps, int K,
@@ -485,17 +490,28 @@ typedef struct gs_server_stats {
     uint64_t ticks, rebuilds, rt_syncs;
 } gs_server_stats;
 
+/* Starts the worker thread and opts->build_threads mesh builders (0: 4);
+ * opts nullable = defaults.  GS_ENOMEM if the threads cannot be started. */
 GS_API gs_status gs_server_create(gs_ctx* ctx, const gs_server_opts* opts, gs_server** out);
 /* Stops the server thread; pending queries end as GS_ECANCELLED. */
 GS_API void gs_server_destroy(gs_server* server);
-/* GS_ENOMEM at once if the query alone exceeds the whole budget. */
+/* The query is deep-copied (its buffers may be freed on return).  GS_ENOMEM
+ * at once if the query alone exceeds the whole budget; GS_EINTERNAL once the
+ * worker has stopped on a host-side failure. */
 GS_API gs_status gs_query_submit(gs_server* server, const gs_query* q, uint64_t* ticket);
 /* GS_OK (result filled; free it with gs_result_free), GS_PENDING /
  * GS_ETIMEOUT (not done within timeout_ms; 0 = do not wait), GS_ECANCELLED,
- * GS_ENONFINITE, GS_ENOTFOUND. */
+ * GS_ENONFINITE, GS_ENOTFOUND, GS_EINTERNAL (the worker stopped on a
+ * host-side failure).  A finished ticket is collected by this call and is
+ * unknown afterwards. */
 GS_API gs_status gs_query_poll(gs_server* server, uint64_t ticket, gs_result* out, int timeout_ms);
+/* Marks the query cancelled: a query still queued is dropped, a running one
+ * stops at the worker's next tick (steps already enqueued still run); either
+ * ends as GS_ECANCELLED.  GS_ENOTFOUND for an unknown ticket. */
 GS_API gs_status gs_query_cancel(gs_server* server, uint64_t ticket);
+/* Counts, latency percentiles and the time breakdown since creation. */
 GS_API gs_status gs_server_stats_get(gs_server* server, gs_server_stats* out);
+/* Frees a polled result's host arrays and clears their pointers (NULL-safe). */
 GS_API void gs_result_free(gs_result* r);
 
 /* ---- self-test of the kernels' failure path (no paper counterpart) --------
