@@ -312,9 +312,9 @@ T tri_energy_t(const T* x, const double* Dminv, double A, T mu, T lam, T act) {
     return A * (0.5 * mu * (Ic - 2.0) + 0.5 * lam * (J - alpha) * (J - alpha) - 0.5 * mu * flog(Ic + 1.0));
 }
 
-// Air on a triangle (App. A.1 "Deformable Thin-Shells" adds a lift/drag model
-// of the surrounding air but prints no formula).  Reading, a flat plate in a
-// uniform wind:
+// Air on a triangle (App. A.1 "Deformable Thin-Shells" adds lift and drag
+// forces from the air around the cloth but prints no formula).  Reading, a
+// flat plate in a uniform wind:
 //   v_r = (v_0 + v_1 + v_2)/3 - wind        velocity of the plate through the air
 //   N   = (x_1 - x_0) x (x_2 - x_0) / 2     vector area, |N| = A, N/A = n
 //   s   = N . v_r = A |v_r| cos(theta)

@@ -76,9 +76,9 @@ typedef struct orc_model {
     const double* tet_act_seq;
     const double* tri_act_seq;
     const double* hinge_act_seq;
-    /* air on the cloth surface (App. A.1 "Deformable Thin-Shells": a
-     * lift/drag model of the surrounding air; the paper gives no formula,
-     * the reading is stated at air_forces_t): per triangle, drag and lift
+    /* air on the cloth surface (App. A.1 "Deformable Thin-Shells": lift and
+     * drag from the air around the cloth; the paper gives no formula, the
+     * reading is stated at air_forces_t): per triangle, drag and lift
      * coefficients k_drag, k_lift (kg/m^3) against a uniform wind (m/s) */
     int air_on;
     double k_drag, k_lift;

@@ -348,7 +348,7 @@ def hinge_angle_grad(x):
 
 def air_forces(x, v, k_drag, k_lift, wind=(0.0, 0.0, 0.0)):
     """Air force on the corners of one triangle ([3, 3] positions and
-    velocities) under the oracle's flat-plate reading of the lift/drag model."""
+    velocities) under the oracle's flat-plate reading of the air's lift and drag."""
     x = _d(np.asarray(x).reshape(9))
     v = _d(np.asarray(v).reshape(9))
     w = _d(np.asarray(wind).reshape(3))

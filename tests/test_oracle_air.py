@@ -1,5 +1,5 @@
 """Pins of the oracle's air model on cloth (App. A.1 "Deformable Thin-Shells"
-adds a lift/drag model of the surrounding air; no formula is printed, the
+adds lift and drag from the air around the cloth; no formula is printed, the
 flat-plate reading is stated in the oracle).
 
 Pinned against physics and invariants rather than the formula itself:
