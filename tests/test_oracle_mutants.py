@@ -101,6 +101,26 @@ MUTANTS = {
                         "f[9 + k] = s * ((p13 * g1[k]) - p23 * g2[k]);", 1),
     # density gradient summing one corner's m_bar four times
     "density_grad_corner": ("s += m_b[m->tets[4 * e + c]];", "s += m_b[m->tets[4 * e]];", 1),
+    # adjoint force seed f_bar = -dt W c_u without the inverse mass
+    "adjoint_seed_no_mass": ("y[3 * i + k] = -dt * w[i] * cu[3 * i + k];", "y[3 * i + k] = -dt * cu[3 * i + k];", 1),
+    # adjoint: a triangle's corner x_bar added to the next corner's node
+    "adjoint_tri_scatter_corner": (
+        "lq_new[3 * (size_t)m->tris[3 * e + c] + k] += xb_e[9 * (size_t)e + 3 * c + k];",
+        "lq_new[3 * (size_t)m->tris[3 * e + (c + 1) % 3] + k] += xb_e[9 * (size_t)e + 3 * c + k];", 1),
+    # adjoint: a hinge's corner x_bar added to the next corner's node
+    "adjoint_hinge_scatter_corner": (
+        "lq_new[3 * (size_t)m->hinges[4 * h + c] + k] += xb_e[12 * (size_t)h + 3 * c + k];",
+        "lq_new[3 * (size_t)m->hinges[4 * h + (c + 1) % 4] + k] += xb_e[12 * (size_t)h + 3 * c + k];", 1),
+    # dL/dmu and dL/dlambda of a tet swapped
+    "adjoint_mu_lambda_swapped": ("tmu_b[e] += pb[0]; tlam_b[e] += pb[1];", "tmu_b[e] += pb[1]; tlam_b[e] += pb[0];", 1),
+    # the contact force's dependence on v dropped from the velocity adjoint
+    "adjoint_contact_v_dropped": ("lq_new[3 * i + k] += xb[k]; lu_new[3 * i + k] += xb[3 + k];",
+                                  "lq_new[3 * i + k] += xb[k];", 1),
+    # the bending stiffness gradient dropped
+    "adjoint_kb_dropped": ("kb_b[h] += pb[0]; hact_b[h] += pb[1];", "hact_b[h] += pb[1];", 1),
+    # dl/du- = -c_u replaced by -c_q (the wrong multiplier)
+    "adjoint_velocity_multiplier": ("{ lq_new[i] = -cq[i]; lu_new[i] = -cu[i]; }",
+                                    "{ lq_new[i] = -cq[i]; lu_new[i] = -cq[i]; }", 1),
 }
 # the same for the air model, the rigid-body step and the actuation sequence,
 # each against its own pins: name: (text, replacement, occurrences, pin file)
@@ -129,6 +149,9 @@ MUTANTS_MORE = {
     # flat-plate lift without the area normalisation of N
     "air_lift_area": ("const T c = k_lift * s / (fsqrt(A2) * fsqrt(q));", "const T c = k_lift * s / fsqrt(q);", 1,
                       "test_oracle_air.py"),
+    # the air force's dependence on the corner velocities dropped from the adjoint
+    "adjoint_air_v_dropped": ("lu_new[3 * (size_t)m->tris[3 * e + c] + k] += xb_e[18 * (size_t)e + 9 + 3 * c + k];",
+                              "lu_new[3 * (size_t)m->tris[3 * e + c] + k] += 0.0;", 1, "test_oracle_air.py"),
     # the row of the actuation sequence added at half weight
     "act_seq_scale": ("ta[e] += tseq[(size_t)n * m->n_tets + e];", "ta[e] += 0.5 * tseq[(size_t)n * m->n_tets + e];",
                       1, "test_oracle_actuation.py"),
